@@ -1,0 +1,267 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics.
+
+None of these tests re-types an oracle formula: each compares the oracle with a
+closed form, an exact brute force, a library routine, an identity of the
+method's analysis (Lemma / Theorem of Section 3) or a value printed in the paper.
+"""
+import json
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import ibmi_oracle as O
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def rand_spd(p, seed, cond=50.0):
+    rng = np.random.default_rng(seed)
+    q, _ = np.linalg.qr(rng.standard_normal((p, p)))
+    lam = np.exp(rng.uniform(0.0, math.log(cond), p))
+    a = (q * lam) @ q.T
+    return 0.5 * (a + a.T)
+
+
+def kms_inverse(p, rho):
+    """Textbook tridiagonal inverse of the AR(1) matrix rho^|i-j|."""
+    inv = np.zeros((p, p))
+    c = 1.0 / (1.0 - rho * rho)
+    for i in range(p):
+        inv[i, i] = c * (1.0 + rho * rho) if 0 < i < p - 1 else c
+        if i + 1 < p:
+            inv[i, i + 1] = inv[i + 1, i] = -rho * c
+    return inv
+
+
+# ------------------------------------------------------------- partition --
+
+def test_partition_layout_c2():
+    # Section 4: end sets m + h, interior sets m + 2h; p = 4096, K = 8, h = 32.
+    sets = O.partition(4096, 8, 32)
+    assert sets[0] == (0, 544) and sets[-1] == (3552, 4096)
+    assert [hi - lo for lo, hi in sets] == [544] + [576] * 6 + [544]
+    for (l0, h0), (l1, h1) in zip(sets, sets[1:]):
+        assert h0 - l1 == 64          # consecutive overlap 2h
+    assert O.partition(256, 2, 0) == [(0, 128), (128, 256)]
+
+
+def test_partition_uneven_covers():
+    for p, K, h in [(320, 3, 16), (1000, 7, 5), (65, 4, 3)]:
+        sets = O.partition(p, K, h)
+        cov = np.zeros(p, int)
+        for lo, hi in sets:
+            cov[lo:hi] += 1
+        assert cov.min() >= 1 and sets[0][0] == 0 and sets[-1][1] == p
+
+
+# ------------------------------------------------------ direct inverse ----
+
+def _exact_inverse(a_frac):
+    n = len(a_frac)
+    m = [row[:] + [Fraction(int(i == j)) for j in range(n)] for i, row in enumerate(a_frac)]
+    for c in range(n):
+        piv = next(r for r in range(c, n) if m[r][c] != 0)
+        m[c], m[piv] = m[piv], m[c]
+        inv = 1 / m[c][c]
+        m[c] = [v * inv for v in m[c]]
+        for r in range(n):
+            if r != c and m[r][c] != 0:
+                f = m[r][c]
+                m[r] = [vr - f * vc for vr, vc in zip(m[r], m[c])]
+    return [[float(v) for v in row[n:]] for row in m]
+
+
+@pytest.mark.parametrize("p", [1, 2, 5, 8])
+def test_spd_inverse_vs_exact_rational(p):
+    rng = np.random.default_rng(p)
+    g = rng.integers(-4, 5, size=(p, p))
+    a_int = g @ g.T + p * np.eye(p, dtype=int)          # integer SPD
+    exact = np.array(_exact_inverse([[Fraction(int(v)) for v in row] for row in a_int]))
+    got = O.spd_inverse(a_int.astype(np.float64))
+    assert np.max(np.abs(got - exact)) <= 1e-13 * np.max(np.abs(exact))
+
+
+def test_cholesky_vs_lapack():
+    a = rand_spd(60, 1)
+    np.testing.assert_allclose(O.cholesky(a), np.linalg.cholesky(a), rtol=0, atol=1e-12)
+
+
+def test_spd_inverse_kms_closed_form():
+    a = wl.kms(256, 0.5)
+    np.testing.assert_allclose(O.spd_inverse(a), kms_inverse(256, 0.5), rtol=0, atol=1e-13)
+
+
+def test_spd_inverse_sherman_morrison():
+    p, a, b = 50, 0.7, 0.4
+    want = (np.eye(p) - b / (a + p * b) * np.ones((p, p))) / a
+    np.testing.assert_allclose(O.spd_inverse(wl.compound_symmetry(p, a, b)), want, rtol=0, atol=1e-13)
+
+
+def test_not_spd_detected():
+    a = rand_spd(40, 2)
+    a[25, 25] = -1.0
+    res = O.ibmi(a, O.partition(40, 2, 4), 1e-10)
+    assert res.status == "not_spd" and res.bad_block == 1
+
+
+# ------------------------------------------------- block update (eq. IBMI) --
+
+@pytest.mark.parametrize("lo,hi", [(0, 13), (9, 27), (30, 40), (0, 40 - 1)])
+def test_exact_schur_complement_gives_exact_inverse(lo, hi):
+    """eq. BMIQ: with T equal to the exact inverse Schur complement
+    (A^{-1})[I^c, I^c], one application of eq. IBMI returns A^{-1}."""
+    a = rand_spd(40, 3)
+    ainv = np.linalg.inv(a)
+    ainv = 0.5 * (ainv + ainv.T)
+    h = ainv.copy()
+    h[lo:hi, :] = 7.0          # garbage in the rows/cols being rewritten
+    h[:, lo:hi] = -3.0
+    O.block_update(h, O.block_invariants(a, lo, hi))
+    np.testing.assert_allclose(h, ainv, rtol=0, atol=1e-11 * np.abs(ainv).max())
+    assert np.array_equal(h, h.T)
+
+
+def test_c1_kms_converges_in_one_sweep():
+    a = wl.c1_kms()
+    res = O.ibmi(a, O.partition(256, 2, 0), tol=1e-12)
+    assert res.status == "converged" and res.sweeps == 1
+    np.testing.assert_allclose(res.h, kms_inverse(256, 0.5), rtol=0, atol=5e-15)
+
+
+@pytest.mark.parametrize("p,rho,c", [(16, 0.5, 2.0), (256, 0.5, 2.0), (40, 0.8, 3.0)])
+def test_kms_trajectory_closed_form(p, rho, c):
+    """Two blocks, T_0 = c I.  Lemma of Section 3 with A_1^{-1} A_12 = rho e_m v^T
+    gives the error after r sweeps exactly:
+    delta rho^{4r-2} [[1, -rho], [-rho, rho^2]] on rows/cols (m-1, m), zero
+    elsewhere, delta = (c (1 - rho^p) - 1) / (1 - rho^2)."""
+    a = wl.kms(p, rho)
+    m = p // 2
+    sig = kms_inverse(p, rho)
+    delta = (c * (1.0 - rho ** p) - 1.0) / (1.0 - rho * rho)
+    for r in (1, 2, 3):
+        res = O.ibmi(a, [(0, m), (m, p)], tol=0.0, max_sweeps=r, h0=c * np.eye(p))
+        want = sig.copy()
+        e = delta * rho ** (4 * r - 2)
+        want[m - 1, m - 1] += e
+        want[m - 1, m] -= e * rho
+        want[m, m - 1] -= e * rho
+        want[m, m] += e * rho * rho
+        assert res.sweeps == r
+        np.testing.assert_allclose(res.h, want, rtol=0, atol=2e-14 * max(1.0, abs(delta)))
+        # paper's estimate (eq. error) on I_2: rank one, closed form
+        est = abs(delta) * rho ** (4 * r - 1) * math.sqrt((1 - rho * rho) * (1 - rho ** p))
+        assert O.paper_error(a, res.h, m, p) == pytest.approx(est, rel=1e-9, abs=1e-15)
+
+
+def test_compound_symmetry_trajectory_closed_form():
+    """aI + b11^T, two halves of size m: M = lam (11^T/m), lam = (mb/(a+mb))^2,
+    so by the Lemma the error of H[I_2, I_2] after r sweeps is
+    lam^{2r} [1 - 1/a + b m / (a (a + p b))] 11^T / m for T_0 = I."""
+    p, a_, b_ = 64, 0.5, 1.0
+    m = p // 2
+    A = wl.compound_symmetry(p, a_, b_)
+    sig = (np.eye(p) - b_ / (a_ + p * b_) * np.ones((p, p))) / a_
+    lam = (m * b_ / (a_ + m * b_)) ** 2
+    c0 = 1.0 - 1.0 / a_ + b_ * m / (a_ * (a_ + p * b_))
+    P = np.ones((m, m)) / m
+    for r in (1, 2, 5):
+        res = O.ibmi(A, [(0, m), (m, p)], tol=0.0, max_sweeps=r)
+        err = res.h[m:, m:] - sig[m:, m:]
+        np.testing.assert_allclose(err, lam ** (2 * r) * c0 * P, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("seed,p,m", [(5, 24, 10), (6, 40, 23), (7, 48, 24)])
+def test_lemma_recurrence_and_theorem_bound(seed, p, m):
+    """Lemma (Section 3): E_r = M^r E_0 (M^T)^r with M = A_2^{-1} A_21 A_1^{-1} A_12;
+    Theorem: ||E_r||_2 <= ||M||_2^{2r} ||E_0||_2; and rho(M) < 1."""
+    a = rand_spd(p, seed)
+    rng = np.random.default_rng(seed + 100)
+    g = rng.standard_normal((p - m, p - m))
+    t0 = g @ g.T / (p - m) + np.eye(p - m)                     # SPD initial guess
+    h0 = np.eye(p)
+    h0[m:, m:] = t0
+    A1, A2, A12 = a[:m, :m], a[m:, m:], a[:m, m:]
+    M = np.linalg.solve(A2, A12.T) @ np.linalg.solve(A1, A12)
+    sig2 = np.linalg.inv(a)[m:, m:]
+    E0 = t0 - sig2
+    assert max(abs(np.linalg.eigvals(M))) < 1.0
+    nM = np.linalg.norm(M, 2)
+    for r in (1, 2, 4):
+        res = O.ibmi(a, [(0, m), (m, p)], tol=0.0, max_sweeps=r, h0=h0)
+        Er = res.h[m:, m:] - sig2
+        Mr = np.linalg.matrix_power(M, r)
+        want = Mr @ E0 @ Mr.T
+        np.testing.assert_allclose(Er, want, rtol=0, atol=1e-10 * max(1.0, np.abs(E0).max()))
+        assert np.linalg.norm(Er, 2) <= nM ** (2 * r) * np.linalg.norm(E0, 2) * (1 + 1e-9) + 1e-13
+
+
+def test_symmetry_exact():
+    a = rand_spd(70, 8)
+    res = O.ibmi(a, O.partition(70, 3, 5), tol=0.0, max_sweeps=3)
+    assert np.array_equal(res.h, res.h.T)
+
+
+def test_multiblock_overlap_converges_to_inverse():
+    """Remark of Section 3: the multi-block overlapping sweep converges in
+    practice; checked against LAPACK's inverse."""
+    a = wl.c2_matern(p=512, seed=11)
+    res = O.ibmi(a, O.partition(512, 4, 16), tol=1e-11, max_sweeps=300)
+    assert res.status == "converged"
+    inv = np.linalg.inv(a)
+    assert np.max(np.abs(res.h - inv)) <= 1e-8 * np.max(np.abs(inv))
+
+
+# ----------------------------------------------------------- residuals ----
+
+def test_residual_closed_forms():
+    p = 64
+    a = wl.kms(p, 0.6)
+    assert O.residual_f(a, kms_inverse(p, 0.6)) < 1e-15
+    assert O.residual_f(a, np.zeros((p, p))) == pytest.approx(1.0, abs=1e-15)
+    h = kms_inverse(p, 0.6)
+    i, j, eps = 5, 40, 1e-3
+    h[i, j] += eps
+    # I - A (A^{-1} + eps e_i e_j^T) = -eps (A e_i) e_j^T
+    want = eps * np.linalg.norm(a[:, i]) / math.sqrt(p)
+    assert O.residual_f(a, h) == pytest.approx(want, rel=1e-9)
+
+
+def test_paper_error_zero_at_inverse():
+    a = rand_spd(30, 9)
+    assert O.paper_error(a, np.linalg.inv(a), 10, 20) < 1e-12
+
+
+def test_newton_schulz_squares_the_residual():
+    """eq. newton: I - A X_{n+1} = (I - A X_n)^2."""
+    a = rand_spd(50, 10)
+    x = np.linalg.inv(a) + 1e-3 * rand_spd(50, 11) / 50
+    R0 = np.eye(50) - a @ x
+    x1, nr = O.newton_schulz_step(a, x)
+    assert nr == pytest.approx(np.linalg.norm(R0), rel=1e-12)
+    np.testing.assert_allclose(np.eye(50) - a @ x1, R0 @ R0, rtol=0, atol=1e-12)
+
+
+def test_hybrid_tail_reaches_tolerance():
+    a = wl.random_spd(192, seed=12, lam_lo=1.0, lam_hi=1e3)
+    res = O.ibmi(a, O.partition(192, 2, 48), tol=1e-12, max_sweeps=200, ns_theta=0.5)
+    assert res.status == "converged" and res.ns_steps >= 1
+    inv = np.linalg.inv(a)
+    assert np.max(np.abs(res.h - inv)) <= 1e-9 * np.max(np.abs(inv))
+
+
+# ------------------------------------------------------ paper's numbers ----
+
+def test_table2_exp_1d_one_iteration():
+    g = json.load(open(os.path.join(HERE, "golden", "table2_1d_exp.json")))
+    for row in g["rows"]:
+        p = row["p"]
+        a = wl.exp_1d(p)
+        h = int(round(0.2 * (p // 2) / 2))      # 20% overlap of the core width
+        res = O.ibmi(a, O.partition(p, 2, h), tol=g["tol"], stop_rule="paper", max_sweeps=50)
+        assert res.status == "converged" and res.sweeps == row["iterations"]
+        err = np.linalg.norm(res.h - np.linalg.inv(a), 2)
+        assert err <= 10 * row["error_2norm"]
