@@ -1,0 +1,174 @@
+/*
+ * ibmi.h -- C ABI of the GB300 IBMI block-sweep inverter.
+ *
+ * IBMI (Iterative Block Matrix Inversion) approximates the whole inverse
+ * H ~= A^{-1} of a dense symmetric positive definite A in R^{p x p}
+ * (Section 2, Algorithm 1).  The index range {0..p-1} is covered by K
+ * contiguous, possibly overlapping sets I_k = [lo_k, hi_k).  One sweep visits
+ * k = 1..K in order and rewrites rows and columns I_k of H with the approximate
+ * block-inversion formula (eq. IBMI), taking T = H[I_k^c, I_k^c] from the most
+ * recent iterate as the approximation of the inverse Schur complement:
+ *
+ *     H[I,I^c] = -A_I^{-1} A_{I,I^c} T,   H[I^c,I] = H[I,I^c]^T,
+ *     H[I,I]   =  A_I^{-1} + A_I^{-1} A_{I,I^c} T A_{I^c,I} A_I^{-1}.
+ *
+ * Sweeps repeat until the stop quantity is <= tol (Algorithm 1).  The default
+ * stop quantity is rho_F = ||I - A H||_F / sqrt(p); the paper's own estimate
+ * (eq. error, on the last set) can be selected instead.  An optional
+ * Newton-Schulz tail (eq. newton) refines H once ||I - A H||_F <= ns_theta.
+ *
+ * Conventions for every entry point:
+ *   - Matrices are dense, row-major, FP64, with a leading dimension ld >= p
+ *     (in elements).  Since A and H are symmetric, row- and column-major agree.
+ *   - A is read-only.  H is owned by the caller and written in full.
+ *   - Device pointers must be CUDA device memory of the current device;
+ *     "_host" variants take host memory and copy inside the call.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Calls are synchronous with respect to the host: when an entry point
+ *     returns, its result is final.
+ *   - Every call returns an ibmi_status; nothing aborts the process.  On a CUDA
+ *     error the call returns IBMI_ERR_CUDA and ibmi_last_error() describes it.
+ */
+#ifndef IBMI_H_
+#define IBMI_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum ibmi_status {
+  IBMI_OK = 0,
+  IBMI_ERR_INVALID_ARG = 1,   /* bad size, set layout, pointer or option          */
+  IBMI_ERR_NOT_SPD = 2,       /* Cholesky of a diagonal block A_{I_k} failed      */
+  IBMI_NOT_CONVERGED = 3,     /* max_sweeps (and ns_max) reached; H = last iterate */
+  IBMI_ERR_NONFINITE = 4,     /* the residual became NaN or Inf                   */
+  IBMI_ERR_BUDGET = 5,        /* request exceeds the server's HBM budget          */
+  IBMI_ERR_OOM = 6,           /* device allocation failed                         */
+  IBMI_ERR_TIMEOUT = 7,       /* a bounded device-side wait gave up               */
+  IBMI_ERR_CUDA = 8,          /* CUDA runtime error, see ibmi_last_error()        */
+  IBMI_NOT_READY = 9,         /* served request still in flight                   */
+  IBMI_ERR_CANCELLED = 10     /* served request was cancelled                     */
+} ibmi_status;
+
+/* Arithmetic of the sweep products (a3/a4).  The Cholesky of the diagonal
+ * blocks and the residual are FP64 in both modes. */
+typedef enum ibmi_precision {
+  IBMI_FP64 = 0,    /* every product in FP64 (DFMA)                                 */
+  IBMI_MIXED = 1    /* sweep products on tcgen05 tensor cores with split-BF16 operands
+                       and FP32 accumulation; FP64 Newton-Schulz tail restores accuracy */
+} ibmi_precision;
+
+typedef enum ibmi_stop_rule {
+  IBMI_STOP_RESID_F = 0,    /* ||I - A H||_F / sqrt(p) <= tol                       */
+  IBMI_STOP_PAPER_EST = 1   /* eq. error on the last set, ||(H A)_{I_K, I_K^c}||_2 <= tol */
+} ibmi_stop_rule;
+
+typedef enum ibmi_init {
+  IBMI_INIT_IDENTITY = 0,   /* H[I_1^c, I_1^c] = identity (Section 2.4)              */
+  IBMI_INIT_USER = 1        /* the caller's H holds the initial guess in H[I_1^c, I_1^c];
+                               it should be SPD (Theorem of Section 3)               */
+} ibmi_init;
+
+/* Plan description.  Fill with ibmi_plan_desc_init() then override fields. */
+typedef struct ibmi_plan_desc {
+  int64_t p;               /* matrix order, >= 2                                           */
+  int32_t K;               /* number of index sets, 1 <= K <= p (K = 1 is a direct inverse) */
+  int64_t h;               /* overlap half-width for the default layout (see below)        */
+  const int64_t* lo;       /* optional explicit sets: K ascending starts (host, copied) ... */
+  const int64_t* hi;       /* ... and ends; NULL = default layout                           */
+  int32_t precision;       /* ibmi_precision                                                */
+  double tol;              /* stop tolerance (default 1e-10)                                */
+  int32_t max_sweeps;      /* sweep cap (default 500, the cap used in Section 5)           */
+  int32_t stop_rule;       /* ibmi_stop_rule                                                */
+  int32_t check_every;     /* evaluate the stop quantity every s sweeps (default 1)        */
+  double ns_theta;         /* enter Newton-Schulz once ||I - A H||_F <= ns_theta; 0 = off  */
+  int32_t ns_max;          /* Newton-Schulz step cap (default 8)                            */
+  int32_t init;            /* ibmi_init                                                     */
+} ibmi_plan_desc;
+/* Default layout (Section 4 cost model): core k = [floor(k p/K), floor((k+1) p/K)),
+ * set k = core widened by h on each side that has a neighbour, clipped to [0,p).
+ * Explicit sets must be contiguous, ascending (lo_k < lo_{k+1}, hi_k < hi_{k+1}),
+ * cover {0..p-1}, and each must leave a non-empty complement when K >= 2.        */
+
+typedef struct ibmi_result {
+  int32_t status;          /* same value as the call's return                              */
+  int32_t sweeps;          /* sweeps r performed                                            */
+  int32_t ns_steps;        /* Newton-Schulz steps performed                                 */
+  int32_t bad_block;       /* IBMI_ERR_NOT_SPD: set index k (0-based), else -1              */
+  int64_t bad_pivot;       /* IBMI_ERR_NOT_SPD: global row of the failed pivot, else -1     */
+  double resid_f;          /* last ||I - A H||_F / sqrt(p) evaluated (FP64)                 */
+  double paper_est;        /* last eq. error estimate (NaN unless evaluated)                */
+  double seconds;          /* wall time of the call on the stream                          */
+  double flops;            /* algorithmic flops: plan + sweeps + residuals + Newton-Schulz */
+} ibmi_result;
+
+typedef struct ibmi_plan_s* ibmi_plan_t;
+
+/* Fills *desc with defaults: K=2, h=0, FP64, tol=1e-10, max_sweeps=500,
+ * RESID_F, check_every=1, ns_theta=0, ns_max=8, IDENTITY. */
+void ibmi_plan_desc_init(ibmi_plan_desc* desc);
+
+/* Validates the description (set coverage, sizes) and allocates the plan's
+ * device workspace on the current device: per set A_I^{-1} (m x m) and
+ * W = A_I^{-1} A_{I,:} stored m x p with zero columns on I, plus scratch.
+ * The plan owns that memory until ibmi_plan_destroy.  Returns
+ * IBMI_ERR_INVALID_ARG (nothing allocated) or IBMI_ERR_OOM. */
+ibmi_status ibmi_plan(const ibmi_plan_desc* desc, ibmi_plan_t* out);
+ibmi_status ibmi_plan_destroy(ibmi_plan_t plan);
+
+/* Copies the plan's sets to host arrays lo[K], hi[K] (either may be NULL). */
+ibmi_status ibmi_plan_sets(ibmi_plan_t plan, int32_t* K, int64_t* lo, int64_t* hi);
+
+/* Algorithm 1 on device buffers.  A: p x p SPD (lda >= p), read-only.
+ * H: p x p output (ldh >= p); with IBMI_INIT_USER it also carries the initial
+ * guess.  A and H must not overlap.  Returns IBMI_OK, IBMI_NOT_CONVERGED
+ * (H = last iterate), IBMI_ERR_NOT_SPD (bad_block/bad_pivot set, H undefined),
+ * IBMI_ERR_NONFINITE, IBMI_ERR_INVALID_ARG or IBMI_ERR_CUDA.  `out` may be NULL. */
+ibmi_status ibmi_invert(ibmi_plan_t plan, const double* A, int64_t lda, double* H,
+                        int64_t ldh, void* stream, ibmi_result* out);
+
+/* Same on host buffers: copies A (and H for IBMI_INIT_USER) to the device,
+ * runs ibmi_invert, copies H back.  Uses device scratch owned by the plan. */
+ibmi_status ibmi_invert_host(ibmi_plan_t plan, const double* A_host, int64_t lda,
+                             double* H_host, int64_t ldh, void* stream, ibmi_result* out);
+
+/* rho_F = ||I - A H||_F / sqrt(p) in FP64 for device A, H (p x p, ld >= p).
+ * Allocates nothing when p <= 65536; the value is written to *out (host). */
+ibmi_status ibmi_residual(const double* A, int64_t lda, const double* H, int64_t ldh,
+                          int64_t p, void* stream, double* out);
+
+/* Kernel profiling, for the benchmark's roofline figures.  While enabled, the
+ * library records a CUDA event pair on the launching stream around every
+ * launch of each kernel class below and sums their durations; it also counts
+ * every kernel launch it makes.  ibmi_prof_enable(1) clears the counters.
+ * ibmi_prof_get synchronises the recorded events.  Not thread-safe: profile
+ * one thread at a time. */
+typedef enum ibmi_kernel_class {
+  IBMI_K_SWEEP_X = 0,     /* a3: X = -W T and its scatter into H                 */
+  IBMI_K_SWEEP_S = 1,     /* a4: S = A_I^{-1} - X W^T                             */
+  IBMI_K_RESIDUAL = 2,    /* a6: ||I - A H||_F                                    */
+  IBMI_K_NS = 3,          /* a7: Newton-Schulz products                           */
+  IBMI_K_INVARIANTS = 4,  /* a2: Cholesky, triangular solves                      */
+  IBMI_K_OTHER = 5,       /* splits, symmetrisation, copies                       */
+  IBMI_K_COUNT = 6
+} ibmi_kernel_class;
+void ibmi_prof_enable(int on);
+/* launches: launches of that class; ms: summed event time; flops: algorithmic
+ * flops of those launches.  Returns IBMI_ERR_INVALID_ARG for a bad class. */
+ibmi_status ibmi_prof_get(int32_t kernel_class, int64_t* launches, double* ms, double* flops);
+/* Total kernel launches made by this library since the last ibmi_prof_enable(1)
+ * (counted whether or not profiling is on). */
+int64_t ibmi_launch_count(void);
+
+/* Human-readable name of a status, and the text of the last CUDA error seen by
+ * this thread (empty if none). */
+const char* ibmi_status_string(ibmi_status s);
+const char* ibmi_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IBMI_H_ */

@@ -1,0 +1,121 @@
+"""GB300-native IBMI (Iterative Block Matrix Inversion) block-sweep inverter.
+
+The compute path is the CUDA library libibmi.so behind the C ABI declared in
+include/ibmi.h; this package is its thin Python binding.  Functions keep the
+C names and take torch CUDA tensors (or numpy arrays for the *_host variants)
+in place of raw pointers.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _lib
+from ._lib import (IBMI_FP64, IBMI_MIXED, IBMI_INIT_IDENTITY, IBMI_INIT_USER,  # noqa: F401
+                   IBMI_STOP_RESID_F, IBMI_STOP_PAPER_EST, IBMI_OK, IBMI_NOT_CONVERGED,
+                   IBMI_ERR_NOT_SPD, IBMI_ERR_INVALID_ARG, ibmi_plan_desc, ibmi_result)
+
+
+class IbmiError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        lib = _lib.load()
+        msg = lib.ibmi_status_string(status).decode()
+        err = lib.ibmi_last_error().decode()
+        super().__init__(f"{what}: {msg}" + (f" ({err})" if err else ""))
+        self.status = status
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    return C.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+
+
+def ibmi_plan_desc_init(**kw) -> ibmi_plan_desc:
+    d = ibmi_plan_desc()
+    _lib.load().ibmi_plan_desc_init(C.byref(d))
+    for k, v in kw.items():
+        if k in ("lo", "hi"):
+            continue
+        setattr(d, k, v)
+    return d
+
+
+class Plan:
+    """Owns an ibmi_plan_t; the explicit set arrays are kept alive here."""
+
+    def __init__(self, desc: ibmi_plan_desc, lo=None, hi=None):
+        self._lib = _lib.load()
+        self._keep = []
+        if lo is not None:
+            lo_a = (C.c_int64 * len(lo))(*[int(v) for v in lo])
+            hi_a = (C.c_int64 * len(hi))(*[int(v) for v in hi])
+            self._keep += [lo_a, hi_a]
+            desc.lo = C.cast(lo_a, C.POINTER(C.c_int64))
+            desc.hi = C.cast(hi_a, C.POINTER(C.c_int64))
+            desc.K = len(lo)
+        self.desc = desc
+        h = C.c_void_p()
+        s = self._lib.ibmi_plan(C.byref(desc), C.byref(h))
+        if s != IBMI_OK:
+            raise IbmiError(s, "ibmi_plan")
+        self.handle = h
+
+    def sets(self):
+        K = C.c_int32()
+        self._lib.ibmi_plan_sets(self.handle, C.byref(K), None, None)
+        lo = (C.c_int64 * K.value)()
+        hi = (C.c_int64 * K.value)()
+        self._lib.ibmi_plan_sets(self.handle, None, lo, hi)
+        return list(zip(list(lo), list(hi)))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self._lib.ibmi_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def ibmi_plan(p: int, K: int = 2, h: int = 0, lo=None, hi=None, **kw) -> Plan:
+    return Plan(ibmi_plan_desc_init(p=p, K=K, h=h, **kw), lo, hi)
+
+
+def ibmi_invert(plan: Plan, A, H, stream=None):
+    """A, H: torch float64 CUDA tensors (p x p, row stride >= p).  Returns
+    (status, result dict)."""
+    assert A.dtype == H.dtype and str(A.dtype) == "torch.float64" and A.is_cuda and H.is_cuda
+    assert A.stride(1) == 1 and H.stride(1) == 1
+    res = ibmi_result()
+    s = _lib.load().ibmi_invert(plan.handle, C.c_void_p(A.data_ptr()), A.stride(0),
+                                C.c_void_p(H.data_ptr()), H.stride(0), _stream_ptr(stream), C.byref(res))
+    return s, res.as_dict()
+
+
+def ibmi_invert_host(plan: Plan, A: np.ndarray, H: np.ndarray, stream=None):
+    """A, H: C-contiguous float64 numpy arrays (ideally pinned)."""
+    assert A.dtype == np.float64 and H.dtype == np.float64
+    assert A.flags.c_contiguous and H.flags.c_contiguous
+    res = ibmi_result()
+    s = _lib.load().ibmi_invert_host(plan.handle, C.c_void_p(A.ctypes.data), A.shape[1],
+                                     C.c_void_p(H.ctypes.data), H.shape[1], _stream_ptr(stream),
+                                     C.byref(res))
+    return s, res.as_dict()
+
+
+def ibmi_residual(A, H, stream=None) -> float:
+    out = C.c_double()
+    s = _lib.load().ibmi_residual(C.c_void_p(A.data_ptr()), A.stride(0), C.c_void_p(H.data_ptr()),
+                                  H.stride(0), A.shape[0], _stream_ptr(stream), C.byref(out))
+    if s != IBMI_OK:
+        raise IbmiError(s, "ibmi_residual")
+    return out.value
+
+
+def ibmi_status_string(s: int) -> str:
+    return _lib.load().ibmi_status_string(s).decode()

@@ -1,0 +1,96 @@
+"""ctypes binding of libibmi.so (include/ibmi.h).
+
+Argument marshalling only: every step of the inversion runs in the CUDA
+library.  If the library has not been built the import fails loudly; there is
+no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libibmi.so")
+
+# ibmi_status
+IBMI_OK = 0
+IBMI_ERR_INVALID_ARG = 1
+IBMI_ERR_NOT_SPD = 2
+IBMI_NOT_CONVERGED = 3
+IBMI_ERR_NONFINITE = 4
+IBMI_ERR_BUDGET = 5
+IBMI_ERR_OOM = 6
+IBMI_ERR_TIMEOUT = 7
+IBMI_ERR_CUDA = 8
+IBMI_NOT_READY = 9
+IBMI_ERR_CANCELLED = 10
+# ibmi_precision / stop rule / init
+IBMI_FP64 = 0
+IBMI_MIXED = 1
+IBMI_STOP_RESID_F = 0
+IBMI_STOP_PAPER_EST = 1
+IBMI_INIT_IDENTITY = 0
+IBMI_INIT_USER = 1
+
+
+class ibmi_plan_desc(C.Structure):
+    _fields_ = [
+        ("p", C.c_int64), ("K", C.c_int32), ("h", C.c_int64),
+        ("lo", C.POINTER(C.c_int64)), ("hi", C.POINTER(C.c_int64)),
+        ("precision", C.c_int32), ("tol", C.c_double), ("max_sweeps", C.c_int32),
+        ("stop_rule", C.c_int32), ("check_every", C.c_int32), ("ns_theta", C.c_double),
+        ("ns_max", C.c_int32), ("init", C.c_int32),
+    ]
+
+
+class ibmi_result(C.Structure):
+    _fields_ = [
+        ("status", C.c_int32), ("sweeps", C.c_int32), ("ns_steps", C.c_int32),
+        ("bad_block", C.c_int32), ("bad_pivot", C.c_int64), ("resid_f", C.c_double),
+        ("paper_est", C.c_double), ("seconds", C.c_double), ("flops", C.c_double),
+    ]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_P = C.c_void_p
+_D = C.POINTER(C.c_double)
+
+_SIGS = {
+    "ibmi_plan_desc_init": (None, [C.POINTER(ibmi_plan_desc)]),
+    "ibmi_plan": (C.c_int, [C.POINTER(ibmi_plan_desc), C.POINTER(_P)]),
+    "ibmi_plan_destroy": (C.c_int, [_P]),
+    "ibmi_plan_sets": (C.c_int, [_P, C.POINTER(C.c_int32), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+    "ibmi_invert": (C.c_int, [_P, _P, C.c_int64, _P, C.c_int64, _P, C.POINTER(ibmi_result)]),
+    "ibmi_invert_host": (C.c_int, [_P, _P, C.c_int64, _P, C.c_int64, _P, C.POINTER(ibmi_result)]),
+    "ibmi_residual": (C.c_int, [_P, C.c_int64, _P, C.c_int64, C.c_int64, _P, _D]),
+    "ibmi_prof_enable": (None, [C.c_int]),
+    "ibmi_prof_get": (C.c_int, [C.c_int32, C.POINTER(C.c_int64), _D, _D]),
+    "ibmi_launch_count": (C.c_int64, []),
+    "ibmi_status_string": (C.c_char_p, [C.c_int]),
+    "ibmi_last_error": (C.c_char_p, []),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> C.CDLL:
+    """Loads the CUDA library (once).  Raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with "
+                          "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = C.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    return list(_SIGS)

@@ -1,0 +1,451 @@
+// C ABI entry points (include/ibmi.h): plan validation and workspace,
+// Algorithm 1 driver (sweep loop, stop test, Newton-Schulz tail), residual.
+#include <math.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <string>
+
+#include "gemm_f64.cuh"
+#include "mixed.cuh"
+#include "plan.cuh"
+
+namespace ibmi {
+
+static thread_local std::string g_last_error;
+void set_last_error(const std::string& s) { g_last_error = s; }
+
+// Default layout of the sets (Section 4): cores [floor(k p/K), floor((k+1) p/K)),
+// widened by h on each side with a neighbour.
+static void default_sets(int64_t p, int32_t K, int64_t h, std::vector<int64_t>& lo,
+                         std::vector<int64_t>& hi) {
+  lo.resize(K);
+  hi.resize(K);
+  for (int32_t k = 0; k < K; ++k) {
+    int64_t b0 = (int64_t)k * p / K, b1 = (int64_t)(k + 1) * p / K;
+    lo[k] = std::max<int64_t>(0, b0 - h);
+    hi[k] = std::min<int64_t>(p, b1 + h);
+  }
+}
+
+static ibmi_status validate_sets(int64_t p, const std::vector<int64_t>& lo, const std::vector<int64_t>& hi) {
+  const size_t K = lo.size();
+  if (K == 0 || hi.size() != K) return IBMI_ERR_INVALID_ARG;
+  if (lo[0] != 0 || hi[K - 1] != p) return IBMI_ERR_INVALID_ARG;
+  for (size_t k = 0; k < K; ++k) {
+    if (!(lo[k] >= 0 && lo[k] < hi[k] && hi[k] <= p)) return IBMI_ERR_INVALID_ARG;
+    if (K > 1 && hi[k] - lo[k] >= p) return IBMI_ERR_INVALID_ARG;   // empty complement
+    if (k > 0) {
+      if (!(lo[k] > lo[k - 1] && hi[k] > hi[k - 1])) return IBMI_ERR_INVALID_ARG;
+      if (lo[k] > hi[k - 1]) return IBMI_ERR_INVALID_ARG;            // gap: not covered
+    }
+  }
+  return IBMI_OK;
+}
+
+static bool is_device_ptr(const void* ptr) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+static double flops_sweep(const ibmi_plan_s* P) {
+  double f = 0;
+  for (size_t k = 0; k < P->lo.size(); ++k) {
+    double m = (double)(P->hi[k] - P->lo[k]), n = (double)P->d.p - m;
+    f += 2.0 * m * n * n + 2.0 * m * m * n;
+  }
+  return f;
+}
+
+static double flops_plan(const ibmi_plan_s* P) {
+  double f = 0;
+  for (size_t k = 0; k < P->lo.size(); ++k) {
+    double m = (double)(P->hi[k] - P->lo[k]), n = (double)P->d.p - m;
+    f += m * m * m / 3.0 + 2.0 * m * m * m + 2.0 * m * m * n;
+  }
+  return f;
+}
+
+static ibmi_status ensure_ns_buffers(ibmi_plan_s* P) {
+  if (P->nsR) return IBMI_OK;
+  const size_t b = sizeof(double) * (size_t)P->d.p * P->d.p;
+  IBMI_CUDA_TRY(cudaMalloc(&P->nsR, b));
+  IBMI_CUDA_TRY(cudaMalloc(&P->nsX, b));
+  return IBMI_OK;
+}
+
+// Reads rho_F computed on the device (syncs the stream).
+static ibmi_status residual_host(ibmi_plan_s* P, const double* A, int64_t lda, const double* H,
+                                 int64_t ldh, cudaStream_t st, double* rho) {
+  IBMI_TRY(residual_f64_dev(A, lda, H, ldh, P->d.p, P->partials, P->n_partials, P->dscalar, st));
+  double v[2];
+  IBMI_CUDA_TRY(cudaMemcpyAsync(v, P->dscalar, sizeof(v), cudaMemcpyDeviceToHost, st));
+  IBMI_CUDA_TRY(cudaStreamSynchronize(st));
+  *rho = v[0];
+  return IBMI_OK;
+}
+
+static ibmi_status invert_impl(ibmi_plan_s* P, const double* A, int64_t lda, double* H, int64_t ldh,
+                               cudaStream_t st, ibmi_result* res) {
+  const int64_t p = P->d.p;
+  const int K = (int)P->lo.size();
+  const ibmi_plan_desc& d = P->d;
+  const double sqrtp = sqrt((double)p);
+  double flops = 0.0;
+  // a2: invariants
+  IBMI_CUDA_TRY(cudaMemsetAsync(P->dstatus, 0, sizeof(DevStatus), st));
+  const bool mixed = d.precision == IBMI_MIXED;
+  for (int k = 0; k < K; ++k) IBMI_TRY(invariants_f64(P, k, A, lda, st));
+  flops += flops_plan(P);
+  DevStatus hs;
+  IBMI_CUDA_TRY(cudaMemcpyAsync(&hs, P->dstatus, sizeof(hs), cudaMemcpyDeviceToHost, st));
+  IBMI_CUDA_TRY(cudaStreamSynchronize(st));
+  if (hs.code == IBMI_ERR_NOT_SPD) {
+    res->bad_block = hs.block;
+    res->bad_pivot = hs.pivot;
+    return IBMI_ERR_NOT_SPD;
+  }
+  if (d.init == IBMI_INIT_IDENTITY) IBMI_TRY(set_identity(H, ldh, p, st));
+  if (mixed) IBMI_TRY(mixed_prepare(P, H, ldh, st));
+  // Algorithm 1: sweeps with the stop test every check_every sweeps
+  ibmi_status status = IBMI_NOT_CONVERGED;
+  bool to_ns = false;
+  int r = 0;
+  const double fs = flops_sweep(P), fr = 2.0 * (double)p * p * p;
+  while (true) {
+    ++r;
+    for (int k = 0; k < K; ++k) {
+      if (mixed) IBMI_TRY(mixed_sweep_step(P, k, st));
+      else IBMI_TRY(sweep_step_f64(P, k, H, ldh, st));
+    }
+    flops += fs;
+    res->sweeps = r;
+    if (r % d.check_every != 0 && r < d.max_sweeps) continue;
+    if (mixed) IBMI_TRY(mixed_export(P, H, ldh, st));
+    double rho;
+    IBMI_TRY(residual_host(P, A, lda, H, ldh, st, &rho));
+    flops += fr;
+    res->resid_f = rho;
+    if (!isfinite(rho)) { status = IBMI_ERR_NONFINITE; break; }
+    if (rho <= d.tol) { status = IBMI_OK; break; }
+    if (d.ns_theta > 0.0 && rho * sqrtp <= d.ns_theta) { to_ns = true; break; }
+    if (r >= d.max_sweeps) break;
+  }
+  if (to_ns) {
+    IBMI_TRY(ensure_ns_buffers(P));
+    status = IBMI_NOT_CONVERGED;
+    double prev = res->resid_f;
+    for (int s = 0; s < d.ns_max; ++s) {
+      IBMI_TRY(ns_step_f64(P, A, lda, H, ldh, st));
+      flops += 2.0 * fr;
+      double rho;
+      IBMI_TRY(residual_host(P, A, lda, H, ldh, st, &rho));
+      flops += fr;
+      res->ns_steps = s + 1;
+      res->resid_f = rho;
+      if (!isfinite(rho)) { status = IBMI_ERR_NONFINITE; break; }
+      if (rho <= d.tol) { status = IBMI_OK; break; }
+      if (!(rho < prev)) break;   // a step that does not reduce the residual ends the tail
+      prev = rho;
+    }
+  }
+  res->flops = flops;
+  return status;
+}
+
+}  // namespace ibmi
+
+using namespace ibmi;
+
+extern "C" {
+
+void ibmi_plan_desc_init(ibmi_plan_desc* d) {
+  if (!d) return;
+  memset(d, 0, sizeof(*d));
+  d->K = 2;
+  d->h = 0;
+  d->precision = IBMI_FP64;
+  d->tol = 1e-10;
+  d->max_sweeps = 500;
+  d->stop_rule = IBMI_STOP_RESID_F;
+  d->check_every = 1;
+  d->ns_theta = 0.0;
+  d->ns_max = 8;
+  d->init = IBMI_INIT_IDENTITY;
+}
+
+ibmi_status ibmi_plan(const ibmi_plan_desc* desc, ibmi_plan_t* out) {
+  if (!desc || !out) return IBMI_ERR_INVALID_ARG;
+  *out = nullptr;
+  const ibmi_plan_desc& d = *desc;
+  if (d.p < 2 || d.K < 1 || d.K > d.p || d.h < 0) return IBMI_ERR_INVALID_ARG;
+  if (d.p > (int64_t)1 << 20) return IBMI_ERR_INVALID_ARG;
+  if (d.precision != IBMI_FP64 && d.precision != IBMI_MIXED) return IBMI_ERR_INVALID_ARG;
+  if (d.stop_rule != IBMI_STOP_RESID_F && d.stop_rule != IBMI_STOP_PAPER_EST) return IBMI_ERR_INVALID_ARG;
+  if (d.stop_rule == IBMI_STOP_PAPER_EST) return IBMI_ERR_INVALID_ARG;  // not offered by this build
+  if (d.init != IBMI_INIT_IDENTITY && d.init != IBMI_INIT_USER) return IBMI_ERR_INVALID_ARG;
+  if (d.max_sweeps < 1 || d.check_every < 1 || d.ns_max < 0 || !(d.tol >= 0.0) || !(d.ns_theta >= 0.0))
+    return IBMI_ERR_INVALID_ARG;
+  ibmi_plan_s* P = new ibmi_plan_s();
+  P->d = d;
+  P->d.lo = P->d.hi = nullptr;
+  if (d.lo || d.hi) {
+    if (!d.lo || !d.hi) { delete P; return IBMI_ERR_INVALID_ARG; }
+    P->lo.assign(d.lo, d.lo + d.K);
+    P->hi.assign(d.hi, d.hi + d.K);
+  } else {
+    default_sets(d.p, d.K, d.h, P->lo, P->hi);
+  }
+  if (validate_sets(d.p, P->lo, P->hi) != IBMI_OK) { delete P; return IBMI_ERR_INVALID_ARG; }
+  cudaGetDevice(&P->device);
+  const int64_t p = d.p;
+  int64_t mmax = 0, ainv_elems = 0, w_elems = 0;
+  for (int k = 0; k < d.K; ++k) {
+    int64_t m = P->hi[k] - P->lo[k];
+    mmax = std::max(mmax, m);
+    ainv_elems += m * m;
+    w_elems += m * p;
+  }
+  P->mmax = mmax;
+  P->n_partials = gemm_f64_ctas(p, p);
+  const int64_t nb_tiles = (mmax + CHOL_NB - 1) / CHOL_NB;
+  const int64_t scratch = mmax * mmax /*lwork*/ + nb_tiles * CHOL_NB * CHOL_NB /*linv*/ +
+                          (int64_t)CHOL_NB * p /*tmp*/ + mmax * mmax /*S*/ + P->n_partials + 4;
+  const size_t total = sizeof(double) * (size_t)(ainv_elems + w_elems + scratch);
+  if (cudaMalloc(&P->pool, total) != cudaSuccess) {
+    cudaGetLastError();
+    delete P;
+    return IBMI_ERR_OOM;
+  }
+  P->pool_bytes = total;
+  double* q = P->pool;
+  for (int k = 0; k < d.K; ++k) {
+    int64_t m = P->hi[k] - P->lo[k];
+    P->ainv.push_back(q); q += m * m;
+  }
+  for (int k = 0; k < d.K; ++k) {
+    int64_t m = P->hi[k] - P->lo[k];
+    P->w.push_back(q); q += m * p;
+  }
+  P->lwork = q; q += mmax * mmax;
+  P->linv = q; q += nb_tiles * CHOL_NB * CHOL_NB;
+  P->tmp = q; q += (int64_t)CHOL_NB * p;
+  P->S = q; q += mmax * mmax;
+  P->partials = q; q += P->n_partials;
+  P->dscalar = q; q += 4;
+  if (cudaMalloc(&P->dstatus, sizeof(DevStatus)) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(P->pool);
+    delete P;
+    return IBMI_ERR_OOM;
+  }
+  if (d.precision == IBMI_MIXED) {
+    ibmi_status s = mixed_create(P);
+    if (s != IBMI_OK) { ibmi_plan_destroy(P); return s; }
+  }
+  *out = P;
+  return IBMI_OK;
+}
+
+ibmi_status ibmi_plan_destroy(ibmi_plan_t P) {
+  if (!P) return IBMI_ERR_INVALID_ARG;
+  if (P->mixed) mixed_destroy(P);
+  cudaFree(P->pool);
+  cudaFree(P->dstatus);
+  cudaFree(P->nsR);
+  cudaFree(P->nsX);
+  cudaFree(P->dA);
+  cudaFree(P->dH);
+  delete P;
+  return IBMI_OK;
+}
+
+ibmi_status ibmi_plan_sets(ibmi_plan_t P, int32_t* K, int64_t* lo, int64_t* hi) {
+  if (!P) return IBMI_ERR_INVALID_ARG;
+  if (K) *K = (int32_t)P->lo.size();
+  for (size_t k = 0; k < P->lo.size(); ++k) {
+    if (lo) lo[k] = P->lo[k];
+    if (hi) hi[k] = P->hi[k];
+  }
+  return IBMI_OK;
+}
+
+ibmi_status ibmi_invert(ibmi_plan_t P, const double* A, int64_t lda, double* H, int64_t ldh,
+                        void* stream, ibmi_result* out) {
+  ibmi_result tmp;
+  ibmi_result* res = out ? out : &tmp;
+  memset(res, 0, sizeof(*res));
+  res->bad_block = -1;
+  res->bad_pivot = -1;
+  res->resid_f = NAN;
+  res->paper_est = NAN;
+  ibmi_status s;
+  if (!P || !A || !H || lda < P->d.p || ldh < P->d.p) {
+    s = IBMI_ERR_INVALID_ARG;
+  } else if (!is_device_ptr(A) || !is_device_ptr(H)) {
+    s = IBMI_ERR_INVALID_ARG;
+  } else {
+    cudaStream_t st = (cudaStream_t)stream;
+    auto t0 = std::chrono::steady_clock::now();
+    s = invert_impl(P, A, lda, H, ldh, st, res);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess && s == IBMI_OK) { set_last_error(cudaGetErrorString(e)); s = IBMI_ERR_CUDA; }
+    res->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  res->status = s;
+  return s;
+}
+
+ibmi_status ibmi_invert_host(ibmi_plan_t P, const double* A_host, int64_t lda, double* H_host, int64_t ldh,
+                             void* stream, ibmi_result* out) {
+  if (!P || !A_host || !H_host || lda < P->d.p || ldh < P->d.p) return IBMI_ERR_INVALID_ARG;
+  const int64_t p = P->d.p;
+  const size_t row = sizeof(double) * p;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!P->dA) {
+    IBMI_CUDA_TRY(cudaMalloc(&P->dA, row * p));
+    IBMI_CUDA_TRY(cudaMalloc(&P->dH, row * p));
+  }
+  auto t0 = std::chrono::steady_clock::now();
+  IBMI_CUDA_TRY(cudaMemcpy2DAsync(P->dA, row, A_host, sizeof(double) * lda, row, p, cudaMemcpyHostToDevice, st));
+  if (P->d.init == IBMI_INIT_USER)
+    IBMI_CUDA_TRY(cudaMemcpy2DAsync(P->dH, row, H_host, sizeof(double) * ldh, row, p, cudaMemcpyHostToDevice, st));
+  ibmi_status s = ibmi_invert(P, P->dA, p, P->dH, p, stream, out);
+  if (s == IBMI_OK || s == IBMI_NOT_CONVERGED) {
+    IBMI_CUDA_TRY(cudaMemcpy2DAsync(H_host, sizeof(double) * ldh, P->dH, row, row, p, cudaMemcpyDeviceToHost, st));
+    IBMI_CUDA_TRY(cudaStreamSynchronize(st));
+  }
+  if (out) out->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  return s;
+}
+
+ibmi_status ibmi_residual(const double* A, int64_t lda, const double* H, int64_t ldh, int64_t p,
+                          void* stream, double* out) {
+  if (!A || !H || !out || p < 1 || lda < p || ldh < p) return IBMI_ERR_INVALID_ARG;
+  if (!is_device_ptr(A) || !is_device_ptr(H)) return IBMI_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t n = gemm_f64_ctas(p, p);
+  double* buf = nullptr;
+  IBMI_CUDA_TRY(cudaMallocAsync(&buf, sizeof(double) * (n + 2), st));
+  ibmi_status s = residual_f64_dev(A, lda, H, ldh, p, buf, n, buf + n, st);
+  double v[2] = {NAN, NAN};
+  if (s == IBMI_OK) {
+    cudaMemcpyAsync(v, buf + n, sizeof(v), cudaMemcpyDeviceToHost, st);
+  }
+  cudaFreeAsync(buf, st);
+  IBMI_CUDA_TRY(cudaStreamSynchronize(st));
+  *out = v[0];
+  return s;
+}
+
+const char* ibmi_status_string(ibmi_status s) {
+  switch (s) {
+    case IBMI_OK: return "IBMI_OK";
+    case IBMI_ERR_INVALID_ARG: return "IBMI_ERR_INVALID_ARG";
+    case IBMI_ERR_NOT_SPD: return "IBMI_ERR_NOT_SPD";
+    case IBMI_NOT_CONVERGED: return "IBMI_NOT_CONVERGED";
+    case IBMI_ERR_NONFINITE: return "IBMI_ERR_NONFINITE";
+    case IBMI_ERR_BUDGET: return "IBMI_ERR_BUDGET";
+    case IBMI_ERR_OOM: return "IBMI_ERR_OOM";
+    case IBMI_ERR_TIMEOUT: return "IBMI_ERR_TIMEOUT";
+    case IBMI_ERR_CUDA: return "IBMI_ERR_CUDA";
+    case IBMI_NOT_READY: return "IBMI_NOT_READY";
+    case IBMI_ERR_CANCELLED: return "IBMI_ERR_CANCELLED";
+  }
+  return "IBMI_UNKNOWN";
+}
+
+const char* ibmi_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"
+
+// ------------------------------------------------------------- profiling --
+#include <atomic>
+namespace ibmi {
+namespace {
+struct ProfClass {
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
+  int64_t launches = 0;
+  double flops = 0.0;
+  double ms = 0.0;
+};
+bool g_prof_on = false;
+ProfClass g_prof[IBMI_K_COUNT];
+std::vector<cudaEvent_t> g_event_pool;
+std::atomic<int64_t> g_launches{0};
+int g_open_class = -1;
+cudaEvent_t g_open_event = nullptr;
+
+cudaEvent_t take_event() {
+  if (!g_event_pool.empty()) {
+    cudaEvent_t e = g_event_pool.back();
+    g_event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+}  // namespace
+
+void note_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+void prof_begin(int k, cudaStream_t st) {
+  if (!g_prof_on || k < 0 || k >= IBMI_K_COUNT) return;
+  g_open_class = k;
+  g_open_event = take_event();
+  cudaEventRecord(g_open_event, st);
+}
+
+void prof_end(int k, cudaStream_t st, double flops) {
+  if (!g_prof_on || k != g_open_class || !g_open_event) return;
+  cudaEvent_t e = take_event();
+  cudaEventRecord(e, st);
+  g_prof[k].ev.emplace_back(g_open_event, e);
+  g_prof[k].launches += 1;
+  g_prof[k].flops += flops;
+  g_open_event = nullptr;
+  g_open_class = -1;
+}
+}  // namespace ibmi
+
+extern "C" {
+void ibmi_prof_enable(int on) {
+  using namespace ibmi;
+  for (auto& c : g_prof) {
+    for (auto& pr : c.ev) {
+      cudaEventSynchronize(pr.second);
+      g_event_pool.push_back(pr.first);
+      g_event_pool.push_back(pr.second);
+    }
+    c = ProfClass();
+  }
+  g_launches.store(0);
+  g_prof_on = on != 0;
+}
+
+ibmi_status ibmi_prof_get(int32_t k, int64_t* launches, double* ms, double* flops) {
+  using namespace ibmi;
+  if (k < 0 || k >= IBMI_K_COUNT) return IBMI_ERR_INVALID_ARG;
+  ProfClass& c = g_prof[k];
+  for (auto& pr : c.ev) {
+    float t = 0.f;
+    cudaEventSynchronize(pr.second);
+    if (cudaEventElapsedTime(&t, pr.first, pr.second) == cudaSuccess) c.ms += t;
+    g_event_pool.push_back(pr.first);
+    g_event_pool.push_back(pr.second);
+  }
+  c.ev.clear();
+  if (launches) *launches = c.launches;
+  if (ms) *ms = c.ms;
+  if (flops) *flops = c.flops;
+  return IBMI_OK;
+}
+
+int64_t ibmi_launch_count(void) { return ibmi::g_launches.load(); }
+}  // extern "C"

@@ -1,0 +1,181 @@
+// FP64 (DFMA) tiled GEMM with index-gap operand maps and functor epilogues.
+//
+// C[i, j] = sum_l opA(i, l) * opB(l, j) for i < M, j < N, l < K, where
+//   opA(i, l) = A[mA(i) * lda + kA(l)]            (A_KMAJOR: row-major M x K)
+//             = A[kA(l) * lda + mA(i)]            (otherwise: column-major)
+//   opB(l, j) = B[kB(l) * ldb + nB(j)]            (B_NMAJOR: row-major K x N)
+//             = B[nB(j) * ldb + kB(l)]            (otherwise: "B^T" storage)
+// and every map is a GapMap (identity when len = 0).  The epilogue functor is
+// called once per valid (i, j) with the FP64 accumulator.
+//
+// On GB300 FP64 runs at ~1.2 TFLOP/s (DFMA), about 1/60 of FP32 CUDA-core
+// throughput, so this kernel is DFMA-bound by a wide margin: a 64 x 64 tile
+// with a 4 x 4 register block per thread keeps shared-memory traffic at
+// 0.5 loads per FMA and global traffic negligible.
+#pragma once
+#include "common.cuh"
+
+namespace ibmi {
+
+constexpr int F64_BM = 64, F64_BN = 64, F64_BK = 16, F64_THREADS = 256;
+
+struct F64Operands {
+  const double* A; int64_t lda; GapMap mA, kA;
+  const double* B; int64_t ldb; GapMap kB, nB;
+  int64_t M, N, K;
+};
+
+template <bool A_KMAJOR, bool B_NMAJOR, class Epi>
+__global__ void __launch_bounds__(F64_THREADS)
+k_gemm_f64(F64Operands op, Epi epi) {
+  __shared__ double As[F64_BK][F64_BM + 1];
+  __shared__ double Bs[F64_BK][F64_BN + 1];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int64_t i0 = (int64_t)blockIdx.y * F64_BM, j0 = (int64_t)blockIdx.x * F64_BN;
+  double acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+
+  for (int64_t l0 = 0; l0 < op.K; l0 += F64_BK) {
+    // A tile: 64 x 16 = 1024 values, 4 per thread.
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      int e = threadIdx.x + t * F64_THREADS;
+      int r, c;  // r: M within tile, c: K within tile
+      if (A_KMAJOR) { r = e >> 4; c = e & 15; } else { r = e & 63; c = e >> 6; }
+      int64_t i = i0 + r, l = l0 + c;
+      double v = 0.0;
+      if (i < op.M && l < op.K)
+        v = A_KMAJOR ? op.A[op.mA(i) * op.lda + op.kA(l)] : op.A[op.kA(l) * op.lda + op.mA(i)];
+      As[c][r] = v;
+    }
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      int e = threadIdx.x + t * F64_THREADS;
+      int r, c;  // r: K within tile, c: N within tile
+      if (B_NMAJOR) { r = e >> 6; c = e & 63; } else { r = e & 15; c = e >> 4; }
+      int64_t l = l0 + r, j = j0 + c;
+      double v = 0.0;
+      if (l < op.K && j < op.N)
+        v = B_NMAJOR ? op.B[op.kB(l) * op.ldb + op.nB(j)] : op.B[op.nB(j) * op.ldb + op.kB(l)];
+      Bs[r][c] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < F64_BK; ++k) {
+      double a[4], b[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) { a[q] = As[k][ty + 16 * q]; b[q] = Bs[k][tx + 16 * q]; }
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) acc[x][y] = fma(a[x], b[y], acc[x][y]);
+    }
+    __syncthreads();
+  }
+  epi.begin();
+#pragma unroll
+  for (int x = 0; x < 4; ++x)
+#pragma unroll
+    for (int y = 0; y < 4; ++y) {
+      int64_t i = i0 + ty + 16 * x, j = j0 + tx + 16 * y;
+      if (i < op.M && j < op.N) epi(i, j, acc[x][y]);
+    }
+  epi.end();
+}
+
+// ---------------------------------------------------------------- epilogues --
+
+// C[i*ldc + j] = alpha * acc + beta * C[i*ldc + j]   (beta == 0 never reads C)
+struct EpiStore {
+  double* C; int64_t ldc; double alpha, beta;
+  __device__ void begin() {}
+  __device__ void end() {}
+  __device__ __forceinline__ void operator()(int64_t i, int64_t j, double acc) {
+    double* c = C + i * ldc + j;
+    *c = beta == 0.0 ? alpha * acc : fma(beta, *c, alpha * acc);
+  }
+};
+
+// Sweep product a3: X = -W T, written to H[lo + i, phys(j)] and H[phys(j), lo + i].
+struct EpiSweepX {
+  double* H; int64_t ldh; int64_t lo; GapMap nmap;
+  __device__ void begin() {}
+  __device__ void end() {}
+  __device__ __forceinline__ void operator()(int64_t i, int64_t j, double acc) {
+    int64_t jp = nmap(j), ip = lo + i;
+    double x = -acc;
+    H[ip * ldh + jp] = x;
+    H[jp * ldh + ip] = x;
+  }
+};
+
+// Sweep product a4: S = A_I^{-1} - X W^T into scratch S (m x m, ld m).
+struct EpiSweepS {
+  const double* Ainv; double* S; int64_t m;
+  __device__ void begin() {}
+  __device__ void end() {}
+  __device__ __forceinline__ void operator()(int64_t i, int64_t j, double acc) {
+    S[i * m + j] = Ainv[i * m + j] - acc;
+  }
+};
+
+// Residual: accumulate (delta_ij - acc)^2 and write one partial per CTA.
+struct EpiResidual {
+  double* partials;
+  double s;
+  __device__ void begin() { s = 0.0; }
+  __device__ __forceinline__ void operator()(int64_t i, int64_t j, double acc) {
+    double r = (i == j ? 1.0 : 0.0) - acc;
+    s = fma(r, r, s);
+  }
+  __device__ void end() {
+    __shared__ double red[F64_THREADS / 32];
+    double v = s;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < F64_THREADS / 32; ++w) t += red[w];
+      partials[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = t;
+    }
+  }
+};
+
+// Newton-Schulz: R = I - acc (store).
+struct EpiIdentityMinus {
+  double* R; int64_t ldr;
+  __device__ void begin() {}
+  __device__ void end() {}
+  __device__ __forceinline__ void operator()(int64_t i, int64_t j, double acc) {
+    R[i * ldr + j] = (i == j ? 1.0 : 0.0) - acc;
+  }
+};
+
+// Newton-Schulz: Xn = X + acc.
+struct EpiAddTo {
+  const double* X; int64_t ldx; double* Xn; int64_t ldn;
+  __device__ void begin() {}
+  __device__ void end() {}
+  __device__ __forceinline__ void operator()(int64_t i, int64_t j, double acc) {
+    Xn[i * ldn + j] = X[i * ldx + j] + acc;
+  }
+};
+
+template <bool A_KMAJOR, bool B_NMAJOR, class Epi>
+inline cudaError_t launch_gemm_f64(const F64Operands& op, const Epi& epi, cudaStream_t st) {
+  if (op.M <= 0 || op.N <= 0) return cudaSuccess;
+  dim3 grid((unsigned)((op.N + F64_BN - 1) / F64_BN), (unsigned)((op.M + F64_BM - 1) / F64_BM));
+  note_launch();
+  k_gemm_f64<A_KMAJOR, B_NMAJOR, Epi><<<grid, F64_THREADS, 0, st>>>(op, epi);
+  return cudaGetLastError();
+}
+
+inline int64_t gemm_f64_ctas(int64_t M, int64_t N) {
+  return ((N + F64_BN - 1) / F64_BN) * ((M + F64_BM - 1) / F64_BM);
+}
+
+}  // namespace ibmi

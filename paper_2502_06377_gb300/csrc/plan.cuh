@@ -1,0 +1,56 @@
+// Internal plan object and the host-side drivers of each hot-path step.
+#pragma once
+#include "common.cuh"
+
+struct ibmi_plan_s {
+  ibmi_plan_desc d{};
+  std::vector<int64_t> lo, hi;   // sets I_k = [lo_k, hi_k)
+  int64_t mmax = 0;
+  int device = 0;
+  // persistent per-set invariants (eq. IBMI terms that do not depend on H)
+  std::vector<double*> ainv;     // A_I^{-1}, m x m
+  std::vector<double*> w;        // W = A_I^{-1} A_{I,:}, m x p, zero columns on I
+  double* pool = nullptr;        // one allocation backing ainv / w / scratch
+  size_t pool_bytes = 0;
+  // scratch
+  double* lwork = nullptr;       // Cholesky factor of one block, mmax x mmax
+  double* linv = nullptr;        // inverses of the nb x nb diagonal tiles
+  double* tmp = nullptr;         // nb x p
+  double* S = nullptr;           // mmax x mmax, a4 result before symmetrisation
+  double* partials = nullptr;    // residual partial sums
+  int64_t n_partials = 0;
+  double* dscalar = nullptr;     // device scalar results
+  ibmi::DevStatus* dstatus = nullptr;
+  // Newton-Schulz buffers (allocated on first use)
+  double* nsR = nullptr;
+  double* nsX = nullptr;
+  // host-variant staging (allocated on first use)
+  double* dA = nullptr;
+  double* dH = nullptr;
+  // mixed-precision state (allocated at plan time when precision == MIXED)
+  void* mixed = nullptr;
+};
+
+namespace ibmi {
+
+constexpr int CHOL_NB = 32;
+
+// a2: A_I^{-1} and W for set k, FP64.  Non-SPD blocks are reported through
+// plan->dstatus (read by the caller after a stream sync).
+ibmi_status invariants_f64(ibmi_plan_s* P, int k, const double* A, int64_t lda, cudaStream_t st);
+
+// a3 + a4 for set k on an FP64 iterate H.
+ibmi_status sweep_step_f64(ibmi_plan_s* P, int k, double* H, int64_t ldh, cudaStream_t st);
+
+// a6: rho_F = ||I - A H||_F / sqrt(p), FP64, value left in *dout (device).
+ibmi_status residual_f64_dev(const double* A, int64_t lda, const double* H, int64_t ldh, int64_t p,
+                             double* partials, int64_t n_partials, double* dout, cudaStream_t st);
+
+// a7: one Newton-Schulz step X <- sym(X + X (I - A X)) in FP64; leaves
+// ||I - A X_old||_F^2 in *dout.
+ibmi_status ns_step_f64(ibmi_plan_s* P, const double* A, int64_t lda, double* X, int64_t ldx,
+                        cudaStream_t st);
+
+ibmi_status set_identity(double* H, int64_t ldh, int64_t p, cudaStream_t st);
+
+}  // namespace ibmi

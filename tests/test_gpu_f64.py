@@ -1,0 +1,209 @@
+"""FP64 GPU path vs the FP64 oracle, through the C ABI.
+
+Tolerances: fixed-sweep trajectories agree to 1e-12 in relative Frobenius norm
+(both sides are FP64; only the summation order differs); converged runs both
+reach ||I - A H||_F / sqrt(p) <= 1e-10 with the same sweep count +-1.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import ibmi_oracle as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ibmi():
+    import __graft_entry__ as g
+    g.build()
+    import paper_2502_06377_gb300 as m
+    return m
+
+
+def run_gpu(ibmi, A, H0=None, **kw):
+    p = A.shape[0]
+    dA = torch.from_numpy(np.ascontiguousarray(A)).cuda()
+    dH = torch.from_numpy(H0.copy()).cuda() if H0 is not None else torch.empty_like(dA)
+    lo = kw.pop("lo", None)
+    hi = kw.pop("hi", None)
+    plan = ibmi.ibmi_plan(p, lo=lo, hi=hi, **kw)
+    s, res = ibmi.ibmi_invert(plan, dA, dH)
+    torch.cuda.synchronize()
+    H = dH.cpu().numpy()
+    plan.close()
+    return s, res, H
+
+
+def rel_fro(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def kms_inverse(p, rho):
+    inv = np.zeros((p, p))
+    c = 1.0 / (1.0 - rho * rho)
+    for i in range(p):
+        inv[i, i] = c * (1.0 + rho * rho) if 0 < i < p - 1 else c
+        if i + 1 < p:
+            inv[i, i + 1] = inv[i + 1, i] = -rho * c
+    return inv
+
+
+def test_c1_kms_one_sweep(ibmi):
+    A = wl.c1_kms()
+    s, res, H = run_gpu(ibmi, A, K=2, h=0, tol=1e-12)
+    assert s == ibmi.IBMI_OK and res["sweeps"] == 1
+    assert np.abs(H - kms_inverse(256, 0.5)).max() < 1e-14
+    ref = O.ibmi(A, O.partition(256, 2, 0), tol=1e-12)
+    assert rel_fro(H, ref.h) < 1e-14
+    assert np.array_equal(H, H.T)
+
+
+@pytest.mark.parametrize("r", [1, 2, 3])
+def test_kms_trajectory_user_init(ibmi, r):
+    p, rho, c = 256, 0.5, 2.0
+    A = wl.kms(p, rho)
+    s, res, H = run_gpu(ibmi, A, H0=c * np.eye(p), K=2, h=0, tol=0.0, max_sweeps=r, init=ibmi.IBMI_INIT_USER)
+    assert s == ibmi.IBMI_NOT_CONVERGED and res["sweeps"] == r
+    m = p // 2
+    delta = (c * (1.0 - rho ** p) - 1.0) / (1.0 - rho * rho)
+    e = delta * rho ** (4 * r - 2)
+    want = kms_inverse(p, rho)
+    want[m - 1, m - 1] += e
+    want[m - 1, m] -= e * rho
+    want[m, m - 1] -= e * rho
+    want[m, m] += e * rho * rho
+    assert np.abs(H - want).max() < 1e-14
+
+
+CASES = [
+    # (generator, p, K, h)  -- ragged sizes spanning several 64-wide tiles
+    ("matern", 200, 3, 10),
+    ("matern", 333, 4, 7),
+    ("matern", 517, 5, 16),
+    ("se", 390, 2, 40),
+    ("random", 150, 2, 30),
+    ("matern", 96, 4, 0),
+]
+
+
+def make(gen, p, seed=1):
+    rng = np.random.default_rng(seed)
+    if gen == "matern":
+        return wl.matern32(wl.uniform_points(rng, p, 2), 0.1, 1.0, 1e-2)
+    if gen == "se":
+        return wl.squared_exp(wl.uniform_points(rng, p, 3), 0.2, 1.0, 1e-3)
+    return wl.random_spd(p, seed, 1.0, 1e2)
+
+
+@pytest.mark.parametrize("gen,p,K,h", CASES)
+@pytest.mark.parametrize("r", [1, 2, 5])
+def test_fixed_sweep_parity(ibmi, gen, p, K, h, r):
+    A = make(gen, p)
+    ref = O.ibmi(A, O.partition(p, K, h), tol=0.0, max_sweeps=r)
+    s, res, H = run_gpu(ibmi, A, K=K, h=h, tol=0.0, max_sweeps=r)
+    assert s == ibmi.IBMI_NOT_CONVERGED and res["sweeps"] == r
+    assert rel_fro(H, ref.h) < 1e-12
+    assert np.array_equal(H, H.T)
+    assert res["resid_f"] == pytest.approx(ref.resid_f, rel=1e-6, abs=1e-14)
+
+
+def test_explicit_uneven_sets(ibmi):
+    p = 300
+    A = make("matern", p, 3)
+    lo, hi = [0, 70, 150, 220], [100, 180, 260, 300]
+    ref = O.ibmi(A, list(zip(lo, hi)), tol=0.0, max_sweeps=3)
+    s, res, H = run_gpu(ibmi, A, lo=lo, hi=hi, tol=0.0, max_sweeps=3)
+    assert rel_fro(H, ref.h) < 1e-12
+
+
+def test_single_set_is_direct_inverse(ibmi):
+    p = 130
+    A = make("random", p, 4)
+    s, res, H = run_gpu(ibmi, A, K=1, tol=1e-12)
+    assert s == ibmi.IBMI_OK and res["sweeps"] == 1
+    assert rel_fro(H, O.spd_inverse(A)) < 1e-13
+
+
+def test_tiny_p2(ibmi):
+    A = np.array([[2.0, 0.5], [0.5, 1.0]])
+    s, res, H = run_gpu(ibmi, A, K=2, h=0, tol=1e-14, max_sweeps=100)
+    assert s == ibmi.IBMI_OK
+    np.testing.assert_allclose(H, np.linalg.inv(A), atol=1e-14)
+
+
+def test_converged_parity_matern(ibmi):
+    p, K, h = 512, 4, 16
+    A = make("matern", p, 5)
+    ref = O.ibmi(A, O.partition(p, K, h), tol=1e-10, max_sweeps=400)
+    s, res, H = run_gpu(ibmi, A, K=K, h=h, tol=1e-10, max_sweeps=400)
+    assert ref.status == "converged" and s == ibmi.IBMI_OK
+    assert abs(res["sweeps"] - ref.sweeps) <= 1
+    assert res["resid_f"] <= 1e-10 and O.residual_f(A, H) <= 1e-10
+    inv = np.linalg.inv(A)
+    assert np.abs(H - inv).max() <= 1e-8 * np.abs(inv).max()
+
+
+def test_not_spd_reported(ibmi):
+    p = 120
+    A = make("random", p, 6)
+    A[70, 70] = -5.0
+    s, res, H = run_gpu(ibmi, A, K=2, h=10, tol=1e-10)
+    ref = O.ibmi(A, O.partition(p, 2, 10), tol=1e-10)
+    assert s == ibmi.IBMI_ERR_NOT_SPD and ref.status == "not_spd"
+    assert res["bad_block"] == ref.bad_block == 1
+
+
+def test_newton_schulz_tail(ibmi):
+    p = 256
+    A = wl.random_spd(p, 8, 1.0, 1e3)
+    ref = O.ibmi(A, O.partition(p, 2, 64), tol=1e-11, max_sweeps=300, ns_theta=0.5)
+    s, res, H = run_gpu(ibmi, A, K=2, h=64, tol=1e-11, max_sweeps=300, ns_theta=0.5)
+    assert ref.status == "converged" and s == ibmi.IBMI_OK
+    assert res["ns_steps"] >= 1 and abs(res["sweeps"] - ref.sweeps) <= 1
+    assert O.residual_f(A, H) <= 1e-11
+
+
+def test_residual_entry_point(ibmi):
+    p = 333
+    A = make("matern", p, 9)
+    rng = np.random.default_rng(0)
+    Hm = np.linalg.inv(A) + 1e-6 * rng.standard_normal((p, p))
+    got = ibmi.ibmi_residual(torch.from_numpy(A).cuda(), torch.from_numpy(Hm).cuda())
+    assert got == pytest.approx(O.residual_f(A, Hm), rel=1e-10)
+
+
+def test_host_variant_matches_device(ibmi):
+    p = 260
+    A = make("matern", p, 10)
+    plan = ibmi.ibmi_plan(p, K=3, h=12, tol=0.0, max_sweeps=4)
+    Hh = np.zeros((p, p))
+    s1, r1 = ibmi.ibmi_invert_host(plan, np.ascontiguousarray(A), Hh)
+    dA = torch.from_numpy(A).cuda()
+    dH = torch.empty_like(dA)
+    s2, r2 = ibmi.ibmi_invert(plan, dA, dH)
+    assert s1 == s2 == ibmi.IBMI_NOT_CONVERGED
+    assert np.array_equal(Hh, dH.cpu().numpy())
+
+
+def test_full_size_c2_fp64_sampled(ibmi):
+    """p = 4096 Matern 3/2, K = 8 (sets 544/576, 64-row overlap) to 1e-10,
+    checked on sampled columns against the oracle's Cholesky solve and on
+    sampled rows of the residual."""
+    A = wl.c2_matern()
+    p = A.shape[0]
+    s, res, H = run_gpu(ibmi, A, K=8, h=32, tol=1e-10, max_sweeps=500, check_every=4)
+    assert s == ibmi.IBMI_OK and res["resid_f"] <= 1e-10
+    rng = np.random.default_rng(0)
+    rows = rng.choice(p, 16, replace=False)
+    R = np.eye(p)[rows] - A[rows] @ H
+    assert np.abs(R).max() < 1e-9
+    L = O.cholesky(A)
+    cols = rng.choice(p, 4, replace=False)
+    E = np.zeros((p, len(cols)))
+    E[cols, np.arange(len(cols))] = 1.0
+    X = O.backward_subst(L.T, O.forward_subst(L, E))
+    assert np.abs(H[:, cols] - X).max() <= 1e-8 * np.abs(X).max()
