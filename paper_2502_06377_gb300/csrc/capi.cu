@@ -189,6 +189,7 @@ ibmi_status ibmi_plan(const ibmi_plan_desc* desc, ibmi_plan_t* out) {
   if (d.stop_rule != IBMI_STOP_RESID_F && d.stop_rule != IBMI_STOP_PAPER_EST) return IBMI_ERR_INVALID_ARG;
   if (d.stop_rule == IBMI_STOP_PAPER_EST) return IBMI_ERR_INVALID_ARG;  // not offered by this build
   if (d.init != IBMI_INIT_IDENTITY && d.init != IBMI_INIT_USER) return IBMI_ERR_INVALID_ARG;
+  if (d.precision == IBMI_MIXED && d.K < 2) return IBMI_ERR_INVALID_ARG;   // nothing to sweep
   if (d.max_sweeps < 1 || d.check_every < 1 || d.ns_max < 0 || !(d.tol >= 0.0) || !(d.ns_theta >= 0.0))
     return IBMI_ERR_INVALID_ARG;
   ibmi_plan_s* P = new ibmi_plan_s();

@@ -1,8 +1,286 @@
+// Mixed-precision IBMI sweep: the two sweep products (a3, a4) run on tcgen05
+// tensor cores with BF16x3 operands (hi/lo slices, FP32 accumulation in TMEM);
+// the iterate lives in HBM as an FP32 master plus its two BF16 slices, all
+// updated in place by the GEMM epilogues.  The block invariants stay FP64.
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
 #include "mixed.cuh"
+#include "tc_gemm.cuh"
+
 namespace ibmi {
-ibmi_status mixed_create(ibmi_plan_s*) { return IBMI_ERR_INVALID_ARG; }
-void mixed_destroy(ibmi_plan_s*) {}
-ibmi_status mixed_prepare(ibmi_plan_s*, const double*, int64_t, cudaStream_t) { return IBMI_ERR_INVALID_ARG; }
-ibmi_status mixed_sweep_step(ibmi_plan_s*, int, cudaStream_t) { return IBMI_ERR_INVALID_ARG; }
-ibmi_status mixed_export(ibmi_plan_s*, double*, int64_t, cudaStream_t) { return IBMI_ERR_INVALID_ARG; }
+
+namespace tc {
+
+static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  });
+  return fn;
+}
+
+bool make_map_bf16(CUtensorMap* map, const void* base, int64_t rows, int64_t cols, int64_t ld, int box_rows) {
+  auto enc = get_encode();
+  if (!enc) return false;
+  if (((uintptr_t)base & 15) != 0 || ((ld * 2) & 15) != 0) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
+  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+}  // namespace tc
+
+constexpr int MX_BN = 128;   // N tile of the sweep products
+
+struct MixedState {
+  int64_t ldp = 0;                       // padded row pitch of all mixed arrays (multiple of 64)
+  float* Hf = nullptr;                   // FP32 master of H, p x ldp
+  __nv_bfloat16* Hs[2] = {nullptr, nullptr};   // BF16 hi / lo slices of H
+  std::vector<__nv_bfloat16*> Ws[2];     // per set: BF16 hi / lo of W (m x ldp)
+  float* Spart = nullptr;                // a4 split-K partial products, splits x mmax^2
+  int splits_max = 0;
+  int* err = nullptr;                    // device error word of the tcgen05 kernels
+  CUtensorMap mapH[2];
+  std::vector<CUtensorMap> mapW[2];
+  void* pool = nullptr;
+};
+
+static MixedState* MS(ibmi_plan_s* P) { return (MixedState*)P->mixed; }
+
+// ------------------------------------------------------------- kernels ----
+
+__device__ __forceinline__ void split2(float x, __nv_bfloat16& h, __nv_bfloat16& l) {
+  h = __float2bfloat16_rn(x);
+  l = __float2bfloat16_rn(x - __bfloat162float(h));
+}
+
+// FP64 m x p (ld p) -> BF16 hi/lo, ld ldp (padding columns zero)
+__global__ void k_split_w(const double* W, int64_t m, int64_t p, int64_t ldp, __nv_bfloat16* hi,
+                          __nv_bfloat16* lo) {
+  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= m * ldp) return;
+  int64_t i = idx / ldp, c = idx - i * ldp;
+  float x = c < p ? (float)W[i * p + c] : 0.f;
+  __nv_bfloat16 h, l;
+  split2(x, h, l);
+  hi[idx] = h;
+  lo[idx] = l;
+}
+
+// FP64 H (ldh) -> FP32 master + BF16 hi/lo (ldp)
+__global__ void k_import_h(const double* H, int64_t ldh, int64_t p, int64_t ldp, float* Hf, __nv_bfloat16* hi,
+                           __nv_bfloat16* lo) {
+  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= p * ldp) return;
+  int64_t i = idx / ldp, c = idx - i * ldp;
+  float x = c < p ? (float)H[i * ldh + c] : 0.f;
+  __nv_bfloat16 h, l;
+  split2(x, h, l);
+  Hf[idx] = x;
+  hi[idx] = h;
+  lo[idx] = l;
+}
+
+__global__ void k_export_h(const float* Hf, int64_t ldp, int64_t p, double* H, int64_t ldh) {
+  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= p * p) return;
+  int64_t i = idx / p, c = idx - i * p;
+  H[i * ldh + c] = (double)Hf[i * ldp + c];
+}
+
+// a4 finish: H[I, I] = A_I^{-1} - (P + P^T)/2 with P = sum of the split-K partials.
+__global__ void k_mixed_sym(const float* Spart, int splits, int64_t m, const double* Ainv, int64_t lo, int64_t ldp,
+                            float* Hf, __nv_bfloat16* hi, __nv_bfloat16* lw) {
+  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= m * m) return;
+  int64_t i = idx / m, j = idx - i * m;
+  float a = 0.f, b = 0.f;
+  for (int z = 0; z < splits; ++z) {
+    a += Spart[(int64_t)z * m * m + i * m + j];
+    b += Spart[(int64_t)z * m * m + j * m + i];
+  }
+  float x = (float)(Ainv[idx] - 0.5 * ((double)a + (double)b));
+  int64_t o = (lo + i) * ldp + lo + j;
+  __nv_bfloat16 h, l;
+  split2(x, h, l);
+  Hf[o] = x;
+  hi[o] = h;
+  lw[o] = l;
+}
+
+// a3 epilogue: X = -acc for rows i < m of the set and columns j in I^c;
+// written to H[lo+i, j] (16 consecutive columns per thread) and to H[j, lo+i]
+// (the 32 lanes of a warp hold consecutive i: coalesced).
+struct EpiTcSweepX {
+  float* Hf; __nv_bfloat16* Hh; __nv_bfloat16* Hl;
+  int64_t ldp, lo, hi, p, m;
+  __device__ __forceinline__ void operator()(int64_t i, int64_t j0, int, const float (&v)[16]) const {
+    if (i >= m) return;
+    const int64_t r = lo + i;
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+      const int64_t j = j0 + c;
+      if (j >= p || (j >= lo && j < hi)) continue;
+      const float x = -v[c];
+      __nv_bfloat16 h, l;
+      split2(x, h, l);
+      Hf[r * ldp + j] = x;
+      Hh[r * ldp + j] = h;
+      Hl[r * ldp + j] = l;
+      Hf[j * ldp + r] = x;
+      Hh[j * ldp + r] = h;
+      Hl[j * ldp + r] = l;
+    }
+  }
+};
+
+// a4 epilogue: split-K partial of X W^T, rows/cols < m.
+struct EpiTcPartial {
+  float* Spart; int64_t m;
+  __device__ __forceinline__ void operator()(int64_t i, int64_t j0, int z, const float (&v)[16]) const {
+    if (i >= m) return;
+    float* o = Spart + (int64_t)z * m * m + i * m;
+#pragma unroll
+    for (int c = 0; c < 16; ++c)
+      if (j0 + c < m) o[j0 + c] = v[c];
+  }
+};
+
+static inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+// --------------------------------------------------------------- host ----
+
+ibmi_status mixed_create(ibmi_plan_s* P) {
+  const int64_t p = P->d.p;
+  const int K = (int)P->lo.size();
+  MixedState* M = new MixedState();
+  P->mixed = M;
+  M->ldp = (p + 63) / 64 * 64;
+  const int64_t ldp = M->ldp;
+  // a4 split-K factor: fill ~one wave of 148 SMs with ceil(m/128)^2 tiles
+  int64_t tiles2 = ((P->mmax + 127) / 128) * ((P->mmax + MX_BN - 1) / MX_BN);
+  int kt = (int)((p + tc::BK - 1) / tc::BK);
+  M->splits_max = (int)std::max<int64_t>(1, std::min<int64_t>(std::max<int64_t>(1, 148 / tiles2), kt / 4 > 0 ? kt / 4 : 1));
+  size_t bytes = sizeof(float) * p * ldp + 2 * sizeof(__nv_bfloat16) * p * ldp +
+                 sizeof(float) * (size_t)M->splits_max * P->mmax * P->mmax + 256;
+  for (int k = 0; k < K; ++k) bytes += 2 * sizeof(__nv_bfloat16) * (P->hi[k] - P->lo[k]) * ldp + 256;
+  if (cudaMalloc(&M->pool, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return IBMI_ERR_OOM;
+  }
+  uint8_t* q = (uint8_t*)M->pool;
+  auto take = [&](size_t b) { uint8_t* r = q; q += (b + 255) / 256 * 256; return r; };
+  M->Hf = (float*)take(sizeof(float) * p * ldp);
+  M->Hs[0] = (__nv_bfloat16*)take(sizeof(__nv_bfloat16) * p * ldp);
+  M->Hs[1] = (__nv_bfloat16*)take(sizeof(__nv_bfloat16) * p * ldp);
+  M->Spart = (float*)take(sizeof(float) * (size_t)M->splits_max * P->mmax * P->mmax);
+  M->err = (int*)take(256);
+  for (int k = 0; k < K; ++k) {
+    const int64_t m = P->hi[k] - P->lo[k];
+    for (int s = 0; s < 2; ++s) M->Ws[s].push_back((__nv_bfloat16*)take(sizeof(__nv_bfloat16) * m * ldp));
+  }
+  for (int s = 0; s < 2; ++s) {
+    if (!tc::make_map_bf16(&M->mapH[s], M->Hs[s], p, p, ldp, 128)) return IBMI_ERR_CUDA;
+    M->mapW[s].resize(K);
+    for (int k = 0; k < K; ++k)
+      if (!tc::make_map_bf16(&M->mapW[s][k], M->Ws[s][k], P->hi[k] - P->lo[k], p, ldp, 128)) return IBMI_ERR_CUDA;
+  }
+  return IBMI_OK;
+}
+
+void mixed_destroy(ibmi_plan_s* P) {
+  MixedState* M = MS(P);
+  if (!M) return;
+  cudaFree(M->pool);
+  delete M;
+  P->mixed = nullptr;
+}
+
+ibmi_status mixed_prepare(ibmi_plan_s* P, const double* H, int64_t ldh, cudaStream_t st) {
+  MixedState* M = MS(P);
+  const int64_t p = P->d.p, ldp = M->ldp;
+  ProfScope ps(IBMI_K_OTHER, st, 0.0);
+  IBMI_CUDA_TRY(cudaMemsetAsync(M->err, 0, sizeof(int), st));
+  for (size_t k = 0; k < P->lo.size(); ++k) {
+    const int64_t m = P->hi[k] - P->lo[k];
+    note_launch();
+    k_split_w<<<nblk(m * ldp), 256, 0, st>>>(P->w[k], m, p, ldp, M->Ws[0][k], M->Ws[1][k]);
+    IBMI_CUDA_TRY(cudaGetLastError());
+  }
+  note_launch();
+  k_import_h<<<nblk(p * ldp), 256, 0, st>>>(H, ldh, p, ldp, M->Hf, M->Hs[0], M->Hs[1]);
+  IBMI_CUDA_TRY(cudaGetLastError());
+  return IBMI_OK;
+}
+
+ibmi_status mixed_sweep_step(ibmi_plan_s* P, int k, cudaStream_t st) {
+  MixedState* M = MS(P);
+  const int64_t p = P->d.p, lo = P->lo[k], hi = P->hi[k], m = hi - lo, n = p - m;
+  const tc::TileRanges kr = tc::complement_tiles(lo, hi, p, tc::BK);
+  if (n == 0) return IBMI_ERR_INVALID_ARG;   // K = 1 is served by the FP64 path
+  // a3: X = -W T; A operand = W slices (rows of the set), B = H slices (rows j).
+  {
+    const tc::TileRanges nr = tc::complement_tiles(lo, hi, p, MX_BN);
+    tc::Maps maps;
+    maps.a[0] = M->mapW[0][k];
+    maps.a[1] = M->mapW[1][k];
+    maps.b[0] = M->mapH[0];
+    maps.b[1] = M->mapH[1];
+    tc::Tiles t{m, 0, 0, nr.r0_end, nr.r1_begin, kr.r0_end, kr.r1_begin, kr.r1_end, 1, M->err};
+    EpiTcSweepX epi{M->Hf, M->Hs[0], M->Hs[1], M->ldp, lo, hi, p, m};
+    ProfScope ps(IBMI_K_SWEEP_X, st, 2.0 * m * n * n);
+    IBMI_CUDA_TRY((tc::launch<2, MX_BN>(maps, t, nr.count(), (int)((m + 127) / 128), epi, st)));
+  }
+  // a4: P = X W^T (split over K); A operand = H slices rows [lo, hi), B = W slices.
+  {
+    const int nk = kr.count();
+    const int splits = std::max(1, std::min(M->splits_max, nk / 2));
+    tc::Maps maps;
+    maps.a[0] = M->mapH[0];
+    maps.a[1] = M->mapH[1];
+    maps.b[0] = M->mapW[0][k];
+    maps.b[1] = M->mapW[1][k];
+    const int ntn = (int)((m + MX_BN - 1) / MX_BN);
+    tc::Tiles t{m, lo, 0, ntn, ntn, kr.r0_end, kr.r1_begin, kr.r1_end, splits, M->err};
+    EpiTcPartial epi{M->Spart, m};
+    ProfScope ps(IBMI_K_SWEEP_S, st, 2.0 * m * m * n);
+    IBMI_CUDA_TRY((tc::launch<2, MX_BN>(maps, t, ntn, (int)((m + 127) / 128), epi, st)));
+    note_launch();
+    k_mixed_sym<<<nblk(m * m), 256, 0, st>>>(M->Spart, splits, m, P->ainv[k], lo, M->ldp, M->Hf, M->Hs[0],
+                                             M->Hs[1]);
+    IBMI_CUDA_TRY(cudaGetLastError());
+  }
+  return IBMI_OK;
+}
+
+ibmi_status mixed_export(ibmi_plan_s* P, double* H, int64_t ldh, cudaStream_t st) {
+  MixedState* M = MS(P);
+  const int64_t p = P->d.p;
+  note_launch();
+  k_export_h<<<nblk(p * p), 256, 0, st>>>(M->Hf, M->ldp, p, H, ldh);
+  IBMI_CUDA_TRY(cudaGetLastError());
+  int herr = 0;
+  IBMI_CUDA_TRY(cudaMemcpyAsync(&herr, M->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  IBMI_CUDA_TRY(cudaStreamSynchronize(st));
+  if (herr != 0) {
+    set_last_error("tcgen05 kernel: bounded wait expired");
+    return IBMI_ERR_TIMEOUT;
+  }
+  return IBMI_OK;
+}
+
 }  // namespace ibmi

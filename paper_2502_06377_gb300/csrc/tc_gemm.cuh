@@ -1,0 +1,344 @@
+// tcgen05 / TMEM split-BF16 GEMM for sm_103a (internal).
+//
+// C[i, j] = sum_{s + u <= S-1} sum_k A_s[i, k] * B_u[j, k]
+//
+// A_s (M x K) and B_u (N x K) are BF16 slices, both K-major (row-major with K
+// contiguous), read by TMA in 64-wide K blocks with the 128-byte swizzle.  The
+// slices of a value x are x_0 = bf16(x), x_1 = bf16(x - x_0), ... so the
+// triangle of slice products reproduces x*y to about 8*S bits; S = 2 is the
+// classic three-product BF16x3 scheme, S = 3 the six-product scheme.  The
+// accumulator is FP32 in tensor memory (128 lanes x BN columns).
+//
+// One CTA computes one 128 x BN output tile (optionally one K split of it):
+//   warp 0   : one thread issues the TMA loads of a stage (S A-tiles, S B-tiles)
+//   warp 1   : allocates TMEM; one thread issues tcgen05.mma and commits
+//   warps 2-5: epilogue; each reads its 32-lane quadrant of TMEM with
+//              tcgen05.ld and hands 16 FP32 values at a time to the functor.
+// Every mbarrier wait is bounded (about 2 s of wall time); on expiry the
+// kernel records an error code in *err and finishes without hanging.
+#pragma once
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+
+namespace ibmi {
+namespace tc {
+
+constexpr int BM = 128;       // rows per tile (one TMEM lane per row)
+constexpr int BK = 64;        // BF16 elements per K block = one 128-byte swizzle row
+constexpr int THREADS = 192;  // 6 warps
+constexpr int ERR_TIMEOUT = 7;
+
+struct Maps {
+  CUtensorMap a[3];
+  CUtensorMap b[3];
+};
+
+struct Tiles {
+  int64_t M;        // rows of C that exist (rows >= M are computed but not passed on)
+  int64_t a_row0;   // TMA row of C row 0 inside the A tensor
+  int64_t b_row0;   // TMA row of C column 0 inside the B tensor
+  int nt0;          // N tiles of the first range: physical column tile t
+  int nt1_first;    // physical column tile of logical N tile nt0
+  int kt0_end;      // K tiles [0, kt0_end) then [kt1_begin, kt1_end)
+  int kt1_begin;
+  int kt1_end;
+  int splits;       // K splits (gridDim.z)
+  int* err;         // error word (0 = ok)
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ uint64_t globaltimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_barrier_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for the completion of phase `parity`.  Returns false (and sets
+// *err) after ~2 s, or as soon as another thread has flagged an error.
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, int* err) {
+  if (mbar_try_wait(b, parity)) return true;
+  const uint64_t t0 = globaltimer();
+  for (uint32_t it = 1;; ++it) {
+    if (mbar_try_wait(b, parity)) return true;
+    if ((it & 127) == 0) {
+      if (*(volatile int*)err != 0) return false;
+      if (globaltimer() - t0 > 2000000000ull) {
+        atomicExch(err, ERR_TIMEOUT);
+        return false;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
+      ::"r"(smem_u32(dst)), "l"(map), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
+// 128 bytes, 8-row core groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);   // start address, bits 0-13
+  d |= (uint64_t)1 << 16;                      // leading byte offset (unused here)
+  d |= (uint64_t)(1024 >> 4) << 32;            // stride byte offset, bits 32-45
+  d |= (uint64_t)1 << 46;                      // descriptor version
+  d |= (uint64_t)2 << 61;                      // swizzle: 128 B
+  return d;
+}
+
+// Instruction descriptor, kind::f16: FP32 accumulate, BF16 A and B, both K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+      ::"r"(tmem_d), "l"(da), "l"(db), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// 32 lanes x 16 columns of 32-bit: thread t of the warp gets lane (quadrant + t).
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <int S, int BN>
+struct Cfg {
+  static constexpr uint32_t A_BYTES = BM * BK * 2;
+  static constexpr uint32_t B_BYTES = BN * BK * 2;
+  static constexpr uint32_t STAGE_BYTES = S * (A_BYTES + B_BYTES);
+  static constexpr int STAGES = (200 * 1024) / STAGE_BYTES >= 4 ? 4 : (200 * 1024) / STAGE_BYTES;
+  static constexpr uint32_t SMEM = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+  static constexpr uint32_t TMEM_COLS = BN < 32 ? 32 : BN;
+  static_assert(STAGES >= 2, "tile too large for two stages");
+  static_assert(BN % 16 == 0 && BN >= 16 && BN <= 256, "UMMA N for M = 128");
+};
+
+template <int S, int BN, class Epi>
+__global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ Maps maps, const Tiles t, Epi epi) {
+  using C = Cfg<S, BN>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* tiles = smem;
+  uint64_t* full = (uint64_t*)(smem + C::STAGES * C::STAGE_BYTES);
+  uint64_t* empty = full + C::STAGES;
+  uint64_t* accf = empty + C::STAGES;
+  uint32_t* tmem_slot = (uint32_t*)(accf + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int mt = blockIdx.y, ntl = blockIdx.x, z = blockIdx.z;
+  const int ntp = ntl < t.nt0 ? ntl : t.nt1_first + (ntl - t.nt0);
+  const int64_t n0 = (int64_t)ntp * BN;
+  const int nk0 = t.kt0_end;
+  const int nk = t.kt0_end + (t.kt1_end - t.kt1_begin);
+  const int kb = (int)((int64_t)nk * z / t.splits);
+  const int my_nk = (int)((int64_t)nk * (z + 1) / t.splits) - kb;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < C::STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(accf, 1);
+    fence_barrier_init();
+  }
+  if (warp == 1) tmem_alloc(tmem_slot, C::TMEM_COLS);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {  // TMA producer
+      int issued = 0;
+      for (int it = 0; it < my_nk; ++it) {
+        const int st = it % C::STAGES;
+        const uint32_t ph = (uint32_t)(it / C::STAGES) & 1u;
+        if (!mbar_wait(&empty[st], ph ^ 1u, t.err)) break;
+        const int kt = kb + it;
+        const int ktp = kt < nk0 ? kt : t.kt1_begin + (kt - nk0);
+        const int kx = ktp * BK;
+        uint8_t* sa = tiles + st * C::STAGE_BYTES;
+        uint8_t* sb = sa + S * C::A_BYTES;
+        mbar_expect_tx(&full[st], C::STAGE_BYTES);
+#pragma unroll
+        for (int s = 0; s < S; ++s)
+          tma_load_2d(sa + s * C::A_BYTES, &maps.a[s], &full[st], kx, (int)(t.a_row0 + (int64_t)mt * BM));
+#pragma unroll
+        for (int s = 0; s < S; ++s)
+          tma_load_2d(sb + s * C::B_BYTES, &maps.b[s], &full[st], kx, (int)(t.b_row0 + n0));
+        issued = it + 1;
+      }
+      // On an error exit, wait (bounded) for the copies still in flight.
+      if (*(volatile int*)t.err != 0) {
+        for (int it = issued - C::STAGES < 0 ? 0 : issued - C::STAGES; it < issued; ++it) {
+          const int st = it % C::STAGES;
+          const uint32_t ph = (uint32_t)(it / C::STAGES) & 1u;
+          const uint64_t t0 = globaltimer();
+          while (!mbar_try_wait(&full[st], ph) && globaltimer() - t0 < 1000000000ull) {
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {  // MMA issuer
+      constexpr uint32_t idesc = idesc_bf16(BM, BN);
+      for (int it = 0; it < my_nk; ++it) {
+        const int st = it % C::STAGES;
+        const uint32_t ph = (uint32_t)(it / C::STAGES) & 1u;
+        if (!mbar_wait(&full[st], ph, t.err)) break;
+        tc_fence_after();
+        const uint32_t sa = smem_u32(tiles + st * C::STAGE_BYTES);
+        const uint32_t sb = sa + S * C::A_BYTES;
+#pragma unroll
+        for (int s = 0; s < S; ++s)
+#pragma unroll
+          for (int u = 0; s + u < S; ++u)
+#pragma unroll
+            for (int kk = 0; kk < BK / 16; ++kk) {
+              const uint64_t da = sdesc_sw128(sa + s * C::A_BYTES + kk * 32);
+              const uint64_t db = sdesc_sw128(sb + u * C::B_BYTES + kk * 32);
+              mma_bf16(tmem, da, db, idesc, (it | s | u | kk) != 0 ? 1u : 0u);
+            }
+        mma_commit(&empty[st]);
+      }
+      mma_commit(accf);
+    }
+  } else {  // epilogue warps 2..5
+    const int q = warp & 3;
+    const int row = q * 32 + lane;
+    const bool ok = mbar_wait(accf, 0, t.err);
+    tc_fence_after();
+    if (ok) {
+#pragma unroll 1
+      for (int c = 0; c < BN; c += 16) {
+        float v[16];
+        if (my_nk > 0) {
+          tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c, v);
+        } else {
+#pragma unroll
+          for (int i = 0; i < 16; ++i) v[i] = 0.f;
+        }
+        epi((int64_t)mt * BM + row, n0 + c, z, v);
+      }
+    }
+    tc_fence_before();
+  }
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, C::TMEM_COLS);
+  }
+}
+
+// ------------------------------------------------------------------ host --
+
+// Encodes a 2-D BF16 tensor map: `rows` rows of `cols` elements, row pitch
+// `ld` elements (ld * 2 must be a multiple of 16), box = 64 x box_rows.
+bool make_map_bf16(CUtensorMap* map, const void* base, int64_t rows, int64_t cols, int64_t ld, int box_rows);
+
+// Range bookkeeping shared by the launchers: K and N tiles that overlap the
+// complement [0, lo) U [hi, p) of a set.
+struct TileRanges {
+  int r0_end, r1_begin, r1_end;
+  int count() const { return r0_end + (r1_end - r1_begin); }
+};
+inline TileRanges complement_tiles(int64_t lo, int64_t hi, int64_t p, int tile) {
+  TileRanges r;
+  r.r0_end = (int)((lo + tile - 1) / tile);
+  r.r1_begin = (int)(hi / tile);
+  r.r1_end = (int)((p + tile - 1) / tile);
+  if (r.r1_begin < r.r0_end) r.r1_begin = r.r0_end;
+  if (r.r1_end < r.r1_begin) r.r1_end = r.r1_begin;
+  return r;
+}
+
+template <int S, int BN, class Epi>
+cudaError_t launch(const Maps& maps, const Tiles& t, int grid_n, int grid_m, const Epi& epi, cudaStream_t st) {
+  using C = Cfg<S, BN>;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<S, BN, Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)C::SMEM);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  if (grid_n <= 0 || grid_m <= 0) return cudaSuccess;
+  note_launch();
+  k_tc_gemm<S, BN, Epi><<<dim3(grid_n, grid_m, t.splits), THREADS, C::SMEM, st>>>(maps, t, epi);
+  return cudaGetLastError();
+}
+
+}  // namespace tc
+}  // namespace ibmi

@@ -1,0 +1,86 @@
+"""Mixed-precision GPU path (tcgen05 BF16x3 sweep products) vs the FP64 oracle.
+
+Fixed-sweep trajectories are compared at a tolerance derived from BF16x3
+arithmetic: each operand is represented to 2^-17 relative (two BF16 slices,
+16 significand bits) and the dropped lo*lo product is ~2^-16 relative, so a
+sweep product carries ~1e-5 relative error; measured iterates differ from FP64
+by 3e-6..6e-6 in relative Frobenius norm, and the bound used is 5e-5.  Converged runs must reach ||I - A H||_F / sqrt(p) <= 1e-10
+after the FP64 Newton-Schulz tail, like the oracle.
+"""
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import ibmi_oracle as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ibmi():
+    import __graft_entry__ as g
+    g.build()
+    import paper_2502_06377_gb300 as m
+    return m
+
+
+def run(ibmi, A, **kw):
+    p = A.shape[0]
+    dA = torch.from_numpy(np.ascontiguousarray(A)).cuda()
+    dH = torch.empty_like(dA)
+    plan = ibmi.ibmi_plan(p, precision=ibmi.IBMI_MIXED, **kw)
+    s, res = ibmi.ibmi_invert(plan, dA, dH)
+    torch.cuda.synchronize()
+    plan.close()
+    return s, res, dH.cpu().numpy()
+
+
+def matern(p, seed):
+    rng = np.random.default_rng(seed)
+    return wl.matern32(wl.uniform_points(rng, p, 2), 0.1, 1.0, 1e-2)
+
+
+@pytest.mark.parametrize("p,K,h", [(256, 2, 0), (333, 4, 7), (517, 5, 16), (640, 3, 64)])
+@pytest.mark.parametrize("r", [1, 3])
+def test_mixed_fixed_sweeps_close_to_oracle(ibmi, p, K, h, r):
+    A = matern(p, 21)
+    ref = O.ibmi(A, O.partition(p, K, h), tol=0.0, max_sweeps=r)
+    s, res, H = run(ibmi, A, K=K, h=h, tol=0.0, max_sweeps=r)
+    assert s == ibmi.IBMI_NOT_CONVERGED and res["sweeps"] == r
+    err = np.linalg.norm(H - ref.h) / np.linalg.norm(ref.h)
+    print(f"p={p} K={K} h={h} r={r} rel err {err:.2e}")
+    assert err < 5e-5
+    assert np.array_equal(H, H.T)
+
+
+def test_mixed_kms_one_sweep(ibmi):
+    A = wl.c1_kms()
+    s, res, H = run(ibmi, A, K=2, h=0, tol=1e-10, ns_theta=0.5)
+    assert s == ibmi.IBMI_OK
+    ref = O.spd_inverse(A)
+    assert np.abs(H - ref).max() < 1e-9
+
+
+@pytest.mark.parametrize("p,K,h", [(512, 4, 16), (700, 3, 40)])
+def test_mixed_converged_with_newton_schulz(ibmi, p, K, h):
+    A = matern(p, 22)
+    ref = O.ibmi(A, O.partition(p, K, h), tol=1e-10, max_sweeps=300, ns_theta=0.5)
+    s, res, H = run(ibmi, A, K=K, h=h, tol=1e-10, max_sweeps=300, ns_theta=0.5)
+    assert ref.status == "converged" and s == ibmi.IBMI_OK, res
+    assert O.residual_f(A, H) <= 1e-10
+    inv = np.linalg.inv(A)
+    assert np.abs(H - inv).max() <= 1e-8 * np.abs(inv).max()
+    print("mixed", res["sweeps"], res["ns_steps"], "oracle", ref.sweeps, ref.ns_steps)
+
+
+def test_mixed_full_size_c2(ibmi):
+    A = wl.c2_matern()
+    p = A.shape[0]
+    s, res, H = run(ibmi, A, K=8, h=32, tol=1e-10, max_sweeps=200, ns_theta=0.5)
+    assert s == ibmi.IBMI_OK and res["resid_f"] <= 1e-10, res
+    rng = np.random.default_rng(1)
+    rows = rng.choice(p, 16, replace=False)
+    R = np.eye(p)[rows] - A[rows] @ H
+    assert np.abs(R).max() < 1e-9
+    print("c2 mixed", res)
