@@ -135,8 +135,9 @@ ibmi_status ibmi_invert(ibmi_plan_t plan, const double* A, int64_t lda, double* 
 ibmi_status ibmi_invert_host(ibmi_plan_t plan, const double* A_host, int64_t lda,
                              double* H_host, int64_t ldh, void* stream, ibmi_result* out);
 
-/* rho_F = ||I - A H||_F / sqrt(p) in FP64 for device A, H (p x p, ld >= p).
- * Allocates nothing when p <= 65536; the value is written to *out (host). */
+/* rho_F = ||I - A H||_F / sqrt(p) in FP64 (DFMA) for device A, H (p x p,
+ * ld >= p); the value is written to *out (host).  Allocates a small buffer of
+ * per-tile partial sums (stream-ordered) for the duration of the call. */
 ibmi_status ibmi_residual(const double* A, int64_t lda, const double* H, int64_t ldh,
                           int64_t p, void* stream, double* out);
 
@@ -162,6 +163,31 @@ ibmi_status ibmi_prof_get(int32_t kernel_class, int64_t* launches, double* ms, d
 /* Total kernel launches made by this library since the last ibmi_prof_enable(1)
  * (counted whether or not profiling is on). */
 int64_t ibmi_launch_count(void);
+
+/* Newton-Schulz tail of the method on its own (eq. newton): refines a
+ * symmetric approximate inverse X of the SPD matrix A in place,
+ *     X <- sym(X + X (I - A X)),
+ * until ||I - A X||_F / sqrt(p) <= tol, at most ns_max updates, stopping early
+ * when an update does not reduce the residual.  IBMI_FP64 runs every product
+ * with DFMA; IBMI_MIXED evaluates the residual with the error-free sliced
+ * tensor-core products (FP64-accurate) and the update X (I - A X) from the five
+ * leading digit slices of each operand (exact digit-pair products on tcgen05,
+ * 2^-34 relative truncation).  Converges when ||I - A X_0|| < 1 (the
+ * condition stated with eq. newton).  out->ns_steps counts updates and
+ * out->resid_f is the last residual evaluated.  Allocates its workspace for
+ * the duration of the call. */
+ibmi_status ibmi_refine(const double* A, int64_t lda, double* X, int64_t ldx, int64_t p, int32_t precision,
+                        double tol, int32_t ns_max, void* stream, ibmi_result* out);
+
+/* rho_F = ||I - A H||_F / sqrt(p) for symmetric device A, H, computed on the
+ * tcgen05 tensor cores with the error-free sliced products of the Newton-Schulz
+ * tail (every row cut into eight signed 7-bit digits; 36 exact digit-pair
+ * products accumulated in integers and combined once in FP64), so the value
+ * agrees with an FP64 evaluation to FP64 rounding.  Allocates its workspace
+ * (about 26 p^2 bytes) for the duration of the call.  A and H must be
+ * symmetric: the kernel evaluates ||I - H A||_F. */
+ibmi_status ibmi_residual_tc(const double* A, int64_t lda, const double* H, int64_t ldh, int64_t p,
+                             void* stream, double* out);
 
 /* Human-readable name of a status, and the text of the last CUDA error seen by
  * this thread (empty if none). */

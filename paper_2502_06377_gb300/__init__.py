@@ -119,3 +119,21 @@ def ibmi_residual(A, H, stream=None) -> float:
 
 def ibmi_status_string(s: int) -> str:
     return _lib.load().ibmi_status_string(s).decode()
+
+
+def ibmi_residual_tc(A, H, stream=None) -> float:
+    """FP64-accurate ||I - A H||_F / sqrt(p) on tensor cores (sliced error-free products)."""
+    out = C.c_double()
+    s = _lib.load().ibmi_residual_tc(C.c_void_p(A.data_ptr()), A.stride(0), C.c_void_p(H.data_ptr()),
+                                     H.stride(0), A.shape[0], _stream_ptr(stream), C.byref(out))
+    if s != IBMI_OK:
+        raise IbmiError(s, "ibmi_residual_tc")
+    return out.value
+
+
+def ibmi_refine(A, X, precision=IBMI_MIXED, tol=1e-10, ns_max=8, stream=None):
+    """Newton-Schulz refinement of the symmetric approximate inverse X (in place)."""
+    res = ibmi_result()
+    s = _lib.load().ibmi_refine(C.c_void_p(A.data_ptr()), A.stride(0), C.c_void_p(X.data_ptr()), X.stride(0),
+                                A.shape[0], precision, tol, ns_max, _stream_ptr(stream), C.byref(res))
+    return s, res.as_dict()

@@ -65,6 +65,9 @@ _SIGS = {
     "ibmi_invert": (C.c_int, [_P, _P, C.c_int64, _P, C.c_int64, _P, C.POINTER(ibmi_result)]),
     "ibmi_invert_host": (C.c_int, [_P, _P, C.c_int64, _P, C.c_int64, _P, C.POINTER(ibmi_result)]),
     "ibmi_residual": (C.c_int, [_P, C.c_int64, _P, C.c_int64, C.c_int64, _P, _D]),
+    "ibmi_residual_tc": (C.c_int, [_P, C.c_int64, _P, C.c_int64, C.c_int64, _P, _D]),
+    "ibmi_refine": (C.c_int, [_P, C.c_int64, _P, C.c_int64, C.c_int64, C.c_int32, C.c_double, C.c_int32, _P,
+                              C.POINTER(ibmi_result)]),
     "ibmi_prof_enable": (None, [C.c_int]),
     "ibmi_prof_get": (C.c_int, [C.c_int32, C.POINTER(C.c_int64), _D, _D]),
     "ibmi_launch_count": (C.c_int64, []),

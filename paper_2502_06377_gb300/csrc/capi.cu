@@ -10,6 +10,7 @@
 #include "gemm_f64.cuh"
 #include "mixed.cuh"
 #include "plan.cuh"
+#include "refine.cuh"
 
 namespace ibmi {
 
@@ -111,7 +112,11 @@ static ibmi_status invert_impl(ibmi_plan_s* P, const double* A, int64_t lda, dou
     return IBMI_ERR_NOT_SPD;
   }
   if (d.init == IBMI_INIT_IDENTITY) IBMI_TRY(set_identity(H, ldh, p, st));
-  if (mixed) IBMI_TRY(mixed_prepare(P, H, ldh, st));
+  if (mixed) {
+    ibmi_status s = mixed_run(P, A, lda, H, ldh, st, res, &flops);
+    res->flops = flops;
+    return s;
+  }
   // Algorithm 1: sweeps with the stop test every check_every sweeps
   ibmi_status status = IBMI_NOT_CONVERGED;
   bool to_ns = false;
@@ -119,14 +124,10 @@ static ibmi_status invert_impl(ibmi_plan_s* P, const double* A, int64_t lda, dou
   const double fs = flops_sweep(P), fr = 2.0 * (double)p * p * p;
   while (true) {
     ++r;
-    for (int k = 0; k < K; ++k) {
-      if (mixed) IBMI_TRY(mixed_sweep_step(P, k, st));
-      else IBMI_TRY(sweep_step_f64(P, k, H, ldh, st));
-    }
+    for (int k = 0; k < K; ++k) IBMI_TRY(sweep_step_f64(P, k, H, ldh, st));
     flops += fs;
     res->sweeps = r;
     if (r % d.check_every != 0 && r < d.max_sweeps) continue;
-    if (mixed) IBMI_TRY(mixed_export(P, H, ldh, st));
     double rho;
     IBMI_TRY(residual_host(P, A, lda, H, ldh, st, &rho));
     flops += fr;
@@ -341,6 +342,103 @@ ibmi_status ibmi_residual(const double* A, int64_t lda, const double* H, int64_t
   cudaFreeAsync(buf, st);
   IBMI_CUDA_TRY(cudaStreamSynchronize(st));
   *out = v[0];
+  return s;
+}
+
+ibmi_status ibmi_residual_tc(const double* A, int64_t lda, const double* H, int64_t ldh, int64_t p,
+                             void* stream, double* out) {
+  if (!A || !H || !out || p < 1 || lda < p || ldh < p || p > (int64_t)1 << 16) return IBMI_ERR_INVALID_ARG;
+  if (!is_device_ptr(A) || !is_device_ptr(H)) return IBMI_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  int* err = nullptr;
+  IBMI_CUDA_TRY(cudaMalloc(&err, sizeof(int)));
+  IBMI_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
+  RefineState R;
+  ibmi_status s = refine_create(&R, p, err);
+  if (s == IBMI_OK) s = refine_set_matrix(&R, A, lda, st);
+  if (s == IBMI_OK) s = refine_residual(&R, H, ldh, st, out);
+  cudaStreamSynchronize(st);
+  refine_destroy(&R);
+  cudaFree(err);
+  return s;
+}
+
+ibmi_status ibmi_refine(const double* A, int64_t lda, double* X, int64_t ldx, int64_t p, int32_t precision,
+                        double tol, int32_t ns_max, void* stream, ibmi_result* out) {
+  ibmi_result tmp;
+  ibmi_result* res = out ? out : &tmp;
+  memset(res, 0, sizeof(*res));
+  res->bad_block = -1;
+  res->bad_pivot = -1;
+  res->resid_f = NAN;
+  res->paper_est = NAN;
+  if (!A || !X || p < 2 || lda < p || ldx < p || p > (int64_t)1 << 16 || ns_max < 0 || !(tol >= 0.0) ||
+      (precision != IBMI_FP64 && precision != IBMI_MIXED))
+    return (ibmi_status)(res->status = IBMI_ERR_INVALID_ARG);
+  if (!is_device_ptr(A) || !is_device_ptr(X)) return (ibmi_status)(res->status = IBMI_ERR_INVALID_ARG);
+  cudaStream_t st = (cudaStream_t)stream;
+  auto t0 = std::chrono::steady_clock::now();
+  const double fr = 2.0 * (double)p * p * p;
+  ibmi_status s = IBMI_NOT_CONVERGED;
+  if (precision == IBMI_MIXED) {
+    int* err = nullptr;
+    IBMI_CUDA_TRY(cudaMalloc(&err, sizeof(int)));
+    IBMI_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
+    RefineState R;
+    s = refine_create(&R, p, err);
+    if (s == IBMI_OK) s = refine_set_matrix(&R, A, lda, st);
+    double prev = INFINITY;
+    for (int it = 0; s == IBMI_OK; ++it) {
+      double rho;
+      s = refine_residual(&R, X, ldx, st, &rho);
+      if (s != IBMI_OK) break;
+      res->flops += fr;
+      res->resid_f = rho;
+      if (!isfinite(rho)) { s = IBMI_ERR_NONFINITE; break; }
+      if (rho <= tol) { s = IBMI_OK; break; }
+      if (it >= ns_max || !(rho < prev)) { s = IBMI_NOT_CONVERGED; break; }
+      prev = rho;
+      s = refine_ns_update(&R, X, ldx, st);
+      res->flops += fr;
+      res->ns_steps = it + 1;
+    }
+    cudaStreamSynchronize(st);
+    refine_destroy(&R);
+    cudaFree(err);
+  } else {
+    ibmi_plan_s P;
+    P.d.p = p;
+    P.n_partials = gemm_f64_ctas(p, p);
+    const size_t b = sizeof(double) * (size_t)p * p;
+    IBMI_CUDA_TRY(cudaMalloc(&P.nsR, b));
+    IBMI_CUDA_TRY(cudaMalloc(&P.nsX, b));
+    IBMI_CUDA_TRY(cudaMalloc(&P.partials, sizeof(double) * (P.n_partials + 4)));
+    P.dscalar = P.partials + P.n_partials;
+    double prev = INFINITY;
+    for (int it = 0;; ++it) {
+      double rho;
+      s = residual_host(&P, A, lda, X, ldx, st, &rho);
+      if (s != IBMI_OK) break;
+      res->flops += fr;
+      res->resid_f = rho;
+      if (!isfinite(rho)) { s = IBMI_ERR_NONFINITE; break; }
+      if (rho <= tol) { s = IBMI_OK; break; }
+      if (it >= ns_max || !(rho < prev)) { s = IBMI_NOT_CONVERGED; break; }
+      prev = rho;
+      s = ns_step_f64(&P, A, lda, X, ldx, st);
+      if (s != IBMI_OK) break;
+      res->flops += 2.0 * fr;
+      res->ns_steps = it + 1;
+    }
+    cudaStreamSynchronize(st);
+    cudaFree(P.nsR);
+    cudaFree(P.nsX);
+    cudaFree(P.partials);
+    P.nsR = P.nsX = nullptr;
+    P.partials = nullptr;
+  }
+  res->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  res->status = s;
   return s;
 }
 

@@ -8,6 +8,7 @@
 #include <mutex>
 
 #include "mixed.cuh"
+#include "refine.cuh"
 #include "tc_gemm.cuh"
 
 namespace ibmi {
@@ -57,6 +58,7 @@ struct MixedState {
   CUtensorMap mapH[2];
   std::vector<CUtensorMap> mapW[2];
   void* pool = nullptr;
+  RefineState ref;                       // FP64-accurate residual + Newton-Schulz
 };
 
 static MixedState* MS(ibmi_plan_s* P) { return (MixedState*)P->mixed; }
@@ -125,7 +127,7 @@ __global__ void k_mixed_sym(const float* Spart, int splits, int64_t m, const dou
 // a3 epilogue: X = -acc for rows i < m of the set and columns j in I^c;
 // written to H[lo+i, j] (16 consecutive columns per thread) and to H[j, lo+i]
 // (the 32 lanes of a warp hold consecutive i: coalesced).
-struct EpiTcSweepX {
+struct EpiTcSweepX : tc::EpiBase {
   float* Hf; __nv_bfloat16* Hh; __nv_bfloat16* Hl;
   int64_t ldp, lo, hi, p, m;
   __device__ __forceinline__ void operator()(int64_t i, int64_t j0, int, const float (&v)[16]) const {
@@ -149,7 +151,7 @@ struct EpiTcSweepX {
 };
 
 // a4 epilogue: split-K partial of X W^T, rows/cols < m.
-struct EpiTcPartial {
+struct EpiTcPartial : tc::EpiBase {
   float* Spart; int64_t m;
   __device__ __forceinline__ void operator()(int64_t i, int64_t j0, int z, const float (&v)[16]) const {
     if (i >= m) return;
@@ -199,12 +201,13 @@ ibmi_status mixed_create(ibmi_plan_s* P) {
     for (int k = 0; k < K; ++k)
       if (!tc::make_map_bf16(&M->mapW[s][k], M->Ws[s][k], P->hi[k] - P->lo[k], p, ldp, 128)) return IBMI_ERR_CUDA;
   }
-  return IBMI_OK;
+  return refine_create(&M->ref, p, M->err);
 }
 
 void mixed_destroy(ibmi_plan_s* P) {
   MixedState* M = MS(P);
   if (!M) return;
+  refine_destroy(&M->ref);
   cudaFree(M->pool);
   delete M;
   P->mixed = nullptr;
@@ -241,7 +244,7 @@ ibmi_status mixed_sweep_step(ibmi_plan_s* P, int k, cudaStream_t st) {
     maps.b[0] = M->mapH[0];
     maps.b[1] = M->mapH[1];
     tc::Tiles t{m, 0, 0, nr.r0_end, nr.r1_begin, kr.r0_end, kr.r1_begin, kr.r1_end, 1, M->err};
-    EpiTcSweepX epi{M->Hf, M->Hs[0], M->Hs[1], M->ldp, lo, hi, p, m};
+    EpiTcSweepX epi{{}, M->Hf, M->Hs[0], M->Hs[1], M->ldp, lo, hi, p, m};
     ProfScope ps(IBMI_K_SWEEP_X, st, 2.0 * m * n * n);
     IBMI_CUDA_TRY((tc::launch<2, MX_BN>(maps, t, nr.count(), (int)((m + 127) / 128), epi, st)));
   }
@@ -256,7 +259,7 @@ ibmi_status mixed_sweep_step(ibmi_plan_s* P, int k, cudaStream_t st) {
     maps.b[1] = M->mapW[1][k];
     const int ntn = (int)((m + MX_BN - 1) / MX_BN);
     tc::Tiles t{m, lo, 0, ntn, ntn, kr.r0_end, kr.r1_begin, kr.r1_end, splits, M->err};
-    EpiTcPartial epi{M->Spart, m};
+    EpiTcPartial epi{{}, M->Spart, m};
     ProfScope ps(IBMI_K_SWEEP_S, st, 2.0 * m * m * n);
     IBMI_CUDA_TRY((tc::launch<2, MX_BN>(maps, t, ntn, (int)((m + 127) / 128), epi, st)));
     note_launch();
@@ -281,6 +284,62 @@ ibmi_status mixed_export(ibmi_plan_s* P, double* H, int64_t ldh, cudaStream_t st
     return IBMI_ERR_TIMEOUT;
   }
   return IBMI_OK;
+}
+
+ibmi_status mixed_run(ibmi_plan_s* P, const double* A, int64_t lda, double* H, int64_t ldh, cudaStream_t st,
+                      ibmi_result* res, double* flops) {
+  MixedState* M = MS(P);
+  RefineState* R = &M->ref;
+  const ibmi_plan_desc& d = P->d;
+  const int64_t p = d.p;
+  const int K = (int)P->lo.size();
+  const double sqrtp = sqrt((double)p), fr = 2.0 * (double)p * p * p;
+  double fs = 0.0;
+  for (int k = 0; k < K; ++k) {
+    const double m = (double)(P->hi[k] - P->lo[k]), n = (double)p - m;
+    fs += 2.0 * m * n * n + 2.0 * m * m * n;
+  }
+  IBMI_TRY(mixed_prepare(P, H, ldh, st));
+  IBMI_TRY(refine_set_matrix(R, A, lda, st));
+  int r = 0;
+  while (true) {
+    ++r;
+    for (int k = 0; k < K; ++k) IBMI_TRY(mixed_sweep_step(P, k, st));
+    *flops += fs;
+    res->sweeps = r;
+    if (r % d.check_every != 0 && r < d.max_sweeps) continue;
+    double rho;
+    IBMI_TRY(refine_cheap_residual(R, M->mapH, st, &rho));
+    *flops += fr;
+    res->resid_f = rho;
+    if (!isfinite(rho)) return IBMI_ERR_NONFINITE;
+    if (d.ns_theta > 0.0 && rho * sqrtp <= d.ns_theta) break;
+    if (rho <= d.tol || r >= d.max_sweeps) {
+      // BF16x3 cannot certify tol: confirm with the FP64-accurate residual
+      IBMI_TRY(mixed_export(P, H, ldh, st));
+      double acc;
+      IBMI_TRY(refine_residual(R, H, ldh, st, &acc));
+      *flops += fr;
+      res->resid_f = acc;
+      if (acc <= d.tol) return IBMI_OK;
+      if (r >= d.max_sweeps) return IBMI_NOT_CONVERGED;
+    }
+  }
+  IBMI_TRY(mixed_export(P, H, ldh, st));
+  double prev = INFINITY;
+  for (int s = 0;; ++s) {
+    double rho;
+    IBMI_TRY(refine_residual(R, H, ldh, st, &rho));
+    *flops += fr;
+    res->resid_f = rho;
+    if (!isfinite(rho)) return IBMI_ERR_NONFINITE;
+    if (rho <= d.tol) return IBMI_OK;
+    if (s >= d.ns_max || !(rho < prev)) return IBMI_NOT_CONVERGED;
+    prev = rho;
+    IBMI_TRY(refine_ns_update(R, H, ldh, st));
+    *flops += fr;
+    res->ns_steps = s + 1;
+  }
 }
 
 }  // namespace ibmi

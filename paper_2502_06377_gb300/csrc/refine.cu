@@ -1,0 +1,364 @@
+// FP64-accurate residual (sliced error-free products on tcgen05) and the
+// Newton-Schulz update of eq. newton, for the mixed-precision path.
+#include <math.h>
+
+#include "refine.cuh"
+
+namespace ibmi {
+
+static inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+// ------------------------------------------------------------ slicing ----
+
+// One CTA per row: exponent e with max|row| < 2^e, then the fixed-point value
+// F = rint(x 2^{55-e}) (|F| < 2^55) is cut into signed digits of weight
+// 2^{49-7s}: d_s = round(F_s / 2^{49-7s}), F_{s+1} = F_s - d_s 2^{49-7s}
+// (round half up, so F_{s+1} in [-2^{48-7s}, 2^{48-7s})).  Digits 7..9 come
+// from F' = F_7 2^14 + rint((x 2^{55-e} - F) 2^14), the exact FP64 remainder
+// of the 55-bit scaling carried 14 bits further.  All |d_s| <= 64.
+struct SlicePtrs {
+  __nv_bfloat16* s[OZ_S];
+};
+
+__global__ void k_oz_slices(const double* X, int64_t ldx, int64_t p, int64_t ldp, SlicePtrs out, int nslices,
+                            int* expo) {
+  const int64_t i = blockIdx.x;
+  const double* row = X + i * ldx;
+  double mx = 0.0;
+  for (int64_t c = threadIdx.x; c < p; c += blockDim.x) mx = fmax(mx, fabs(row[c]));
+  __shared__ double red[32];
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = threadIdx.x < blockDim.x / 32 ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (threadIdx.x == 0) red[0] = v;
+  }
+  __syncthreads();
+  int e = 0;
+  if (red[0] > 0.0) frexp(red[0], &e);   // red[0] = f 2^e, f in [0.5, 1)
+  if (threadIdx.x == 0) expo[i] = e;
+  for (int64_t c = threadIdx.x; c < ldp; c += blockDim.x) {
+    const double xs = c < p ? ldexp(row[c], 55 - e) : 0.0;
+    long long F = __double2ll_rn(xs);
+    const long long Flo = __double2ll_rn((xs - (double)F) * 16384.0);   // |Flo| <= 2^13
+#pragma unroll
+    for (int s = 0; s < 7; ++s) {
+      if (s >= nslices) break;
+      const int sh = 49 - 7 * s;
+      const long long d = (F + (1ll << (sh - 1))) >> sh;
+      F -= d << sh;
+      out.s[s][i * ldp + c] = __int2bfloat16_rn((int)d);
+    }
+    if (nslices > 7) {
+      long long G = (F << 14) + Flo;   // F = F_7 in [-64, 64)
+#pragma unroll
+      for (int s = 7; s < OZ_S; ++s) {
+        if (s >= nslices) break;
+        const int sh = 14 - 7 * (s - 7);
+        long long d;
+        if (s == OZ_S - 1 || sh == 0) {
+          d = G;
+        } else {
+          d = (G + (1ll << (sh - 1))) >> sh;
+          G -= d << sh;
+        }
+        out.s[s][i * ldp + c] = __int2bfloat16_rn((int)d);
+      }
+    }
+  }
+}
+
+__global__ void k_fsplit2(const double* X, int64_t ldx, int64_t p, int64_t ldp, __nv_bfloat16* s0,
+                          __nv_bfloat16* s1) {
+  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= p * ldp) return;
+  int64_t i = idx / ldp, c = idx - i * ldp;
+  float x = c < p ? (float)X[i * ldx + c] : 0.f;
+  __nv_bfloat16 h = __float2bfloat16_rn(x);
+  s0[idx] = h;
+  s1[idx] = __float2bfloat16_rn(x - __bfloat162float(h));
+}
+
+// ---------------------------------------------------------- epilogues ----
+
+// Group sum T_q[i, j] (+)= exact FP32 pair product (an integer below 2^24).
+struct EpiOzAcc : tc::EpiBase {
+  int* T; int64_t ldt, M, N; int first;
+  __device__ __forceinline__ void operator()(int64_t i, int64_t j0, int, const float (&v)[16]) const {
+    if (i >= M) return;
+    int* t = T + i * ldt + j0;
+    if (j0 + 16 <= N) {
+      int4* t4 = reinterpret_cast<int4*>(t);
+#pragma unroll
+      for (int g = 0; g < 4; ++g) {
+        int4 o = first ? make_int4(0, 0, 0, 0) : t4[g];
+        o.x += __float2int_rn(v[4 * g + 0]);
+        o.y += __float2int_rn(v[4 * g + 1]);
+        o.z += __float2int_rn(v[4 * g + 2]);
+        o.w += __float2int_rn(v[4 * g + 3]);
+        t4[g] = o;
+      }
+    } else {
+      for (int c = 0; c < 16 && j0 + c < N; ++c) t[c] = (first ? 0 : t[c]) + __float2int_rn(v[c]);
+    }
+  }
+};
+
+// Cheap residual: per-thread sum of (delta_ij - acc)^2, one partial per warp.
+struct EpiResidSq {
+  double* partials; int64_t p;
+  double s;
+  __device__ __forceinline__ void operator()(int64_t i, int64_t j0, int, const float (&v)[16]) {
+    if (i >= p) return;
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+      if (j0 + c < p) {
+        double r = (i == j0 + c ? 1.0 : 0.0) - (double)v[c];
+        s += r * r;
+      }
+    }
+  }
+  __device__ __forceinline__ void done(int q) {
+    double x = s;
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if ((threadIdx.x & 31) == 0) {
+      const int64_t cta = blockIdx.x + (int64_t)gridDim.x * (blockIdx.y + (int64_t)gridDim.y * blockIdx.z);
+      partials[cta * 4 + q] = x;
+    }
+  }
+};
+
+// ------------------------------------------------------------ combine ----
+
+// C = 2^{e_i + f_j - 12} sum_q T_q 2^{-7q};  Q = I - C (FP64, ld p);
+// sum Q^2 per CTA.
+__global__ void k_oz_combine(const int* T, int64_t p, int64_t ldp, const int* ex, const int* ea, int qmax,
+                             double* Q, double* partials) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double sq = 0.0;
+  if (idx < p * ldp) {
+    const int64_t i = idx / ldp, j = idx - i * ldp;
+    double q = 0.0;
+    if (j < p) {
+      const int64_t plane = p * ldp;
+      double acc = (double)T[(int64_t)qmax * plane + idx];
+      for (int g = qmax - 1; g >= 0; --g) acc = fma(acc, 0.0078125, (double)T[(int64_t)g * plane + idx]);
+      const double c = ldexp(acc, ex[i] + ea[j] - 12);
+      q = (i == j ? 1.0 : 0.0) - c;
+      sq = q * q;
+      Q[i * p + j] = q;
+    }
+  }
+  __shared__ double red[8];
+  for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sq;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x / 32); ++w) t += red[w];
+    partials[blockIdx.x] = t;
+  }
+}
+
+__global__ void k_sum_partials(const double* partials, int64_t n, int64_t p, double* out) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += partials[i];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x / 32); ++w) t += red[w];
+    out[0] = sqrt(t) / sqrt((double)p);
+  }
+}
+
+// Newton-Schulz update: Xn = X + 2^{e_i + g_j - 12} sum_{q <= qmax} T_q 2^{-7q}.
+__global__ void k_oz_update(const int* T, int64_t p, int64_t ldp, const int* ex, const int* eq, int qmax,
+                            const double* X, int64_t ldx, double* Xn) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= p * p) return;
+  const int64_t i = idx / p, j = idx - i * p;
+  const int64_t plane = p * ldp, t = i * ldp + j;
+  double acc = (double)T[(int64_t)qmax * plane + t];
+  for (int g = qmax - 1; g >= 0; --g) acc = fma(acc, 0.0078125, (double)T[(int64_t)g * plane + t]);
+  Xn[idx] = X[i * ldx + j] + ldexp(acc, ex[i] + eq[j] - 12);
+}
+
+__global__ void k_sym_into(const double* Xn, int64_t p, double* X, int64_t ldx) {
+  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= p * p) return;
+  int64_t i = idx / p, j = idx - i * p;
+  X[i * ldx + j] = 0.5 * (Xn[i * p + j] + Xn[j * p + i]);
+}
+
+// --------------------------------------------------------------- host ----
+
+static constexpr int RF_BN = 128;
+
+ibmi_status refine_create(RefineState* R, int64_t p, int* err) {
+  R->p = p;
+  R->ldp = (p + 63) / 64 * 64;
+  R->err = err;
+  const int64_t ldp = R->ldp;
+  const size_t plane16 = sizeof(__nv_bfloat16) * p * ldp;
+  const int64_t tiles = ((p + 127) / 128) * ((p + RF_BN - 1) / RF_BN);
+  R->n_partials = std::max<int64_t>(tiles * 4, (p * ldp + 255) / 256) + 8;
+  size_t bytes = plane16 * (OZ_SA + OZ_SX + NS_S + 2) + sizeof(int) * (size_t)(OZ_QMAX + 1) * p * ldp +
+                 sizeof(double) * p * p + sizeof(double) * R->n_partials + 3 * sizeof(int) * p + 64 * 256;
+  if (cudaMalloc(&R->pool, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return IBMI_ERR_OOM;
+  }
+  uint8_t* q = (uint8_t*)R->pool;
+  auto take = [&](size_t b) { uint8_t* r = q; q += (b + 255) / 256 * 256; return r; };
+  for (int s = 0; s < OZ_SA; ++s) R->Ao[s] = (__nv_bfloat16*)take(plane16);
+  for (int s = 0; s < OZ_SX; ++s) R->Xo[s] = (__nv_bfloat16*)take(plane16);
+  for (int s = 0; s < NS_S; ++s) R->Qo[s] = (__nv_bfloat16*)take(plane16);
+  for (int s = 0; s < 2; ++s) R->Af[s] = (__nv_bfloat16*)take(plane16);
+  R->T = (int*)take(sizeof(int) * (size_t)(OZ_QMAX + 1) * p * ldp);
+  R->Xn = (double*)take(sizeof(double) * p * p);
+  R->partials = (double*)take(sizeof(double) * R->n_partials);
+  R->dout = (double*)take(256);
+  R->expA = (int*)take(sizeof(int) * p);
+  R->expX = (int*)take(sizeof(int) * p);
+  R->expQ = (int*)take(sizeof(int) * p);
+  bool ok = true;
+  for (int s = 0; s < OZ_SA; ++s) ok &= tc::make_map_bf16(&R->mAo[s], R->Ao[s], p, p, ldp, RF_BN);
+  for (int s = 0; s < OZ_SX; ++s) ok &= tc::make_map_bf16(&R->mXo[s], R->Xo[s], p, p, ldp, 128);
+  for (int s = 0; s < NS_S; ++s) ok &= tc::make_map_bf16(&R->mQo[s], R->Qo[s], p, p, ldp, RF_BN);
+  for (int s = 0; s < 2; ++s) ok &= tc::make_map_bf16(&R->mAf[s], R->Af[s], p, p, ldp, RF_BN);
+  return ok ? IBMI_OK : IBMI_ERR_CUDA;
+}
+
+void refine_destroy(RefineState* R) {
+  cudaFree(R->pool);
+  R->pool = nullptr;
+}
+
+static ibmi_status slice_digits(RefineState* R, const double* X, int64_t ldx, __nv_bfloat16* const* dst, int nslices,
+                                int* expo, cudaStream_t st) {
+  SlicePtrs sp;
+  for (int s = 0; s < OZ_S; ++s) sp.s[s] = s < nslices ? dst[s] : nullptr;
+  note_launch();
+  k_oz_slices<<<(unsigned)R->p, 256, 0, st>>>(X, ldx, R->p, R->ldp, sp, nslices, expo);
+  IBMI_CUDA_TRY(cudaGetLastError());
+  return IBMI_OK;
+}
+
+ibmi_status refine_set_matrix(RefineState* R, const double* A, int64_t lda, cudaStream_t st) {
+  ProfScope ps(IBMI_K_OTHER, st, 0.0);
+  IBMI_TRY(slice_digits(R, A, lda, R->Ao, OZ_SA, R->expA, st));
+  note_launch();
+  k_fsplit2<<<nblk(R->p * R->ldp), 256, 0, st>>>(A, lda, R->p, R->ldp, R->Af[0], R->Af[1]);
+  IBMI_CUDA_TRY(cudaGetLastError());
+  return IBMI_OK;
+}
+
+static ibmi_status read_scalar(RefineState* R, cudaStream_t st, double* v) {
+  int herr = 0;
+  IBMI_CUDA_TRY(cudaMemcpyAsync(v, R->dout, sizeof(double), cudaMemcpyDeviceToHost, st));
+  IBMI_CUDA_TRY(cudaMemcpyAsync(&herr, R->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  IBMI_CUDA_TRY(cudaStreamSynchronize(st));
+  if (herr != 0) {
+    set_last_error("tcgen05 kernel: bounded wait expired");
+    return IBMI_ERR_TIMEOUT;
+  }
+  return IBMI_OK;
+}
+
+// Digit-group sums T_q = sum_{s+u=q} (slice_s of the A operand) (slice_u of the
+// B operand)^T for q <= qmax, each pair an exact FP32 accumulation over at
+// most 4096 terms, added up in int32.
+static ibmi_status pair_products(RefineState* R, const CUtensorMap* ma, int nsa, const CUtensorMap* mb, int nsb,
+                                 int qmax, cudaStream_t st) {
+  const int64_t p = R->p, ldp = R->ldp;
+  const int nkt = (int)((p + tc::BK - 1) / tc::BK);
+  const int chunk_tiles = OZ_KCHUNK / tc::BK;
+  const int nchunks = (nkt + chunk_tiles - 1) / chunk_tiles;
+  const int grid_n = (int)((p + RF_BN - 1) / RF_BN), grid_m = (int)((p + 127) / 128);
+  for (int q = 0; q <= qmax; ++q) {
+    bool first = true;
+    for (int s = 0; s <= q; ++s) {
+      const int u = q - s;
+      if (s >= nsa || u >= nsb) continue;
+      tc::Maps maps;
+      maps.a[0] = ma[s];
+      maps.b[0] = mb[u];
+      for (int c = 0; c < nchunks; ++c) {
+        const int k0 = c * chunk_tiles, k1 = std::min(nkt, k0 + chunk_tiles);
+        // K tiles [k0, k1): an empty first range plus [k0, k1)
+        tc::Tiles t{p, 0, 0, grid_n, 0, 0, k0, k1, 1, R->err};
+        EpiOzAcc epi{{}, R->T + (int64_t)q * p * ldp, ldp, p, p, first ? 1 : 0};
+        IBMI_CUDA_TRY((tc::launch<1, RF_BN>(maps, t, grid_n, grid_m, epi, st)));
+        first = false;
+      }
+    }
+  }
+  return IBMI_OK;
+}
+
+ibmi_status refine_residual(RefineState* R, const double* X, int64_t ldx, cudaStream_t st, double* rho) {
+  const int64_t p = R->p, ldp = R->ldp;
+  {
+    ProfScope ps(IBMI_K_OTHER, st, 0.0);
+    IBMI_TRY(slice_digits(R, X, ldx, R->Xo, OZ_SX, R->expX, st));
+  }
+  {
+    ProfScope ps(IBMI_K_RESIDUAL, st, 2.0 * (double)p * p * p);
+    IBMI_TRY(pair_products(R, R->mXo, OZ_SX, R->mAo, OZ_SA, OZ_QMAX, st));
+  }
+  {
+    ProfScope ps(IBMI_K_OTHER, st, 0.0);
+    const unsigned nb = nblk(p * ldp);
+    note_launch();
+    k_oz_combine<<<nb, 256, 0, st>>>(R->T, p, ldp, R->expX, R->expA, OZ_QMAX, R->Xn, R->partials);
+    IBMI_CUDA_TRY(cudaGetLastError());
+    note_launch();
+    k_sum_partials<<<1, 1024, 0, st>>>(R->partials, nb, p, R->dout);
+    IBMI_CUDA_TRY(cudaGetLastError());
+  }
+  return read_scalar(R, st, rho);
+}
+
+ibmi_status refine_ns_update(RefineState* R, double* X, int64_t ldx, cudaStream_t st) {
+  const int64_t p = R->p, ldp = R->ldp;
+  ProfScope ps(IBMI_K_NS, st, 2.0 * (double)p * p * p);
+  IBMI_TRY(slice_digits(R, R->Xn, p, R->Qo, NS_S, R->expQ, st));
+  IBMI_TRY(pair_products(R, R->mXo, NS_S, R->mQo, NS_S, NS_S - 1, st));
+  note_launch();
+  k_oz_update<<<nblk(p * p), 256, 0, st>>>(R->T, p, ldp, R->expX, R->expQ, NS_S - 1, X, ldx, R->Xn);
+  IBMI_CUDA_TRY(cudaGetLastError());
+  note_launch();
+  k_sym_into<<<nblk(p * p), 256, 0, st>>>(R->Xn, p, X, ldx);
+  IBMI_CUDA_TRY(cudaGetLastError());
+  return IBMI_OK;
+}
+
+ibmi_status refine_cheap_residual(RefineState* R, const CUtensorMap* mapH2, cudaStream_t st, double* rho) {
+  const int64_t p = R->p;
+  tc::Maps maps;
+  maps.a[0] = mapH2[0];
+  maps.a[1] = mapH2[1];
+  maps.b[0] = R->mAf[0];
+  maps.b[1] = R->mAf[1];
+  const int nkt = (int)((p + tc::BK - 1) / tc::BK);
+  const int grid_n = (int)((p + RF_BN - 1) / RF_BN), grid_m = (int)((p + 127) / 128);
+  const int64_t nparts = (int64_t)grid_n * grid_m * 4;
+  if (nparts > R->n_partials) return IBMI_ERR_INVALID_ARG;
+  {
+    ProfScope ps(IBMI_K_RESIDUAL, st, 2.0 * (double)p * p * p);
+    tc::Tiles t{p, 0, 0, grid_n, 0, 0, 0, nkt, 1, R->err};
+    EpiResidSq epi{R->partials, p, 0.0};
+    IBMI_CUDA_TRY((tc::launch<2, RF_BN>(maps, t, grid_n, grid_m, epi, st)));
+    note_launch();
+    k_sum_partials<<<1, 1024, 0, st>>>(R->partials, nparts, p, R->dout);
+    IBMI_CUDA_TRY(cudaGetLastError());
+  }
+  return read_scalar(R, st, rho);
+}
+
+}  // namespace ibmi

@@ -1,0 +1,67 @@
+// FP64-accurate residual and Newton-Schulz refinement on tcgen05 (internal).
+#pragma once
+#include <cuda_bf16.h>
+
+#include "tc_gemm.cuh"
+
+namespace ibmi {
+
+// Error-free sliced product (Ozaki scheme): every row of an FP64 matrix is
+// written as 2^e_i * sum_s d_s 2^{-6-7s} with signed integer digits
+// |d_s| <= 64.  Digits are exact in BF16, a digit product is at most 2^12, so
+// a single slice-pair product accumulated in FP32 over K <= 4096 terms is an
+// exact integer; pair products are summed per digit group q = s + u in int32
+// and combined once in FP64.  The iterate X = A^{-1} is strongly diagonal, so
+// its digits are fixed-point relative to a large row maximum; it gets ten
+// digits (69 bits) against eight (55 bits) for A, which keeps the error of
+// I - X A below the FP64 rounding of a direct evaluation.
+constexpr int OZ_S = 10;        // maximum digit slices per operand
+constexpr int OZ_SX = 10;       // digits of the iterate
+constexpr int OZ_SA = 8;        // digits of A
+constexpr int OZ_QMAX = 9;      // highest digit group kept (52 pair products)
+constexpr int OZ_KCHUNK = 4096; // exactness bound on K per accumulation
+constexpr int NS_S = 5;         // digit slices of the Newton-Schulz update operands (34 bits,
+                                // digit groups q <= 4: 15 exact pair products)
+
+struct RefineState {
+  int64_t p = 0, ldp = 0;
+  __nv_bfloat16* Ao[OZ_SA] = {};  // digit slices of A (rows), p x ldp
+  __nv_bfloat16* Xo[OZ_S] = {};   // digit slices of the iterate X
+  int* expA = nullptr;            // row exponents
+  int* expX = nullptr;
+  int* expQ = nullptr;
+  int* T = nullptr;               // (OZ_QMAX+1) x p x ldp int32 group sums
+  __nv_bfloat16* Qo[NS_S] = {};   // leading digit slices of Q = I - X A
+  __nv_bfloat16* Af[2] = {};      // BF16 hi/lo of A (cheap residual)
+  double* Xn = nullptr;           // p x p FP64: Q after a residual, then X + X Q^T
+  double* partials = nullptr;     // reduction partials
+  int64_t n_partials = 0;
+  double* dout = nullptr;         // device scalars
+  int* err = nullptr;
+  CUtensorMap mAo[OZ_SA], mXo[OZ_S], mQo[NS_S], mAf[2];
+  void* pool = nullptr;
+};
+
+ibmi_status refine_create(RefineState* R, int64_t p, int* err);
+void refine_destroy(RefineState* R);
+
+// Digit slices of A (once per matrix) and its BF16 hi/lo split.
+ibmi_status refine_set_matrix(RefineState* R, const double* A, int64_t lda, cudaStream_t st);
+
+// rho_F = ||I - X A||_F / sqrt(p) (= ||I - A X||_F / sqrt(p) for symmetric
+// A, X), accurate to FP64 rounding; leaves Q = I - X A (FP64) and the digit
+// slices of X for ns_update.  Host value in *rho (syncs the stream).
+ibmi_status refine_residual(RefineState* R, const double* X, int64_t ldx, cudaStream_t st, double* rho);
+
+// X <- sym(X + X Q^T) = sym(X (2I - A X)), the update of eq. newton; the
+// product X Q^T uses the five leading digits of X and of Q (exact pair
+// products, 2^-34 relative truncation), so its error stays proportional to Q.
+// Must follow refine_residual on the same X.
+ibmi_status refine_ns_update(RefineState* R, double* X, int64_t ldx, cudaStream_t st);
+
+// ||I - H A||_F / sqrt(p) from BF16x3 products, for H given by its BF16 hi/lo
+// slice maps (about 5 significant digits; used to decide the hand-over to
+// Newton-Schulz).  Host value in *rho.
+ibmi_status refine_cheap_residual(RefineState* R, const CUtensorMap* mapH2, cudaStream_t st, double* rho);
+
+}  // namespace ibmi

@@ -31,8 +31,8 @@ constexpr int THREADS = 192;  // 6 warps
 constexpr int ERR_TIMEOUT = 7;
 
 struct Maps {
-  CUtensorMap a[3];
-  CUtensorMap b[3];
+  CUtensorMap a[4];
+  CUtensorMap b[4];
 };
 
 struct Tiles {
@@ -158,6 +158,12 @@ __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
   asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
 }
 
+// Epilogue functors: operator()(row, col0, z, v[16]) per 16-column chunk of a
+// row (called by the thread owning that TMEM lane), then done(quadrant) once.
+struct EpiBase {
+  __device__ __forceinline__ void done(int) {}
+};
+
 // 32 lanes x 16 columns of 32-bit: thread t of the warp gets lane (quadrant + t).
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   uint32_t r[16];
@@ -280,6 +286,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
     const int row = q * 32 + lane;
     const bool ok = mbar_wait(accf, 0, t.err);
     tc_fence_after();
+    Epi e = epi;
     if (ok) {
 #pragma unroll 1
       for (int c = 0; c < BN; c += 16) {
@@ -290,9 +297,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
 #pragma unroll
           for (int i = 0; i < 16; ++i) v[i] = 0.f;
         }
-        epi((int64_t)mt * BM + row, n0 + c, z, v);
+        e((int64_t)mt * BM + row, n0 + c, z, v);
       }
     }
+    e.done(q);
     tc_fence_before();
   }
   __syncthreads();

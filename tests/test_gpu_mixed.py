@@ -84,3 +84,48 @@ def test_mixed_full_size_c2(ibmi):
     R = np.eye(p)[rows] - A[rows] @ H
     assert np.abs(R).max() < 1e-9
     print("c2 mixed", res)
+
+
+@pytest.mark.parametrize("p", [200, 1000, 4160])
+def test_tc_residual_matches_fp64(ibmi, p):
+    """The sliced error-free tensor-core residual agrees with FP64 evaluations
+    at the level of FP64 rounding, both far from and at the inverse."""
+    A = matern(p, 31)
+    rng = np.random.default_rng(2)
+    inv = np.linalg.inv(A)
+    inv = 0.5 * (inv + inv.T)
+    for H in (inv, inv + 1e-6 * (lambda g: g + g.T)(rng.standard_normal((p, p)))):
+        dA, dH = torch.from_numpy(A).cuda(), torch.from_numpy(np.ascontiguousarray(H)).cuda()
+        got = ibmi.ibmi_residual_tc(dA, dH)
+        want = O.residual_f(A, H)
+        dfma = ibmi.ibmi_residual(dA, dH)
+        print(f"p={p} tc={got:.6e} oracle={want:.6e} dfma={dfma:.6e}")
+        assert abs(got - want) <= 1e-3 * want + 1e-14
+        assert abs(got - dfma) <= 1e-3 * dfma + 1e-14
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("p", [300, 1024])
+def test_refine_newton_schulz_entry(ibmi, precision, p):
+    """eq. newton on its own: from a perturbed inverse (||I - A X_0|| < 1) the
+    tail converges quadratically to the FP64 floor; the residual it reports is
+    the oracle's."""
+    A = matern(p, 41)
+    inv = np.linalg.inv(A)
+    rng = np.random.default_rng(5)
+    N = rng.standard_normal((p, p))
+    X0 = 0.5 * (inv + inv.T) + 1e-6 * (N + N.T)
+    dA, dX = torch.from_numpy(A).cuda(), torch.from_numpy(X0).cuda()
+    prec = ibmi.IBMI_MIXED if precision == "mixed" else ibmi.IBMI_FP64
+    s, res = ibmi.ibmi_refine(dA, dX, precision=prec, tol=1e-11, ns_max=6)
+    X = dX.cpu().numpy()
+    assert s == ibmi.IBMI_OK and 1 <= res["ns_steps"] <= 3, res
+    assert O.residual_f(A, X) <= 1e-11
+    assert res["resid_f"] == pytest.approx(O.residual_f(A, X), rel=0.05, abs=1e-13)
+    assert np.array_equal(X, X.T)
+
+
+def test_refine_rejects_bad_args(ibmi):
+    A = torch.eye(8, dtype=torch.float64, device="cuda")
+    s, _ = ibmi.ibmi_refine(A, A.clone(), precision=5)
+    assert s == ibmi.IBMI_ERR_INVALID_ARG
