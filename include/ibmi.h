@@ -150,12 +150,18 @@ ibmi_status ibmi_residual(const double* A, int64_t lda, const double* H, int64_t
 typedef enum ibmi_kernel_class {
   IBMI_K_SWEEP_X = 0,     /* a3: X = -W T and its scatter into H                 */
   IBMI_K_SWEEP_S = 1,     /* a4: S = A_I^{-1} - X W^T                             */
-  IBMI_K_RESIDUAL = 2,    /* a6: ||I - A H||_F                                    */
-  IBMI_K_NS = 3,          /* a7: Newton-Schulz products                           */
-  IBMI_K_INVARIANTS = 4,  /* a2: Cholesky, triangular solves                      */
-  IBMI_K_OTHER = 5,       /* splits, symmetrisation, copies                       */
-  IBMI_K_COUNT = 6
+  IBMI_K_RESIDUAL = 2,    /* a6: ||I - A H||_F products                           */
+  IBMI_K_NS = 3,          /* a7: Newton-Schulz update products                    */
+  IBMI_K_INVARIANTS = 4,  /* a2: Cholesky, triangular solves (FP64)               */
+  IBMI_K_OTHER = 5,       /* slicing, combines, symmetrisation, copies            */
+  IBMI_K_INVARIANTS_TC = 6, /* a2, mixed path: W = A_I^{-1} A_{I,:} on tensor cores */
+  IBMI_K_COUNT = 7
 } ibmi_kernel_class;
+/* The flops recorded per class are the operations issued to the unit that
+ * executes them: FP64 DFMA for the FP64 path and the block factorisations;
+ * tensor-pipe BF16 MMA flops for the tcgen05 kernels (a BF16x3 product issues
+ * three times the flops of the product it represents, a digit-sliced FP64
+ * product one plain GEMM per digit pair). */
 void ibmi_prof_enable(int on);
 /* launches: launches of that class; ms: summed event time; flops: algorithmic
  * flops of those launches.  Returns IBMI_ERR_INVALID_ARG for a bad class. */

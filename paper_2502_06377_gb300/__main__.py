@@ -1,0 +1,68 @@
+"""Command-line runner for single library calls on cuda:0.
+
+  python -m paper_2502_06377_gb300 invert   --p 4096 --K 8 --h 32 --precision mixed
+  python -m paper_2502_06377_gb300 residual --p 4096 --method tc
+
+Inputs are the seeded Matern-3/2 covariance of the benchmark (points in the
+unit square sorted by x, length scale 0.1, nugget 1e-2).  `residual` evaluates
+||I - A H||_F / sqrt(p) for H = the identity-initialised IBMI result after one
+sweep (a realistic iterate).  Prints one JSON line.
+"""
+import argparse
+import json
+import os
+import sys
+import time
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+
+
+def main():
+    ap = argparse.ArgumentParser(prog="python -m paper_2502_06377_gb300")
+    ap.add_argument("cmd", choices=["invert", "residual"])
+    ap.add_argument("--p", type=int, default=4096)
+    ap.add_argument("--K", type=int, default=8)
+    ap.add_argument("--h", type=int, default=32)
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="mixed")
+    ap.add_argument("--method", choices=["tc", "fp64"], default="tc")
+    ap.add_argument("--tol", type=float, default=1e-10)
+    ap.add_argument("--repeat", type=int, default=1)
+    a = ap.parse_args()
+
+    import numpy as np
+    import torch
+
+    from paper_2502_06377_gb300 import build as _b
+    _b.build()
+    import paper_2502_06377_gb300 as ibmi
+    import workloads as wl
+
+    A = wl.c2_matern(a.p, seed=2)
+    dA = torch.from_numpy(A).cuda()
+    dH = torch.empty_like(dA)
+    prec = ibmi.IBMI_MIXED if a.precision == "mixed" else ibmi.IBMI_FP64
+    if a.cmd == "invert":
+        plan = ibmi.ibmi_plan(a.p, K=a.K, h=a.h, precision=prec, tol=a.tol,
+                              ns_theta=0.5 if prec == ibmi.IBMI_MIXED else 0.0)
+        out = None
+        for _ in range(a.repeat):
+            t0 = time.perf_counter()
+            s, res = ibmi.ibmi_invert(plan, dA, dH)
+            torch.cuda.synchronize()
+            out = dict(res, status_name=ibmi.ibmi_status_string(s), wall_s=time.perf_counter() - t0)
+        print(json.dumps(out))
+    else:
+        plan = ibmi.ibmi_plan(a.p, K=a.K, h=a.h, precision=ibmi.IBMI_FP64, tol=0.0, max_sweeps=1)
+        ibmi.ibmi_invert(plan, dA, dH)
+        torch.cuda.synchronize()
+        fn = ibmi.ibmi_residual_tc if a.method == "tc" else ibmi.ibmi_residual
+        v = None
+        for _ in range(a.repeat):
+            t0 = time.perf_counter()
+            v = fn(dA, dH)
+            dt = time.perf_counter() - t0
+        print(json.dumps({"resid_f": v, "method": a.method, "p": a.p, "wall_s": dt}))
+
+
+if __name__ == "__main__":
+    main()

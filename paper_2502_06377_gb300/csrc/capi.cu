@@ -101,7 +101,7 @@ static ibmi_status invert_impl(ibmi_plan_s* P, const double* A, int64_t lda, dou
   // a2: invariants
   IBMI_CUDA_TRY(cudaMemsetAsync(P->dstatus, 0, sizeof(DevStatus), st));
   const bool mixed = d.precision == IBMI_MIXED;
-  for (int k = 0; k < K; ++k) IBMI_TRY(invariants_f64(P, k, A, lda, st));
+  IBMI_TRY(invariants_all(P, A, lda, !mixed, st));
   flops += flops_plan(P);
   DevStatus hs;
   IBMI_CUDA_TRY(cudaMemcpyAsync(&hs, P->dstatus, sizeof(hs), cudaMemcpyDeviceToHost, st));
@@ -215,9 +215,9 @@ ibmi_status ibmi_plan(const ibmi_plan_desc* desc, ibmi_plan_t* out) {
   }
   P->mmax = mmax;
   P->n_partials = gemm_f64_ctas(p, p);
-  const int64_t nb_tiles = (mmax + CHOL_NB - 1) / CHOL_NB;
-  const int64_t scratch = mmax * mmax /*lwork*/ + nb_tiles * CHOL_NB * CHOL_NB /*linv*/ +
-                          (int64_t)CHOL_NB * p /*tmp*/ + mmax * mmax /*S*/ + P->n_partials + 4;
+  const bool mixed = d.precision == IBMI_MIXED;
+  if (mixed) w_elems = 0;   // the mixed path keeps W only as BF16 slices
+  const int64_t scratch = mmax * mmax /*S*/ + P->n_partials + 4;
   const size_t total = sizeof(double) * (size_t)(ainv_elems + w_elems + scratch);
   if (cudaMalloc(&P->pool, total) != cudaSuccess) {
     cudaGetLastError();
@@ -226,25 +226,47 @@ ibmi_status ibmi_plan(const ibmi_plan_desc* desc, ibmi_plan_t* out) {
   }
   P->pool_bytes = total;
   double* q = P->pool;
+  std::vector<int64_t> hoff_ainv(d.K), hoff_w(d.K, 0), hm(d.K);
   for (int k = 0; k < d.K; ++k) {
     int64_t m = P->hi[k] - P->lo[k];
+    hm[k] = m;
+    hoff_ainv[k] = q - P->pool;
     P->ainv.push_back(q); q += m * m;
   }
   for (int k = 0; k < d.K; ++k) {
     int64_t m = P->hi[k] - P->lo[k];
+    if (mixed) { P->w.push_back(nullptr); continue; }
+    hoff_w[k] = q - P->pool;
     P->w.push_back(q); q += m * p;
   }
-  P->lwork = q; q += mmax * mmax;
-  P->linv = q; q += nb_tiles * CHOL_NB * CHOL_NB;
-  P->tmp = q; q += (int64_t)CHOL_NB * p;
   P->S = q; q += mmax * mmax;
   P->partials = q; q += P->n_partials;
   P->dscalar = q; q += 4;
-  if (cudaMalloc(&P->dstatus, sizeof(DevStatus)) != cudaSuccess) {
+  // batched factorisation scratch
+  const int64_t ncols = mixed ? mmax : p;
+  const size_t bat_doubles = (size_t)d.K * (mmax * mmax + mmax * ncols + mmax * CHOL_NB + (int64_t)CHOL_NB * ncols);
+  if (cudaMalloc(&P->bat_pool, sizeof(double) * bat_doubles + sizeof(int64_t) * 4 * d.K) != cudaSuccess ||
+      cudaMalloc(&P->dstatus, sizeof(DevStatus)) != cudaSuccess) {
     cudaGetLastError();
-    cudaFree(P->pool);
-    delete P;
+    ibmi_plan_destroy(P);
     return IBMI_ERR_OOM;
+  }
+  double* b = (double*)P->bat_pool;
+  P->bat_L = b; b += d.K * mmax * mmax;
+  P->bat_R = b; b += d.K * mmax * ncols;
+  P->bat_linv = b; b += d.K * mmax * CHOL_NB;
+  P->bat_tmp = b; b += d.K * (int64_t)CHOL_NB * ncols;
+  int64_t* ib = (int64_t*)b;
+  P->dlo = ib; P->dm = ib + d.K; P->doff_ainv = ib + 2 * d.K; P->doff_w = ib + 3 * d.K;
+  std::vector<int64_t> packed;
+  packed.insert(packed.end(), P->lo.begin(), P->lo.end());
+  packed.insert(packed.end(), hm.begin(), hm.end());
+  packed.insert(packed.end(), hoff_ainv.begin(), hoff_ainv.end());
+  packed.insert(packed.end(), hoff_w.begin(), hoff_w.end());
+  if (cudaMemcpy(ib, packed.data(), sizeof(int64_t) * packed.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaGetLastError();
+    ibmi_plan_destroy(P);
+    return IBMI_ERR_CUDA;
   }
   if (d.precision == IBMI_MIXED) {
     ibmi_status s = mixed_create(P);
@@ -258,6 +280,7 @@ ibmi_status ibmi_plan_destroy(ibmi_plan_t P) {
   if (!P) return IBMI_ERR_INVALID_ARG;
   if (P->mixed) mixed_destroy(P);
   cudaFree(P->pool);
+  cudaFree(P->bat_pool);
   cudaFree(P->dstatus);
   cudaFree(P->nsR);
   cudaFree(P->nsX);

@@ -23,6 +23,8 @@ struct F64Operands {
   const double* A; int64_t lda; GapMap mA, kA;
   const double* B; int64_t ldb; GapMap kB, nB;
   int64_t M, N, K;
+  int64_t zA = 0, zB = 0;   // element offset of operand z of a batch (blockIdx.z)
+  int batch = 1;
 };
 
 template <bool A_KMAJOR, bool B_NMAJOR, class Epi>
@@ -32,6 +34,8 @@ k_gemm_f64(F64Operands op, Epi epi) {
   __shared__ double Bs[F64_BK][F64_BN + 1];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const int64_t i0 = (int64_t)blockIdx.y * F64_BM, j0 = (int64_t)blockIdx.x * F64_BN;
+  op.A += blockIdx.z * op.zA;
+  op.B += blockIdx.z * op.zB;
   double acc[4][4];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
@@ -91,7 +95,8 @@ k_gemm_f64(F64Operands op, Epi epi) {
 // C[i*ldc + j] = alpha * acc + beta * C[i*ldc + j]   (beta == 0 never reads C)
 struct EpiStore {
   double* C; int64_t ldc; double alpha, beta;
-  __device__ void begin() {}
+  int64_t zC = 0;
+  __device__ void begin() { C += blockIdx.z * zC; }
   __device__ void end() {}
   __device__ __forceinline__ void operator()(int64_t i, int64_t j, double acc) {
     double* c = C + i * ldc + j;
@@ -168,7 +173,7 @@ struct EpiAddTo {
 template <bool A_KMAJOR, bool B_NMAJOR, class Epi>
 inline cudaError_t launch_gemm_f64(const F64Operands& op, const Epi& epi, cudaStream_t st) {
   if (op.M <= 0 || op.N <= 0) return cudaSuccess;
-  dim3 grid((unsigned)((op.N + F64_BN - 1) / F64_BN), (unsigned)((op.M + F64_BM - 1) / F64_BM));
+  dim3 grid((unsigned)((op.N + F64_BN - 1) / F64_BN), (unsigned)((op.M + F64_BM - 1) / F64_BM), (unsigned)op.batch);
   note_launch();
   k_gemm_f64<A_KMAJOR, B_NMAJOR, Epi><<<grid, F64_THREADS, 0, st>>>(op, epi);
   return cudaGetLastError();

@@ -10,15 +10,24 @@
 namespace ibmi {
 
 // ------------------------------------------------------------ Cholesky ----
+//
+// All K diagonal blocks are factorised together: block k is embedded in an
+// mmax x mmax matrix [[A_{I_k}, 0], [0, I]] (its Cholesky factor and inverse
+// are [[L, 0], [0, I]] and [[A_{I_k}^{-1}, 0], [0, I]]), so every launch below
+// works on the whole batch with blockIdx.z = k.
 
 // Factors the jb x jb diagonal tile T (lower part, row-major, ld) in place:
 // T = L L^T, and writes L^{-1} (jb x jb, ld jb) to linv.  One CTA of 32 x 32
-// threads.  A non-positive or non-finite pivot records NOT_SPD (set `blk`,
-// global pivot `row0 + j`) and is replaced by 1 so the factorisation finishes.
-__global__ void __launch_bounds__(1024) k_potrf_tile(double* T, int64_t ld, int jb, double* linv,
-                                                     DevStatus* st, int blk, int64_t row0) {
+// threads per block of the batch.  A non-positive or non-finite pivot records
+// NOT_SPD (set z, global pivot lo_z + row0 + j) and is replaced by 1 so the
+// factorisation finishes.
+__global__ void __launch_bounds__(1024) k_potrf_tile(double* T, int64_t ld, int64_t zT, int jb, double* linv,
+                                                     int64_t zL, DevStatus* st, const int64_t* dlo, int64_t row0) {
   __shared__ double L[CHOL_NB][CHOL_NB + 1];
   __shared__ double X[CHOL_NB][CHOL_NB + 1];
+  const int z = blockIdx.z;
+  T += z * zT;
+  linv += z * zL;
   const int c = threadIdx.x, r = threadIdx.y;
   L[r][c] = (r < jb && c <= r) ? T[r * ld + c] : 0.0;
   __syncthreads();
@@ -27,8 +36,8 @@ __global__ void __launch_bounds__(1024) k_potrf_tile(double* T, int64_t ld, int 
       double d = L[j][j];
       if (!(d > 0.0) || !isfinite(d)) {
         if (atomicCAS(&st->code, 0, (int)IBMI_ERR_NOT_SPD) == 0) {
-          st->block = blk;
-          st->pivot = row0 + j;
+          st->block = z;
+          st->pivot = dlo[z] + row0 + j;
         }
         d = 1.0;
       }
@@ -40,7 +49,7 @@ __global__ void __launch_bounds__(1024) k_potrf_tile(double* T, int64_t ld, int 
     if (c > j && r >= c && r < jb) L[r][c] -= L[r][j] * L[c][j];
     __syncthreads();
   }
-  // X = L^{-1} by forward substitution, one column per thread of warp 0..
+  // X = L^{-1} by forward substitution, one column per thread of the first row.
   if (r == 0 && c < jb) {
     for (int i = 0; i < jb; ++i) {
       double s = (i == c) ? 1.0 : 0.0;
@@ -55,112 +64,144 @@ __global__ void __launch_bounds__(1024) k_potrf_tile(double* T, int64_t ld, int 
   }
 }
 
-// Right-hand side of the two solves: B = A[I, :] with B[:, I] = identity, so
-// that L^{-T} L^{-1} B = [A_I^{-1} on columns I | A_I^{-1} A_{I,I^c} elsewhere].
-__global__ void k_build_rhs(const double* A, int64_t lda, int64_t lo, int64_t m, int64_t p,
-                            double* W) {
+// Lw[z] = [[A[I_z, I_z], 0], [0, I]]  (mmax x mmax)
+__global__ void k_bat_copy_block(const double* A, int64_t lda, const int64_t* dlo, const int64_t* dm, int64_t mmax,
+                                 double* Lw) {
+  const int z = blockIdx.z;
   int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= m * p) return;
-  int64_t i = idx / p, c = idx - i * p;
-  W[idx] = (c >= lo && c < lo + m) ? ((c - lo == i) ? 1.0 : 0.0) : A[(lo + i) * lda + c];
+  if (idx >= mmax * mmax) return;
+  int64_t i = idx / mmax, j = idx - i * mmax;
+  const int64_t lo = dlo[z], m = dm[z];
+  Lw[z * mmax * mmax + idx] = (i < m && j < m) ? A[(lo + i) * lda + lo + j] : (i == j ? 1.0 : 0.0);
 }
 
-// A_I^{-1} = W[:, I]; then W[:, I] = 0 (the zero columns keep sweep tiles that
-// straddle I harmless and let W be addressed with physical column indices).
-__global__ void k_extract_ainv(double* W, int64_t lo, int64_t m, int64_t p, double* ainv) {
+// Right-hand sides R[z] (mmax x ncols).  full_w: rows i < m_z hold A[I_z, :]
+// with the identity on the columns of I_z (so the solution is A_I^{-1} on the
+// columns of I and A_I^{-1} A_{I,I^c} elsewhere); otherwise R[z] = identity.
+__global__ void k_bat_rhs(const double* A, int64_t lda, const int64_t* dlo, const int64_t* dm, int64_t mmax,
+                          int64_t ncols, int full_w, double* R) {
+  const int z = blockIdx.z;
   int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= m * m) return;
-  int64_t i = idx / m, j = idx - i * m;
-  // symmetrise: A_I^{-1} is symmetric in exact arithmetic
-  double v = 0.5 * (W[i * p + lo + j] + W[j * p + lo + i]);
-  ainv[idx] = v;
+  if (idx >= mmax * ncols) return;
+  int64_t i = idx / ncols, c = idx - i * ncols;
+  const int64_t lo = dlo[z], m = dm[z];
+  double v;
+  if (full_w) {
+    if (i >= m) v = 0.0;
+    else if (c >= lo && c < lo + m) v = (c - lo == i) ? 1.0 : 0.0;
+    else v = A[(lo + i) * lda + c];
+  } else {
+    v = (i == c) ? 1.0 : 0.0;
+  }
+  R[z * mmax * ncols + idx] = v;
 }
 
-__global__ void k_zero_cols(double* W, int64_t lo, int64_t m, int64_t p) {
+// Scatter of the solutions: A_I^{-1} (symmetrised) and, for full_w, W with
+// zero columns on I.  Offsets of the per-set outputs come from doff_*.
+__global__ void k_bat_extract(const double* R, const int64_t* dlo, const int64_t* dm, int64_t mmax, int64_t ncols,
+                              int full_w, double* base, const int64_t* doff_ainv, const int64_t* doff_w,
+                              int64_t p) {
+  const int z = blockIdx.z;
+  const int64_t lo = dlo[z], m = dm[z];
+  const double* Rz = R + z * mmax * ncols;
   int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= m * m) return;
-  int64_t i = idx / m, j = idx - i * m;
-  W[i * p + lo + j] = 0.0;
-}
-
-__global__ void k_copy_block(const double* A, int64_t lda, int64_t lo, int64_t m, double* L) {
-  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= m * m) return;
-  int64_t i = idx / m, j = idx - i * m;
-  L[idx] = A[(lo + i) * lda + lo + j];
+  if (idx < m * m) {
+    int64_t i = idx / m, j = idx - i * m;
+    const int64_t cj = full_w ? lo + j : j, ci = full_w ? lo + i : i;
+    base[doff_ainv[z] + idx] = 0.5 * (Rz[i * ncols + cj] + Rz[j * ncols + ci]);
+  }
+  if (full_w && idx < m * p) {
+    int64_t i = idx / p, c = idx - i * p;
+    base[doff_w[z] + idx] = (c >= lo && c < lo + m) ? 0.0 : Rz[i * ncols + c];
+  }
 }
 
 static inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
-ibmi_status invariants_f64(ibmi_plan_s* P, int k, const double* A, int64_t lda, cudaStream_t st) {
-  const int64_t p = P->d.p, lo = P->lo[k], m = P->hi[k] - P->lo[k];
-  double* Lw = P->lwork;   // m x m, ld m
-  double* W = P->w[k];     // m x p
-  ProfScope ps(IBMI_K_INVARIANTS, st, m * m * m / 3.0 + 2.0 * m * m * p);
-  note_launch();
-  k_copy_block<<<nblk(m * m), 256, 0, st>>>(A, lda, lo, m, Lw);
-  IBMI_CUDA_TRY(cudaGetLastError());
+ibmi_status invariants_all(ibmi_plan_s* P, const double* A, int64_t lda, bool full_w, cudaStream_t st) {
+  const int64_t p = P->d.p, mmax = P->mmax;
+  const int K = (int)P->lo.size();
+  const int64_t ncols = full_w ? p : mmax;
+  const int64_t zL = mmax * mmax, zLi = mmax * CHOL_NB, zR = mmax * ncols, zT = (int64_t)CHOL_NB * ncols;
+  double* Lw = P->bat_L;
+  double* R = P->bat_R;
+  double* tmp = P->bat_tmp;
+  double flops = 0.0;
+  for (int k = 0; k < K; ++k) {
+    const double m = (double)(P->hi[k] - P->lo[k]);
+    flops += m * m * m / 3.0 + 2.0 * m * m * (full_w ? (double)p : m);
+  }
+  ProfScope ps(IBMI_K_INVARIANTS, st, flops);
   const GapMap id{0, 0};
-  // blocked right-looking Cholesky, nb = 32
-  for (int64_t j0 = 0; j0 < m; j0 += CHOL_NB) {
-    const int jb = (int)std::min<int64_t>(CHOL_NB, m - j0);
-    double* Ljj = Lw + j0 * m + j0;
-    double* Li = P->linv + j0 * CHOL_NB;  // jb x jb, ld jb
-    note_launch();
-    k_potrf_tile<<<1, dim3(32, 32), 0, st>>>(Ljj, m, jb, Li, P->dstatus, k, lo + j0);
-    IBMI_CUDA_TRY(cudaGetLastError());
-    const int64_t rest = m - j0 - jb;
-    if (rest <= 0) break;
-    // panel: L[j0+jb:, j0:j0+jb] = A[...] L_jj^{-T}   (in place; one CTA column owns each row)
-    {
-      F64Operands op{Lw + (j0 + jb) * m + j0, m, id, id, Li, jb, id, id, rest, jb, jb};
-      IBMI_CUDA_TRY((launch_gemm_f64<true, false>(op, EpiStore{Lw + (j0 + jb) * m + j0, m, 1.0, 0.0}, st)));
-    }
-    // trailing: A22 -= L21 L21^T
-    {
-      F64Operands op{Lw + (j0 + jb) * m + j0, m, id, id, Lw + (j0 + jb) * m + j0, m, id, id, rest, rest, jb};
-      IBMI_CUDA_TRY((launch_gemm_f64<true, false>(
-          op, EpiStore{Lw + (j0 + jb) * m + (j0 + jb), m, -1.0, 1.0}, st)));
-    }
-  }
-  // B = [A_{I,:} with identity on I];  W <- L^{-T} L^{-1} B  (forward, then backward)
+  auto bat = [&](F64Operands op, int64_t za, int64_t zb) {
+    op.zA = za;
+    op.zB = zb;
+    op.batch = K;
+    return op;
+  };
   note_launch();
-  k_build_rhs<<<nblk(m * p), 256, 0, st>>>(A, lda, lo, m, p, W);
+  k_bat_copy_block<<<dim3(nblk(mmax * mmax), 1, K), 256, 0, st>>>(A, lda, P->dlo, P->dm, mmax, Lw);
   IBMI_CUDA_TRY(cudaGetLastError());
-  for (int64_t j0 = 0; j0 < m; j0 += CHOL_NB) {
-    const int jb = (int)std::min<int64_t>(CHOL_NB, m - j0);
-    const double* Li = P->linv + j0 * CHOL_NB;
-    {  // tmp = L_jj^{-1} W[j0:j0+jb, :]
-      F64Operands op{Li, jb, id, id, W + j0 * p, p, id, id, jb, p, jb};
-      IBMI_CUDA_TRY((launch_gemm_f64<true, true>(op, EpiStore{P->tmp, p, 1.0, 0.0}, st)));
+  // blocked right-looking Cholesky, nb = 32
+  for (int64_t j0 = 0; j0 < mmax; j0 += CHOL_NB) {
+    const int jb = (int)std::min<int64_t>(CHOL_NB, mmax - j0);
+    double* Li = P->bat_linv + j0 * CHOL_NB;
+    note_launch();
+    k_potrf_tile<<<dim3(1, 1, K), dim3(32, 32), 0, st>>>(Lw + j0 * mmax + j0, mmax, zL, jb, Li, zLi, P->dstatus,
+                                                          P->dlo, j0);
+    IBMI_CUDA_TRY(cudaGetLastError());
+    const int64_t rest = mmax - j0 - jb;
+    if (rest <= 0) break;
+    double* panel = Lw + (j0 + jb) * mmax + j0;
+    {  // panel = panel L_jj^{-T} (in place: one CTA column owns each row)
+      F64Operands op = bat(F64Operands{panel, mmax, id, id, Li, jb, id, id, rest, jb, jb}, zL, zLi);
+      IBMI_CUDA_TRY((launch_gemm_f64<true, false>(op, EpiStore{panel, mmax, 1.0, 0.0, zL}, st)));
     }
-    IBMI_CUDA_TRY(cudaMemcpyAsync(W + j0 * p, P->tmp, sizeof(double) * jb * p, cudaMemcpyDeviceToDevice, st));
-    const int64_t rest = m - j0 - jb;
-    if (rest > 0) {  // W[j0+jb:, :] -= L[j0+jb:, j0:j0+jb] tmp
-      F64Operands op{Lw + (j0 + jb) * m + j0, m, id, id, P->tmp, p, id, id, rest, p, jb};
-      IBMI_CUDA_TRY((launch_gemm_f64<true, true>(op, EpiStore{W + (j0 + jb) * p, p, -1.0, 1.0}, st)));
+    {  // trailing -= panel panel^T
+      F64Operands op = bat(F64Operands{panel, mmax, id, id, panel, mmax, id, id, rest, rest, jb}, zL, zL);
+      IBMI_CUDA_TRY((launch_gemm_f64<true, false>(op, EpiStore{panel + jb, mmax, -1.0, 1.0, zL}, st)));
     }
   }
-  const int64_t nbk = (m + CHOL_NB - 1) / CHOL_NB;
+  // R <- L^{-T} L^{-1} R
+  note_launch();
+  k_bat_rhs<<<dim3(nblk(mmax * ncols), 1, K), 256, 0, st>>>(A, lda, P->dlo, P->dm, mmax, ncols, full_w ? 1 : 0, R);
+  IBMI_CUDA_TRY(cudaGetLastError());
+  for (int64_t j0 = 0; j0 < mmax; j0 += CHOL_NB) {
+    const int jb = (int)std::min<int64_t>(CHOL_NB, mmax - j0);
+    const double* Li = P->bat_linv + j0 * CHOL_NB;
+    {  // tmp = L_jj^{-1} R[j0:j0+jb, :]
+      F64Operands op = bat(F64Operands{Li, jb, id, id, R + j0 * ncols, ncols, id, id, jb, ncols, jb}, zLi, zR);
+      IBMI_CUDA_TRY((launch_gemm_f64<true, true>(op, EpiStore{tmp, ncols, 1.0, 0.0, zT}, st)));
+    }
+    const int64_t rest = mmax - j0 - jb;
+    if (rest > 0) {  // R[j0+jb:, :] -= L[j0+jb:, j0:j0+jb] tmp
+      F64Operands op = bat(F64Operands{Lw + (j0 + jb) * mmax + j0, mmax, id, id, tmp, ncols, id, id, rest, ncols, jb},
+                           zL, zT);
+      IBMI_CUDA_TRY((launch_gemm_f64<true, true>(op, EpiStore{R + (j0 + jb) * ncols, ncols, -1.0, 1.0, zR}, st)));
+    }
+    IBMI_CUDA_TRY(cudaMemcpy2DAsync(R + j0 * ncols, sizeof(double) * zR, tmp, sizeof(double) * zT,
+                                    sizeof(double) * jb * ncols, K, cudaMemcpyDeviceToDevice, st));
+  }
+  const int64_t nbk = (mmax + CHOL_NB - 1) / CHOL_NB;
   for (int64_t b = nbk - 1; b >= 0; --b) {
     const int64_t j0 = b * CHOL_NB;
-    const int jb = (int)std::min<int64_t>(CHOL_NB, m - j0);
-    const double* Li = P->linv + j0 * CHOL_NB;
-    {  // tmp = L_jj^{-T} W[j0:j0+jb, :]   (A operand column-major view of L_jj^{-1})
-      F64Operands op{Li, jb, id, id, W + j0 * p, p, id, id, jb, p, jb};
-      IBMI_CUDA_TRY((launch_gemm_f64<false, true>(op, EpiStore{P->tmp, p, 1.0, 0.0}, st)));
+    const int jb = (int)std::min<int64_t>(CHOL_NB, mmax - j0);
+    const double* Li = P->bat_linv + j0 * CHOL_NB;
+    {  // tmp = L_jj^{-T} R[j0:j0+jb, :]
+      F64Operands op = bat(F64Operands{Li, jb, id, id, R + j0 * ncols, ncols, id, id, jb, ncols, jb}, zLi, zR);
+      IBMI_CUDA_TRY((launch_gemm_f64<false, true>(op, EpiStore{tmp, ncols, 1.0, 0.0, zT}, st)));
     }
-    IBMI_CUDA_TRY(cudaMemcpyAsync(W + j0 * p, P->tmp, sizeof(double) * jb * p, cudaMemcpyDeviceToDevice, st));
-    if (j0 > 0) {  // W[0:j0, :] -= L[j0:j0+jb, 0:j0]^T tmp
-      F64Operands op{Lw + j0 * m, m, id, id, P->tmp, p, id, id, j0, p, jb};
-      IBMI_CUDA_TRY((launch_gemm_f64<false, true>(op, EpiStore{W, p, -1.0, 1.0}, st)));
+    if (j0 > 0) {  // R[0:j0, :] -= L[j0:j0+jb, 0:j0]^T tmp
+      F64Operands op = bat(F64Operands{Lw + j0 * mmax, mmax, id, id, tmp, ncols, id, id, j0, ncols, jb}, zL, zT);
+      IBMI_CUDA_TRY((launch_gemm_f64<false, true>(op, EpiStore{R, ncols, -1.0, 1.0, zR}, st)));
     }
+    IBMI_CUDA_TRY(cudaMemcpy2DAsync(R + j0 * ncols, sizeof(double) * zR, tmp, sizeof(double) * zT,
+                                    sizeof(double) * jb * ncols, K, cudaMemcpyDeviceToDevice, st));
   }
+  const int64_t nout = std::max(mmax * mmax, full_w ? mmax * p : 0);
   note_launch();
-  k_extract_ainv<<<nblk(m * m), 256, 0, st>>>(W, lo, m, p, P->ainv[k]);
-  IBMI_CUDA_TRY(cudaGetLastError());
-  note_launch();
-  k_zero_cols<<<nblk(m * m), 256, 0, st>>>(W, lo, m, p);
+  k_bat_extract<<<dim3(nblk(nout), 1, K), 256, 0, st>>>(R, P->dlo, P->dm, mmax, ncols, full_w ? 1 : 0, P->pool,
+                                                         P->doff_ainv, P->doff_w, p);
   IBMI_CUDA_TRY(cudaGetLastError());
   return IBMI_OK;
 }

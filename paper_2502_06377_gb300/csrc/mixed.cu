@@ -70,19 +70,6 @@ __device__ __forceinline__ void split2(float x, __nv_bfloat16& h, __nv_bfloat16&
   l = __float2bfloat16_rn(x - __bfloat162float(h));
 }
 
-// FP64 m x p (ld p) -> BF16 hi/lo, ld ldp (padding columns zero)
-__global__ void k_split_w(const double* W, int64_t m, int64_t p, int64_t ldp, __nv_bfloat16* hi,
-                          __nv_bfloat16* lo) {
-  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= m * ldp) return;
-  int64_t i = idx / ldp, c = idx - i * ldp;
-  float x = c < p ? (float)W[i * p + c] : 0.f;
-  __nv_bfloat16 h, l;
-  split2(x, h, l);
-  hi[idx] = h;
-  lo[idx] = l;
-}
-
 // FP64 H (ldh) -> FP32 master + BF16 hi/lo (ldp)
 __global__ void k_import_h(const double* H, int64_t ldh, int64_t p, int64_t ldp, float* Hf, __nv_bfloat16* hi,
                            __nv_bfloat16* lo) {
@@ -217,13 +204,6 @@ ibmi_status mixed_prepare(ibmi_plan_s* P, const double* H, int64_t ldh, cudaStre
   MixedState* M = MS(P);
   const int64_t p = P->d.p, ldp = M->ldp;
   ProfScope ps(IBMI_K_OTHER, st, 0.0);
-  IBMI_CUDA_TRY(cudaMemsetAsync(M->err, 0, sizeof(int), st));
-  for (size_t k = 0; k < P->lo.size(); ++k) {
-    const int64_t m = P->hi[k] - P->lo[k];
-    note_launch();
-    k_split_w<<<nblk(m * ldp), 256, 0, st>>>(P->w[k], m, p, ldp, M->Ws[0][k], M->Ws[1][k]);
-    IBMI_CUDA_TRY(cudaGetLastError());
-  }
   note_launch();
   k_import_h<<<nblk(p * ldp), 256, 0, st>>>(H, ldh, p, ldp, M->Hf, M->Hs[0], M->Hs[1]);
   IBMI_CUDA_TRY(cudaGetLastError());
@@ -245,7 +225,7 @@ ibmi_status mixed_sweep_step(ibmi_plan_s* P, int k, cudaStream_t st) {
     maps.b[1] = M->mapH[1];
     tc::Tiles t{m, 0, 0, nr.r0_end, nr.r1_begin, kr.r0_end, kr.r1_begin, kr.r1_end, 1, M->err};
     EpiTcSweepX epi{{}, M->Hf, M->Hs[0], M->Hs[1], M->ldp, lo, hi, p, m};
-    ProfScope ps(IBMI_K_SWEEP_X, st, 2.0 * m * n * n);
+    ProfScope ps(IBMI_K_SWEEP_X, st, 3.0 * 2.0 * m * n * n);
     IBMI_CUDA_TRY((tc::launch<2, MX_BN>(maps, t, nr.count(), (int)((m + 127) / 128), epi, st)));
   }
   // a4: P = X W^T (split over K); A operand = H slices rows [lo, hi), B = W slices.
@@ -260,7 +240,7 @@ ibmi_status mixed_sweep_step(ibmi_plan_s* P, int k, cudaStream_t st) {
     const int ntn = (int)((m + MX_BN - 1) / MX_BN);
     tc::Tiles t{m, lo, 0, ntn, ntn, kr.r0_end, kr.r1_begin, kr.r1_end, splits, M->err};
     EpiTcPartial epi{{}, M->Spart, m};
-    ProfScope ps(IBMI_K_SWEEP_S, st, 2.0 * m * m * n);
+    ProfScope ps(IBMI_K_SWEEP_S, st, 3.0 * 2.0 * m * m * n);
     IBMI_CUDA_TRY((tc::launch<2, MX_BN>(maps, t, ntn, (int)((m + 127) / 128), epi, st)));
     note_launch();
     k_mixed_sym<<<nblk(m * m), 256, 0, st>>>(M->Spart, splits, m, P->ainv[k], lo, M->ldp, M->Hf, M->Hs[0],
@@ -299,8 +279,12 @@ ibmi_status mixed_run(ibmi_plan_s* P, const double* A, int64_t lda, double* H, i
     const double m = (double)(P->hi[k] - P->lo[k]), n = (double)p - m;
     fs += 2.0 * m * n * n + 2.0 * m * m * n;
   }
-  IBMI_TRY(mixed_prepare(P, H, ldh, st));
+  IBMI_CUDA_TRY(cudaMemsetAsync(M->err, 0, sizeof(int), st));
   IBMI_TRY(refine_set_matrix(R, A, lda, st));
+  // a2 on tensor cores: W_k = A_I^{-1} A_{I,:} from exact digit-sliced products
+  for (int k = 0; k < K; ++k)
+    IBMI_TRY(refine_form_w(R, P->ainv[k], P->hi[k] - P->lo[k], P->lo[k], P->hi[k], M->Ws[0][k], M->Ws[1][k], st));
+  IBMI_TRY(mixed_prepare(P, H, ldh, st));
   int r = 0;
   while (true) {
     ++r;

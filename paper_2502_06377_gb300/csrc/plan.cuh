@@ -12,10 +12,17 @@ struct ibmi_plan_s {
   std::vector<double*> w;        // W = A_I^{-1} A_{I,:}, m x p, zero columns on I
   double* pool = nullptr;        // one allocation backing ainv / w / scratch
   size_t pool_bytes = 0;
+  // batched factorisation scratch (all K blocks padded to mmax, blockIdx.z = k)
+  double* bat_L = nullptr;       // K x mmax x mmax Cholesky factors
+  double* bat_R = nullptr;       // K x mmax x ncols right-hand sides / solutions
+  double* bat_linv = nullptr;    // K x mmax x 32 inverted diagonal tiles
+  double* bat_tmp = nullptr;     // K x 32 x ncols
+  int64_t* dlo = nullptr;        // device copies of lo_k, m_k and of the pool offsets
+  int64_t* dm = nullptr;         // of A_I^{-1} and W for each set
+  int64_t* doff_ainv = nullptr;
+  int64_t* doff_w = nullptr;
+  void* bat_pool = nullptr;
   // scratch
-  double* lwork = nullptr;       // Cholesky factor of one block, mmax x mmax
-  double* linv = nullptr;        // inverses of the nb x nb diagonal tiles
-  double* tmp = nullptr;         // nb x p
   double* S = nullptr;           // mmax x mmax, a4 result before symmetrisation
   double* partials = nullptr;    // residual partial sums
   int64_t n_partials = 0;
@@ -35,9 +42,11 @@ namespace ibmi {
 
 constexpr int CHOL_NB = 32;
 
-// a2: A_I^{-1} and W for set k, FP64.  Non-SPD blocks are reported through
-// plan->dstatus (read by the caller after a stream sync).
-ibmi_status invariants_f64(ibmi_plan_s* P, int k, const double* A, int64_t lda, cudaStream_t st);
+// a2 for all sets at once, FP64: A_I^{-1} for every set and, with full_w,
+// W = A_I^{-1} A_{I,:} (zero columns on I) -- the mixed path forms W on tensor
+// cores instead.  Non-SPD blocks are reported through plan->dstatus (read by
+// the caller after a stream sync).
+ibmi_status invariants_all(ibmi_plan_s* P, const double* A, int64_t lda, bool full_w, cudaStream_t st);
 
 // a3 + a4 for set k on an FP64 iterate H.
 ibmi_status sweep_step_f64(ibmi_plan_s* P, int k, double* H, int64_t ldh, cudaStream_t st);

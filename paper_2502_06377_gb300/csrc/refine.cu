@@ -20,12 +20,12 @@ struct SlicePtrs {
   __nv_bfloat16* s[OZ_S];
 };
 
-__global__ void k_oz_slices(const double* X, int64_t ldx, int64_t p, int64_t ldp, SlicePtrs out, int nslices,
-                            int* expo) {
+__global__ void k_oz_slices(const double* X, int64_t ldx, int64_t ncols, int64_t c0, int64_t ldp, SlicePtrs out,
+                            int nslices, int* expo) {
   const int64_t i = blockIdx.x;
   const double* row = X + i * ldx;
   double mx = 0.0;
-  for (int64_t c = threadIdx.x; c < p; c += blockDim.x) mx = fmax(mx, fabs(row[c]));
+  for (int64_t c = threadIdx.x; c < ncols; c += blockDim.x) mx = fmax(mx, fabs(row[c]));
   __shared__ double red[32];
   for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
@@ -39,8 +39,9 @@ __global__ void k_oz_slices(const double* X, int64_t ldx, int64_t p, int64_t ldp
   int e = 0;
   if (red[0] > 0.0) frexp(red[0], &e);   // red[0] = f 2^e, f in [0.5, 1)
   if (threadIdx.x == 0) expo[i] = e;
+  const double sc = ldexp(1.0, 55 - e);   // exact power of two
   for (int64_t c = threadIdx.x; c < ldp; c += blockDim.x) {
-    const double xs = c < p ? ldexp(row[c], 55 - e) : 0.0;
+    const double xs = (c >= c0 && c < c0 + ncols) ? row[c - c0] * sc : 0.0;
     long long F = __double2ll_rn(xs);
     const long long Flo = __double2ll_rn((xs - (double)F) * 16384.0);   // |Flo| <= 2^13
 #pragma unroll
@@ -132,6 +133,29 @@ struct EpiResidSq {
 
 // ------------------------------------------------------------ combine ----
 
+// 2^k for integer k in the normal range, built from the exponent field.
+__device__ __forceinline__ double pow2i(int k) {
+  k = k < -1022 ? -1022 : (k > 1023 ? 1023 : k);
+  return __longlong_as_double((long long)(k + 1023) << 52);
+}
+
+// 2^e * sum_{q <= qmax} T_q 2^{-7q} for the int32 group sums at `idx` of
+// planes `plane` apart.  The sum is formed exactly in two int64 halves
+// (groups 0..4 and 5..qmax, each below 2^59), so only the final conversion and
+// scaling round.
+__device__ __forceinline__ double oz_value(const int* T, int64_t plane, int64_t idx, int qmax, int e) {
+  long long hi = 0, lo = 0;
+#pragma unroll
+  for (int q = 0; q < 10; ++q) {
+    if (q > qmax) break;
+    const long long t = T[(int64_t)q * plane + idx];
+    if (q < 5) hi += t * (1ll << (7 * (4 - q)));
+    else lo += t * (1ll << (7 * (9 - q)));
+  }
+  // sum = hi 2^-28 + lo 2^-63
+  return (double)hi * pow2i(e - 28) + (double)lo * pow2i(e - 63);
+}
+
 // C = 2^{e_i + f_j - 12} sum_q T_q 2^{-7q};  Q = I - C (FP64, ld p);
 // sum Q^2 per CTA.
 __global__ void k_oz_combine(const int* T, int64_t p, int64_t ldp, const int* ex, const int* ea, int qmax,
@@ -142,10 +166,7 @@ __global__ void k_oz_combine(const int* T, int64_t p, int64_t ldp, const int* ex
     const int64_t i = idx / ldp, j = idx - i * ldp;
     double q = 0.0;
     if (j < p) {
-      const int64_t plane = p * ldp;
-      double acc = (double)T[(int64_t)qmax * plane + idx];
-      for (int g = qmax - 1; g >= 0; --g) acc = fma(acc, 0.0078125, (double)T[(int64_t)g * plane + idx]);
-      const double c = ldexp(acc, ex[i] + ea[j] - 12);
+      const double c = oz_value(T, p * ldp, idx, qmax, ex[i] + ea[j] - 12);
       q = (i == j ? 1.0 : 0.0) - c;
       sq = q * q;
       Q[i * p + j] = q;
@@ -182,10 +203,7 @@ __global__ void k_oz_update(const int* T, int64_t p, int64_t ldp, const int* ex,
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= p * p) return;
   const int64_t i = idx / p, j = idx - i * p;
-  const int64_t plane = p * ldp, t = i * ldp + j;
-  double acc = (double)T[(int64_t)qmax * plane + t];
-  for (int g = qmax - 1; g >= 0; --g) acc = fma(acc, 0.0078125, (double)T[(int64_t)g * plane + t]);
-  Xn[idx] = X[i * ldx + j] + ldexp(acc, ex[i] + eq[j] - 12);
+  Xn[idx] = X[i * ldx + j] + oz_value(T, p * ldp, i * ldp + j, qmax, ex[i] + eq[j] - 12);
 }
 
 __global__ void k_sym_into(const double* Xn, int64_t p, double* X, int64_t ldx) {
@@ -240,11 +258,13 @@ void refine_destroy(RefineState* R) {
 }
 
 static ibmi_status slice_digits(RefineState* R, const double* X, int64_t ldx, __nv_bfloat16* const* dst, int nslices,
-                                int* expo, cudaStream_t st) {
+                                int* expo, cudaStream_t st, int64_t rows = -1, int64_t ncols = -1, int64_t c0 = 0) {
   SlicePtrs sp;
   for (int s = 0; s < OZ_S; ++s) sp.s[s] = s < nslices ? dst[s] : nullptr;
+  if (rows < 0) rows = R->p;
+  if (ncols < 0) ncols = R->p;
   note_launch();
-  k_oz_slices<<<(unsigned)R->p, 256, 0, st>>>(X, ldx, R->p, R->ldp, sp, nslices, expo);
+  k_oz_slices<<<(unsigned)rows, 256, 0, st>>>(X, ldx, ncols, c0, R->ldp, sp, nslices, expo);
   IBMI_CUDA_TRY(cudaGetLastError());
   return IBMI_OK;
 }
@@ -271,33 +291,81 @@ static ibmi_status read_scalar(RefineState* R, cudaStream_t st, double* v) {
 }
 
 // Digit-group sums T_q = sum_{s+u=q} (slice_s of the A operand) (slice_u of the
-// B operand)^T for q <= qmax, each pair an exact FP32 accumulation over at
-// most 4096 terms, added up in int32.
-static ibmi_status pair_products(RefineState* R, const CUtensorMap* ma, int nsa, const CUtensorMap* mb, int nsb,
-                                 int qmax, cudaStream_t st) {
+// B operand)^T for q <= qmax, over the K tiles [kt0, kt1): each pair an exact
+// FP32 accumulation over at most 4096 terms, added up in int32 into the
+// M x N (ld ldp) planes of T.
+struct DigitGemm {
+  const CUtensorMap* ma; int nsa;
+  const CUtensorMap* mb; int nsb;
+  int64_t M, N;
+  int kt0, kt1;
+  int qmax;
+  int kclass;
+};
+
+static ibmi_status digit_gemm(RefineState* R, const DigitGemm& g, cudaStream_t st) {
   const int64_t p = R->p, ldp = R->ldp;
-  const int nkt = (int)((p + tc::BK - 1) / tc::BK);
   const int chunk_tiles = OZ_KCHUNK / tc::BK;
-  const int nchunks = (nkt + chunk_tiles - 1) / chunk_tiles;
-  const int grid_n = (int)((p + RF_BN - 1) / RF_BN), grid_m = (int)((p + 127) / 128);
-  for (int q = 0; q <= qmax; ++q) {
+  const int grid_n = (int)((g.N + RF_BN - 1) / RF_BN), grid_m = (int)((g.M + 127) / 128);
+  for (int q = 0; q <= g.qmax; ++q) {
     bool first = true;
     for (int s = 0; s <= q; ++s) {
       const int u = q - s;
-      if (s >= nsa || u >= nsb) continue;
+      if (s >= g.nsa || u >= g.nsb) continue;
       tc::Maps maps;
-      maps.a[0] = ma[s];
-      maps.b[0] = mb[u];
-      for (int c = 0; c < nchunks; ++c) {
-        const int k0 = c * chunk_tiles, k1 = std::min(nkt, k0 + chunk_tiles);
+      maps.a[0] = g.ma[s];
+      maps.b[0] = g.mb[u];
+      for (int k0 = g.kt0; k0 < g.kt1; k0 += chunk_tiles) {
+        const int k1 = std::min(g.kt1, k0 + chunk_tiles);
         // K tiles [k0, k1): an empty first range plus [k0, k1)
-        tc::Tiles t{p, 0, 0, grid_n, 0, 0, k0, k1, 1, R->err};
-        EpiOzAcc epi{{}, R->T + (int64_t)q * p * ldp, ldp, p, p, first ? 1 : 0};
+        tc::Tiles t{g.M, 0, 0, grid_n, 0, 0, k0, k1, 1, R->err};
+        EpiOzAcc epi{{}, R->T + (int64_t)q * p * ldp, ldp, g.M, g.N, first ? 1 : 0};
+        ProfScope ps(g.kclass, st, 2.0 * (double)g.M * g.N * (double)(k1 - k0) * tc::BK);
         IBMI_CUDA_TRY((tc::launch<1, RF_BN>(maps, t, grid_n, grid_m, epi, st)));
         first = false;
       }
     }
   }
+  return IBMI_OK;
+}
+
+static ibmi_status pair_products(RefineState* R, const CUtensorMap* ma, int nsa, const CUtensorMap* mb, int nsb,
+                                 int qmax, int kclass, cudaStream_t st) {
+  const int nkt = (int)((R->p + tc::BK - 1) / tc::BK);
+  return digit_gemm(R, DigitGemm{ma, nsa, mb, nsb, R->p, R->p, 0, nkt, qmax, kclass}, st);
+}
+
+// W = A_I^{-1} A_{I,:} from digit products, written as BF16 hi/lo (zero on
+// the columns of I and on the padding).
+__global__ void k_oz_wcombine(const int* T, int64_t m, int64_t p, int64_t ldp, const int* ea, const int* eb, int qmax,
+                              int64_t lo, int64_t hi, __nv_bfloat16* Wh, __nv_bfloat16* Wl) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= m * ldp) return;
+  const int64_t i = idx / ldp, j = idx - i * ldp;
+  float w = 0.f;
+  if (j < p && (j < lo || j >= hi)) {
+    w = (float)oz_value(T, p * ldp, idx, qmax, ea[i] + eb[j] - 12);
+  }
+  const __nv_bfloat16 h = __float2bfloat16_rn(w);
+  Wh[idx] = h;
+  Wl[idx] = __float2bfloat16_rn(w - __bfloat162float(h));
+}
+
+ibmi_status refine_form_w(RefineState* R, const double* Ainv, int64_t m, int64_t lo, int64_t hi, __nv_bfloat16* Wh,
+                          __nv_bfloat16* Wl, cudaStream_t st) {
+  const int64_t p = R->p, ldp = R->ldp;
+  constexpr int NW_A = 5, NW_B = 4, QW = 4;   // 34-bit A_I^{-1} digits, 27-bit A digits
+  {
+    ProfScope ps(IBMI_K_OTHER, st, 0.0);
+    // A_I^{-1} embedded at columns [lo, hi) of an m x p operand (digit planes borrowed from X)
+    IBMI_TRY(slice_digits(R, Ainv, m, R->Xo, NW_A, R->expX, st, m, m, lo));
+  }
+  IBMI_TRY(digit_gemm(R, DigitGemm{R->mXo, NW_A, R->mAo, NW_B, m, p, (int)(lo / tc::BK),
+                                   (int)((hi + tc::BK - 1) / tc::BK), QW, IBMI_K_INVARIANTS_TC}, st));
+  ProfScope ps(IBMI_K_OTHER, st, 0.0);
+  note_launch();
+  k_oz_wcombine<<<nblk(m * ldp), 256, 0, st>>>(R->T, m, p, ldp, R->expX, R->expA, QW, lo, hi, Wh, Wl);
+  IBMI_CUDA_TRY(cudaGetLastError());
   return IBMI_OK;
 }
 
@@ -307,10 +375,7 @@ ibmi_status refine_residual(RefineState* R, const double* X, int64_t ldx, cudaSt
     ProfScope ps(IBMI_K_OTHER, st, 0.0);
     IBMI_TRY(slice_digits(R, X, ldx, R->Xo, OZ_SX, R->expX, st));
   }
-  {
-    ProfScope ps(IBMI_K_RESIDUAL, st, 2.0 * (double)p * p * p);
-    IBMI_TRY(pair_products(R, R->mXo, OZ_SX, R->mAo, OZ_SA, OZ_QMAX, st));
-  }
+  IBMI_TRY(pair_products(R, R->mXo, OZ_SX, R->mAo, OZ_SA, OZ_QMAX, IBMI_K_RESIDUAL, st));
   {
     ProfScope ps(IBMI_K_OTHER, st, 0.0);
     const unsigned nb = nblk(p * ldp);
@@ -326,9 +391,12 @@ ibmi_status refine_residual(RefineState* R, const double* X, int64_t ldx, cudaSt
 
 ibmi_status refine_ns_update(RefineState* R, double* X, int64_t ldx, cudaStream_t st) {
   const int64_t p = R->p, ldp = R->ldp;
-  ProfScope ps(IBMI_K_NS, st, 2.0 * (double)p * p * p);
-  IBMI_TRY(slice_digits(R, R->Xn, p, R->Qo, NS_S, R->expQ, st));
-  IBMI_TRY(pair_products(R, R->mXo, NS_S, R->mQo, NS_S, NS_S - 1, st));
+  {
+    ProfScope ps(IBMI_K_OTHER, st, 0.0);
+    IBMI_TRY(slice_digits(R, R->Xn, p, R->Qo, NS_S, R->expQ, st));
+  }
+  IBMI_TRY(pair_products(R, R->mXo, NS_S, R->mQo, NS_S, NS_S - 1, IBMI_K_NS, st));
+  ProfScope ps(IBMI_K_OTHER, st, 0.0);
   note_launch();
   k_oz_update<<<nblk(p * p), 256, 0, st>>>(R->T, p, ldp, R->expX, R->expQ, NS_S - 1, X, ldx, R->Xn);
   IBMI_CUDA_TRY(cudaGetLastError());
@@ -350,10 +418,13 @@ ibmi_status refine_cheap_residual(RefineState* R, const CUtensorMap* mapH2, cuda
   const int64_t nparts = (int64_t)grid_n * grid_m * 4;
   if (nparts > R->n_partials) return IBMI_ERR_INVALID_ARG;
   {
-    ProfScope ps(IBMI_K_RESIDUAL, st, 2.0 * (double)p * p * p);
+    ProfScope ps(IBMI_K_RESIDUAL, st, 3.0 * 2.0 * (double)p * p * p);
     tc::Tiles t{p, 0, 0, grid_n, 0, 0, 0, nkt, 1, R->err};
     EpiResidSq epi{R->partials, p, 0.0};
     IBMI_CUDA_TRY((tc::launch<2, RF_BN>(maps, t, grid_n, grid_m, epi, st)));
+  }
+  {
+    ProfScope ps(IBMI_K_OTHER, st, 0.0);
     note_launch();
     k_sum_partials<<<1, 1024, 0, st>>>(R->partials, nparts, p, R->dout);
     IBMI_CUDA_TRY(cudaGetLastError());

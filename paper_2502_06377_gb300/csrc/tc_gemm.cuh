@@ -179,12 +179,17 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// Pipeline depth: when three stages fit in half of the 227 KB of shared
+// memory, two CTAs share an SM (one CTA's epilogue overlaps the other's main
+// loop); otherwise one CTA per SM with as many stages as fit.
 template <int S, int BN>
 struct Cfg {
   static constexpr uint32_t A_BYTES = BM * BK * 2;
   static constexpr uint32_t B_BYTES = BN * BK * 2;
   static constexpr uint32_t STAGE_BYTES = S * (A_BYTES + B_BYTES);
-  static constexpr int STAGES = (200 * 1024) / STAGE_BYTES >= 4 ? 4 : (200 * 1024) / STAGE_BYTES;
+  static constexpr bool TWO_PER_SM = 3 * STAGE_BYTES + 1280 <= 113 * 1024;
+  static constexpr int STAGES =
+      TWO_PER_SM ? 3 : ((200 * 1024) / STAGE_BYTES >= 4 ? 4 : (200 * 1024) / STAGE_BYTES);
   static constexpr uint32_t SMEM = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
   static constexpr uint32_t TMEM_COLS = BN < 32 ? 32 : BN;
   static_assert(STAGES >= 2, "tile too large for two stages");
@@ -192,7 +197,7 @@ struct Cfg {
 };
 
 template <int S, int BN, class Epi>
-__global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ Maps maps, const Tiles t, Epi epi) {
+__global__ void __launch_bounds__(THREADS, 2) k_tc_gemm(const __grid_constant__ Maps maps, const Tiles t, Epi epi) {
   using C = Cfg<S, BN>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
