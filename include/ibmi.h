@@ -141,6 +141,67 @@ ibmi_status ibmi_invert_host(ibmi_plan_t plan, const double* A_host, int64_t lda
 ibmi_status ibmi_residual(const double* A, int64_t lda, const double* H, int64_t ldh,
                           int64_t p, void* stream, double* out);
 
+/* ------------------------------------------------------------------------
+ * Many matrices: batched inversion and the continuous-batching server.
+ *
+ * Both run the single-matrix pipeline (Algorithm 1 with the options below) on
+ * a pool of worker threads, one CUDA stream each, so the kernels of different
+ * matrices overlap on the GPU.  A matrix of order p is padded to a size bucket
+ * (multiples of 64 up to 1024, of 128 up to 4096, of 256 beyond) by embedding
+ * it in [[A, 0], [0, I]], whose inverse is [[A^{-1}, 0], [0, I]]; one plan per
+ * bucket then serves all matrices of that bucket.  With autotune set, the
+ * partition (K in 2..4, overlap 2h of 10/20/30% of the core width) of each
+ * bucket is chosen by timing the candidates on the first matrix of the bucket
+ * (cached for the process).  Results are bitwise independent of which other
+ * matrices run at the same time: every kernel is deterministic and each
+ * matrix has its own buffers.
+ * ------------------------------------------------------------------------ */
+typedef struct ibmi_batch_opts {
+  int32_t precision;   /* IBMI_MIXED (default) or IBMI_FP64                     */
+  double tol;          /* default 1e-10 (rho_F)                                */
+  int32_t max_sweeps;  /* default 500                                          */
+  double ns_theta;     /* Newton-Schulz hand-over (mixed), default 0.5         */
+  int32_t ns_max;      /* default 8                                            */
+  int32_t workers;     /* concurrent streams, 1..64, default 8                 */
+  int32_t autotune;    /* 1 (default): tune (K, h) per size bucket              */
+} ibmi_batch_opts;
+void ibmi_batch_opts_init(ibmi_batch_opts* opts);
+
+/* Device bytes a plan with this description allocates (estimate). */
+size_t ibmi_plan_bytes(const ibmi_plan_desc* desc);
+
+/* Inverts n SPD matrices; A[i], H[i] are device pointers to p[i] x p[i]
+ * row-major FP64 matrices with leading dimensions lda[i], ldh[i].  Per-matrix
+ * results in out[i] (status, sweeps, ...).  Returns IBMI_OK when all
+ * converged, else the first failure status (NOT_CONVERGED ranks lowest).
+ * Synchronous. */
+ibmi_status ibmi_invert_batched(int32_t n, const int64_t* p, const double* const* A, const int64_t* lda,
+                                double* const* H, const int64_t* ldh, const ibmi_batch_opts* opts,
+                                ibmi_result* out);
+
+/* Continuous-batching server.  Requests (host matrices) are queued; a request
+ * is admitted when its device bytes (A, H and padded staging, 16 (p^2 + pb^2)
+ * bytes) fit in three quarters of hbm_budget beside the admitted ones (the
+ * last quarter caps the workers' plan caches); admitted requests run as soon
+ * as a worker is free, overlapping on the device with the others; finishing
+ * frees their bytes for the next ones in arrival order.  ibmi_serve_submit
+ * copies A (p x p, lda); IBMI_ERR_BUDGET if one request alone exceeds the
+ * budget.  ibmi_serve_poll returns IBMI_NOT_READY until the request is done,
+ * then copies H (ldh) and the result and forgets the request.
+ * ibmi_serve_cancel removes a queued request (IBMI_NOT_READY once it has been
+ * admitted).  ibmi_serve_stats: p50/p99 latency (submit to completion,
+ * seconds) and completion throughput over all completed requests. */
+typedef struct ibmi_server_impl* ibmi_server_t;
+ibmi_status ibmi_serve_create(size_t hbm_budget, const ibmi_batch_opts* opts, ibmi_server_t* out);
+ibmi_status ibmi_serve_submit(ibmi_server_t server, const double* A_host, int64_t p, int64_t lda, double tol,
+                              uint64_t* request);
+ibmi_status ibmi_serve_poll(ibmi_server_t server, uint64_t request, double* H_host, int64_t ldh,
+                            ibmi_result* out);
+ibmi_status ibmi_serve_cancel(ibmi_server_t server, uint64_t request);
+ibmi_status ibmi_serve_stats(ibmi_server_t server, double* p50_s, double* p99_s, double* inverses_per_s,
+                             int64_t* completed, uint64_t* bytes_in_use);
+ibmi_status ibmi_serve_destroy(ibmi_server_t server);
+
 /* Kernel profiling, for the benchmark's roofline figures.  While enabled, the
  * library records a CUDA event pair on the launching stream around every
  * launch of each kernel class below and sums their durations; it also counts

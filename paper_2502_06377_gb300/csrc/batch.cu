@@ -1,0 +1,546 @@
+// Batched inversion (many SPD matrices of uneven order) and the
+// continuous-batching request server.
+//
+// Both run on a pool of worker threads; each worker owns one CUDA stream and
+// a cache of plans keyed by (padded order, K, h), and runs the single-matrix
+// pipeline of ibmi_invert on its stream, so the kernels of different matrices
+// overlap on the GPU.  Orders are padded up to size buckets by embedding A in
+// [[A, 0], [0, I]], whose inverse is [[A^{-1}, 0], [0, I]]: one plan then
+// serves every matrix of a bucket.  The partition (K, h) of each bucket is
+// chosen by measuring candidate partitions on the first matrix of the bucket.
+#include <math.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <tuple>
+#include <unordered_map>
+#include <vector>
+
+#include "plan.cuh"
+
+namespace ibmi {
+
+// Padded order of a bucket: multiples of 64 up to 1024, of 128 up to 4096,
+// of 256 beyond.
+static int64_t bucket_of(int64_t p) {
+  const int64_t g = p <= 1024 ? 64 : (p <= 4096 ? 128 : 256);
+  return (p + g - 1) / g * g;
+}
+
+// Copies A (p x p, lda) into the top-left of Ab (pb x pb) and fills the rest
+// with the identity; H is copied back by the caller from the top-left block.
+__global__ void k_pad_embed(const double* A, int64_t lda, int64_t p, double* Ab, int64_t pb) {
+  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= pb * pb) return;
+  int64_t i = idx / pb, j = idx - i * pb;
+  Ab[idx] = (i < p && j < p) ? A[i * lda + j] : (i == j ? 1.0 : 0.0);
+}
+
+__global__ void k_unpad(const double* Hb, int64_t pb, int64_t p, double* H, int64_t ldh) {
+  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= p * p) return;
+  int64_t i = idx / p, j = idx - i * p;
+  H[i * ldh + j] = Hb[i * pb + j];
+}
+
+struct Shape {
+  int64_t p;
+  int32_t K;
+  int64_t h;
+  bool operator<(const Shape& o) const { return std::tie(p, K, h) < std::tie(o.p, o.K, o.h); }
+};
+
+// Default partition of a bucket when not tuned: ~256-row cores, 2..4 sets,
+// overlap 2h = 20% of the core.
+static Shape default_shape(int64_t pb) {
+  int32_t K = (int32_t)std::min<int64_t>(4, std::max<int64_t>(2, (pb + 255) / 256));
+  int64_t h = std::max<int64_t>(8, (int64_t)llround(0.1 * (double)pb / K));
+  return Shape{pb, K, h};
+}
+
+static ibmi_plan_desc desc_for(const Shape& s, const ibmi_batch_opts& o) {
+  ibmi_plan_desc d;
+  ibmi_plan_desc_init(&d);
+  d.p = s.p;
+  d.K = s.K;
+  d.h = s.h;
+  d.precision = o.precision;
+  d.tol = o.tol;
+  d.max_sweeps = o.max_sweeps;
+  d.check_every = 1;
+  d.ns_theta = o.precision == IBMI_MIXED ? o.ns_theta : 0.0;
+  d.ns_max = o.ns_max;
+  return d;
+}
+
+// One worker: a stream, padded staging buffers and a small plan cache.
+struct Worker {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  std::map<Shape, ibmi_plan_t> plans;
+  double* Ab = nullptr;
+  double* Hb = nullptr;
+  int64_t cap = 0;     // staging capacity in elements
+  size_t plan_bytes = 0;
+
+  ibmi_status init(int dev) {
+    device = dev;
+    cudaSetDevice(dev);
+    IBMI_CUDA_TRY(cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking));
+    return IBMI_OK;
+  }
+  void release_plans() {
+    for (auto& kv : plans) ibmi_plan_destroy(kv.second);
+    plans.clear();
+    plan_bytes = 0;
+  }
+  void destroy() {
+    cudaSetDevice(device);
+    release_plans();
+    cudaFree(Ab);
+    cudaFree(Hb);
+    if (stream) cudaStreamDestroy(stream);
+  }
+  ibmi_status staging(int64_t pb) {
+    if (pb * pb <= cap) return IBMI_OK;
+    cudaFree(Ab);
+    cudaFree(Hb);
+    Ab = Hb = nullptr;
+    cap = 0;
+    IBMI_CUDA_TRY(cudaMalloc(&Ab, sizeof(double) * pb * pb));
+    IBMI_CUDA_TRY(cudaMalloc(&Hb, sizeof(double) * pb * pb));
+    cap = pb * pb;
+    return IBMI_OK;
+  }
+  ibmi_status plan(const Shape& s, const ibmi_batch_opts& o, size_t max_plan_bytes, ibmi_plan_t* out) {
+    auto it = plans.find(s);
+    if (it != plans.end()) { *out = it->second; return IBMI_OK; }
+    ibmi_plan_desc d = desc_for(s, o);
+    const size_t need = ibmi_plan_bytes(&d);
+    if (max_plan_bytes && plan_bytes + need > max_plan_bytes) release_plans();
+    ibmi_plan_t P = nullptr;
+    IBMI_TRY(ibmi_plan(&d, &P));
+    plans[s] = P;
+    plan_bytes += need;
+    *out = P;
+    return IBMI_OK;
+  }
+  // Inverts one matrix (device A, H of order p) with the plan for `s`.
+  ibmi_status run(const Shape& s, const ibmi_batch_opts& o, size_t max_plan_bytes, const double* A, int64_t lda,
+                  int64_t p, double* H, int64_t ldh, ibmi_result* res) {
+    ibmi_plan_t P;
+    IBMI_TRY(plan(s, o, max_plan_bytes, &P));
+    const int64_t pb = s.p;
+    if (pb == p) return ibmi_invert(P, A, lda, H, ldh, stream, res);
+    IBMI_TRY(staging(pb));
+    note_launch();
+    k_pad_embed<<<(unsigned)((pb * pb + 255) / 256), 256, 0, stream>>>(A, lda, p, Ab, pb);
+    IBMI_CUDA_TRY(cudaGetLastError());
+    ibmi_status st = ibmi_invert(P, Ab, pb, Hb, pb, stream, res);
+    if (st == IBMI_OK || st == IBMI_NOT_CONVERGED) {
+      note_launch();
+      k_unpad<<<(unsigned)((p * p + 255) / 256), 256, 0, stream>>>(Hb, pb, p, H, ldh);
+      IBMI_CUDA_TRY(cudaGetLastError());
+      IBMI_CUDA_TRY(cudaStreamSynchronize(stream));
+    }
+    return st;
+  }
+};
+
+// Process-wide cache of tuned partitions per (bucket, precision).
+static std::mutex g_tune_mu;
+static std::map<std::pair<int64_t, int>, Shape> g_tuned;
+
+// Times candidate partitions of bucket pb on one matrix and keeps the fastest
+// that converges.  Candidates: K in {2, 3, 4}, 2h in {10%, 20%, 30%} of the
+// core width.
+static Shape tune_bucket(Worker& w, int64_t pb, const ibmi_batch_opts& o, const double* A, int64_t lda, int64_t p,
+                         double* H, int64_t ldh) {
+  {
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    auto it = g_tuned.find({pb, o.precision});
+    if (it != g_tuned.end()) return it->second;
+  }
+  Shape best = default_shape(pb);
+  double best_t = INFINITY;
+  for (int32_t K = 2; K <= 4; ++K) {
+    for (double f : {0.1, 0.2, 0.3}) {
+      const int64_t m = pb / K;
+      const int64_t h = std::max<int64_t>(4, (int64_t)llround(0.5 * f * (double)m));
+      if (K * m < pb / 2 || 2 * h >= m) continue;
+      Shape s{pb, K, h};
+      ibmi_result r;
+      double t = INFINITY;
+      for (int rep = 0; rep < 2; ++rep) {   // first run includes plan creation
+        auto t0 = std::chrono::steady_clock::now();
+        ibmi_status st = w.run(s, o, 0, A, lda, p, H, ldh, &r);
+        double dt = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (st != IBMI_OK) { t = INFINITY; break; }
+        t = dt;
+      }
+      if (t < best_t) { best_t = t; best = s; }
+    }
+  }
+  w.release_plans();
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  g_tuned[{pb, o.precision}] = best;
+  return best;
+}
+
+static Shape shape_for(int64_t p, const ibmi_batch_opts& o) {
+  const int64_t pb = bucket_of(p);
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  auto it = g_tuned.find({pb, o.precision});
+  if (it != g_tuned.end()) return it->second;
+  return default_shape(pb);
+}
+
+// ----------------------------------------------------------------- server --
+
+struct Request {
+  uint64_t id = 0;
+  int64_t p = 0;
+  double tol = 0.0;
+  std::vector<double> A;     // host copy of the input
+  std::vector<double> H;     // host result
+  ibmi_result res{};
+  int state = 0;             // 0 queued, 1 admitted, 2 done, 3 cancelled
+  size_t bytes = 0;          // device bytes charged while admitted
+  std::chrono::steady_clock::time_point t_submit, t_admit, t_done;
+};
+
+}  // namespace ibmi
+
+struct ibmi_server_impl {
+  ibmi_batch_opts opts{};
+  size_t budget = 0;       // total device bytes the server may hold
+  size_t req_budget = 0;   // part of it for admitted requests (the rest caps the plan caches)
+  size_t in_use = 0;
+  int device = 0;
+  std::mutex mu;
+  std::condition_variable cv;
+  bool stop = false;
+  uint64_t next_id = 1;
+  std::deque<uint64_t> queue;
+  std::unordered_map<uint64_t, std::shared_ptr<ibmi::Request>> reqs;
+  std::vector<double> latencies;     // seconds, completed requests
+  std::chrono::steady_clock::time_point t_first_done, t_last_done;
+  int64_t completed = 0;
+  std::vector<std::thread> threads;
+  std::vector<ibmi::Worker> workers;
+};
+
+namespace ibmi {
+
+static size_t request_bytes(int64_t p) {
+  // device copies of A and H plus the padded staging of one worker
+  const int64_t pb = bucket_of(p);
+  return sizeof(double) * (size_t)(2 * p * p + 2 * pb * pb);
+}
+
+static void server_loop(ibmi_server_impl* S, int wi) {
+  Worker& w = S->workers[wi];
+  cudaSetDevice(S->device);
+  double* dA = nullptr;
+  double* dH = nullptr;
+  int64_t dcap = 0;
+  while (true) {
+    std::shared_ptr<Request> r;
+    {
+      std::unique_lock<std::mutex> lk(S->mu);
+      S->cv.wait(lk, [&] {
+        if (S->stop) return true;
+        // admission: the oldest queued request whose bytes fit in the budget
+        for (uint64_t id : S->queue) {
+          auto& q = S->reqs[id];
+          if (q->state == 0 && (S->in_use + q->bytes <= S->req_budget || S->in_use == 0)) return true;
+        }
+        return false;
+      });
+      if (S->stop) break;
+      for (auto it = S->queue.begin(); it != S->queue.end(); ++it) {
+        auto& q = S->reqs[*it];
+        if (q->state == 0 && (S->in_use + q->bytes <= S->req_budget || S->in_use == 0)) {
+          r = q;
+          S->queue.erase(it);
+          break;
+        }
+      }
+      if (!r) continue;
+      r->state = 1;
+      r->t_admit = std::chrono::steady_clock::now();
+      S->in_use += r->bytes;
+    }
+    const int64_t p = r->p;
+    ibmi_status st = IBMI_OK;
+    if (p * p > dcap) {
+      cudaFree(dA);
+      cudaFree(dH);
+      dA = dH = nullptr;
+      dcap = 0;
+      if (cudaMalloc(&dA, sizeof(double) * p * p) != cudaSuccess ||
+          cudaMalloc(&dH, sizeof(double) * p * p) != cudaSuccess) {
+        cudaGetLastError();
+        st = IBMI_ERR_OOM;
+      } else {
+        dcap = p * p;
+      }
+    }
+    ibmi_batch_opts o = S->opts;
+    o.tol = r->tol;
+    if (st == IBMI_OK && cudaMemcpyAsync(dA, r->A.data(), sizeof(double) * p * p, cudaMemcpyHostToDevice,
+                                         w.stream) != cudaSuccess)
+      st = IBMI_ERR_CUDA;
+    if (st == IBMI_OK)
+      st = w.run(shape_for(p, o), o, (S->budget - S->req_budget) / S->workers.size(), dA, p, p, dH, p, &r->res);
+    if (st == IBMI_OK || st == IBMI_NOT_CONVERGED) {
+      r->H.resize((size_t)p * p);
+      if (cudaMemcpyAsync(r->H.data(), dH, sizeof(double) * p * p, cudaMemcpyDeviceToHost, w.stream) != cudaSuccess ||
+          cudaStreamSynchronize(w.stream) != cudaSuccess)
+        st = IBMI_ERR_CUDA;
+    }
+    r->res.status = st;
+    {
+      std::lock_guard<std::mutex> lk(S->mu);
+      r->t_done = std::chrono::steady_clock::now();
+      S->in_use -= r->bytes;
+      if (r->state != 3) r->state = 2;
+      std::vector<double>().swap(r->A);
+      S->latencies.push_back(std::chrono::duration<double>(r->t_done - r->t_submit).count());
+      if (S->completed == 0) S->t_first_done = r->t_done;
+      S->t_last_done = r->t_done;
+      ++S->completed;
+    }
+    S->cv.notify_all();
+  }
+  cudaFree(dA);
+  cudaFree(dH);
+}
+
+}  // namespace ibmi
+
+using namespace ibmi;
+
+extern "C" {
+
+void ibmi_batch_opts_init(ibmi_batch_opts* o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->precision = IBMI_MIXED;
+  o->tol = 1e-10;
+  o->max_sweeps = 500;
+  o->ns_theta = 0.5;
+  o->ns_max = 8;
+  o->workers = 8;
+  o->autotune = 1;
+}
+
+size_t ibmi_plan_bytes(const ibmi_plan_desc* d) {
+  if (!d || d->p < 2 || d->K < 1) return 0;
+  const double p = (double)d->p, K = (double)d->K;
+  const double m = std::min(p, p / K + 2.0 * (double)d->h);
+  double b = 8.0 * (K * m * m + m * m + p * p / 4096.0 + 64.0);              // A_I^{-1}, S, partials
+  const double ncols = d->precision == IBMI_MIXED ? m : p;
+  b += 8.0 * K * (m * m + m * ncols + 64.0 * m + 32.0 * ncols);              // batched factorisation
+  if (d->precision == IBMI_MIXED) {
+    const double ldp = ceil(p / 64.0) * 64.0;
+    b += 4.0 * p * ldp + 4.0 * p * ldp + 4.0 * K * m * ldp + 4.0 * 64.0 * m * m;   // H master + slices, W, split-K
+    b += 2.0 * p * ldp * 25.0 + 4.0 * p * ldp * 10.0 + 8.0 * p * p;           // refinement planes
+  } else {
+    b += 8.0 * K * m * p;                                                     // W
+    b += (d->ns_theta > 0.0 ? 16.0 * p * p : 0.0);
+  }
+  return (size_t)b;
+}
+
+ibmi_status ibmi_invert_batched(int32_t n, const int64_t* p, const double* const* A, const int64_t* lda,
+                                double* const* H, const int64_t* ldh, const ibmi_batch_opts* opts,
+                                ibmi_result* out) {
+  if (n < 0 || (n > 0 && (!p || !A || !H || !lda || !ldh || !out))) return IBMI_ERR_INVALID_ARG;
+  ibmi_batch_opts o;
+  if (opts) o = *opts; else ibmi_batch_opts_init(&o);
+  if (o.workers < 1 || o.workers > 64 || (o.precision != IBMI_FP64 && o.precision != IBMI_MIXED))
+    return IBMI_ERR_INVALID_ARG;
+  for (int32_t i = 0; i < n; ++i)
+    if (p[i] < 2 || lda[i] < p[i] || ldh[i] < p[i] || !A[i] || !H[i]) return IBMI_ERR_INVALID_ARG;
+  if (n == 0) return IBMI_OK;
+  int dev = 0;
+  IBMI_CUDA_TRY(cudaGetDevice(&dev));
+  const int W = std::min<int>(o.workers, n);
+  std::vector<Worker> workers(W);
+  for (auto& w : workers) IBMI_TRY(w.init(dev));
+  // largest matrices first: better balance across workers
+  std::vector<int32_t> order(n);
+  for (int32_t i = 0; i < n; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return p[a] > p[b]; });
+  // autotune: first matrix of each untuned bucket, in parallel across workers
+  if (o.autotune) {
+    std::vector<int32_t> firsts;
+    std::map<int64_t, bool> seen;
+    for (int32_t i : order) {
+      const int64_t pb = bucket_of(p[i]);
+      if (seen.count(pb)) continue;
+      seen[pb] = true;
+      std::lock_guard<std::mutex> g(g_tune_mu);
+      if (!g_tuned.count({pb, o.precision})) firsts.push_back(i);
+    }
+    std::atomic<int> next{0};
+    std::vector<std::thread> th;
+    for (int wi = 0; wi < W; ++wi)
+      th.emplace_back([&, wi] {
+        cudaSetDevice(dev);
+        for (int j; (j = next.fetch_add(1)) < (int)firsts.size();) {
+          const int32_t i = firsts[j];
+          tune_bucket(workers[wi], bucket_of(p[i]), o, A[i], lda[i], p[i], H[i], ldh[i]);
+        }
+      });
+    for (auto& t : th) t.join();
+  }
+  std::atomic<int> next{0};
+  std::vector<ibmi_status> st(n, IBMI_OK);
+  std::vector<std::thread> th;
+  for (int wi = 0; wi < W; ++wi)
+    th.emplace_back([&, wi] {
+      cudaSetDevice(dev);
+      Worker& w = workers[wi];
+      for (int j; (j = next.fetch_add(1)) < n;) {
+        const int32_t i = order[j];
+        memset(&out[i], 0, sizeof(ibmi_result));
+        st[i] = w.run(shape_for(p[i], o), o, 0, A[i], lda[i], p[i], H[i], ldh[i], &out[i]);
+        out[i].status = st[i];
+      }
+    });
+  for (auto& t : th) t.join();
+  for (auto& w : workers) w.destroy();
+  ibmi_status worst = IBMI_OK;
+  for (int32_t i = 0; i < n; ++i)
+    if (st[i] != IBMI_OK && (worst == IBMI_OK || worst == IBMI_NOT_CONVERGED)) worst = st[i];
+  return worst;
+}
+
+ibmi_status ibmi_serve_create(size_t hbm_budget, const ibmi_batch_opts* opts, ibmi_server_t* out) {
+  if (!out || hbm_budget == 0) return IBMI_ERR_INVALID_ARG;
+  auto* S = new ibmi_server_impl();
+  if (opts) S->opts = *opts; else ibmi_batch_opts_init(&S->opts);
+  if (S->opts.workers < 1 || S->opts.workers > 64) { delete S; return IBMI_ERR_INVALID_ARG; }
+  S->budget = hbm_budget;
+  S->req_budget = hbm_budget - hbm_budget / 4;
+  cudaGetDevice(&S->device);
+  S->workers.resize(S->opts.workers);
+  for (auto& w : S->workers) {
+    if (w.init(S->device) != IBMI_OK) {
+      for (auto& x : S->workers) x.destroy();
+      delete S;
+      return IBMI_ERR_CUDA;
+    }
+  }
+  for (int i = 0; i < S->opts.workers; ++i) S->threads.emplace_back(server_loop, S, i);
+  *out = (ibmi_server_t)S;
+  return IBMI_OK;
+}
+
+ibmi_status ibmi_serve_submit(ibmi_server_t h, const double* A_host, int64_t p, int64_t lda, double tol,
+                              uint64_t* req) {
+  auto* S = (ibmi_server_impl*)h;
+  if (!S || !A_host || !req || p < 2 || lda < p || !(tol >= 0.0)) return IBMI_ERR_INVALID_ARG;
+  auto r = std::make_shared<Request>();
+  r->p = p;
+  r->tol = tol;
+  r->bytes = request_bytes(p);
+  if (r->bytes > S->req_budget) return IBMI_ERR_BUDGET;
+  r->A.resize((size_t)p * p);
+  for (int64_t i = 0; i < p; ++i) memcpy(&r->A[(size_t)i * p], A_host + i * lda, sizeof(double) * p);
+  r->t_submit = std::chrono::steady_clock::now();
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    r->id = S->next_id++;
+    S->reqs[r->id] = r;
+    S->queue.push_back(r->id);
+    *req = r->id;
+  }
+  S->cv.notify_all();
+  return IBMI_OK;
+}
+
+ibmi_status ibmi_serve_poll(ibmi_server_t h, uint64_t req, double* H_host, int64_t ldh, ibmi_result* res) {
+  auto* S = (ibmi_server_impl*)h;
+  if (!S) return IBMI_ERR_INVALID_ARG;
+  std::shared_ptr<Request> r;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    auto it = S->reqs.find(req);
+    if (it == S->reqs.end()) return IBMI_ERR_INVALID_ARG;
+    r = it->second;
+    if (r->state == 3) { S->reqs.erase(it); return IBMI_ERR_CANCELLED; }
+    if (r->state != 2) return IBMI_NOT_READY;
+    S->reqs.erase(it);
+  }
+  if (res) *res = r->res;
+  if (H_host && !r->H.empty()) {
+    if (ldh < r->p) return IBMI_ERR_INVALID_ARG;
+    for (int64_t i = 0; i < r->p; ++i) memcpy(H_host + i * ldh, &r->H[(size_t)i * r->p], sizeof(double) * r->p);
+  }
+  return (ibmi_status)r->res.status;
+}
+
+ibmi_status ibmi_serve_cancel(ibmi_server_t h, uint64_t req) {
+  auto* S = (ibmi_server_impl*)h;
+  if (!S) return IBMI_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(S->mu);
+  auto it = S->reqs.find(req);
+  if (it == S->reqs.end()) return IBMI_ERR_INVALID_ARG;
+  auto& r = it->second;
+  if (r->state == 0) {
+    S->queue.erase(std::remove(S->queue.begin(), S->queue.end(), req), S->queue.end());
+    r->state = 3;
+    return IBMI_OK;
+  }
+  return r->state == 3 ? IBMI_OK : IBMI_NOT_READY;   // admitted or finished: runs to completion
+}
+
+ibmi_status ibmi_serve_stats(ibmi_server_t h, double* p50, double* p99, double* inv_per_s, int64_t* completed,
+                             uint64_t* bytes_in_use) {
+  auto* S = (ibmi_server_impl*)h;
+  if (!S) return IBMI_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(S->mu);
+  std::vector<double> l = S->latencies;
+  std::sort(l.begin(), l.end());
+  auto pct = [&](double q) {
+    if (l.empty()) return (double)NAN;
+    size_t i = (size_t)std::min<double>((double)l.size() - 1, floor(q * (double)(l.size() - 1) + 0.5));
+    return l[i];
+  };
+  if (p50) *p50 = pct(0.50);
+  if (p99) *p99 = pct(0.99);
+  if (inv_per_s) {
+    const double span = std::chrono::duration<double>(S->t_last_done - S->t_first_done).count();
+    *inv_per_s = (S->completed > 1 && span > 0) ? (double)(S->completed - 1) / span : NAN;
+  }
+  if (completed) *completed = S->completed;
+  if (bytes_in_use) *bytes_in_use = S->in_use;
+  return IBMI_OK;
+}
+
+ibmi_status ibmi_serve_destroy(ibmi_server_t h) {
+  auto* S = (ibmi_server_impl*)h;
+  if (!S) return IBMI_ERR_INVALID_ARG;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->stop = true;
+  }
+  S->cv.notify_all();
+  for (auto& t : S->threads) t.join();
+  for (auto& w : S->workers) w.destroy();
+  delete S;
+  return IBMI_OK;
+}
+
+}  // extern "C"

@@ -488,6 +488,7 @@ const char* ibmi_last_error(void) { return g_last_error.c_str(); }
 
 // ------------------------------------------------------------- profiling --
 #include <atomic>
+#include <mutex>
 namespace ibmi {
 namespace {
 struct ProfClass {
@@ -496,12 +497,13 @@ struct ProfClass {
   double flops = 0.0;
   double ms = 0.0;
 };
-bool g_prof_on = false;
+std::atomic<bool> g_prof_on{false};
+std::mutex g_prof_mu;                    // guards g_prof and the event pool
 ProfClass g_prof[IBMI_K_COUNT];
 std::vector<cudaEvent_t> g_event_pool;
 std::atomic<int64_t> g_launches{0};
-int g_open_class = -1;
-cudaEvent_t g_open_event = nullptr;
+thread_local int g_open_class = -1;      // scopes are per thread (one stream each)
+thread_local cudaEvent_t g_open_event = nullptr;
 
 cudaEvent_t take_event() {
   if (!g_event_pool.empty()) {
@@ -518,14 +520,16 @@ cudaEvent_t take_event() {
 void note_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 void prof_begin(int k, cudaStream_t st) {
-  if (!g_prof_on || k < 0 || k >= IBMI_K_COUNT) return;
+  if (!g_prof_on.load(std::memory_order_relaxed) || k < 0 || k >= IBMI_K_COUNT) return;
+  std::lock_guard<std::mutex> g(g_prof_mu);
   g_open_class = k;
   g_open_event = take_event();
   cudaEventRecord(g_open_event, st);
 }
 
 void prof_end(int k, cudaStream_t st, double flops) {
-  if (!g_prof_on || k != g_open_class || !g_open_event) return;
+  if (!g_prof_on.load(std::memory_order_relaxed) || k != g_open_class || !g_open_event) return;
+  std::lock_guard<std::mutex> g(g_prof_mu);
   cudaEvent_t e = take_event();
   cudaEventRecord(e, st);
   g_prof[k].ev.emplace_back(g_open_event, e);
@@ -539,6 +543,7 @@ void prof_end(int k, cudaStream_t st, double flops) {
 extern "C" {
 void ibmi_prof_enable(int on) {
   using namespace ibmi;
+  std::lock_guard<std::mutex> g(g_prof_mu);
   for (auto& c : g_prof) {
     for (auto& pr : c.ev) {
       cudaEventSynchronize(pr.second);
@@ -548,12 +553,13 @@ void ibmi_prof_enable(int on) {
     c = ProfClass();
   }
   g_launches.store(0);
-  g_prof_on = on != 0;
+  g_prof_on.store(on != 0);
 }
 
 ibmi_status ibmi_prof_get(int32_t k, int64_t* launches, double* ms, double* flops) {
   using namespace ibmi;
   if (k < 0 || k >= IBMI_K_COUNT) return IBMI_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> g(g_prof_mu);
   ProfClass& c = g_prof[k];
   for (auto& pr : c.ev) {
     float t = 0.f;

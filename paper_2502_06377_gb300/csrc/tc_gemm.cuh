@@ -20,6 +20,8 @@
 #include <cuda.h>
 #include <cuda_bf16.h>
 
+#include <atomic>
+
 #include "common.cuh"
 
 namespace ibmi {
@@ -340,12 +342,12 @@ inline TileRanges complement_tiles(int64_t lo, int64_t hi, int64_t p, int tile) 
 template <int S, int BN, class Epi>
 cudaError_t launch(const Maps& maps, const Tiles& t, int grid_n, int grid_m, const Epi& epi, cudaStream_t st) {
   using C = Cfg<S, BN>;
-  static bool attr_set = false;
-  if (!attr_set) {
+  static std::atomic<bool> attr_set{false};
+  if (!attr_set.load(std::memory_order_acquire)) {
     cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<S, BN, Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)C::SMEM);
     if (e != cudaSuccess) return e;
-    attr_set = true;
+    attr_set.store(true, std::memory_order_release);
   }
   if (grid_n <= 0 || grid_m <= 0) return cudaSuccess;
   note_launch();
