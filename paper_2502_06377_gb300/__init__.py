@@ -137,3 +137,92 @@ def ibmi_refine(A, X, precision=IBMI_MIXED, tol=1e-10, ns_max=8, stream=None):
     s = _lib.load().ibmi_refine(C.c_void_p(A.data_ptr()), A.stride(0), C.c_void_p(X.data_ptr()), X.stride(0),
                                 A.shape[0], precision, tol, ns_max, _stream_ptr(stream), C.byref(res))
     return s, res.as_dict()
+
+
+# ----------------------------------------------------------------- batches --
+
+from ._lib import ibmi_batch_opts  # noqa: E402
+
+IBMI_NOT_READY = _lib.IBMI_NOT_READY
+IBMI_ERR_CANCELLED = _lib.IBMI_ERR_CANCELLED
+IBMI_ERR_BUDGET = _lib.IBMI_ERR_BUDGET
+
+
+def ibmi_batch_opts_init(**kw) -> ibmi_batch_opts:
+    o = ibmi_batch_opts()
+    _lib.load().ibmi_batch_opts_init(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def ibmi_plan_bytes(p: int, K: int = 2, h: int = 0, **kw) -> int:
+    return _lib.load().ibmi_plan_bytes(C.byref(ibmi_plan_desc_init(p=p, K=K, h=h, **kw)))
+
+
+def ibmi_invert_batched(As, Hs, **opts):
+    """As, Hs: lists of torch float64 CUDA tensors (square, row stride >= p).
+    Returns (status, [result dict per matrix])."""
+    n = len(As)
+    P = (C.c_int64 * n)(*[a.shape[0] for a in As])
+    LA = (C.c_int64 * n)(*[a.stride(0) for a in As])
+    LH = (C.c_int64 * n)(*[h.stride(0) for h in Hs])
+    PA = (C.c_void_p * n)(*[a.data_ptr() for a in As])
+    PH = (C.c_void_p * n)(*[h.data_ptr() for h in Hs])
+    out = (ibmi_result * n)()
+    o = ibmi_batch_opts_init(**opts)
+    s = _lib.load().ibmi_invert_batched(n, P, PA, LA, PH, LH, C.byref(o), out)
+    return s, [out[i].as_dict() for i in range(n)]
+
+
+class Server:
+    """Continuous-batching inversion server (ibmi_serve_*)."""
+
+    def __init__(self, hbm_budget_bytes: int, **opts):
+        self._lib = _lib.load()
+        self._opts = ibmi_batch_opts_init(**opts)
+        h = C.c_void_p()
+        s = self._lib.ibmi_serve_create(int(hbm_budget_bytes), C.byref(self._opts), C.byref(h))
+        if s != IBMI_OK:
+            raise IbmiError(s, "ibmi_serve_create")
+        self.handle = h
+
+    def submit(self, A: np.ndarray, tol: float = 1e-10) -> int:
+        A = np.ascontiguousarray(A, dtype=np.float64)
+        rid = C.c_uint64()
+        s = self._lib.ibmi_serve_submit(self.handle, C.c_void_p(A.ctypes.data), A.shape[0], A.shape[1], tol,
+                                        C.byref(rid))
+        if s != IBMI_OK:
+            raise IbmiError(s, "ibmi_serve_submit")
+        return rid.value
+
+    def poll(self, rid: int, p: int):
+        """Returns (status, H or None, result dict)."""
+        H = np.empty((p, p), dtype=np.float64)
+        res = ibmi_result()
+        s = self._lib.ibmi_serve_poll(self.handle, rid, C.c_void_p(H.ctypes.data), p, C.byref(res))
+        if s == IBMI_NOT_READY or s == IBMI_ERR_CANCELLED:
+            return s, None, None
+        return s, H, res.as_dict()
+
+    def cancel(self, rid: int) -> int:
+        return self._lib.ibmi_serve_cancel(self.handle, rid)
+
+    def stats(self):
+        p50, p99, ips = C.c_double(), C.c_double(), C.c_double()
+        n, used = C.c_int64(), C.c_uint64()
+        self._lib.ibmi_serve_stats(self.handle, C.byref(p50), C.byref(p99), C.byref(ips), C.byref(n),
+                                   C.byref(used))
+        return {"p50_s": p50.value, "p99_s": p99.value, "inverses_per_s": ips.value, "completed": n.value,
+                "bytes_in_use": used.value}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self._lib.ibmi_serve_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -97,3 +97,26 @@ def load(path: str = LIB_PATH) -> C.CDLL:
 
 def exported_symbols():
     return list(_SIGS)
+
+
+class ibmi_batch_opts(C.Structure):
+    _fields_ = [
+        ("precision", C.c_int32), ("tol", C.c_double), ("max_sweeps", C.c_int32),
+        ("ns_theta", C.c_double), ("ns_max", C.c_int32), ("workers", C.c_int32), ("autotune", C.c_int32),
+    ]
+
+
+_SIGS.update({
+    "ibmi_batch_opts_init": (None, [C.POINTER(ibmi_batch_opts)]),
+    "ibmi_plan_bytes": (C.c_size_t, [C.POINTER(ibmi_plan_desc)]),
+    "ibmi_invert_batched": (C.c_int, [C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_void_p),
+                                      C.POINTER(C.c_int64), C.POINTER(C.c_void_p), C.POINTER(C.c_int64),
+                                      C.POINTER(ibmi_batch_opts), C.POINTER(ibmi_result)]),
+    "ibmi_serve_create": (C.c_int, [C.c_size_t, C.POINTER(ibmi_batch_opts), C.POINTER(C.c_void_p)]),
+    "ibmi_serve_submit": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_double,
+                                    C.POINTER(C.c_uint64)]),
+    "ibmi_serve_poll": (C.c_int, [C.c_void_p, C.c_uint64, C.c_void_p, C.c_int64, C.POINTER(ibmi_result)]),
+    "ibmi_serve_cancel": (C.c_int, [C.c_void_p, C.c_uint64]),
+    "ibmi_serve_stats": (C.c_int, [C.c_void_p, _D, _D, _D, C.POINTER(C.c_int64), C.POINTER(C.c_uint64)]),
+    "ibmi_serve_destroy": (C.c_int, [C.c_void_p]),
+})

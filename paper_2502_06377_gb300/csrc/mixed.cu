@@ -285,7 +285,8 @@ ibmi_status mixed_run(ibmi_plan_s* P, const double* A, int64_t lda, double* H, i
   for (int k = 0; k < K; ++k)
     IBMI_TRY(refine_form_w(R, P->ainv[k], P->hi[k] - P->lo[k], P->lo[k], P->hi[k], M->Ws[0][k], M->Ws[1][k], st));
   IBMI_TRY(mixed_prepare(P, H, ldh, st));
-  int r = 0;
+  int r = 0, stalled = 0;
+  double best = INFINITY;
   while (true) {
     ++r;
     for (int k = 0; k < K; ++k) IBMI_TRY(mixed_sweep_step(P, k, st));
@@ -298,6 +299,13 @@ ibmi_status mixed_run(ibmi_plan_s* P, const double* A, int64_t lda, double* H, i
     res->resid_f = rho;
     if (!isfinite(rho)) return IBMI_ERR_NONFINITE;
     if (d.ns_theta > 0.0 && rho * sqrtp <= d.ns_theta) break;
+    // The BF16x3 sweep has an accuracy floor of about kappa(A) * 1e-5 in rho;
+    // when the residual stops falling (three checks without a 5% gain) the
+    // Frobenius test may never pass although ||I - A H||_2 < 1 already holds,
+    // so the Newton-Schulz tail is tried (it stops if a step does not help).
+    stalled = rho > 0.95 * best ? stalled + 1 : 0;
+    best = fmin(best, rho);
+    if (d.ns_theta > 0.0 && stalled >= 3 && rho < 1.0) break;
     if (rho <= d.tol || r >= d.max_sweeps) {
       // BF16x3 cannot certify tol: confirm with the FP64-accurate residual
       IBMI_TRY(mixed_export(P, H, ldh, st));

@@ -73,3 +73,20 @@ def test_invalid_explicit_sets(lib, lo, hi):
     with pytest.raises(ibmi.IbmiError) as e:
         ibmi.ibmi_plan(100, lo=lo, hi=hi)
     assert e.value.status == ibmi.IBMI_ERR_INVALID_ARG
+
+
+def test_batch_opts_and_plan_bytes(lib):
+    import paper_2502_06377_gb300 as ibmi
+    o = ibmi.ibmi_batch_opts_init()
+    assert o.workers == 8 and o.autotune == 1 and o.tol == 1e-10 and o.precision == ibmi.IBMI_MIXED
+    b = [ibmi.ibmi_plan_bytes(p, 4, 16, precision=ibmi.IBMI_MIXED) for p in (256, 1024, 4096)]
+    assert b[0] < b[1] < b[2]
+    assert ibmi.ibmi_plan_bytes(1) == 0
+
+
+def test_batched_and_server_reject_invalid_without_gpu(lib):
+    import ctypes as C
+    assert lib.ibmi_invert_batched(-1, None, None, None, None, None, None, None) == 1
+    h = C.c_void_p()
+    assert lib.ibmi_serve_create(0, None, C.byref(h)) == 1
+    assert lib.ibmi_serve_poll(None, 1, None, 0, None) == 1

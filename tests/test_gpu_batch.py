@@ -1,0 +1,166 @@
+"""Batched inversion and the continuous-batching server vs the FP64 oracle.
+
+Matrices whose condition number puts the FP64 floor of ||I - A H||_F/sqrt(p)
+(about eps_64 * kappa) above the 1e-10 tolerance cannot reach it in any FP64
+arithmetic -- the oracle's Newton-Schulz tail stalls there too.  For those the
+check is that the GPU reaches the oracle's own final residual within 5x.
+"""
+import threading
+import time
+
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import ibmi_oracle as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ibmi():
+    import __graft_entry__ as g
+    g.build()
+    import paper_2502_06377_gb300 as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def batch():
+    mats = wl.c4_batch(n=16, seed=40, p_max=512)
+    mats += [wl.matern32(wl.uniform_points(np.random.default_rng(s), p, 2), 0.1, 1.0, 1e-2)
+             for s, p in [(1, 100), (2, 250), (3, 333)]]          # orders off the 64-grid
+    refs = []
+    for A in mats:
+        p = A.shape[0]
+        K = 2 if p <= 256 else 3
+        h = max(4, round(0.1 * (p // K)))
+        refs.append(O.ibmi(A, O.partition(p, K, h), tol=1e-10, max_sweeps=300, ns_theta=0.5))
+    return mats, refs
+
+
+def _run_batched(ibmi, mats, **opts):
+    As = [torch.from_numpy(A).cuda() for A in mats]
+    Hs = [torch.empty_like(a) for a in As]
+    s, res = ibmi.ibmi_invert_batched(As, Hs, **opts)
+    torch.cuda.synchronize()
+    return s, res, [h.cpu().numpy() for h in Hs]
+
+
+def _check(A, H, res, ref):
+    rf = O.residual_f(A, H)
+    if ref.status == "converged":
+        assert rf <= 1e-10, (A.shape, rf, res)
+        inv = np.linalg.inv(A)
+        assert np.abs(H - inv).max() <= 1e-6 * np.abs(inv).max()
+    else:
+        assert rf <= max(1e-10, 5 * ref.resid_f), (A.shape, rf, ref.resid_f, res)
+    assert np.array_equal(H, H.T)
+
+
+def test_batched_mixed_vs_oracle(ibmi, batch):
+    mats, refs = batch
+    s, res, Hs = _run_batched(ibmi, mats, workers=8)
+    for A, H, r, ref in zip(mats, Hs, res, refs):
+        _check(A, H, r, ref)
+        if ref.status == "converged":
+            assert r["status"] == ibmi.IBMI_OK
+
+
+def test_batched_alone_equals_in_mix(ibmi, batch):
+    """Each result is the same whether the matrix runs alone or among others."""
+    mats, _ = batch
+    _, _, H8 = _run_batched(ibmi, mats, workers=8)
+    for i in (0, 5, 17):
+        _, _, H1 = _run_batched(ibmi, [mats[i]], workers=1)
+        assert np.array_equal(H1[0], H8[i])
+
+
+def test_batched_fp64(ibmi, batch):
+    mats, refs = batch
+    sel = [i for i, r in enumerate(refs) if r.status == "converged"][:4]
+    s, res, Hs = _run_batched(ibmi, [mats[i] for i in sel], workers=4, precision=ibmi.IBMI_FP64, autotune=0)
+    for i, H, r in zip(sel, Hs, res):
+        assert r["status"] == ibmi.IBMI_OK
+        assert O.residual_f(mats[i], H) <= 1e-10
+
+
+def test_batched_empty_and_invalid(ibmi):
+    s, res = ibmi.ibmi_invert_batched([], [])
+    assert s == ibmi.IBMI_OK and res == []
+
+
+def test_serve_results_alone_and_in_mix(ibmi, batch):
+    mats, refs = batch
+    srv = ibmi.Server(8 << 30, workers=6)
+    rid = srv.submit(mats[3])
+    while True:
+        st, H_alone, r = srv.poll(rid, mats[3].shape[0])
+        if st != ibmi.IBMI_NOT_READY:
+            break
+        time.sleep(0.002)
+    ids = [(i, srv.submit(A)) for i, A in enumerate(mats)]
+    out = {}
+    t_end = time.time() + 120
+    while len(out) < len(ids) and time.time() < t_end:
+        for i, rid in ids:
+            if i in out:
+                continue
+            st, H, r = srv.poll(rid, mats[i].shape[0])
+            if st != ibmi.IBMI_NOT_READY:
+                out[i] = (st, H, r)
+        time.sleep(0.002)
+    stats = srv.stats()
+    srv.close()
+    assert len(out) == len(ids)
+    assert np.array_equal(out[3][1], H_alone)
+    for i, (st, H, r) in out.items():
+        _check(mats[i], H, r, refs[i])
+    assert stats["completed"] == len(ids) + 1 and stats["p99_s"] >= stats["p50_s"] > 0
+
+
+def test_serve_admission_respects_budget(ibmi, batch):
+    mats, _ = batch
+    p = 512
+    per_req = 16 * (p * p + p * p)              # bytes charged per request of order 512
+    budget = int(per_req * 2.5 / 0.75)          # room for two admitted requests
+    srv = ibmi.Server(budget, workers=8)
+    big = [A for A in mats if A.shape[0] == p][:1] * 8
+    if not big:
+        pytest.skip("no p = 512 matrix in the batch")
+    ids = [srv.submit(A) for A in big]
+    peak = 0
+    done = set()
+    t_end = time.time() + 120
+    while len(done) < len(ids) and time.time() < t_end:
+        peak = max(peak, srv.stats()["bytes_in_use"])
+        for rid in ids:
+            if rid not in done and srv.poll(rid, p)[0] != ibmi.IBMI_NOT_READY:
+                done.add(rid)
+        time.sleep(0.0005)
+    srv.close()
+    assert len(done) == len(ids)
+    assert peak <= 2 * per_req
+
+
+def test_serve_cancel_and_budget_reject(ibmi, batch):
+    mats, _ = batch
+    srv = ibmi.Server(64 << 20, workers=1)    # 64 MB: one small request at a time
+    with pytest.raises(ibmi.IbmiError) as e:
+        srv.submit(np.eye(2048))                # 2048^2 * 32 bytes > budget
+    assert e.value.status == ibmi.IBMI_ERR_BUDGET
+    small = [A for A in mats if A.shape[0] <= 256][:4]
+    ids = [srv.submit(A) for A in small]
+    assert srv.cancel(ids[-1]) in (ibmi.IBMI_OK, ibmi.IBMI_NOT_READY)
+    t_end = time.time() + 60
+    pending = set(ids)
+    while pending and time.time() < t_end:
+        for rid, A in zip(ids, small):
+            if rid in pending:
+                st, H, r = srv.poll(rid, A.shape[0])
+                if st != ibmi.IBMI_NOT_READY:
+                    pending.discard(rid)
+        time.sleep(0.002)
+    srv.close()
+    assert not pending
