@@ -231,6 +231,25 @@ ibmi_status ibmi_prof_get(int32_t kernel_class, int64_t* launches, double* ms, d
  * (counted whether or not profiling is on). */
 int64_t ibmi_launch_count(void);
 
+/* ibmi_residual without any device allocation.  The paper has no counterpart:
+ * this entry exists for callers that cannot call cudaMalloc -- code running
+ * under an external manager that owns the device memory budget (a serving
+ * process with hard admission limits) or a latency-critical loop in which an
+ * allocation, and the device synchronisation it can imply, is not allowed.
+ * Same arguments, result and meaning as ibmi_residual (FP64 DFMA,
+ * rho_F = ||I - A H||_F / sqrt(p) written to *out), same kernels.
+ * Scratch: a fixed array of 16,386 doubles (about 128 KB) inside the library,
+ * held on every GPU that loads the library until the process exits; it limits
+ * the order to p <= 8192 -- larger p returns IBMI_ERR_INVALID_ARG with a
+ * message in ibmi_last_error().  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress); make that first call before
+ * any stream capture.  Every call reuses the same array (each call writes all
+ * the partial sums it reads, so nothing has to start at zero): calls that can
+ * overlap on the GPU -- on different streams or from different host threads --
+ * race on it and must be serialised by the caller.  Synchronises `stream`. */
+ibmi_status ibmi_residual_noalloc(const double* A, int64_t lda, const double* H, int64_t ldh, int64_t p,
+                                  void* stream, double* out);
+
 /* Newton-Schulz tail of the method on its own (eq. newton): refines a
  * symmetric approximate inverse X of the SPD matrix A in place,
  *     X <- sym(X + X (I - A X)),

@@ -121,6 +121,16 @@ def ibmi_status_string(s: int) -> str:
     return _lib.load().ibmi_status_string(s).decode()
 
 
+def ibmi_residual_noalloc(A, H, stream=None) -> float:
+    """ibmi_residual without device allocation (fixed library scratch, p <= 8192)."""
+    out = C.c_double()
+    s = _lib.load().ibmi_residual_noalloc(C.c_void_p(A.data_ptr()), A.stride(0), C.c_void_p(H.data_ptr()),
+                                          H.stride(0), A.shape[0], _stream_ptr(stream), C.byref(out))
+    if s != IBMI_OK:
+        raise IbmiError(s, "ibmi_residual_noalloc")
+    return out.value
+
+
 def ibmi_residual_tc(A, H, stream=None) -> float:
     """FP64-accurate ||I - A H||_F / sqrt(p) on tensor cores (sliced error-free products)."""
     out = C.c_double()
