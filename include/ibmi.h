@@ -63,7 +63,8 @@ typedef enum ibmi_precision {
 
 typedef enum ibmi_stop_rule {
   IBMI_STOP_RESID_F = 0,    /* ||I - A H||_F / sqrt(p) <= tol                       */
-  IBMI_STOP_PAPER_EST = 1   /* eq. error on the last set, ||(H A)_{I_K, I_K^c}||_2 <= tol */
+  IBMI_STOP_PAPER_EST = 1   /* eq. error on the last set, ||(H A)_{I_K, I_K^c}||_2 <= tol
+                               (FP64 path only; the residual is evaluated once at the end) */
 } ibmi_stop_rule;
 
 typedef enum ibmi_init {

@@ -128,6 +128,22 @@ static ibmi_status invert_impl(ibmi_plan_s* P, const double* A, int64_t lda, dou
     flops += fs;
     res->sweeps = r;
     if (r % d.check_every != 0 && r < d.max_sweeps) continue;
+    if (d.stop_rule == IBMI_STOP_PAPER_EST) {
+      // eq. error on the last set; the residual is evaluated once at the end
+      double e;
+      IBMI_TRY(paper_estimate_f64(P, A, lda, H, ldh, st, &e));
+      res->paper_est = e;
+      if (!isfinite(e)) { status = IBMI_ERR_NONFINITE; break; }
+      if (e <= d.tol || r >= d.max_sweeps) {
+        double rho;
+        IBMI_TRY(residual_host(P, A, lda, H, ldh, st, &rho));
+        flops += fr;
+        res->resid_f = rho;
+        status = e <= d.tol ? IBMI_OK : IBMI_NOT_CONVERGED;
+        break;
+      }
+      continue;
+    }
     double rho;
     IBMI_TRY(residual_host(P, A, lda, H, ldh, st, &rho));
     flops += fr;
@@ -188,7 +204,10 @@ ibmi_status ibmi_plan(const ibmi_plan_desc* desc, ibmi_plan_t* out) {
   if (d.p > (int64_t)1 << 20) return IBMI_ERR_INVALID_ARG;
   if (d.precision != IBMI_FP64 && d.precision != IBMI_MIXED) return IBMI_ERR_INVALID_ARG;
   if (d.stop_rule != IBMI_STOP_RESID_F && d.stop_rule != IBMI_STOP_PAPER_EST) return IBMI_ERR_INVALID_ARG;
-  if (d.stop_rule == IBMI_STOP_PAPER_EST) return IBMI_ERR_INVALID_ARG;  // not offered by this build
+  if (d.stop_rule == IBMI_STOP_PAPER_EST && d.precision == IBMI_MIXED) {
+    set_last_error("the paper's estimate is offered as stop rule on the FP64 path only");
+    return IBMI_ERR_INVALID_ARG;
+  }
   if (d.init != IBMI_INIT_IDENTITY && d.init != IBMI_INIT_USER) return IBMI_ERR_INVALID_ARG;
   if (d.precision == IBMI_MIXED && d.K < 2) return IBMI_ERR_INVALID_ARG;   // nothing to sweep
   if (d.max_sweeps < 1 || d.check_every < 1 || d.ns_max < 0 || !(d.tol >= 0.0) || !(d.ns_theta >= 0.0))
@@ -284,6 +303,7 @@ ibmi_status ibmi_plan_destroy(ibmi_plan_t P) {
   cudaFree(P->dstatus);
   cudaFree(P->nsR);
   cudaFree(P->nsX);
+  cudaFree(P->pe);
   cudaFree(P->dA);
   cudaFree(P->dH);
   delete P;

@@ -303,6 +303,97 @@ ibmi_status ns_step_f64(ibmi_plan_s* P, const double* A, int64_t lda, double* X,
   return IBMI_OK;
 }
 
+// ------------------------------------------------- paper's estimate ----
+//
+// eq. error for the set I = [lo, hi): B = (H A)[I, I^c] (the (1,2) block of
+// H A, i.e. H_I A_{I,I^c} + H_{I,I^c} A_{I^c}) and its spectral norm by power
+// iteration on B^T B.
+
+struct EpiStoreB {
+  double* B; int64_t ldb;
+  __device__ void begin() {}
+  __device__ void end() {}
+  __device__ __forceinline__ void operator()(int64_t i, int64_t j, double acc) { B[i * ldb + j] = acc; }
+};
+
+// y = B x (B m x n, row-major); one warp per row.
+__global__ void k_gemv(const double* B, int64_t m, int64_t n, const double* x, double* y) {
+  const int64_t row = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= m) return;
+  double s = 0.0;
+  for (int64_t j = lane; j < n; j += 32) s = fma(B[row * n + j], x[j], s);
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) y[row] = s;
+}
+
+// x = B^T y; one thread per column.
+__global__ void k_gemvT(const double* B, int64_t m, int64_t n, const double* y, double* x) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  double s = 0.0;
+  for (int64_t i = 0; i < m; ++i) s = fma(B[i * n + j], y[i], s);
+  x[j] = s;
+}
+
+// v <- x / ||x||, sigma = sqrt(||x||) (x = B^T B v with ||v|| = 1); one CTA.
+__global__ void k_normalize(double* x, int64_t n, double* v, double* sigma) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int64_t j = threadIdx.x; j < n; j += blockDim.x) s = fma(x[j], x[j], s);
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x / 32); ++w) t += red[w];
+    red[0] = sqrt(t);
+    sigma[0] = sqrt(red[0]);
+  }
+  __syncthreads();
+  const double nrm = red[0];
+  for (int64_t j = threadIdx.x; j < n; j += blockDim.x) v[j] = nrm > 0.0 ? x[j] / nrm : 0.0;
+}
+
+__global__ void k_fill_ones(double* v, int64_t n) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < n) v[j] = 1.0 / sqrt((double)n) * (1.0 + 1e-3 * (double)(j % 7));
+}
+
+ibmi_status paper_estimate_f64(ibmi_plan_s* P, const double* A, int64_t lda, const double* H, int64_t ldh,
+                               cudaStream_t st, double* out) {
+  const int K = (int)P->lo.size();
+  const int64_t p = P->d.p, lo = P->lo[K - 1], m = P->hi[K - 1] - lo, n = p - m;
+  if (n == 0) { *out = 0.0; return IBMI_OK; }
+  if (!P->pe) {
+    IBMI_CUDA_TRY(cudaMalloc(&P->pe, sizeof(double) * (m * n + 2 * n + m + 4)));
+  }
+  double* B = P->pe;
+  double* v = B + m * n;
+  double* x = v + n;
+  double* y = x + n;
+  double* sig = y + m;
+  const GapMap gap{lo, m}, id{0, 0};
+  {
+    ProfScope ps(IBMI_K_RESIDUAL, st, 2.0 * (double)m * n * p);
+    F64Operands op{H + lo * ldh, ldh, id, id, A, lda, id, gap, m, n, p};
+    IBMI_CUDA_TRY((launch_gemm_f64<true, true>(op, EpiStoreB{B, n}, st)));
+  }
+  ProfScope ps(IBMI_K_OTHER, st, 0.0);
+  note_launch();
+  k_fill_ones<<<nblk(n), 256, 0, st>>>(v, n);
+  for (int it = 0; it < 60; ++it) {
+    note_launch(3);
+    k_gemv<<<(unsigned)((m + 7) / 8), 256, 0, st>>>(B, m, n, v, y);
+    k_gemvT<<<nblk(n), 256, 0, st>>>(B, m, n, y, x);
+    k_normalize<<<1, 1024, 0, st>>>(x, n, v, sig);
+  }
+  IBMI_CUDA_TRY(cudaGetLastError());
+  IBMI_CUDA_TRY(cudaMemcpyAsync(out, sig, sizeof(double), cudaMemcpyDeviceToHost, st));
+  IBMI_CUDA_TRY(cudaStreamSynchronize(st));
+  return IBMI_OK;
+}
+
 __global__ void k_set_identity(double* H, int64_t ldh, int64_t p) {
   int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= p * p) return;

@@ -28,6 +28,8 @@ struct ibmi_plan_s {
   int64_t n_partials = 0;
   double* dscalar = nullptr;     // device scalar results
   ibmi::DevStatus* dstatus = nullptr;
+  // paper's estimate (eq. error): B = (H A)[I_K, I_K^c] and power-iteration vectors
+  double* pe = nullptr;
   // Newton-Schulz buffers (allocated on first use)
   double* nsR = nullptr;
   double* nsX = nullptr;
@@ -61,5 +63,10 @@ ibmi_status ns_step_f64(ibmi_plan_s* P, const double* A, int64_t lda, double* X,
                         cudaStream_t st);
 
 ibmi_status set_identity(double* H, int64_t ldh, int64_t p, cudaStream_t st);
+
+// eq. error on the last set: ||(H A)[I_K, I_K^c]||_2 (FP64 GEMM, then power
+// iteration on B^T B); host value in *out (syncs the stream).
+ibmi_status paper_estimate_f64(ibmi_plan_s* P, const double* A, int64_t lda, const double* H, int64_t ldh,
+                               cudaStream_t st, double* out);
 
 }  // namespace ibmi

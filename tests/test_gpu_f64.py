@@ -207,3 +207,38 @@ def test_full_size_c2_fp64_sampled(ibmi):
     E[cols, np.arange(len(cols))] = 1.0
     X = O.backward_subst(L.T, O.forward_subst(L, E))
     assert np.abs(H[:, cols] - X).max() <= 1e-8 * np.abs(X).max()
+
+
+def test_paper_estimate_table2_exp_1d(ibmi):
+    """Stop on the paper's estimate (eq. error) at tol 1e-8: the 1-D exponential
+    kernel converges in one sweep (Table 2); the estimate matches the oracle's."""
+    p = 256
+    A = wl.exp_1d(p)
+    h = round(0.2 * (p // 2) / 2)
+    sets = O.partition(p, 2, h)
+    ref = O.ibmi(A, sets, tol=1e-8, stop_rule="paper", max_sweeps=50)
+    s, res, H = run_gpu(ibmi, A, K=2, h=h, tol=1e-8, max_sweeps=50, stop_rule=ibmi.IBMI_STOP_PAPER_EST)
+    assert s == ibmi.IBMI_OK and res["sweeps"] == ref.sweeps == 1
+    # at convergence both estimates are FP64 rounding noise of a block whose
+    # exact value is ~rho^p; the value itself is pinned by the KMS closed form
+    assert res["paper_est"] <= 1e-12 and ref.paper_est <= 1e-12
+    assert res["resid_f"] == pytest.approx(O.residual_f(A, H), rel=1e-6, abs=1e-15)
+
+
+@pytest.mark.parametrize("r", [1, 2])
+def test_paper_estimate_kms_closed_form(ibmi, r):
+    """eq. error on I_2 after r sweeps from T_0 = 2I equals
+    |delta| rho^{4r-1} sqrt((1 - rho^2)(1 - rho^p)) (rank one)."""
+    p, rho, c = 128, 0.5, 2.0
+    A = wl.kms(p, rho)
+    delta = (c * (1.0 - rho ** p) - 1.0) / (1.0 - rho * rho)
+    want = abs(delta) * rho ** (4 * r - 1) * math.sqrt((1 - rho * rho) * (1 - rho ** p))
+    s, res, H = run_gpu(ibmi, A, H0=c * np.eye(p), K=2, h=0, tol=0.0, max_sweeps=r, init=ibmi.IBMI_INIT_USER,
+                        stop_rule=ibmi.IBMI_STOP_PAPER_EST)
+    assert s == ibmi.IBMI_NOT_CONVERGED and res["sweeps"] == r
+    assert res["paper_est"] == pytest.approx(want, rel=1e-9)
+
+
+def test_paper_estimate_rejected_on_mixed_path(ibmi):
+    with pytest.raises(ibmi.IbmiError):
+        ibmi.ibmi_plan(256, K=2, precision=ibmi.IBMI_MIXED, stop_rule=ibmi.IBMI_STOP_PAPER_EST)
