@@ -415,14 +415,15 @@ ibmi_status refine_cheap_residual(RefineState* R, const CUtensorMap* mapH2, cuda
   maps.b[1] = R->mAf[1];
   const int nkt = (int)((p + tc::BK - 1) / tc::BK);
   const int grid_n = (int)((p + RF_BN - 1) / RF_BN), grid_m = (int)((p + 127) / 128);
-  const int64_t nparts = (int64_t)grid_n * grid_m * 4;
-  if (nparts > R->n_partials) return IBMI_ERR_INVALID_ARG;
+  int grid = 0;
   {
     ProfScope ps(IBMI_K_RESIDUAL, st, 3.0 * 2.0 * (double)p * p * p);
     tc::Tiles t{p, 0, 0, grid_n, 0, 0, 0, nkt, 1, R->err};
     EpiResidSq epi{R->partials, p, 0.0};
-    IBMI_CUDA_TRY((tc::launch<2, RF_BN>(maps, t, grid_n, grid_m, epi, st)));
+    IBMI_CUDA_TRY((tc::launch<2, RF_BN>(maps, t, grid_n, grid_m, epi, st, &grid)));
   }
+  const int64_t nparts = (int64_t)grid * 4;   // one partial per epilogue warp of each (persistent) CTA
+  if (nparts > R->n_partials) return IBMI_ERR_INVALID_ARG;
   {
     ProfScope ps(IBMI_K_OTHER, st, 0.0);
     note_launch();

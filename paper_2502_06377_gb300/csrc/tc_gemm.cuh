@@ -9,17 +9,24 @@
 // classic three-product BF16x3 scheme, S = 3 the six-product scheme.  The
 // accumulator is FP32 in tensor memory (128 lanes x BN columns).
 //
-// One CTA computes one 128 x BN output tile (optionally one K split of it):
-//   warp 0   : one thread issues the TMA loads of a stage (S A-tiles, S B-tiles)
-//   warp 1   : allocates TMEM; one thread issues tcgen05.mma and commits
-//   warps 2-5: epilogue; each reads its 32-lane quadrant of TMEM with
-//              tcgen05.ld and hands 16 FP32 values at a time to the functor.
+// The kernel is persistent: each CTA walks the 128 x BN output tiles (and K
+// splits) tile = blockIdx.x, blockIdx.x + gridDim.x, ...  Roles:
+//   warp 0   : one thread issues the TMA loads of each stage (S A-tiles and
+//              S B-tiles) into a ring of shared-memory stages that runs on
+//              across tiles;
+//   warp 1   : allocates TMEM for two accumulators; one thread issues
+//              tcgen05.mma into accumulator (tile & 1) and commits;
+//   warps 2-5: epilogue; each drains its 32-lane quadrant of the accumulator
+//              with tcgen05.ld, hands 16 FP32 values at a time to the functor
+//              and frees the accumulator, so the MMAs of tile i+1 overlap the
+//              epilogue of tile i.
 // Every mbarrier wait is bounded (about 2 s of wall time); on expiry the
 // kernel records an error code in *err and finishes without hanging.
 #pragma once
 #include <cuda.h>
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <atomic>
 
 #include "common.cuh"
@@ -46,8 +53,10 @@ struct Tiles {
   int kt0_end;      // K tiles [0, kt0_end) then [kt1_begin, kt1_end)
   int kt1_begin;
   int kt1_end;
-  int splits;       // K splits (gridDim.z)
+  int splits;       // K splits
   int* err;         // error word (0 = ok)
+  int grid_n = 0;   // N tiles, M tiles (filled in by launch())
+  int grid_m = 0;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -66,6 +75,10 @@ __device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
 
 __device__ __forceinline__ void fence_barrier_init() {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
 }
 
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
@@ -193,7 +206,9 @@ struct Cfg {
   static constexpr int STAGES =
       TWO_PER_SM ? 3 : ((200 * 1024) / STAGE_BYTES >= 4 ? 4 : (200 * 1024) / STAGE_BYTES);
   static constexpr uint32_t SMEM = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
-  static constexpr uint32_t TMEM_COLS = BN < 32 ? 32 : BN;
+  static constexpr uint32_t TMEM_COLS = 2 * BN < 32 ? 32 : 2 * BN;   // two accumulators
+  static constexpr int CTAS_PER_SM = TWO_PER_SM && 2 * TMEM_COLS <= 512 ? 2 : 1;
+  static_assert(TMEM_COLS <= 512, "two accumulators must fit in TMEM");
   static_assert(STAGES >= 2, "tile too large for two stages");
   static_assert(BN % 16 == 0 && BN >= 16 && BN <= 256, "UMMA N for M = 128");
 };
@@ -206,24 +221,24 @@ __global__ void __launch_bounds__(THREADS, 2) k_tc_gemm(const __grid_constant__ 
   uint8_t* tiles = smem;
   uint64_t* full = (uint64_t*)(smem + C::STAGES * C::STAGE_BYTES);
   uint64_t* empty = full + C::STAGES;
-  uint64_t* accf = empty + C::STAGES;
-  uint32_t* tmem_slot = (uint32_t*)(accf + 1);
+  uint64_t* accf = empty + C::STAGES;   // [2] accumulator ready
+  uint64_t* acce = accf + 2;            // [2] accumulator drained
+  uint32_t* tmem_slot = (uint32_t*)(acce + 2);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int mt = blockIdx.y, ntl = blockIdx.x, z = blockIdx.z;
-  const int ntp = ntl < t.nt0 ? ntl : t.nt1_first + (ntl - t.nt0);
-  const int64_t n0 = (int64_t)ntp * BN;
+  const int total = t.grid_n * t.grid_m * t.splits;
   const int nk0 = t.kt0_end;
   const int nk = t.kt0_end + (t.kt1_end - t.kt1_begin);
-  const int kb = (int)((int64_t)nk * z / t.splits);
-  const int my_nk = (int)((int64_t)nk * (z + 1) / t.splits) - kb;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < C::STAGES; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(accf, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&accf[b], 1);
+      mbar_init(&acce[b], 4);   // one arrival per epilogue warp
+    }
     fence_barrier_init();
   }
   if (warp == 1) tmem_alloc(tmem_slot, C::TMEM_COLS);
@@ -234,30 +249,37 @@ __global__ void __launch_bounds__(THREADS, 2) k_tc_gemm(const __grid_constant__ 
 
   if (warp == 0) {
     if (lane == 0) {  // TMA producer
-      int issued = 0;
-      for (int it = 0; it < my_nk; ++it) {
-        const int st = it % C::STAGES;
-        const uint32_t ph = (uint32_t)(it / C::STAGES) & 1u;
-        if (!mbar_wait(&empty[st], ph ^ 1u, t.err)) break;
-        const int kt = kb + it;
-        const int ktp = kt < nk0 ? kt : t.kt1_begin + (kt - nk0);
-        const int kx = ktp * BK;
-        uint8_t* sa = tiles + st * C::STAGE_BYTES;
-        uint8_t* sb = sa + S * C::A_BYTES;
-        mbar_expect_tx(&full[st], C::STAGE_BYTES);
+      int kc = 0;     // k blocks issued so far (ring position)
+      bool ok = true;
+      for (int tile = blockIdx.x; ok && tile < total; tile += gridDim.x) {
+        const int ntl = tile % t.grid_n, mt = (tile / t.grid_n) % t.grid_m, z = tile / (t.grid_n * t.grid_m);
+        const int ntp = ntl < t.nt0 ? ntl : t.nt1_first + (ntl - t.nt0);
+        const int64_t n0 = (int64_t)ntp * BN;
+        const int kb = (int)((int64_t)nk * z / t.splits);
+        const int my_nk = (int)((int64_t)nk * (z + 1) / t.splits) - kb;
+        for (int it = 0; it < my_nk; ++it, ++kc) {
+          const int st = kc % C::STAGES;
+          const uint32_t ph = (uint32_t)(kc / C::STAGES) & 1u;
+          if (!mbar_wait(&empty[st], ph ^ 1u, t.err)) { ok = false; break; }
+          const int kt = kb + it;
+          const int ktp = kt < nk0 ? kt : t.kt1_begin + (kt - nk0);
+          const int kx = ktp * BK;
+          uint8_t* sa = tiles + st * C::STAGE_BYTES;
+          uint8_t* sb = sa + S * C::A_BYTES;
+          mbar_expect_tx(&full[st], C::STAGE_BYTES);
 #pragma unroll
-        for (int s = 0; s < S; ++s)
-          tma_load_2d(sa + s * C::A_BYTES, &maps.a[s], &full[st], kx, (int)(t.a_row0 + (int64_t)mt * BM));
+          for (int s = 0; s < S; ++s)
+            tma_load_2d(sa + s * C::A_BYTES, &maps.a[s], &full[st], kx, (int)(t.a_row0 + (int64_t)mt * BM));
 #pragma unroll
-        for (int s = 0; s < S; ++s)
-          tma_load_2d(sb + s * C::B_BYTES, &maps.b[s], &full[st], kx, (int)(t.b_row0 + n0));
-        issued = it + 1;
+          for (int s = 0; s < S; ++s)
+            tma_load_2d(sb + s * C::B_BYTES, &maps.b[s], &full[st], kx, (int)(t.b_row0 + n0));
+        }
       }
       // On an error exit, wait (bounded) for the copies still in flight.
       if (*(volatile int*)t.err != 0) {
-        for (int it = issued - C::STAGES < 0 ? 0 : issued - C::STAGES; it < issued; ++it) {
-          const int st = it % C::STAGES;
-          const uint32_t ph = (uint32_t)(it / C::STAGES) & 1u;
+        for (int k = kc - C::STAGES < 0 ? 0 : kc - C::STAGES; k < kc; ++k) {
+          const int st = k % C::STAGES;
+          const uint32_t ph = (uint32_t)(k / C::STAGES) & 1u;
           const uint64_t t0 = globaltimer();
           while (!mbar_try_wait(&full[st], ph) && globaltimer() - t0 < 1000000000ull) {
           }
@@ -267,48 +289,71 @@ __global__ void __launch_bounds__(THREADS, 2) k_tc_gemm(const __grid_constant__ 
   } else if (warp == 1) {
     if (lane == 0) {  // MMA issuer
       constexpr uint32_t idesc = idesc_bf16(BM, BN);
-      for (int it = 0; it < my_nk; ++it) {
-        const int st = it % C::STAGES;
-        const uint32_t ph = (uint32_t)(it / C::STAGES) & 1u;
-        if (!mbar_wait(&full[st], ph, t.err)) break;
+      int kc = 0;
+      int local = 0;
+      bool ok = true;
+      for (int tile = blockIdx.x; ok && tile < total; tile += gridDim.x, ++local) {
+        const int z = tile / (t.grid_n * t.grid_m);
+        const int kb = (int)((int64_t)nk * z / t.splits);
+        const int my_nk = (int)((int64_t)nk * (z + 1) / t.splits) - kb;
+        const int buf = local & 1;
+        const uint32_t use = (uint32_t)(local >> 1);
+        if (!mbar_wait(&acce[buf], (use & 1u) ^ 1u, t.err)) break;   // accumulator drained
         tc_fence_after();
-        const uint32_t sa = smem_u32(tiles + st * C::STAGE_BYTES);
-        const uint32_t sb = sa + S * C::A_BYTES;
+        const uint32_t dacc = tmem + (uint32_t)(buf * BN);
+        for (int it = 0; it < my_nk; ++it, ++kc) {
+          const int st = kc % C::STAGES;
+          const uint32_t ph = (uint32_t)(kc / C::STAGES) & 1u;
+          if (!mbar_wait(&full[st], ph, t.err)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t sa = smem_u32(tiles + st * C::STAGE_BYTES);
+          const uint32_t sb = sa + S * C::A_BYTES;
 #pragma unroll
-        for (int s = 0; s < S; ++s)
+          for (int s = 0; s < S; ++s)
 #pragma unroll
-          for (int u = 0; s + u < S; ++u)
+            for (int u = 0; s + u < S; ++u)
 #pragma unroll
-            for (int kk = 0; kk < BK / 16; ++kk) {
-              const uint64_t da = sdesc_sw128(sa + s * C::A_BYTES + kk * 32);
-              const uint64_t db = sdesc_sw128(sb + u * C::B_BYTES + kk * 32);
-              mma_bf16(tmem, da, db, idesc, (it | s | u | kk) != 0 ? 1u : 0u);
-            }
-        mma_commit(&empty[st]);
+              for (int kk = 0; kk < BK / 16; ++kk) {
+                const uint64_t da = sdesc_sw128(sa + s * C::A_BYTES + kk * 32);
+                const uint64_t db = sdesc_sw128(sb + u * C::B_BYTES + kk * 32);
+                mma_bf16(dacc, da, db, idesc, (it | s | u | kk) != 0 ? 1u : 0u);
+              }
+          mma_commit(&empty[st]);
+        }
+        mma_commit(&accf[buf]);
       }
-      mma_commit(accf);
     }
   } else {  // epilogue warps 2..5
     const int q = warp & 3;
     const int row = q * 32 + lane;
-    const bool ok = mbar_wait(accf, 0, t.err);
-    tc_fence_after();
     Epi e = epi;
-    if (ok) {
+    int local = 0;
+    for (int tile = blockIdx.x; tile < total; tile += gridDim.x, ++local) {
+      const int ntl = tile % t.grid_n, mt = (tile / t.grid_n) % t.grid_m, z = tile / (t.grid_n * t.grid_m);
+      const int ntp = ntl < t.nt0 ? ntl : t.nt1_first + (ntl - t.nt0);
+      const int64_t n0 = (int64_t)ntp * BN;
+      const int kb = (int)((int64_t)nk * z / t.splits);
+      const int my_nk = (int)((int64_t)nk * (z + 1) / t.splits) - kb;
+      const int buf = local & 1;
+      const uint32_t use = (uint32_t)(local >> 1);
+      if (!mbar_wait(&accf[buf], use & 1u, t.err)) break;
+      tc_fence_after();
 #pragma unroll 1
       for (int c = 0; c < BN; c += 16) {
         float v[16];
         if (my_nk > 0) {
-          tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c, v);
+          tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * BN + c), v);
         } else {
 #pragma unroll
           for (int i = 0; i < 16; ++i) v[i] = 0.f;
         }
         e((int64_t)mt * BM + row, n0 + c, z, v);
       }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acce[buf]);
     }
     e.done(q);
-    tc_fence_before();
   }
   __syncthreads();
   if (warp == 1) {
@@ -340,7 +385,8 @@ inline TileRanges complement_tiles(int64_t lo, int64_t hi, int64_t p, int tile) 
 }
 
 template <int S, int BN, class Epi>
-cudaError_t launch(const Maps& maps, const Tiles& t, int grid_n, int grid_m, const Epi& epi, cudaStream_t st) {
+cudaError_t launch(const Maps& maps, const Tiles& t0, int grid_n, int grid_m, const Epi& epi, cudaStream_t st,
+                   int* grid_used = nullptr) {
   using C = Cfg<S, BN>;
   static std::atomic<bool> attr_set{false};
   if (!attr_set.load(std::memory_order_acquire)) {
@@ -349,9 +395,23 @@ cudaError_t launch(const Maps& maps, const Tiles& t, int grid_n, int grid_m, con
     if (e != cudaSuccess) return e;
     attr_set.store(true, std::memory_order_release);
   }
+  if (grid_used) *grid_used = 0;
   if (grid_n <= 0 || grid_m <= 0) return cudaSuccess;
+  static std::atomic<int> sms{0};
+  if (sms.load() == 0) {
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    sms.store(n > 0 ? n : 148);
+  }
+  Tiles t = t0;
+  t.grid_n = grid_n;
+  t.grid_m = grid_m;
+  const int64_t total = (int64_t)grid_n * grid_m * t.splits;
+  const int grid = (int)std::min<int64_t>(total, (int64_t)sms.load() * C::CTAS_PER_SM);
+  if (grid_used) *grid_used = grid;
   note_launch();
-  k_tc_gemm<S, BN, Epi><<<dim3(grid_n, grid_m, t.splits), THREADS, C::SMEM, st>>>(maps, t, epi);
+  k_tc_gemm<S, BN, Epi><<<grid, THREADS, C::SMEM, st>>>(maps, t, epi);
   return cudaGetLastError();
 }
 
