@@ -215,7 +215,8 @@ __global__ void k_sym_into(const double* Xn, int64_t p, double* X, int64_t ldx) 
 
 // --------------------------------------------------------------- host ----
 
-static constexpr int RF_BN = 128;
+static constexpr int RF_BN = 128;   // N tile of the BF16x3 residual
+static constexpr int OZ_BN = 256;   // N tile of the digit-pair GEMMs (128 x 256 per CTA)
 
 ibmi_status refine_create(RefineState* R, int64_t p, int* err) {
   R->p = p;
@@ -245,9 +246,9 @@ ibmi_status refine_create(RefineState* R, int64_t p, int* err) {
   R->expX = (int*)take(sizeof(int) * p);
   R->expQ = (int*)take(sizeof(int) * p);
   bool ok = true;
-  for (int s = 0; s < OZ_SA; ++s) ok &= tc::make_map_bf16(&R->mAo[s], R->Ao[s], p, p, ldp, RF_BN);
+  for (int s = 0; s < OZ_SA; ++s) ok &= tc::make_map_bf16(&R->mAo[s], R->Ao[s], p, p, ldp, OZ_BN);
   for (int s = 0; s < OZ_SX; ++s) ok &= tc::make_map_bf16(&R->mXo[s], R->Xo[s], p, p, ldp, 128);
-  for (int s = 0; s < NS_S; ++s) ok &= tc::make_map_bf16(&R->mQo[s], R->Qo[s], p, p, ldp, RF_BN);
+  for (int s = 0; s < NS_S; ++s) ok &= tc::make_map_bf16(&R->mQo[s], R->Qo[s], p, p, ldp, OZ_BN);
   for (int s = 0; s < 2; ++s) ok &= tc::make_map_bf16(&R->mAf[s], R->Af[s], p, p, ldp, RF_BN);
   return ok ? IBMI_OK : IBMI_ERR_CUDA;
 }
@@ -306,7 +307,7 @@ struct DigitGemm {
 static ibmi_status digit_gemm(RefineState* R, const DigitGemm& g, cudaStream_t st) {
   const int64_t p = R->p, ldp = R->ldp;
   const int chunk_tiles = OZ_KCHUNK / tc::BK;
-  const int grid_n = (int)((g.N + RF_BN - 1) / RF_BN), grid_m = (int)((g.M + 127) / 128);
+  const int grid_n = (int)((g.N + OZ_BN - 1) / OZ_BN), grid_m = (int)((g.M + 127) / 128);
   for (int q = 0; q <= g.qmax; ++q) {
     bool first = true;
     for (int s = 0; s <= q; ++s) {
@@ -321,7 +322,7 @@ static ibmi_status digit_gemm(RefineState* R, const DigitGemm& g, cudaStream_t s
         tc::Tiles t{g.M, 0, 0, grid_n, 0, 0, k0, k1, 1, R->err};
         EpiOzAcc epi{{}, R->T + (int64_t)q * p * ldp, ldp, g.M, g.N, first ? 1 : 0};
         ProfScope ps(g.kclass, st, 2.0 * (double)g.M * g.N * (double)(k1 - k0) * tc::BK);
-        IBMI_CUDA_TRY((tc::launch<1, RF_BN>(maps, t, grid_n, grid_m, epi, st)));
+        IBMI_CUDA_TRY((tc::launch<1, OZ_BN>(maps, t, grid_n, grid_m, epi, st)));
         first = false;
       }
     }

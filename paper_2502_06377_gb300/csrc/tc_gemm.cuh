@@ -214,7 +214,8 @@ struct Cfg {
 };
 
 template <int S, int BN, class Epi>
-__global__ void __launch_bounds__(THREADS, 2) k_tc_gemm(const __grid_constant__ Maps maps, const Tiles t, Epi epi) {
+__global__ void __launch_bounds__(THREADS, Cfg<S, BN>::CTAS_PER_SM) k_tc_gemm(const __grid_constant__ Maps maps,
+                                                                             const Tiles t, Epi epi) {
   using C = Cfg<S, BN>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
