@@ -27,6 +27,10 @@ def main():
     ap.add_argument("--method", choices=["tc", "fp64"], default="tc")
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--repeat", type=int, default=1)
+    ap.add_argument("--family", choices=["matern", "random_spd"], default="matern",
+                    help="matern: the Matern-3/2 workload; random_spd: Q diag(lambda) Q^T, lambda "
+                         "log-uniform in [1, 1e4] (seed 3)")
+    ap.add_argument("--max-sweeps", type=int, default=500)
     a = ap.parse_args()
 
     import numpy as np
@@ -37,19 +41,29 @@ def main():
     import paper_2502_06377_gb300 as ibmi
     import workloads as wl
 
-    A = wl.c2_matern(a.p, seed=2)
+    A = wl.c2_matern(a.p, seed=2) if a.family == "matern" else wl.c3_random_spd(a.p, seed=3)
     dA = torch.from_numpy(A).cuda()
     dH = torch.empty_like(dA)
     prec = ibmi.IBMI_MIXED if a.precision == "mixed" else ibmi.IBMI_FP64
     if a.cmd == "invert":
-        plan = ibmi.ibmi_plan(a.p, K=a.K, h=a.h, precision=prec, tol=a.tol,
+        plan = ibmi.ibmi_plan(a.p, K=a.K, h=a.h, precision=prec, tol=a.tol, max_sweeps=a.max_sweeps,
                               ns_theta=0.5 if prec == ibmi.IBMI_MIXED else 0.0)
+        ibmi._lib.load().ibmi_prof_enable(1)
         out = None
         for _ in range(a.repeat):
             t0 = time.perf_counter()
             s, res = ibmi.ibmi_invert(plan, dA, dH)
             torch.cuda.synchronize()
             out = dict(res, status_name=ibmi.ibmi_status_string(s), wall_s=time.perf_counter() - t0)
+        import ctypes as C
+        lib = ibmi._lib.load()
+        names = ["sweep_x", "sweep_s", "residual", "newton_schulz", "invariants", "other", "invariants_tc"]
+        prof = {}
+        for k, nm in enumerate(names):
+            n, t, f = C.c_int64(), C.c_double(), C.c_double()
+            lib.ibmi_prof_get(k, C.byref(n), C.byref(t), C.byref(f))
+            prof[nm] = round(t.value / a.repeat, 3)
+        out["ms_per_class"] = prof
         print(json.dumps(out))
     else:
         plan = ibmi.ibmi_plan(a.p, K=a.K, h=a.h, precision=ibmi.IBMI_FP64, tol=0.0, max_sweeps=1)

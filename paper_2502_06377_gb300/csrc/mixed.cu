@@ -50,13 +50,14 @@ constexpr int MX_BN = 128;   // N tile of the sweep products
 struct MixedState {
   int64_t ldp = 0;                       // padded row pitch of all mixed arrays (multiple of 64)
   float* Hf = nullptr;                   // FP32 master of H, p x ldp
-  __nv_bfloat16* Hs[2] = {nullptr, nullptr};   // BF16 hi / lo slices of H
-  std::vector<__nv_bfloat16*> Ws[2];     // per set: BF16 hi / lo of W (m x ldp)
+  __nv_bfloat16* Hs[3] = {nullptr, nullptr, nullptr};   // BF16 slices of H: x ~ s0 + s1 + s2
+  std::vector<__nv_bfloat16*> Ws[3];     // per set: BF16 slices of W (m x ldp)
+  int level = 0;                         // sweep products: 0 = two slices (3 MMAs), 1 = three (6)
   float* Spart = nullptr;                // a4 split-K partial products, splits x mmax^2
   int splits_max = 0;
   int* err = nullptr;                    // device error word of the tcgen05 kernels
-  CUtensorMap mapH[2];
-  std::vector<CUtensorMap> mapW[2];
+  CUtensorMap mapH[3];
+  std::vector<CUtensorMap> mapW[3];
   void* pool = nullptr;
   RefineState ref;                       // FP64-accurate residual + Newton-Schulz
 };
@@ -65,23 +66,24 @@ static MixedState* MS(ibmi_plan_s* P) { return (MixedState*)P->mixed; }
 
 // ------------------------------------------------------------- kernels ----
 
-__device__ __forceinline__ void split2(float x, __nv_bfloat16& h, __nv_bfloat16& l) {
-  h = __float2bfloat16_rn(x);
-  l = __float2bfloat16_rn(x - __bfloat162float(h));
+// x (FP32) ~ s0 + s1 + s2 with BF16 slices taken in turn from the remainder;
+// the first two are the classic hi/lo pair.
+__device__ __forceinline__ void split3(float x, __nv_bfloat16& a, __nv_bfloat16& b, __nv_bfloat16& c) {
+  a = __float2bfloat16_rn(x);
+  const float r = x - __bfloat162float(a);
+  b = __float2bfloat16_rn(r);
+  c = __float2bfloat16_rn(r - __bfloat162float(b));
 }
 
 // FP64 H (ldh) -> FP32 master + BF16 hi/lo (ldp)
-__global__ void k_import_h(const double* H, int64_t ldh, int64_t p, int64_t ldp, float* Hf, __nv_bfloat16* hi,
-                           __nv_bfloat16* lo) {
+__global__ void k_import_h(const double* H, int64_t ldh, int64_t p, int64_t ldp, float* Hf, __nv_bfloat16* s0,
+                           __nv_bfloat16* s1, __nv_bfloat16* s2) {
   int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= p * ldp) return;
   int64_t i = idx / ldp, c = idx - i * ldp;
   float x = c < p ? (float)H[i * ldh + c] : 0.f;
-  __nv_bfloat16 h, l;
-  split2(x, h, l);
   Hf[idx] = x;
-  hi[idx] = h;
-  lo[idx] = l;
+  split3(x, s0[idx], s1[idx], s2[idx]);
 }
 
 __global__ void k_export_h(const float* Hf, int64_t ldp, int64_t p, double* H, int64_t ldh) {
@@ -93,7 +95,7 @@ __global__ void k_export_h(const float* Hf, int64_t ldp, int64_t p, double* H, i
 
 // a4 finish: H[I, I] = A_I^{-1} - (P + P^T)/2 with P = sum of the split-K partials.
 __global__ void k_mixed_sym(const float* Spart, int splits, int64_t m, const double* Ainv, int64_t lo, int64_t ldp,
-                            float* Hf, __nv_bfloat16* hi, __nv_bfloat16* lw) {
+                            float* Hf, __nv_bfloat16* s0, __nv_bfloat16* s1, __nv_bfloat16* s2) {
   int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= m * m) return;
   int64_t i = idx / m, j = idx - i * m;
@@ -104,18 +106,15 @@ __global__ void k_mixed_sym(const float* Spart, int splits, int64_t m, const dou
   }
   float x = (float)(Ainv[idx] - 0.5 * ((double)a + (double)b));
   int64_t o = (lo + i) * ldp + lo + j;
-  __nv_bfloat16 h, l;
-  split2(x, h, l);
   Hf[o] = x;
-  hi[o] = h;
-  lw[o] = l;
+  split3(x, s0[o], s1[o], s2[o]);
 }
 
 // a3 epilogue: X = -acc for rows i < m of the set and columns j in I^c;
 // written to H[lo+i, j] (16 consecutive columns per thread) and to H[j, lo+i]
 // (the 32 lanes of a warp hold consecutive i: coalesced).
 struct EpiTcSweepX : tc::EpiBase {
-  float* Hf; __nv_bfloat16* Hh; __nv_bfloat16* Hl;
+  float* Hf; __nv_bfloat16* H0; __nv_bfloat16* H1; __nv_bfloat16* H2;
   int64_t ldp, lo, hi, p, m;
   __device__ __forceinline__ void operator()(int64_t i, int64_t j0, int, const float (&v)[16]) const {
     if (i >= m) return;
@@ -125,14 +124,16 @@ struct EpiTcSweepX : tc::EpiBase {
       const int64_t j = j0 + c;
       if (j >= p || (j >= lo && j < hi)) continue;
       const float x = -v[c];
-      __nv_bfloat16 h, l;
-      split2(x, h, l);
+      __nv_bfloat16 a, b, d;
+      split3(x, a, b, d);
       Hf[r * ldp + j] = x;
-      Hh[r * ldp + j] = h;
-      Hl[r * ldp + j] = l;
+      H0[r * ldp + j] = a;
+      H1[r * ldp + j] = b;
+      H2[r * ldp + j] = d;
       Hf[j * ldp + r] = x;
-      Hh[j * ldp + r] = h;
-      Hl[j * ldp + r] = l;
+      H0[j * ldp + r] = a;
+      H1[j * ldp + r] = b;
+      H2[j * ldp + r] = d;
     }
   }
 };
@@ -164,9 +165,9 @@ ibmi_status mixed_create(ibmi_plan_s* P) {
   int64_t tiles2 = ((P->mmax + 127) / 128) * ((P->mmax + MX_BN - 1) / MX_BN);
   int kt = (int)((p + tc::BK - 1) / tc::BK);
   M->splits_max = (int)std::max<int64_t>(1, std::min<int64_t>(std::max<int64_t>(1, 148 / tiles2), kt / 4 > 0 ? kt / 4 : 1));
-  size_t bytes = sizeof(float) * p * ldp + 2 * sizeof(__nv_bfloat16) * p * ldp +
+  size_t bytes = sizeof(float) * p * ldp + 3 * sizeof(__nv_bfloat16) * p * ldp + 512 +
                  sizeof(float) * (size_t)M->splits_max * P->mmax * P->mmax + 256;
-  for (int k = 0; k < K; ++k) bytes += 2 * sizeof(__nv_bfloat16) * (P->hi[k] - P->lo[k]) * ldp + 256;
+  for (int k = 0; k < K; ++k) bytes += 3 * sizeof(__nv_bfloat16) * (P->hi[k] - P->lo[k]) * ldp + 768;
   if (cudaMalloc(&M->pool, bytes) != cudaSuccess) {
     cudaGetLastError();
     return IBMI_ERR_OOM;
@@ -174,15 +175,14 @@ ibmi_status mixed_create(ibmi_plan_s* P) {
   uint8_t* q = (uint8_t*)M->pool;
   auto take = [&](size_t b) { uint8_t* r = q; q += (b + 255) / 256 * 256; return r; };
   M->Hf = (float*)take(sizeof(float) * p * ldp);
-  M->Hs[0] = (__nv_bfloat16*)take(sizeof(__nv_bfloat16) * p * ldp);
-  M->Hs[1] = (__nv_bfloat16*)take(sizeof(__nv_bfloat16) * p * ldp);
+  for (int s = 0; s < 3; ++s) M->Hs[s] = (__nv_bfloat16*)take(sizeof(__nv_bfloat16) * p * ldp);
   M->Spart = (float*)take(sizeof(float) * (size_t)M->splits_max * P->mmax * P->mmax);
   M->err = (int*)take(256);
   for (int k = 0; k < K; ++k) {
     const int64_t m = P->hi[k] - P->lo[k];
-    for (int s = 0; s < 2; ++s) M->Ws[s].push_back((__nv_bfloat16*)take(sizeof(__nv_bfloat16) * m * ldp));
+    for (int s = 0; s < 3; ++s) M->Ws[s].push_back((__nv_bfloat16*)take(sizeof(__nv_bfloat16) * m * ldp));
   }
-  for (int s = 0; s < 2; ++s) {
+  for (int s = 0; s < 3; ++s) {
     if (!tc::make_map_bf16(&M->mapH[s], M->Hs[s], p, p, ldp, 128)) return IBMI_ERR_CUDA;
     M->mapW[s].resize(K);
     for (int k = 0; k < K; ++k)
@@ -205,7 +205,7 @@ ibmi_status mixed_prepare(ibmi_plan_s* P, const double* H, int64_t ldh, cudaStre
   const int64_t p = P->d.p, ldp = M->ldp;
   ProfScope ps(IBMI_K_OTHER, st, 0.0);
   note_launch();
-  k_import_h<<<nblk(p * ldp), 256, 0, st>>>(H, ldh, p, ldp, M->Hf, M->Hs[0], M->Hs[1]);
+  k_import_h<<<nblk(p * ldp), 256, 0, st>>>(H, ldh, p, ldp, M->Hf, M->Hs[0], M->Hs[1], M->Hs[2]);
   IBMI_CUDA_TRY(cudaGetLastError());
   return IBMI_OK;
 }
@@ -216,35 +216,39 @@ ibmi_status mixed_sweep_step(ibmi_plan_s* P, int k, cudaStream_t st) {
   const tc::TileRanges kr = tc::complement_tiles(lo, hi, p, tc::BK);
   if (n == 0) return IBMI_ERR_INVALID_ARG;   // K = 1 is served by the FP64 path
   // a3: X = -W T; A operand = W slices (rows of the set), B = H slices (rows j).
+  const int S = M->level == 0 ? 2 : 3;
+  const double mult = S == 2 ? 3.0 : 6.0;   // slice products per product
   {
     const tc::TileRanges nr = tc::complement_tiles(lo, hi, p, MX_BN);
     tc::Maps maps;
-    maps.a[0] = M->mapW[0][k];
-    maps.a[1] = M->mapW[1][k];
-    maps.b[0] = M->mapH[0];
-    maps.b[1] = M->mapH[1];
+    for (int s = 0; s < S; ++s) {
+      maps.a[s] = M->mapW[s][k];
+      maps.b[s] = M->mapH[s];
+    }
     tc::Tiles t{m, 0, 0, nr.r0_end, nr.r1_begin, kr.r0_end, kr.r1_begin, kr.r1_end, 1, M->err};
-    EpiTcSweepX epi{{}, M->Hf, M->Hs[0], M->Hs[1], M->ldp, lo, hi, p, m};
-    ProfScope ps(IBMI_K_SWEEP_X, st, 3.0 * 2.0 * m * n * n);
-    IBMI_CUDA_TRY((tc::launch<2, MX_BN>(maps, t, nr.count(), (int)((m + 127) / 128), epi, st)));
+    EpiTcSweepX epi{{}, M->Hf, M->Hs[0], M->Hs[1], M->Hs[2], M->ldp, lo, hi, p, m};
+    ProfScope ps(IBMI_K_SWEEP_X, st, mult * 2.0 * m * n * n);
+    if (S == 2) IBMI_CUDA_TRY((tc::launch<2, MX_BN>(maps, t, nr.count(), (int)((m + 127) / 128), epi, st)));
+    else IBMI_CUDA_TRY((tc::launch<3, MX_BN>(maps, t, nr.count(), (int)((m + 127) / 128), epi, st)));
   }
   // a4: P = X W^T (split over K); A operand = H slices rows [lo, hi), B = W slices.
   {
     const int nk = kr.count();
     const int splits = std::max(1, std::min(M->splits_max, nk / 2));
     tc::Maps maps;
-    maps.a[0] = M->mapH[0];
-    maps.a[1] = M->mapH[1];
-    maps.b[0] = M->mapW[0][k];
-    maps.b[1] = M->mapW[1][k];
+    for (int s = 0; s < S; ++s) {
+      maps.a[s] = M->mapH[s];
+      maps.b[s] = M->mapW[s][k];
+    }
     const int ntn = (int)((m + MX_BN - 1) / MX_BN);
     tc::Tiles t{m, lo, 0, ntn, ntn, kr.r0_end, kr.r1_begin, kr.r1_end, splits, M->err};
     EpiTcPartial epi{{}, M->Spart, m};
-    ProfScope ps(IBMI_K_SWEEP_S, st, 3.0 * 2.0 * m * m * n);
-    IBMI_CUDA_TRY((tc::launch<2, MX_BN>(maps, t, ntn, (int)((m + 127) / 128), epi, st)));
+    ProfScope ps(IBMI_K_SWEEP_S, st, mult * 2.0 * m * m * n);
+    if (S == 2) IBMI_CUDA_TRY((tc::launch<2, MX_BN>(maps, t, ntn, (int)((m + 127) / 128), epi, st)));
+    else IBMI_CUDA_TRY((tc::launch<3, MX_BN>(maps, t, ntn, (int)((m + 127) / 128), epi, st)));
     note_launch();
     k_mixed_sym<<<nblk(m * m), 256, 0, st>>>(M->Spart, splits, m, P->ainv[k], lo, M->ldp, M->Hf, M->Hs[0],
-                                             M->Hs[1]);
+                                             M->Hs[1], M->Hs[2]);
     IBMI_CUDA_TRY(cudaGetLastError());
   }
   return IBMI_OK;
@@ -280,10 +284,12 @@ ibmi_status mixed_run(ibmi_plan_s* P, const double* A, int64_t lda, double* H, i
     fs += 2.0 * m * n * n + 2.0 * m * m * n;
   }
   IBMI_CUDA_TRY(cudaMemsetAsync(M->err, 0, sizeof(int), st));
+  M->level = 0;
   IBMI_TRY(refine_set_matrix(R, A, lda, st));
   // a2 on tensor cores: W_k = A_I^{-1} A_{I,:} from exact digit-sliced products
   for (int k = 0; k < K; ++k)
-    IBMI_TRY(refine_form_w(R, P->ainv[k], P->hi[k] - P->lo[k], P->lo[k], P->hi[k], M->Ws[0][k], M->Ws[1][k], st));
+    IBMI_TRY(refine_form_w(R, P->ainv[k], P->hi[k] - P->lo[k], P->lo[k], P->hi[k], M->Ws[0][k], M->Ws[1][k],
+                           M->Ws[2][k], st));
   IBMI_TRY(mixed_prepare(P, H, ldh, st));
   int r = 0, stalled = 0;
   double best = INFINITY;
@@ -299,13 +305,24 @@ ibmi_status mixed_run(ibmi_plan_s* P, const double* A, int64_t lda, double* H, i
     res->resid_f = rho;
     if (!isfinite(rho)) return IBMI_ERR_NONFINITE;
     if (d.ns_theta > 0.0 && rho * sqrtp <= d.ns_theta) break;
-    // The BF16x3 sweep has an accuracy floor of about kappa(A) * 1e-5 in rho;
-    // when the residual stops falling (three checks without a 5% gain) the
-    // Frobenius test may never pass although ||I - A H||_2 < 1 already holds,
-    // so the Newton-Schulz tail is tried (it stops if a step does not help).
+    // The sweep products have an accuracy floor (two BF16 slices: about
+    // kappa(A) * 1e-5 in rho).  When the residual stops falling (three checks
+    // without a 5% gain) the sweep first moves to three slices (24-bit
+    // operands, six products); if it stalls there too and ||I - A H||_F is
+    // within 8 theta, the 2-norm that eq. newton needs is usually below 1
+    // already, so the Newton-Schulz tail is tried (it stops if a step does not
+    // help).
     stalled = rho > 0.95 * best ? stalled + 1 : 0;
     best = fmin(best, rho);
-    if (d.ns_theta > 0.0 && stalled >= 3 && rho < 1.0) break;
+    if (d.ns_theta > 0.0 && stalled >= 3) {
+      if (M->level == 0) {
+        M->level = 1;
+        stalled = 0;
+        best = INFINITY;
+      } else if (rho * sqrtp <= 8.0 * d.ns_theta) {
+        break;
+      }
+    }
     if (rho <= d.tol || r >= d.max_sweeps) {
       // BF16x3 cannot certify tol: confirm with the FP64-accurate residual
       IBMI_TRY(mixed_export(P, H, ldh, st));

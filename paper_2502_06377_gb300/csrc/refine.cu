@@ -339,7 +339,7 @@ static ibmi_status pair_products(RefineState* R, const CUtensorMap* ma, int nsa,
 // W = A_I^{-1} A_{I,:} from digit products, written as BF16 hi/lo (zero on
 // the columns of I and on the padding).
 __global__ void k_oz_wcombine(const int* T, int64_t m, int64_t p, int64_t ldp, const int* ea, const int* eb, int qmax,
-                              int64_t lo, int64_t hi, __nv_bfloat16* Wh, __nv_bfloat16* Wl) {
+                              int64_t lo, int64_t hi, __nv_bfloat16* W0, __nv_bfloat16* W1, __nv_bfloat16* W2) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= m * ldp) return;
   const int64_t i = idx / ldp, j = idx - i * ldp;
@@ -347,13 +347,16 @@ __global__ void k_oz_wcombine(const int* T, int64_t m, int64_t p, int64_t ldp, c
   if (j < p && (j < lo || j >= hi)) {
     w = (float)oz_value(T, p * ldp, idx, qmax, ea[i] + eb[j] - 12);
   }
-  const __nv_bfloat16 h = __float2bfloat16_rn(w);
-  Wh[idx] = h;
-  Wl[idx] = __float2bfloat16_rn(w - __bfloat162float(h));
+  const __nv_bfloat16 a = __float2bfloat16_rn(w);
+  const float r = w - __bfloat162float(a);
+  const __nv_bfloat16 b = __float2bfloat16_rn(r);
+  W0[idx] = a;
+  W1[idx] = b;
+  W2[idx] = __float2bfloat16_rn(r - __bfloat162float(b));
 }
 
-ibmi_status refine_form_w(RefineState* R, const double* Ainv, int64_t m, int64_t lo, int64_t hi, __nv_bfloat16* Wh,
-                          __nv_bfloat16* Wl, cudaStream_t st) {
+ibmi_status refine_form_w(RefineState* R, const double* Ainv, int64_t m, int64_t lo, int64_t hi, __nv_bfloat16* W0,
+                          __nv_bfloat16* W1, __nv_bfloat16* W2, cudaStream_t st) {
   const int64_t p = R->p, ldp = R->ldp;
   constexpr int NW_A = 5, NW_B = 4, QW = 4;   // 34-bit A_I^{-1} digits, 27-bit A digits
   {
@@ -365,7 +368,7 @@ ibmi_status refine_form_w(RefineState* R, const double* Ainv, int64_t m, int64_t
                                    (int)((hi + tc::BK - 1) / tc::BK), QW, IBMI_K_INVARIANTS_TC}, st));
   ProfScope ps(IBMI_K_OTHER, st, 0.0);
   note_launch();
-  k_oz_wcombine<<<nblk(m * ldp), 256, 0, st>>>(R->T, m, p, ldp, R->expX, R->expA, QW, lo, hi, Wh, Wl);
+  k_oz_wcombine<<<nblk(m * ldp), 256, 0, st>>>(R->T, m, p, ldp, R->expX, R->expA, QW, lo, hi, W0, W1, W2);
   IBMI_CUDA_TRY(cudaGetLastError());
   return IBMI_OK;
 }

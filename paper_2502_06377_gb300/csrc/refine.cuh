@@ -60,10 +60,10 @@ ibmi_status refine_residual(RefineState* R, const double* X, int64_t ldx, cudaSt
 ibmi_status refine_ns_update(RefineState* R, double* X, int64_t ldx, cudaStream_t st);
 
 // W = A_I^{-1} A_{I,:} (m x p, zero columns on I) from exact digit products
-// (five digits of A_I^{-1}, four of A), written as BF16 hi/lo slices with
+// (five digits of A_I^{-1}, four of A), written as three BF16 slices with
 // row pitch ldp.  Needs refine_set_matrix first; uses the X digit planes.
-ibmi_status refine_form_w(RefineState* R, const double* Ainv, int64_t m, int64_t lo, int64_t hi, __nv_bfloat16* Wh,
-                          __nv_bfloat16* Wl, cudaStream_t st);
+ibmi_status refine_form_w(RefineState* R, const double* Ainv, int64_t m, int64_t lo, int64_t hi, __nv_bfloat16* W0,
+                          __nv_bfloat16* W1, __nv_bfloat16* W2, cudaStream_t st);
 
 // ||I - H A||_F / sqrt(p) from BF16x3 products, for H given by its BF16 hi/lo
 // slice maps (about 5 significant digits; used to decide the hand-over to

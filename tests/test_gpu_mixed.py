@@ -130,3 +130,22 @@ def test_refine_rejects_bad_args(ibmi):
     A = torch.eye(8, dtype=torch.float64, device="cuda")
     s, _ = ibmi.ibmi_refine(A, A.clone(), precision=5)
     assert s == ibmi.IBMI_ERR_INVALID_ARG
+
+
+def test_mixed_full_size_c3_random_spd(ibmi):
+    """p = 8192 random SPD (Q diag(lambda) Q^T, lambda log-uniform in [1, 1e4]),
+    two sets with 2048-row overlap: the BF16x3 sweep stalls, escalates to three
+    slices, and the Newton-Schulz tail reaches the tolerance.  Checked on
+    sampled rows of the residual and sampled columns of the inverse."""
+    A = wl.c3_random_spd()
+    p = A.shape[0]
+    s, res, H = run(ibmi, A, K=2, h=1024, tol=1e-10, max_sweeps=500, ns_theta=0.5)
+    assert s == ibmi.IBMI_OK and res["resid_f"] <= 1e-10, res
+    rng = np.random.default_rng(3)
+    rows = rng.choice(p, 8, replace=False)
+    R = np.eye(p)[rows] - A[rows] @ H
+    assert np.abs(R).max() < 1e-9
+    cols = rng.choice(p, 2, replace=False)
+    X = np.linalg.solve(A, np.eye(p)[:, cols])
+    assert np.abs(H[:, cols] - X).max() <= 1e-8 * np.abs(X).max()
+    print("c3 mixed", res)
