@@ -84,7 +84,10 @@ typedef struct ibmi_plan_desc {
   double tol;              /* stop tolerance (default 1e-10)                                */
   int32_t max_sweeps;      /* sweep cap (default 500, the cap used in Section 5)           */
   int32_t stop_rule;       /* ibmi_stop_rule                                                */
-  int32_t check_every;     /* evaluate the stop quantity every s sweeps (default 1)        */
+  int32_t check_every;     /* minimum sweeps between stop tests (default 1); the library
+                              spaces tests up to 8 sweeps apart while the contraction seen
+                              between tests predicts the target is still further away
+                              (never stops earlier than a test on every sweep would)   */
   double ns_theta;         /* enter Newton-Schulz once ||I - A H||_F <= ns_theta; 0 = off  */
   int32_t ns_max;          /* Newton-Schulz step cap (default 8)                            */
   int32_t init;            /* ibmi_init                                                     */

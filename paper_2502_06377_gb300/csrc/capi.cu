@@ -122,17 +122,21 @@ static ibmi_status invert_impl(ibmi_plan_s* P, const double* A, int64_t lda, dou
   bool to_ns = false;
   int r = 0;
   const double fs = flops_sweep(P), fr = 2.0 * (double)p * p * p;
+  CheckCadence cad;
+  cad.gmin = cad.next = d.check_every;
+  const double target = d.ns_theta > 0.0 ? std::max(d.tol, d.ns_theta / sqrtp) : d.tol;
   while (true) {
     ++r;
     for (int k = 0; k < K; ++k) IBMI_TRY(sweep_step_f64(P, k, H, ldh, st));
     flops += fs;
     res->sweeps = r;
-    if (r % d.check_every != 0 && r < d.max_sweeps) continue;
+    if (r < cad.next && r < d.max_sweeps) continue;
     if (d.stop_rule == IBMI_STOP_PAPER_EST) {
       // eq. error on the last set; the residual is evaluated once at the end
       double e;
       IBMI_TRY(paper_estimate_f64(P, A, lda, H, ldh, st, &e));
       res->paper_est = e;
+      cad.next = r + d.check_every;
       if (!isfinite(e)) { status = IBMI_ERR_NONFINITE; break; }
       if (e <= d.tol || r >= d.max_sweeps) {
         double rho;
@@ -152,6 +156,7 @@ static ibmi_status invert_impl(ibmi_plan_s* P, const double* A, int64_t lda, dou
     if (rho <= d.tol) { status = IBMI_OK; break; }
     if (d.ns_theta > 0.0 && rho * sqrtp <= d.ns_theta) { to_ns = true; break; }
     if (r >= d.max_sweeps) break;
+    cad.after(r, rho, target);
   }
   if (to_ns) {
     IBMI_TRY(ensure_ns_buffers(P));

@@ -293,12 +293,15 @@ ibmi_status mixed_run(ibmi_plan_s* P, const double* A, int64_t lda, double* H, i
   IBMI_TRY(mixed_prepare(P, H, ldh, st));
   int r = 0, stalled = 0;
   double best = INFINITY;
+  CheckCadence cad;
+  cad.gmin = cad.next = d.check_every;
+  const double target = d.ns_theta > 0.0 ? std::max(d.tol, d.ns_theta / sqrtp) : d.tol;
   while (true) {
     ++r;
     for (int k = 0; k < K; ++k) IBMI_TRY(mixed_sweep_step(P, k, st));
     *flops += fs;
     res->sweeps = r;
-    if (r % d.check_every != 0 && r < d.max_sweeps) continue;
+    if (r < cad.next && r < d.max_sweeps) continue;
     double rho;
     IBMI_TRY(refine_cheap_residual(R, M->mapH, st, &rho));
     *flops += fr;
@@ -333,6 +336,7 @@ ibmi_status mixed_run(ibmi_plan_s* P, const double* A, int64_t lda, double* H, i
       if (acc <= d.tol) return IBMI_OK;
       if (r >= d.max_sweeps) return IBMI_NOT_CONVERGED;
     }
+    cad.after(r, rho, target);
   }
   IBMI_TRY(mixed_export(P, H, ldh, st));
   double prev = INFINITY;

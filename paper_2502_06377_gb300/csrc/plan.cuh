@@ -1,5 +1,9 @@
 // Internal plan object and the host-side drivers of each hot-path step.
 #pragma once
+#include <math.h>
+
+#include <algorithm>
+
 #include "common.cuh"
 
 struct ibmi_plan_s {
@@ -43,6 +47,28 @@ struct ibmi_plan_s {
 namespace ibmi {
 
 constexpr int CHOL_NB = 32;
+
+// Stop-test cadence (a6 is as costly as a sweep): after a check, the
+// per-sweep contraction f seen since the previous check predicts how many
+// sweeps the residual needs to reach `target`; the next check comes after
+// about half of them (at least `gmin`, at most 8 sweeps).
+struct CheckCadence {
+  int gmin = 1;
+  int next = 1;
+  int last_r = 0;
+  double last_rho = 0.0;
+  void after(int r, double rho, double target) {
+    int gap = gmin;
+    if (last_r > 0 && rho > 0.0 && last_rho > rho && target > 0.0 && rho > target) {
+      const double f = pow(rho / last_rho, 1.0 / (double)(r - last_r));
+      const double need = log(target / rho) / log(f);
+      gap = (int)std::max<double>(gmin, std::min<double>(8.0, floor(0.5 * need)));
+    }
+    last_r = r;
+    last_rho = rho;
+    next = r + gap;
+  }
+};
 
 // a2 for all sets at once, FP64: A_I^{-1} for every set and, with full_w,
 // W = A_I^{-1} A_{I,:} (zero columns on I) -- the mixed path forms W on tensor
