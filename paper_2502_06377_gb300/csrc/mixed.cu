@@ -107,7 +107,18 @@ __global__ void k_mixed_sym(const float* Spart, int splits, int64_t m, const dou
   float x = (float)(Ainv[idx] - 0.5 * ((double)a + (double)b));
   int64_t o = (lo + i) * ldp + lo + j;
   Hf[o] = x;
-  split3(x, s0[o], s1[o], s2[o]);
+  __nv_bfloat16 t0, t1, t2;
+  split3(x, t0, t1, t2);
+  s0[o] = t0;
+  s1[o] = t1;
+  if (s2) s2[o] = t2;
+}
+
+// All three slices of H from the FP32 master (entering the three-slice sweep).
+__global__ void k_reslice_h(const float* Hf, int64_t n, __nv_bfloat16* s0, __nv_bfloat16* s1, __nv_bfloat16* s2) {
+  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n) return;
+  split3(Hf[idx], s0[idx], s1[idx], s2[idx]);
 }
 
 // a3 epilogue: X = -acc for rows i < m of the set and columns j in I^c;
@@ -129,11 +140,13 @@ struct EpiTcSweepX : tc::EpiBase {
       Hf[r * ldp + j] = x;
       H0[r * ldp + j] = a;
       H1[r * ldp + j] = b;
-      H2[r * ldp + j] = d;
       Hf[j * ldp + r] = x;
       H0[j * ldp + r] = a;
       H1[j * ldp + r] = b;
-      H2[j * ldp + r] = d;
+      if (H2) {   // third slice only while the sweep uses three
+        H2[r * ldp + j] = d;
+        H2[j * ldp + r] = d;
+      }
     }
   }
 };
@@ -226,7 +239,7 @@ ibmi_status mixed_sweep_step(ibmi_plan_s* P, int k, cudaStream_t st) {
       maps.b[s] = M->mapH[s];
     }
     tc::Tiles t{m, 0, 0, nr.r0_end, nr.r1_begin, kr.r0_end, kr.r1_begin, kr.r1_end, 1, M->err};
-    EpiTcSweepX epi{{}, M->Hf, M->Hs[0], M->Hs[1], M->Hs[2], M->ldp, lo, hi, p, m};
+    EpiTcSweepX epi{{}, M->Hf, M->Hs[0], M->Hs[1], S == 3 ? M->Hs[2] : nullptr, M->ldp, lo, hi, p, m};
     ProfScope ps(IBMI_K_SWEEP_X, st, mult * 2.0 * m * n * n);
     if (S == 2) IBMI_CUDA_TRY((tc::launch<2, MX_BN>(maps, t, nr.count(), (int)((m + 127) / 128), epi, st)));
     else IBMI_CUDA_TRY((tc::launch<3, MX_BN>(maps, t, nr.count(), (int)((m + 127) / 128), epi, st)));
@@ -248,7 +261,7 @@ ibmi_status mixed_sweep_step(ibmi_plan_s* P, int k, cudaStream_t st) {
     else IBMI_CUDA_TRY((tc::launch<3, MX_BN>(maps, t, ntn, (int)((m + 127) / 128), epi, st)));
     note_launch();
     k_mixed_sym<<<nblk(m * m), 256, 0, st>>>(M->Spart, splits, m, P->ainv[k], lo, M->ldp, M->Hf, M->Hs[0],
-                                             M->Hs[1], M->Hs[2]);
+                                             M->Hs[1], S == 3 ? M->Hs[2] : nullptr);
     IBMI_CUDA_TRY(cudaGetLastError());
   }
   return IBMI_OK;
@@ -322,6 +335,9 @@ ibmi_status mixed_run(ibmi_plan_s* P, const double* A, int64_t lda, double* H, i
         M->level = 1;
         stalled = 0;
         best = INFINITY;
+        note_launch();
+        k_reslice_h<<<nblk(p * M->ldp), 256, 0, st>>>(M->Hf, p * M->ldp, M->Hs[0], M->Hs[1], M->Hs[2]);
+        IBMI_CUDA_TRY(cudaGetLastError());
       } else if (rho * sqrtp <= 8.0 * d.ns_theta) {
         break;
       }

@@ -39,21 +39,50 @@ __global__ void k_oz_slices(const double* X, int64_t ldx, int64_t ncols, int64_t
   int e = 0;
   if (red[0] > 0.0) frexp(red[0], &e);   // red[0] = f 2^e, f in [0.5, 1)
   if (threadIdx.x == 0) expo[i] = e;
-  const double sc = ldexp(1.0, 55 - e);   // exact power of two
+  // F = rint(x 2^{55-e}) and Flo = the remainder carried 14 bits further,
+  // from the bit pattern of x with integer operations only (no FP64 ALU).
   for (int64_t c = threadIdx.x; c < ldp; c += blockDim.x) {
-    const double xs = (c >= c0 && c < c0 + ncols) ? row[c - c0] * sc : 0.0;
-    long long F = __double2ll_rn(xs);
-    const long long Flo = __double2ll_rn((xs - (double)F) * 16384.0);   // |Flo| <= 2^13
+    long long F = 0, Flo = 0;
+    if (c >= c0 && c < c0 + ncols) {
+      const unsigned long long bits = (unsigned long long)__double_as_longlong(row[c - c0]);
+      const int ex = (int)((bits >> 52) & 0x7ff);
+      const bool neg = (bits >> 63) != 0;
+      if (ex != 0) {   // zeros and subnormals are far below 2^(e-69)
+        const unsigned long long m = (bits & 0xfffffffffffffull) | 0x10000000000000ull;   // 53-bit significand
+        const int sh = ex - 1075 + 55 - e;   // x 2^{55-e} = m 2^sh, sh <= 2 because |x| < 2^e
+        long long qq = 0, lo14 = 0;
+        if (sh >= 0) {
+          qq = (long long)(m << sh);
+        } else if (sh > -68) {
+          const int rs = -sh;
+          if (rs >= 54) {   // |x 2^{55-e}| < 1/2: remainder only
+            lo14 = (long long)(m >> (rs - 14));
+          } else {
+            const unsigned long long q = m >> rs;
+            const unsigned long long rem = m - (q << rs);   // 0 <= rem < 2^rs
+            const unsigned long long half = 1ull << (rs - 1);
+            const bool up = rem >= half;                      // round half away from zero
+            qq = (long long)q + (up ? 1 : 0);
+            if (rs > 14)
+              lo14 = up ? -(long long)(((half << 1) - rem) >> (rs - 14)) : (long long)(rem >> (rs - 14));
+            else
+              lo14 = up ? -(long long)(((half << 1) - rem) << (14 - rs)) : (long long)(rem << (14 - rs));
+          }
+        }
+        F = neg ? -qq : qq;
+        Flo = neg ? -lo14 : lo14;
+      }
+    }
 #pragma unroll
     for (int s = 0; s < 7; ++s) {
       if (s >= nslices) break;
       const int sh = 49 - 7 * s;
       const long long d = (F + (1ll << (sh - 1))) >> sh;
-      F -= d << sh;
+      F -= d * (1ll << sh);
       out.s[s][i * ldp + c] = __int2bfloat16_rn((int)d);
     }
     if (nslices > 7) {
-      long long G = (F << 14) + Flo;   // F = F_7 in [-64, 64)
+      long long G = F * 16384 + Flo;   // F = F_7 in [-64, 64)
 #pragma unroll
       for (int s = 7; s < OZ_S; ++s) {
         if (s >= nslices) break;
@@ -63,7 +92,7 @@ __global__ void k_oz_slices(const double* X, int64_t ldx, int64_t ncols, int64_t
           d = G;
         } else {
           d = (G + (1ll << (sh - 1))) >> sh;
-          G -= d << sh;
+          G -= d * (1ll << sh);
         }
         out.s[s][i * ldp + c] = __int2bfloat16_rn((int)d);
       }
