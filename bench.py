@@ -184,6 +184,8 @@ def run_batch(args):
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
+    lib = ibmi._lib.load()
+    l0 = lib.ibmi_launch_count()
     t0 = time.perf_counter()
     for _ in range(args.steps):
         s, res = ibmi.ibmi_invert_batched(As, Hs, precision=prec, workers=16)
@@ -191,6 +193,7 @@ def run_batch(args):
     if dist:
         dist.barrier()
     dt = shard.max_over_ranks((time.perf_counter() - t0) / args.steps, device="cuda")
+    launches = lib.ibmi_launch_count() - l0
     if dist:
         dist.destroy_process_group()
     if rank != 0:
@@ -207,7 +210,7 @@ def run_batch(args):
                        "note": "rank 0's share shown for convergence counts"},
             "converged": ok, "not_converged": len(res) - ok,
             "resid_f_median": rf[len(rf) // 2], "resid_f_max": rf[-1],
-            "achieved_tflops": flops / dt / 1e12,
+            "achieved_tflops": flops / dt / 1e12, "gpu_launches": launches,
             "sum_p3": float(sum(float(m.shape[0]) ** 3 for m in mats))}
     print(json.dumps(line), flush=True)
     return 0

@@ -168,6 +168,9 @@ typedef struct ibmi_batch_opts {
   int32_t ns_max;      /* default 8                                            */
   int32_t workers;     /* concurrent streams, 1..64, default 8                 */
   int32_t autotune;    /* 1 (default): tune (K, h) per size bucket              */
+  int32_t graphs;      /* 1 (default): mixed plans replay captured CUDA graphs
+                          (one capture per plan and phase); 0: direct launches.
+                          Both give bit-identical results.                     */
 } ibmi_batch_opts;
 void ibmi_batch_opts_init(ibmi_batch_opts* opts);
 
@@ -176,12 +179,19 @@ size_t ibmi_plan_bytes(const ibmi_plan_desc* desc);
 
 /* Inverts n SPD matrices; A[i], H[i] are device pointers to p[i] x p[i]
  * row-major FP64 matrices with leading dimensions lda[i], ldh[i].  Per-matrix
- * results in out[i] (status, sweeps, ...).  Returns IBMI_OK when all
+ * results in out[i] (status, sweeps, ...).  A matrix that does not converge
+ * with its bucket's tuned partition is run once more with cores of about 256
+ * rows (2 to 8 sets) and 30% overlap (its counts then include both runs).  Returns IBMI_OK when all
  * converged, else the first failure status (NOT_CONVERGED ranks lowest).
- * Synchronous. */
+ * Synchronous.  The worker pool (streams, plans, captured CUDA graphs) is
+ * kept for the next call on the same device until ibmi_batch_release();
+ * batched calls are serialised. */
 ibmi_status ibmi_invert_batched(int32_t n, const int64_t* p, const double* const* A, const int64_t* lda,
                                 double* const* H, const int64_t* ldh, const ibmi_batch_opts* opts,
                                 ibmi_result* out);
+
+/* Frees the pooled batch workers (streams, plans, graphs) of every device. */
+ibmi_status ibmi_batch_release(void);
 
 /* Continuous-batching server.  Requests (host matrices) are queued; a request
  * is admitted when its device bytes (A, H and padded staging, 16 (p^2 + pb^2)

@@ -185,6 +185,13 @@ def ibmi_invert_batched(As, Hs, **opts):
     return s, [out[i].as_dict() for i in range(n)]
 
 
+def ibmi_batch_release() -> None:
+    """Frees the pooled batch workers (streams, plans, captured graphs)."""
+    s = _lib.load().ibmi_batch_release()
+    if s != IBMI_OK:
+        raise IbmiError(s, "ibmi_batch_release")
+
+
 class Server:
     """Continuous-batching inversion server (ibmi_serve_*)."""
 

@@ -104,6 +104,7 @@ class ibmi_batch_opts(C.Structure):
     _fields_ = [
         ("precision", C.c_int32), ("tol", C.c_double), ("max_sweeps", C.c_int32),
         ("ns_theta", C.c_double), ("ns_max", C.c_int32), ("workers", C.c_int32), ("autotune", C.c_int32),
+        ("graphs", C.c_int32),
     ]
 
 
@@ -113,6 +114,7 @@ _SIGS.update({
     "ibmi_invert_batched": (C.c_int, [C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_void_p),
                                       C.POINTER(C.c_int64), C.POINTER(C.c_void_p), C.POINTER(C.c_int64),
                                       C.POINTER(ibmi_batch_opts), C.POINTER(ibmi_result)]),
+    "ibmi_batch_release": (C.c_int, []),
     "ibmi_serve_create": (C.c_int, [C.c_size_t, C.POINTER(ibmi_batch_opts), C.POINTER(C.c_void_p)]),
     "ibmi_serve_submit": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_double,
                                     C.POINTER(C.c_uint64)]),

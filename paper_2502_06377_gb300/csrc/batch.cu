@@ -24,6 +24,7 @@
 #include <unordered_map>
 #include <vector>
 
+#include "mixed.cuh"
 #include "plan.cuh"
 
 namespace ibmi {
@@ -81,14 +82,13 @@ static ibmi_plan_desc desc_for(const Shape& s, const ibmi_batch_opts& o) {
   return d;
 }
 
-// One worker: a stream, padded staging buffers and a small plan cache.
+// One worker: a stream and a small plan cache.  Every plan runs on its own
+// staging buffers (P->dA, P->dH of the bucket order), so the CUDA graphs the
+// mixed pipeline captures stay valid from one matrix to the next.
 struct Worker {
   int device = 0;
   cudaStream_t stream = nullptr;
-  std::map<Shape, ibmi_plan_t> plans;
-  double* Ab = nullptr;
-  double* Hb = nullptr;
-  int64_t cap = 0;     // staging capacity in elements
+  std::map<std::pair<Shape, int>, ibmi_plan_t> plans;   // by (partition, precision)
   size_t plan_bytes = 0;
 
   ibmi_status init(int dev) {
@@ -105,49 +105,54 @@ struct Worker {
   void destroy() {
     cudaSetDevice(device);
     release_plans();
-    cudaFree(Ab);
-    cudaFree(Hb);
     if (stream) cudaStreamDestroy(stream);
   }
-  ibmi_status staging(int64_t pb) {
-    if (pb * pb <= cap) return IBMI_OK;
-    cudaFree(Ab);
-    cudaFree(Hb);
-    Ab = Hb = nullptr;
-    cap = 0;
-    IBMI_CUDA_TRY(cudaMalloc(&Ab, sizeof(double) * pb * pb));
-    IBMI_CUDA_TRY(cudaMalloc(&Hb, sizeof(double) * pb * pb));
-    cap = pb * pb;
-    return IBMI_OK;
-  }
   ibmi_status plan(const Shape& s, const ibmi_batch_opts& o, size_t max_plan_bytes, ibmi_plan_t* out) {
-    auto it = plans.find(s);
-    if (it != plans.end()) { *out = it->second; return IBMI_OK; }
+    auto it = plans.find({s, o.precision});
+    if (it != plans.end()) {
+      // stopping parameters may differ from call to call
+      ibmi_plan_t P = it->second;
+      const ibmi_plan_desc d = desc_for(s, o);
+      P->d.tol = d.tol;
+      P->d.max_sweeps = d.max_sweeps;
+      P->d.ns_theta = d.ns_theta;
+      P->d.ns_max = d.ns_max;
+      if (o.precision == IBMI_MIXED) mixed_enable_graphs(P, o.graphs != 0);
+      *out = P;
+      return IBMI_OK;
+    }
     ibmi_plan_desc d = desc_for(s, o);
-    const size_t need = ibmi_plan_bytes(&d);
+    const size_t need = ibmi_plan_bytes(&d) + 16 * (size_t)s.p * s.p;
     if (max_plan_bytes && plan_bytes + need > max_plan_bytes) release_plans();
     ibmi_plan_t P = nullptr;
     IBMI_TRY(ibmi_plan(&d, &P));
-    plans[s] = P;
+    if (cudaMalloc(&P->dA, sizeof(double) * s.p * s.p) != cudaSuccess ||
+        cudaMalloc(&P->dH, sizeof(double) * s.p * s.p) != cudaSuccess) {
+      cudaGetLastError();
+      ibmi_plan_destroy(P);
+      return IBMI_ERR_OOM;
+    }
+    if (o.precision == IBMI_MIXED) mixed_enable_graphs(P, o.graphs != 0);
+    plans[{s, o.precision}] = P;
     plan_bytes += need;
     *out = P;
     return IBMI_OK;
   }
-  // Inverts one matrix (device A, H of order p) with the plan for `s`.
+  // Inverts one matrix (device A, H of order p) with the plan for `s`: A is
+  // embedded in the plan's staging buffer (identity padding up to s.p), the
+  // result copied back from its leading block.
   ibmi_status run(const Shape& s, const ibmi_batch_opts& o, size_t max_plan_bytes, const double* A, int64_t lda,
                   int64_t p, double* H, int64_t ldh, ibmi_result* res) {
     ibmi_plan_t P;
     IBMI_TRY(plan(s, o, max_plan_bytes, &P));
     const int64_t pb = s.p;
-    if (pb == p) return ibmi_invert(P, A, lda, H, ldh, stream, res);
-    IBMI_TRY(staging(pb));
     note_launch();
-    k_pad_embed<<<(unsigned)((pb * pb + 255) / 256), 256, 0, stream>>>(A, lda, p, Ab, pb);
+    k_pad_embed<<<(unsigned)((pb * pb + 255) / 256), 256, 0, stream>>>(A, lda, p, P->dA, pb);
     IBMI_CUDA_TRY(cudaGetLastError());
-    ibmi_status st = ibmi_invert(P, Ab, pb, Hb, pb, stream, res);
+    ibmi_status st = ibmi_invert(P, P->dA, pb, P->dH, pb, stream, res);
     if (st == IBMI_OK || st == IBMI_NOT_CONVERGED) {
       note_launch();
-      k_unpad<<<(unsigned)((p * p + 255) / 256), 256, 0, stream>>>(Hb, pb, p, H, ldh);
+      k_unpad<<<(unsigned)((p * p + 255) / 256), 256, 0, stream>>>(P->dH, pb, p, H, ldh);
       IBMI_CUDA_TRY(cudaGetLastError());
       IBMI_CUDA_TRY(cudaStreamSynchronize(stream));
     }
@@ -195,12 +200,51 @@ static Shape tune_bucket(Worker& w, int64_t pb, const ibmi_batch_opts& o, const 
   return best;
 }
 
+// Process-wide pool of batch workers per device: their streams, plans and the
+// CUDA graphs captured in those plans persist from one batched call to the
+// next.  One batched call runs at a time.
+static std::mutex g_pool_mu;
+static std::map<int, std::vector<std::unique_ptr<Worker>>> g_pool;
+static constexpr size_t kWorkerPlanCap = (size_t)6 << 30;   // plan bytes a pooled worker may keep
+
+// The partition used when the tuned one does not converge for a matrix:
+// cores of about 256 rows (2 to 8 sets), overlap 2h = 30% of the core.
+// Smaller blocks keep the mixed-precision floor of the sweeps low.
+static Shape robust_shape(int64_t pb) {
+  const int32_t K = (int32_t)std::min<int64_t>(8, std::max<int64_t>(2, pb / 256));
+  const int64_t m = pb / K;
+  return Shape{pb, K, std::max<int64_t>(4, (int64_t)llround(0.15 * (double)m))};
+}
+
 static Shape shape_for(int64_t p, const ibmi_batch_opts& o) {
   const int64_t pb = bucket_of(p);
   std::lock_guard<std::mutex> g(g_tune_mu);
   auto it = g_tuned.find({pb, o.precision});
   if (it != g_tuned.end()) return it->second;
   return default_shape(pb);
+}
+
+// Inverts one matrix with its bucket's tuned partition; a matrix that does not
+// converge with it is run once more with the robust partition (the counts in
+// *res then cover both runs).
+static ibmi_status run_tuned(Worker& w, const ibmi_batch_opts& o, size_t max_plan_bytes, const double* A, int64_t lda,
+                             int64_t p, double* H, int64_t ldh, ibmi_result* res) {
+  memset(res, 0, sizeof(ibmi_result));
+  const Shape s = shape_for(p, o);
+  ibmi_status st = w.run(s, o, max_plan_bytes, A, lda, p, H, ldh, res);
+  const Shape rs = robust_shape(bucket_of(p));
+  if (st == IBMI_NOT_CONVERGED && (s.K != rs.K || s.h != rs.h)) {
+    ibmi_result again;
+    memset(&again, 0, sizeof(again));
+    st = w.run(rs, o, max_plan_bytes, A, lda, p, H, ldh, &again);
+    again.sweeps += res->sweeps;
+    again.ns_steps += res->ns_steps;
+    again.flops += res->flops;
+    again.seconds += res->seconds;
+    *res = again;
+  }
+  res->status = st;
+  return st;
 }
 
 // ----------------------------------------------------------------- server --
@@ -241,7 +285,7 @@ struct ibmi_server_impl {
 namespace ibmi {
 
 static size_t request_bytes(int64_t p) {
-  // device copies of A and H plus the padded staging of one worker
+  // device copies of A and H plus the padded staging of the plan that runs it
   const int64_t pb = bucket_of(p);
   return sizeof(double) * (size_t)(2 * p * p + 2 * pb * pb);
 }
@@ -300,7 +344,7 @@ static void server_loop(ibmi_server_impl* S, int wi) {
                                          w.stream) != cudaSuccess)
       st = IBMI_ERR_CUDA;
     if (st == IBMI_OK)
-      st = w.run(shape_for(p, o), o, (S->budget - S->req_budget) / S->workers.size(), dA, p, p, dH, p, &r->res);
+      st = run_tuned(w, o, (S->budget - S->req_budget) / S->workers.size(), dA, p, p, dH, p, &r->res);
     if (st == IBMI_OK || st == IBMI_NOT_CONVERGED) {
       r->H.resize((size_t)p * p);
       if (cudaMemcpyAsync(r->H.data(), dH, sizeof(double) * p * p, cudaMemcpyDeviceToHost, w.stream) != cudaSuccess ||
@@ -341,6 +385,7 @@ void ibmi_batch_opts_init(ibmi_batch_opts* o) {
   o->ns_max = 8;
   o->workers = 8;
   o->autotune = 1;
+  o->graphs = 1;
 }
 
 size_t ibmi_plan_bytes(const ibmi_plan_desc* d) {
@@ -374,9 +419,14 @@ ibmi_status ibmi_invert_batched(int32_t n, const int64_t* p, const double* const
   if (n == 0) return IBMI_OK;
   int dev = 0;
   IBMI_CUDA_TRY(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> pool_lock(g_pool_mu);
+  auto& pool = g_pool[dev];
   const int W = std::min<int>(o.workers, n);
-  std::vector<Worker> workers(W);
-  for (auto& w : workers) IBMI_TRY(w.init(dev));
+  while ((int)pool.size() < W) {
+    auto w = std::make_unique<Worker>();
+    IBMI_TRY(w->init(dev));
+    pool.push_back(std::move(w));
+  }
   // largest matrices first: better balance across workers
   std::vector<int32_t> order(n);
   for (int32_t i = 0; i < n; ++i) order[i] = i;
@@ -399,7 +449,7 @@ ibmi_status ibmi_invert_batched(int32_t n, const int64_t* p, const double* const
         cudaSetDevice(dev);
         for (int j; (j = next.fetch_add(1)) < (int)firsts.size();) {
           const int32_t i = firsts[j];
-          tune_bucket(workers[wi], bucket_of(p[i]), o, A[i], lda[i], p[i], H[i], ldh[i]);
+          tune_bucket(*pool[wi], bucket_of(p[i]), o, A[i], lda[i], p[i], H[i], ldh[i]);
         }
       });
     for (auto& t : th) t.join();
@@ -410,20 +460,26 @@ ibmi_status ibmi_invert_batched(int32_t n, const int64_t* p, const double* const
   for (int wi = 0; wi < W; ++wi)
     th.emplace_back([&, wi] {
       cudaSetDevice(dev);
-      Worker& w = workers[wi];
+      Worker& w = *pool[wi];
       for (int j; (j = next.fetch_add(1)) < n;) {
         const int32_t i = order[j];
-        memset(&out[i], 0, sizeof(ibmi_result));
-        st[i] = w.run(shape_for(p[i], o), o, 0, A[i], lda[i], p[i], H[i], ldh[i], &out[i]);
+        st[i] = run_tuned(w, o, kWorkerPlanCap, A[i], lda[i], p[i], H[i], ldh[i], &out[i]);
         out[i].status = st[i];
       }
     });
   for (auto& t : th) t.join();
-  for (auto& w : workers) w.destroy();
   ibmi_status worst = IBMI_OK;
   for (int32_t i = 0; i < n; ++i)
     if (st[i] != IBMI_OK && (worst == IBMI_OK || worst == IBMI_NOT_CONVERGED)) worst = st[i];
   return worst;
+}
+
+ibmi_status ibmi_batch_release(void) {
+  std::lock_guard<std::mutex> pool_lock(g_pool_mu);
+  for (auto& kv : g_pool)
+    for (auto& w : kv.second) w->destroy();
+  g_pool.clear();
+  return IBMI_OK;
 }
 
 ibmi_status ibmi_serve_create(size_t hbm_budget, const ibmi_batch_opts* opts, ibmi_server_t* out) {

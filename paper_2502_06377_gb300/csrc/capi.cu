@@ -98,10 +98,15 @@ static ibmi_status invert_impl(ibmi_plan_s* P, const double* A, int64_t lda, dou
   const ibmi_plan_desc& d = P->d;
   const double sqrtp = sqrt((double)p);
   double flops = 0.0;
+  const bool mixed = d.precision == IBMI_MIXED;
+  if (mixed) {
+    ibmi_status s = mixed_run(P, A, lda, H, ldh, st, res, &flops);
+    res->flops = flops;
+    return s;
+  }
   // a2: invariants
   IBMI_CUDA_TRY(cudaMemsetAsync(P->dstatus, 0, sizeof(DevStatus), st));
-  const bool mixed = d.precision == IBMI_MIXED;
-  IBMI_TRY(invariants_all(P, A, lda, !mixed, st));
+  IBMI_TRY(invariants_all(P, A, lda, true, st));
   flops += flops_plan(P);
   DevStatus hs;
   IBMI_CUDA_TRY(cudaMemcpyAsync(&hs, P->dstatus, sizeof(hs), cudaMemcpyDeviceToHost, st));
@@ -112,11 +117,6 @@ static ibmi_status invert_impl(ibmi_plan_s* P, const double* A, int64_t lda, dou
     return IBMI_ERR_NOT_SPD;
   }
   if (d.init == IBMI_INIT_IDENTITY) IBMI_TRY(set_identity(H, ldh, p, st));
-  if (mixed) {
-    ibmi_status s = mixed_run(P, A, lda, H, ldh, st, res, &flops);
-    res->flops = flops;
-    return s;
-  }
   // Algorithm 1: sweeps with the stop test every check_every sweeps
   ibmi_status status = IBMI_NOT_CONVERGED;
   bool to_ns = false;
@@ -543,6 +543,8 @@ cudaEvent_t take_event() {
 }  // namespace
 
 void note_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+bool prof_on() { return g_prof_on.load(std::memory_order_relaxed); }
 
 void prof_begin(int k, cudaStream_t st) {
   if (!g_prof_on.load(std::memory_order_relaxed) || k < 0 || k >= IBMI_K_COUNT) return;

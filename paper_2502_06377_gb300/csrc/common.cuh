@@ -28,6 +28,7 @@ void set_last_error(const std::string& s);
   } while (0)
 
 // Launch accounting and per-class event timing (ibmi_prof_*).
+bool prof_on();
 void note_launch(int n = 1);
 void prof_begin(int kclass, cudaStream_t st);
 void prof_end(int kclass, cudaStream_t st, double flops);

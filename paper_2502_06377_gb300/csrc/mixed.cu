@@ -46,6 +46,15 @@ bool make_map_bf16(CUtensorMap* map, const void* base, int64_t rows, int64_t col
 }  // namespace tc
 
 constexpr int MX_BN = 128;   // N tile of the sweep products
+constexpr int kRadiusIters = 40;            // power-iteration steps of the radius estimate
+constexpr double kRadiusHandOver = 0.5;     // hand over to Newton-Schulz below this radius
+
+// One captured phase: the executable graph and its kernel-node count (added
+// to the launch counter on every replay).
+struct PhaseGraph {
+  cudaGraphExec_t exec = nullptr;
+  int kernels = 0;
+};
 
 struct MixedState {
   int64_t ldp = 0;                       // padded row pitch of all mixed arrays (multiple of 64)
@@ -60,7 +69,69 @@ struct MixedState {
   std::vector<CUtensorMap> mapW[3];
   void* pool = nullptr;
   RefineState ref;                       // FP64-accurate residual + Newton-Schulz
+  // CUDA graphs of the pipeline's phases (graph mode): captured on first use
+  // for the A and H the plan was run with, replayed afterwards.
+  bool graphs = false;
+  const double* gA = nullptr;
+  const double* gH = nullptr;
+  PhaseGraph g_setup, g_sweep[2], g_cheap, g_reslice, g_export_resid, g_resid, g_update, g_radius;
 };
+
+static void drop_graphs(MixedState* M) {
+  for (PhaseGraph* g : {&M->g_setup, &M->g_sweep[0], &M->g_sweep[1], &M->g_cheap, &M->g_reslice,
+                        &M->g_export_resid, &M->g_resid, &M->g_update, &M->g_radius}) {
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    *g = PhaseGraph{};
+  }
+}
+
+// Runs `body` (kernel launches only, no host synchronisation) directly, or in
+// graph mode captures it once into *g and replays the graph.  While per-class
+// profiling is on, launches are direct (its events are host-side records).
+template <class F>
+static ibmi_status graph_or_run(MixedState* M, PhaseGraph* g, cudaStream_t st, F&& body) {
+  if (!M->graphs || prof_on()) return body();
+  if (!g->exec) {   // the launches noted while capturing count the first run
+    cudaGraph_t graph = nullptr;
+    IBMI_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    const ibmi_status s = body();
+    const cudaError_t e = cudaStreamEndCapture(st, &graph);
+    if (s != IBMI_OK || e != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      if (s == IBMI_OK) set_last_error(std::string("graph capture: ") + cudaGetErrorString(e));
+      return s != IBMI_OK ? s : IBMI_ERR_CUDA;
+    }
+    size_t n = 0;
+    cudaGraphGetNodes(graph, nullptr, &n);
+    std::vector<cudaGraphNode_t> nodes(n);
+    if (n) cudaGraphGetNodes(graph, nodes.data(), &n);
+    int kernels = 0;
+    for (cudaGraphNode_t v : nodes) {
+      cudaGraphNodeType t;
+      if (cudaGraphNodeGetType(v, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++kernels;
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&g->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) {
+      g->exec = nullptr;
+      set_last_error(std::string("graph instantiate: ") + cudaGetErrorString(ei));
+      return IBMI_ERR_CUDA;
+    }
+    g->kernels = kernels;
+  } else {
+    note_launch(g->kernels);
+  }
+  IBMI_CUDA_TRY(cudaGraphLaunch(g->exec, st));
+  return IBMI_OK;
+}
+
+void mixed_enable_graphs(ibmi_plan_s* P, bool on) {
+  MixedState* M = (MixedState*)P->mixed;
+  if (!M) return;
+  if (!on) drop_graphs(M);
+  M->graphs = on;
+}
 
 static MixedState* MS(ibmi_plan_s* P) { return (MixedState*)P->mixed; }
 
@@ -207,6 +278,7 @@ ibmi_status mixed_create(ibmi_plan_s* P) {
 void mixed_destroy(ibmi_plan_s* P) {
   MixedState* M = MS(P);
   if (!M) return;
+  drop_graphs(M);
   refine_destroy(&M->ref);
   cudaFree(M->pool);
   delete M;
@@ -267,12 +339,18 @@ ibmi_status mixed_sweep_step(ibmi_plan_s* P, int k, cudaStream_t st) {
   return IBMI_OK;
 }
 
-ibmi_status mixed_export(ibmi_plan_s* P, double* H, int64_t ldh, cudaStream_t st) {
+static ibmi_status mixed_export_launch(ibmi_plan_s* P, double* H, int64_t ldh, cudaStream_t st) {
   MixedState* M = MS(P);
   const int64_t p = P->d.p;
   note_launch();
   k_export_h<<<nblk(p * p), 256, 0, st>>>(M->Hf, M->ldp, p, H, ldh);
   IBMI_CUDA_TRY(cudaGetLastError());
+  return IBMI_OK;
+}
+
+ibmi_status mixed_export(ibmi_plan_s* P, double* H, int64_t ldh, cudaStream_t st) {
+  MixedState* M = MS(P);
+  IBMI_TRY(mixed_export_launch(P, H, ldh, st));
   int herr = 0;
   IBMI_CUDA_TRY(cudaMemcpyAsync(&herr, M->err, sizeof(int), cudaMemcpyDeviceToHost, st));
   IBMI_CUDA_TRY(cudaStreamSynchronize(st));
@@ -291,32 +369,65 @@ ibmi_status mixed_run(ibmi_plan_s* P, const double* A, int64_t lda, double* H, i
   const int64_t p = d.p;
   const int K = (int)P->lo.size();
   const double sqrtp = sqrt((double)p), fr = 2.0 * (double)p * p * p;
-  double fs = 0.0;
+  double fs = 0.0, fplan = 0.0;
   for (int k = 0; k < K; ++k) {
     const double m = (double)(P->hi[k] - P->lo[k]), n = (double)p - m;
     fs += 2.0 * m * n * n + 2.0 * m * m * n;
+    fplan += m * m * m / 3.0 + 2.0 * m * m * m + 2.0 * m * m * n;
   }
-  IBMI_CUDA_TRY(cudaMemsetAsync(M->err, 0, sizeof(int), st));
+  if (M->graphs && (M->gA != A || M->gH != H)) {   // graphs bake in the buffers they were captured with
+    drop_graphs(M);
+    M->gA = A;
+    M->gH = H;
+  }
+  // a2 (FP64 factorisations; W on tensor cores), the iterate and A's slices
+  IBMI_TRY(graph_or_run(M, &M->g_setup, st, [&]() -> ibmi_status {
+    IBMI_CUDA_TRY(cudaMemsetAsync(P->dstatus, 0, sizeof(DevStatus), st));
+    IBMI_CUDA_TRY(cudaMemsetAsync(M->err, 0, sizeof(int), st));
+    IBMI_TRY(invariants_all(P, A, lda, false, st));
+    if (d.init == IBMI_INIT_IDENTITY) IBMI_TRY(set_identity(H, ldh, p, st));
+    IBMI_TRY(refine_set_matrix(R, A, lda, st));
+    for (int k = 0; k < K; ++k)
+      IBMI_TRY(refine_form_w(R, P->ainv[k], P->hi[k] - P->lo[k], P->lo[k], P->hi[k], M->Ws[0][k], M->Ws[1][k],
+                             M->Ws[2][k], st));
+    return mixed_prepare(P, H, ldh, st);
+  }));
+  *flops += fplan;
+  DevStatus hs;
+  IBMI_CUDA_TRY(cudaMemcpyAsync(&hs, P->dstatus, sizeof(hs), cudaMemcpyDeviceToHost, st));
+  IBMI_CUDA_TRY(cudaStreamSynchronize(st));
+  if (hs.code == IBMI_ERR_NOT_SPD) {
+    res->bad_block = hs.block;
+    res->bad_pivot = hs.pivot;
+    return IBMI_ERR_NOT_SPD;
+  }
   M->level = 0;
-  IBMI_TRY(refine_set_matrix(R, A, lda, st));
-  // a2 on tensor cores: W_k = A_I^{-1} A_{I,:} from exact digit-sliced products
-  for (int k = 0; k < K; ++k)
-    IBMI_TRY(refine_form_w(R, P->ainv[k], P->hi[k] - P->lo[k], P->lo[k], P->hi[k], M->Ws[0][k], M->Ws[1][k],
-                           M->Ws[2][k], st));
-  IBMI_TRY(mixed_prepare(P, H, ldh, st));
+  double pending = NAN;   // accurate residual of the current H when it was just taken
   int r = 0, stalled = 0;
   double best = INFINITY;
   CheckCadence cad;
   cad.gmin = cad.next = d.check_every;
   const double target = d.ns_theta > 0.0 ? std::max(d.tol, d.ns_theta / sqrtp) : d.tol;
+  auto accurate = [&](double* acc) -> ibmi_status {   // export H, FP64-accurate residual
+    IBMI_TRY(graph_or_run(M, &M->g_export_resid, st, [&]() -> ibmi_status {
+      IBMI_TRY(mixed_export_launch(P, H, ldh, st));
+      return refine_residual_launch(R, H, ldh, st);
+    }));
+    *flops += fr;
+    return refine_read(R, st, acc);
+  };
   while (true) {
     ++r;
-    for (int k = 0; k < K; ++k) IBMI_TRY(mixed_sweep_step(P, k, st));
+    IBMI_TRY(graph_or_run(M, &M->g_sweep[M->level], st, [&]() -> ibmi_status {
+      for (int k = 0; k < K; ++k) IBMI_TRY(mixed_sweep_step(P, k, st));
+      return IBMI_OK;
+    }));
     *flops += fs;
     res->sweeps = r;
     if (r < cad.next && r < d.max_sweeps) continue;
     double rho;
-    IBMI_TRY(refine_cheap_residual(R, M->mapH, st, &rho));
+    IBMI_TRY(graph_or_run(M, &M->g_cheap, st, [&]() { return refine_cheap_residual_launch(R, M->mapH, st); }));
+    IBMI_TRY(refine_read(R, st, &rho));
     *flops += fr;
     res->resid_f = rho;
     if (!isfinite(rho)) return IBMI_ERR_NONFINITE;
@@ -324,10 +435,10 @@ ibmi_status mixed_run(ibmi_plan_s* P, const double* A, int64_t lda, double* H, i
     // The sweep products have an accuracy floor (two BF16 slices: about
     // kappa(A) * 1e-5 in rho).  When the residual stops falling (three checks
     // without a 5% gain) the sweep first moves to three slices (24-bit
-    // operands, six products); if it stalls there too and ||I - A H||_F is
-    // within 8 theta, the 2-norm that eq. newton needs is usually below 1
-    // already, so the Newton-Schulz tail is tried (it stops if a step does not
-    // help).
+    // operands, six products); if it stalls there too, the Newton-Schulz
+    // tail is tried when ||I - A H||_F is within 8 theta or the measured
+    // spectral radius of I - X A is at most 1/2 (it stops if a step does not
+    // help); otherwise the sweeps go on.
     stalled = rho > 0.95 * best ? stalled + 1 : 0;
     best = fmin(best, rho);
     if (d.ns_theta > 0.0 && stalled >= 3) {
@@ -335,37 +446,59 @@ ibmi_status mixed_run(ibmi_plan_s* P, const double* A, int64_t lda, double* H, i
         M->level = 1;
         stalled = 0;
         best = INFINITY;
-        note_launch();
-        k_reslice_h<<<nblk(p * M->ldp), 256, 0, st>>>(M->Hf, p * M->ldp, M->Hs[0], M->Hs[1], M->Hs[2]);
-        IBMI_CUDA_TRY(cudaGetLastError());
+        IBMI_TRY(graph_or_run(M, &M->g_reslice, st, [&]() -> ibmi_status {
+          note_launch();
+          k_reslice_h<<<nblk(p * M->ldp), 256, 0, st>>>(M->Hf, p * M->ldp, M->Hs[0], M->Hs[1], M->Hs[2]);
+          IBMI_CUDA_TRY(cudaGetLastError());
+          return IBMI_OK;
+        }));
       } else if (rho * sqrtp <= 8.0 * d.ns_theta) {
         break;
+      } else {
+        // ||I - A H||_F bounds the spectral radius of I - X A that
+        // eq. newton needs from above, often by far; measure the radius.
+        double acc, rad;
+        IBMI_TRY(accurate(&acc));
+        res->resid_f = acc;
+        if (acc <= d.tol) return IBMI_OK;
+        IBMI_TRY(graph_or_run(M, &M->g_radius, st, [&]() { return refine_q_radius_launch(R, kRadiusIters, st); }));
+        *flops += 2.0 * kRadiusIters * (double)p * p;
+        IBMI_TRY(refine_q_radius_read(R, st, &rad));
+        if (rad <= kRadiusHandOver) {
+          pending = acc;
+          break;
+        }
+        stalled = 0;
       }
     }
     if (rho <= d.tol || r >= d.max_sweeps) {
       // BF16x3 cannot certify tol: confirm with the FP64-accurate residual
-      IBMI_TRY(mixed_export(P, H, ldh, st));
       double acc;
-      IBMI_TRY(refine_residual(R, H, ldh, st, &acc));
-      *flops += fr;
+      IBMI_TRY(accurate(&acc));
       res->resid_f = acc;
       if (acc <= d.tol) return IBMI_OK;
       if (r >= d.max_sweeps) return IBMI_NOT_CONVERGED;
     }
     cad.after(r, rho, target);
   }
-  IBMI_TRY(mixed_export(P, H, ldh, st));
   double prev = INFINITY;
   for (int s = 0;; ++s) {
     double rho;
-    IBMI_TRY(refine_residual(R, H, ldh, st, &rho));
-    *flops += fr;
+    if (s == 0 && !isnan(pending)) {
+      rho = pending;
+    } else if (s == 0) {
+      IBMI_TRY(accurate(&rho));
+    } else {
+      IBMI_TRY(graph_or_run(M, &M->g_resid, st, [&]() { return refine_residual_launch(R, H, ldh, st); }));
+      *flops += fr;
+      IBMI_TRY(refine_read(R, st, &rho));
+    }
     res->resid_f = rho;
     if (!isfinite(rho)) return IBMI_ERR_NONFINITE;
     if (rho <= d.tol) return IBMI_OK;
     if (s >= d.ns_max || !(rho < prev)) return IBMI_NOT_CONVERGED;
     prev = rho;
-    IBMI_TRY(refine_ns_update(R, H, ldh, st));
+    IBMI_TRY(graph_or_run(M, &M->g_update, st, [&]() { return refine_ns_update(R, H, ldh, st); }));
     *flops += fr;
     res->ns_steps = s + 1;
   }

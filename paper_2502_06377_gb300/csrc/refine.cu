@@ -242,6 +242,45 @@ __global__ void k_sym_into(const double* Xn, int64_t p, double* X, int64_t ldx) 
   X[i * ldx + j] = 0.5 * (Xn[i * p + j] + Xn[j * p + i]);
 }
 
+// Power iteration on the dense Q (p x p, row pitch p): y = Q v, one warp per row.
+__global__ void k_q_gemv(const double* Q, int64_t p, const double* v, double* y) {
+  const int64_t i = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (i >= p) return;
+  const double* row = Q + i * p;
+  double s = 0.0;
+  for (int64_t j = lane; j < p; j += 32) s += row[j] * v[j];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) y[i] = s;
+}
+
+// v = y / ||y||, est = ||y|| (one block); init: v = a fixed unit start vector
+// with components of both signs and unequal sizes.
+__global__ void k_q_normalize(const double* y, int64_t p, double* v, double* est, int init) {
+  __shared__ double red[32];
+  __shared__ double nrm;
+  double s = 0.0;
+  for (int64_t j = threadIdx.x; j < p; j += blockDim.x) {
+    const double t = init ? (1.0 + 0.37 * (double)(j % 5)) * ((j & 1) ? -1.0 : 1.0) : y[j];
+    s += t * t;
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x / 32); ++w) t += red[w];
+    nrm = sqrt(t);
+    if (!init) est[0] = nrm;
+  }
+  __syncthreads();
+  const double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
+  for (int64_t j = threadIdx.x; j < p; j += blockDim.x) {
+    const double t = init ? (1.0 + 0.37 * (double)(j % 5)) * ((j & 1) ? -1.0 : 1.0) : y[j];
+    v[j] = t * inv;
+  }
+}
+
 // --------------------------------------------------------------- host ----
 
 static constexpr int RF_BN = 128;   // N tile of the BF16x3 residual
@@ -256,7 +295,8 @@ ibmi_status refine_create(RefineState* R, int64_t p, int* err) {
   const int64_t tiles = ((p + 127) / 128) * ((p + RF_BN - 1) / RF_BN);
   R->n_partials = std::max<int64_t>(tiles * 4, (p * ldp + 255) / 256) + 8;
   size_t bytes = plane16 * (OZ_SA + OZ_SX + NS_S + 2) + sizeof(int) * (size_t)(OZ_QMAX + 1) * p * ldp +
-                 sizeof(double) * p * p + sizeof(double) * R->n_partials + 3 * sizeof(int) * p + 64 * 256;
+                 sizeof(double) * p * p + sizeof(double) * R->n_partials + 3 * sizeof(int) * p +
+                 sizeof(double) * (2 * p + 8) + 64 * 256;
   if (cudaMalloc(&R->pool, bytes) != cudaSuccess) {
     cudaGetLastError();
     return IBMI_ERR_OOM;
@@ -274,6 +314,7 @@ ibmi_status refine_create(RefineState* R, int64_t p, int* err) {
   R->expA = (int*)take(sizeof(int) * p);
   R->expX = (int*)take(sizeof(int) * p);
   R->expQ = (int*)take(sizeof(int) * p);
+  R->pv = (double*)take(sizeof(double) * (2 * p + 8));
   bool ok = true;
   for (int s = 0; s < OZ_SA; ++s) ok &= tc::make_map_bf16(&R->mAo[s], R->Ao[s], p, p, ldp, OZ_BN);
   for (int s = 0; s < OZ_SX; ++s) ok &= tc::make_map_bf16(&R->mXo[s], R->Xo[s], p, p, ldp, 128);
@@ -402,7 +443,37 @@ ibmi_status refine_form_w(RefineState* R, const double* Ainv, int64_t m, int64_t
   return IBMI_OK;
 }
 
+ibmi_status refine_read(RefineState* R, cudaStream_t st, double* rho) { return read_scalar(R, st, rho); }
+
+ibmi_status refine_q_radius_launch(RefineState* R, int iters, cudaStream_t st) {
+  const int64_t p = R->p;
+  double* v = R->pv;
+  double* y = v + p;
+  double* est = y + p;
+  ProfScope ps(IBMI_K_OTHER, st, 2.0 * (double)iters * p * p);
+  note_launch();
+  k_q_normalize<<<1, 1024, 0, st>>>(y, p, v, est, 1);
+  for (int it = 0; it < iters; ++it) {
+    note_launch(2);
+    k_q_gemv<<<(unsigned)((p + 7) / 8), 256, 0, st>>>(R->Xn, p, v, y);
+    k_q_normalize<<<1, 1024, 0, st>>>(y, p, v, est, 0);
+  }
+  IBMI_CUDA_TRY(cudaGetLastError());
+  return IBMI_OK;
+}
+
+ibmi_status refine_q_radius_read(RefineState* R, cudaStream_t st, double* radius) {
+  IBMI_CUDA_TRY(cudaMemcpyAsync(radius, R->pv + 2 * R->p, sizeof(double), cudaMemcpyDeviceToHost, st));
+  IBMI_CUDA_TRY(cudaStreamSynchronize(st));
+  return IBMI_OK;
+}
+
 ibmi_status refine_residual(RefineState* R, const double* X, int64_t ldx, cudaStream_t st, double* rho) {
+  IBMI_TRY(refine_residual_launch(R, X, ldx, st));
+  return read_scalar(R, st, rho);
+}
+
+ibmi_status refine_residual_launch(RefineState* R, const double* X, int64_t ldx, cudaStream_t st) {
   const int64_t p = R->p, ldp = R->ldp;
   {
     ProfScope ps(IBMI_K_OTHER, st, 0.0);
@@ -419,7 +490,7 @@ ibmi_status refine_residual(RefineState* R, const double* X, int64_t ldx, cudaSt
     k_sum_partials<<<1, 1024, 0, st>>>(R->partials, nb, p, R->dout);
     IBMI_CUDA_TRY(cudaGetLastError());
   }
-  return read_scalar(R, st, rho);
+  return IBMI_OK;
 }
 
 ibmi_status refine_ns_update(RefineState* R, double* X, int64_t ldx, cudaStream_t st) {
@@ -440,6 +511,11 @@ ibmi_status refine_ns_update(RefineState* R, double* X, int64_t ldx, cudaStream_
 }
 
 ibmi_status refine_cheap_residual(RefineState* R, const CUtensorMap* mapH2, cudaStream_t st, double* rho) {
+  IBMI_TRY(refine_cheap_residual_launch(R, mapH2, st));
+  return read_scalar(R, st, rho);
+}
+
+ibmi_status refine_cheap_residual_launch(RefineState* R, const CUtensorMap* mapH2, cudaStream_t st) {
   const int64_t p = R->p;
   tc::Maps maps;
   maps.a[0] = mapH2[0];
@@ -463,7 +539,7 @@ ibmi_status refine_cheap_residual(RefineState* R, const CUtensorMap* mapH2, cuda
     k_sum_partials<<<1, 1024, 0, st>>>(R->partials, nparts, p, R->dout);
     IBMI_CUDA_TRY(cudaGetLastError());
   }
-  return read_scalar(R, st, rho);
+  return IBMI_OK;
 }
 
 }  // namespace ibmi

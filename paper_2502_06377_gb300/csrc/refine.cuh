@@ -37,6 +37,7 @@ struct RefineState {
   double* partials = nullptr;     // reduction partials
   int64_t n_partials = 0;
   double* dout = nullptr;         // device scalars
+  double* pv = nullptr;           // power-iteration vectors (2 p) and estimate
   int* err = nullptr;
   CUtensorMap mAo[OZ_SA], mXo[OZ_S], mQo[NS_S], mAf[2];
   void* pool = nullptr;
@@ -64,6 +65,23 @@ ibmi_status refine_ns_update(RefineState* R, double* X, int64_t ldx, cudaStream_
 // row pitch ldp.  Needs refine_set_matrix first; uses the X digit planes.
 ibmi_status refine_form_w(RefineState* R, const double* Ainv, int64_t m, int64_t lo, int64_t hi, __nv_bfloat16* W0,
                           __nv_bfloat16* W1, __nv_bfloat16* W2, cudaStream_t st);
+
+// The same two residuals split into their kernels (no host synchronisation,
+// so they can be captured in a CUDA graph) and the read of the value
+// (synchronises the stream, reports a bounded-wait expiry as IBMI_ERR_TIMEOUT).
+ibmi_status refine_residual_launch(RefineState* R, const double* X, int64_t ldx, cudaStream_t st);
+ibmi_status refine_cheap_residual_launch(RefineState* R, const CUtensorMap* mapH2, cudaStream_t st);
+ibmi_status refine_read(RefineState* R, cudaStream_t st, double* rho);
+
+// Spectral radius of Q = I - X A (left by the last accurate residual) by
+// power iteration: v <- Q v / ||Q v|| from a fixed start, `iters` steps; the
+// estimate is the last ||Q v||.  Q is similar to the symmetric
+// I - A^{1/2} X A^{1/2} (X symmetric), so its eigenvalues are real and the
+// estimate approaches their largest magnitude from below.  The Newton-Schulz
+// residual after k steps is Q^(2^k): it converges iff that radius is below 1.
+// The kernels only (capturable) and the read of the value.
+ibmi_status refine_q_radius_launch(RefineState* R, int iters, cudaStream_t st);
+ibmi_status refine_q_radius_read(RefineState* R, cudaStream_t st, double* radius);
 
 // ||I - H A||_F / sqrt(p) from BF16x3 products, for H given by its BF16 hi/lo
 // slice maps (about 5 significant digits; used to decide the hand-over to

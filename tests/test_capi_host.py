@@ -78,7 +78,7 @@ def test_invalid_explicit_sets(lib, lo, hi):
 def test_batch_opts_and_plan_bytes(lib):
     import paper_2502_06377_gb300 as ibmi
     o = ibmi.ibmi_batch_opts_init()
-    assert o.workers == 8 and o.autotune == 1 and o.tol == 1e-10 and o.precision == ibmi.IBMI_MIXED
+    assert o.workers == 8 and o.autotune == 1 and o.graphs == 1 and o.tol == 1e-10 and o.precision == ibmi.IBMI_MIXED
     b = [ibmi.ibmi_plan_bytes(p, 4, 16, precision=ibmi.IBMI_MIXED) for p in (256, 1024, 4096)]
     assert b[0] < b[1] < b[2]
     assert ibmi.ibmi_plan_bytes(1) == 0

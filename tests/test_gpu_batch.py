@@ -77,6 +77,23 @@ def test_batched_alone_equals_in_mix(ibmi, batch):
         assert np.array_equal(H1[0], H8[i])
 
 
+def test_batched_graphs_equal_direct_launches(ibmi, batch):
+    """Replayed CUDA graphs give the bits the direct launches give, on the
+    first call (capture) and on a repeated call (replay of pooled plans)."""
+    mats, _ = batch
+    sub = [mats[i] for i in (0, 3, 9, 16, 18)]
+    _, r0, H0 = _run_batched(ibmi, sub, workers=2, autotune=0, graphs=0)
+    for _ in range(2):
+        _, r1, H1 = _run_batched(ibmi, sub, workers=2, autotune=0, graphs=1)
+        for a, b, x, y in zip(H0, H1, r0, r1):
+            assert np.array_equal(a, b)
+            assert x["sweeps"] == y["sweeps"] and x["ns_steps"] == y["ns_steps"]
+    ibmi.ibmi_batch_release()
+    _, _, H2 = _run_batched(ibmi, sub, workers=2, autotune=0, graphs=1)
+    for a, b in zip(H0, H2):
+        assert np.array_equal(a, b)
+
+
 def test_batched_fp64(ibmi, batch):
     mats, refs = batch
     sel = [i for i, r in enumerate(refs) if r.status == "converged"][:4]

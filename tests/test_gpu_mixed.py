@@ -149,3 +149,19 @@ def test_mixed_full_size_c3_random_spd(ibmi):
     X = np.linalg.solve(A, np.eye(p)[:, cols])
     assert np.abs(H[:, cols] - X).max() <= 1e-8 * np.abs(X).max()
     print("c3 mixed", res)
+
+
+@pytest.mark.parametrize("ell", [0.3, 0.5])
+def test_mixed_floor_hands_over_by_radius(ibmi, ell):
+    """A squared-exponential matrix on 3-D points (kappa 2e5 to 4e5) with two
+    large blocks: the sweeps reach their mixed-precision floor with
+    ||I - A H||_F above 8 theta, yet the spectral radius of I - X A is far below
+    1, so the Newton-Schulz tail of eq. newton converges from there."""
+    rng = np.random.default_rng(7)
+    A = wl.squared_exp(wl.uniform_points(rng, 960, 3), ell, 1.0, 1e-3)
+    s, res, H = run(ibmi, A, K=2, h=48, tol=1e-10, ns_theta=0.5, max_sweeps=300)
+    print(res)
+    assert s == ibmi.IBMI_OK and res["ns_steps"] >= 1
+    assert O.residual_f(A, H) <= 1e-10
+    inv = np.linalg.inv(A)
+    assert np.abs(H - inv).max() <= 1e-6 * np.abs(inv).max()
