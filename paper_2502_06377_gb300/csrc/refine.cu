@@ -116,22 +116,44 @@ __global__ void k_fsplit2(const double* X, int64_t ldx, int64_t p, int64_t ldp, 
 // Group sum T_q[i, j] (+)= exact FP32 pair product (an integer below 2^24).
 struct EpiOzAcc : tc::EpiBase {
   int* T; int64_t ldt, M, N; int first;
-  __device__ __forceinline__ void operator()(int64_t i, int64_t j0, int, const float (&v)[16]) const {
-    if (i >= M) return;
-    int* t = T + i * ldt + j0;
-    if (j0 + 16 <= N) {
-      int4* t4 = reinterpret_cast<int4*>(t);
+  // The warp's 32 x 16 block (rows row0.., columns j0..) from shared memory:
+  // lane = (row 8k + lane/4, columns 4(lane%4)..+3), int4 read-modify-write,
+  // 8 rows of 64 bytes per instruction.
+  __device__ __forceinline__ void warp_tile(int64_t row0, int64_t j0, int, const float* __restrict__ stage,
+                                            int lane) const {
+    // all staged values into registers first, then the loads, then the stores
+    const int c = (lane & 3) * 4, r0 = lane >> 2;
+    int4 a[4];
 #pragma unroll
-      for (int g = 0; g < 4; ++g) {
-        int4 o = first ? make_int4(0, 0, 0, 0) : t4[g];
-        o.x += __float2int_rn(v[4 * g + 0]);
-        o.y += __float2int_rn(v[4 * g + 1]);
-        o.z += __float2int_rn(v[4 * g + 2]);
-        o.w += __float2int_rn(v[4 * g + 3]);
-        t4[g] = o;
+    for (int k = 0; k < 4; ++k) {
+      const float* sv = stage + (8 * k + r0) * 17 + c;
+      a[k] = make_int4(__float2int_rn(sv[0]), __float2int_rn(sv[1]), __float2int_rn(sv[2]), __float2int_rn(sv[3]));
+    }
+    int* __restrict__ t0 = T + (row0 + r0) * ldt + j0 + c;
+    const bool full = j0 + c + 4 <= N;
+    if (full) {
+      int4 o[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        o[k] = (first || row0 + 8 * k + r0 >= M) ? make_int4(0, 0, 0, 0)
+                                                 : *reinterpret_cast<const int4*>(t0 + 8 * k * ldt);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if (row0 + 8 * k + r0 >= M) continue;
+        o[k].x += a[k].x;
+        o[k].y += a[k].y;
+        o[k].z += a[k].z;
+        o[k].w += a[k].w;
+        *reinterpret_cast<int4*>(t0 + 8 * k * ldt) = o[k];
       }
     } else {
-      for (int c = 0; c < 16 && j0 + c < N; ++c) t[c] = (first ? 0 : t[c]) + __float2int_rn(v[c]);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if (row0 + 8 * k + r0 >= M) continue;
+        int* t = t0 + 8 * k * ldt;
+        const int v[4] = {a[k].x, a[k].y, a[k].z, a[k].w};
+        for (int u = 0; u < 4 && j0 + c + u < N; ++u) t[u] = (first ? 0 : t[u]) + v[u];
+      }
     }
   }
 };
@@ -284,7 +306,8 @@ __global__ void k_q_normalize(const double* y, int64_t p, double* v, double* est
 // --------------------------------------------------------------- host ----
 
 static constexpr int RF_BN = 128;   // N tile of the BF16x3 residual
-static constexpr int OZ_BN = 256;   // N tile of the digit-pair GEMMs (128 x 256 per CTA)
+static constexpr int OZ_BN = 224;   // N tile of the digit-pair GEMMs (128 x 224 per CTA: p = 4096 gives
+                                    // 608 tiles, four full rounds of 152 SMs)
 
 ibmi_status refine_create(RefineState* R, int64_t p, int* err) {
   R->p = p;
@@ -390,7 +413,8 @@ static ibmi_status digit_gemm(RefineState* R, const DigitGemm& g, cudaStream_t s
         const int k1 = std::min(g.kt1, k0 + chunk_tiles);
         // K tiles [k0, k1): an empty first range plus [k0, k1)
         tc::Tiles t{g.M, 0, 0, grid_n, 0, 0, k0, k1, 1, R->err};
-        EpiOzAcc epi{{}, R->T + (int64_t)q * p * ldp, ldp, g.M, g.N, first ? 1 : 0};
+        int* Tq = R->T + (int64_t)q * p * ldp;
+        EpiOzAcc epi{{}, Tq, ldp, g.M, g.N, first ? 1 : 0};
         ProfScope ps(g.kclass, st, 2.0 * (double)g.M * g.N * (double)(k1 - k0) * tc::BK);
         IBMI_CUDA_TRY((tc::launch<1, OZ_BN>(maps, t, grid_n, grid_m, epi, st)));
         first = false;

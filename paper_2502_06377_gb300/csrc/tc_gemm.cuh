@@ -28,6 +28,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <type_traits>
 
 #include "common.cuh"
 
@@ -58,6 +59,21 @@ struct Tiles {
   int grid_n = 0;   // N tiles, M tiles (filled in by launch())
   int grid_m = 0;
 };
+
+// Work unit -> output tile, split index and K-tile range: unit u is tile
+// u mod (grid_n grid_m) of K split u / (grid_n grid_m).
+struct Unit {
+  int tile, z, kb, nk;
+};
+__host__ __device__ inline int unit_count(const Tiles& t) { return t.grid_n * t.grid_m * t.splits; }
+__device__ __forceinline__ Unit unit_of(const Tiles& t, int u, int nk) {
+  Unit r;
+  r.tile = u;
+  r.z = u / (t.grid_n * t.grid_m);
+  r.kb = (int)((int64_t)nk * r.z / t.splits);
+  r.nk = (int)((int64_t)nk * (r.z + 1) / t.splits) - r.kb;
+  return r;
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -179,6 +195,16 @@ struct EpiBase {
   __device__ __forceinline__ void done(int) {}
 };
 
+// An epilogue with a member warp_tile(row0, j0, z, stage, lane) gets each
+// warp's 32 x 16 block through shared memory (stage[r * 17 + c] = row r,
+// column c) so that its global accesses can be coalesced along rows; others
+// get one row per lane.
+template <class E, class = void>
+struct has_warp_tile : std::false_type {};
+template <class E>
+struct has_warp_tile<E, std::void_t<decltype(&E::warp_tile)>> : std::true_type {};
+constexpr uint32_t STAGE_TILE_BYTES = 4 * 32 * 17 * 4;   // four epilogue warps
+
 // 32 lanes x 16 columns of 32-bit: thread t of the warp gets lane (quadrant + t).
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   uint32_t r[16];
@@ -206,7 +232,8 @@ struct Cfg {
   static constexpr int STAGES =
       TWO_PER_SM ? 3 : ((200 * 1024) / STAGE_BYTES >= 4 ? 4 : (200 * 1024) / STAGE_BYTES);
   static constexpr uint32_t SMEM = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
-  static constexpr uint32_t TMEM_COLS = 2 * BN < 32 ? 32 : 2 * BN;   // two accumulators
+  // two accumulators; an allocation is a power of two of at least 32 columns
+  static constexpr uint32_t TMEM_COLS = 2 * BN <= 32 ? 32 : 2 * BN <= 64 ? 64 : 2 * BN <= 128 ? 128 : 2 * BN <= 256 ? 256 : 512;
   static constexpr int CTAS_PER_SM = TWO_PER_SM && 2 * TMEM_COLS <= 512 ? 2 : 1;
   static_assert(TMEM_COLS <= 512, "two accumulators must fit in TMEM");
   static_assert(STAGES >= 2, "tile too large for two stages");
@@ -227,7 +254,7 @@ __global__ void __launch_bounds__(THREADS, Cfg<S, BN>::CTAS_PER_SM) k_tc_gemm(co
   uint32_t* tmem_slot = (uint32_t*)(acce + 2);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int total = t.grid_n * t.grid_m * t.splits;
+  const int units = unit_count(t);
   const int nk0 = t.kt0_end;
   const int nk = t.kt0_end + (t.kt1_end - t.kt1_begin);
 
@@ -252,12 +279,12 @@ __global__ void __launch_bounds__(THREADS, Cfg<S, BN>::CTAS_PER_SM) k_tc_gemm(co
     if (lane == 0) {  // TMA producer
       int kc = 0;     // k blocks issued so far (ring position)
       bool ok = true;
-      for (int tile = blockIdx.x; ok && tile < total; tile += gridDim.x) {
-        const int ntl = tile % t.grid_n, mt = (tile / t.grid_n) % t.grid_m, z = tile / (t.grid_n * t.grid_m);
+      for (int u = blockIdx.x; ok && u < units; u += gridDim.x) {
+        const Unit w = unit_of(t, u, nk);
+        const int ntl = w.tile % t.grid_n, mt = (w.tile / t.grid_n) % t.grid_m;
         const int ntp = ntl < t.nt0 ? ntl : t.nt1_first + (ntl - t.nt0);
         const int64_t n0 = (int64_t)ntp * BN;
-        const int kb = (int)((int64_t)nk * z / t.splits);
-        const int my_nk = (int)((int64_t)nk * (z + 1) / t.splits) - kb;
+        const int kb = w.kb, my_nk = w.nk;
         for (int it = 0; it < my_nk; ++it, ++kc) {
           const int st = kc % C::STAGES;
           const uint32_t ph = (uint32_t)(kc / C::STAGES) & 1u;
@@ -293,10 +320,8 @@ __global__ void __launch_bounds__(THREADS, Cfg<S, BN>::CTAS_PER_SM) k_tc_gemm(co
       int kc = 0;
       int local = 0;
       bool ok = true;
-      for (int tile = blockIdx.x; ok && tile < total; tile += gridDim.x, ++local) {
-        const int z = tile / (t.grid_n * t.grid_m);
-        const int kb = (int)((int64_t)nk * z / t.splits);
-        const int my_nk = (int)((int64_t)nk * (z + 1) / t.splits) - kb;
+      for (int u = blockIdx.x; ok && u < units; u += gridDim.x, ++local) {
+        const int my_nk = unit_of(t, u, nk).nk;
         const int buf = local & 1;
         const uint32_t use = (uint32_t)(local >> 1);
         if (!mbar_wait(&acce[buf], (use & 1u) ^ 1u, t.err)) break;   // accumulator drained
@@ -328,13 +353,14 @@ __global__ void __launch_bounds__(THREADS, Cfg<S, BN>::CTAS_PER_SM) k_tc_gemm(co
     const int q = warp & 3;
     const int row = q * 32 + lane;
     Epi e = epi;
+    float* stage = (float*)(smem + C::STAGES * C::STAGE_BYTES + 256) + q * 32 * 17;   // warp_tile epilogues only
     int local = 0;
-    for (int tile = blockIdx.x; tile < total; tile += gridDim.x, ++local) {
-      const int ntl = tile % t.grid_n, mt = (tile / t.grid_n) % t.grid_m, z = tile / (t.grid_n * t.grid_m);
+    for (int u = blockIdx.x; u < units; u += gridDim.x, ++local) {
+      const Unit w = unit_of(t, u, nk);
+      const int ntl = w.tile % t.grid_n, mt = (w.tile / t.grid_n) % t.grid_m, z = w.z;
       const int ntp = ntl < t.nt0 ? ntl : t.nt1_first + (ntl - t.nt0);
       const int64_t n0 = (int64_t)ntp * BN;
-      const int kb = (int)((int64_t)nk * z / t.splits);
-      const int my_nk = (int)((int64_t)nk * (z + 1) / t.splits) - kb;
+      const int my_nk = w.nk;
       const int buf = local & 1;
       const uint32_t use = (uint32_t)(local >> 1);
       if (!mbar_wait(&accf[buf], use & 1u, t.err)) break;
@@ -348,7 +374,15 @@ __global__ void __launch_bounds__(THREADS, Cfg<S, BN>::CTAS_PER_SM) k_tc_gemm(co
 #pragma unroll
           for (int i = 0; i < 16; ++i) v[i] = 0.f;
         }
-        e((int64_t)mt * BM + row, n0 + c, z, v);
+        if constexpr (has_warp_tile<Epi>::value) {
+#pragma unroll
+          for (int k = 0; k < 16; ++k) stage[lane * 17 + k] = v[k];
+          __syncwarp();
+          e.warp_tile((int64_t)mt * BM + q * 32, n0 + c, z, stage, lane);
+          __syncwarp();
+        } else {
+          e((int64_t)mt * BM + row, n0 + c, z, v);
+        }
       }
       tc_fence_before();
       __syncwarp();
@@ -385,19 +419,9 @@ inline TileRanges complement_tiles(int64_t lo, int64_t hi, int64_t p, int tile) 
   return r;
 }
 
-template <int S, int BN, class Epi>
-cudaError_t launch(const Maps& maps, const Tiles& t0, int grid_n, int grid_m, const Epi& epi, cudaStream_t st,
-                   int* grid_used = nullptr) {
-  using C = Cfg<S, BN>;
-  static std::atomic<bool> attr_set{false};
-  if (!attr_set.load(std::memory_order_acquire)) {
-    cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<S, BN, Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)C::SMEM);
-    if (e != cudaSuccess) return e;
-    attr_set.store(true, std::memory_order_release);
-  }
-  if (grid_used) *grid_used = 0;
-  if (grid_n <= 0 || grid_m <= 0) return cudaSuccess;
+// Resident CTAs of the persistent grid (SM count x CTAs per SM).
+template <int S, int BN>
+int resident_ctas() {
   static std::atomic<int> sms{0};
   if (sms.load() == 0) {
     int dev = 0, n = 0;
@@ -405,14 +429,33 @@ cudaError_t launch(const Maps& maps, const Tiles& t0, int grid_n, int grid_m, co
     cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
     sms.store(n > 0 ? n : 148);
   }
+  return sms.load() * Cfg<S, BN>::CTAS_PER_SM;
+}
+
+template <int S, int BN, class Epi>
+cudaError_t launch(const Maps& maps, const Tiles& t0, int grid_n, int grid_m, const Epi& epi, cudaStream_t st,
+                   int* grid_used = nullptr) {
+  using C = Cfg<S, BN>;
+  constexpr uint32_t smem_bytes = C::SMEM + (has_warp_tile<Epi>::value ? STAGE_TILE_BYTES : 0u);
+  static_assert(smem_bytes <= 227 * 1024, "shared memory per CTA");
+  static_assert(!has_warp_tile<Epi>::value || C::CTAS_PER_SM == 1, "staging sized for one CTA per SM");
+  static std::atomic<bool> attr_set{false};
+  if (!attr_set.load(std::memory_order_acquire)) {
+    cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<S, BN, Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem_bytes);
+    if (e != cudaSuccess) return e;
+    attr_set.store(true, std::memory_order_release);
+  }
+  if (grid_used) *grid_used = 0;
+  if (grid_n <= 0 || grid_m <= 0) return cudaSuccess;
   Tiles t = t0;
   t.grid_n = grid_n;
   t.grid_m = grid_m;
-  const int64_t total = (int64_t)grid_n * grid_m * t.splits;
-  const int grid = (int)std::min<int64_t>(total, (int64_t)sms.load() * C::CTAS_PER_SM);
+  const int64_t total = unit_count(t);
+  const int grid = (int)std::min<int64_t>(total, (int64_t)resident_ctas<S, BN>());
   if (grid_used) *grid_used = grid;
   note_launch();
-  k_tc_gemm<S, BN, Epi><<<grid, THREADS, C::SMEM, st>>>(maps, t, epi);
+  k_tc_gemm<S, BN, Epi><<<grid, THREADS, smem_bytes, st>>>(maps, t, epi);
   return cudaGetLastError();
 }
 
