@@ -394,7 +394,7 @@ size_t ibmi_plan_bytes(const ibmi_plan_desc* d) {
   const double m = std::min(p, p / K + 2.0 * (double)d->h);
   double b = 8.0 * (K * m * m + m * m + p * p / 4096.0 + 64.0);              // A_I^{-1}, S, partials
   const double ncols = d->precision == IBMI_MIXED ? m : p;
-  b += 8.0 * K * (m * m + m * ncols + 64.0 * m + 32.0 * ncols);              // batched factorisation
+  b += 8.0 * K * (m * m + m * ncols + 32.0 * m);                             // batched factorisation
   if (d->precision == IBMI_MIXED) {
     const double ldp = ceil(p / 64.0) * 64.0;
     b += 4.0 * p * ldp + 4.0 * p * ldp + 4.0 * K * m * ldp + 4.0 * 64.0 * m * m;   // H master + slices, W, split-K

@@ -268,7 +268,7 @@ ibmi_status ibmi_plan(const ibmi_plan_desc* desc, ibmi_plan_t* out) {
   P->dscalar = q; q += 4;
   // batched factorisation scratch
   const int64_t ncols = mixed ? mmax : p;
-  const size_t bat_doubles = (size_t)d.K * (mmax * mmax + mmax * ncols + mmax * CHOL_NB + (int64_t)CHOL_NB * ncols);
+  const size_t bat_doubles = (size_t)d.K * (mmax * mmax + mmax * ncols + mmax * CHOL_NB);
   if (cudaMalloc(&P->bat_pool, sizeof(double) * bat_doubles + sizeof(int64_t) * 4 * d.K) != cudaSuccess ||
       cudaMalloc(&P->dstatus, sizeof(DevStatus)) != cudaSuccess) {
     cudaGetLastError();
@@ -279,7 +279,6 @@ ibmi_status ibmi_plan(const ibmi_plan_desc* desc, ibmi_plan_t* out) {
   P->bat_L = b; b += d.K * mmax * mmax;
   P->bat_R = b; b += d.K * mmax * ncols;
   P->bat_linv = b; b += d.K * mmax * CHOL_NB;
-  P->bat_tmp = b; b += d.K * (int64_t)CHOL_NB * ncols;
   int64_t* ib = (int64_t*)b;
   P->dlo = ib; P->dm = ib + d.K; P->doff_ainv = ib + 2 * d.K; P->doff_w = ib + 3 * d.K;
   std::vector<int64_t> packed;

@@ -13,6 +13,8 @@
 // with a 4 x 4 register block per thread keeps shared-memory traffic at
 // 0.5 loads per FMA and global traffic negligible.
 #pragma once
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace ibmi {
@@ -27,13 +29,15 @@ struct F64Operands {
   int batch = 1;
 };
 
-template <bool A_KMAJOR, bool B_NMAJOR, class Epi>
-__global__ void __launch_bounds__(F64_THREADS)
+template <bool A_KMAJOR, bool B_NMAJOR, class Epi, int T = F64_BM>
+__global__ void __launch_bounds__((T / 4) * (T / 4))
 k_gemm_f64(F64Operands op, Epi epi) {
-  __shared__ double As[F64_BK][F64_BM + 1];
-  __shared__ double Bs[F64_BK][F64_BN + 1];
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  const int64_t i0 = (int64_t)blockIdx.y * F64_BM, j0 = (int64_t)blockIdx.x * F64_BN;
+  // T x T output tile, (T/4)^2 threads with a 4 x 4 register block each.
+  constexpr int NT = (T / 4) * (T / 4), Q = T / 4;
+  __shared__ double As[F64_BK][T + 1];
+  __shared__ double Bs[F64_BK][T + 1];
+  const int tx = threadIdx.x % Q, ty = threadIdx.x / Q;
+  const int64_t i0 = (int64_t)blockIdx.y * T, j0 = (int64_t)blockIdx.x * T;
   op.A += blockIdx.z * op.zA;
   op.B += blockIdx.z * op.zB;
   double acc[4][4];
@@ -43,12 +47,12 @@ k_gemm_f64(F64Operands op, Epi epi) {
     for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
 
   for (int64_t l0 = 0; l0 < op.K; l0 += F64_BK) {
-    // A tile: 64 x 16 = 1024 values, 4 per thread.
+    // A tile: T x 16 values.
 #pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      int e = threadIdx.x + t * F64_THREADS;
+    for (int t = 0; t < T * F64_BK / NT; ++t) {
+      int e = threadIdx.x + t * NT;
       int r, c;  // r: M within tile, c: K within tile
-      if (A_KMAJOR) { r = e >> 4; c = e & 15; } else { r = e & 63; c = e >> 6; }
+      if (A_KMAJOR) { r = e / F64_BK; c = e % F64_BK; } else { r = e % T; c = e / T; }
       int64_t i = i0 + r, l = l0 + c;
       double v = 0.0;
       if (i < op.M && l < op.K)
@@ -56,10 +60,10 @@ k_gemm_f64(F64Operands op, Epi epi) {
       As[c][r] = v;
     }
 #pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      int e = threadIdx.x + t * F64_THREADS;
+    for (int t = 0; t < T * F64_BK / NT; ++t) {
+      int e = threadIdx.x + t * NT;
       int r, c;  // r: K within tile, c: N within tile
-      if (B_NMAJOR) { r = e >> 6; c = e & 63; } else { r = e & 15; c = e >> 4; }
+      if (B_NMAJOR) { r = e / T; c = e % T; } else { r = e % F64_BK; c = e / F64_BK; }
       int64_t l = l0 + r, j = j0 + c;
       double v = 0.0;
       if (l < op.K && j < op.N)
@@ -71,7 +75,7 @@ k_gemm_f64(F64Operands op, Epi epi) {
     for (int k = 0; k < F64_BK; ++k) {
       double a[4], b[4];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) { a[q] = As[k][ty + 16 * q]; b[q] = Bs[k][tx + 16 * q]; }
+      for (int q = 0; q < 4; ++q) { a[q] = As[k][ty + Q * q]; b[q] = Bs[k][tx + Q * q]; }
 #pragma unroll
       for (int x = 0; x < 4; ++x)
 #pragma unroll
@@ -84,7 +88,7 @@ k_gemm_f64(F64Operands op, Epi epi) {
   for (int x = 0; x < 4; ++x)
 #pragma unroll
     for (int y = 0; y < 4; ++y) {
-      int64_t i = i0 + ty + 16 * x, j = j0 + tx + 16 * y;
+      int64_t i = i0 + ty + Q * x, j = j0 + tx + Q * y;
       if (i < op.M && j < op.N) epi(i, j, acc[x][y]);
     }
   epi.end();
@@ -170,11 +174,25 @@ struct EpiAddTo {
   }
 };
 
+// A launch of fewer than about two rounds of 64 x 64 tiles is latency-bound:
+// one tile's K = 32 update is ~130 K DFMA, tens of microseconds on one SM of
+// GB300 (about two FP64 FMAs per clock).  Store epilogues then use 32 x 32
+// tiles, a quarter of the work per CTA and four times the CTAs.
+constexpr int64_t F64_SMALL_LAUNCH = 300;
+
 template <bool A_KMAJOR, bool B_NMAJOR, class Epi>
 inline cudaError_t launch_gemm_f64(const F64Operands& op, const Epi& epi, cudaStream_t st) {
   if (op.M <= 0 || op.N <= 0) return cudaSuccess;
-  dim3 grid((unsigned)((op.N + F64_BN - 1) / F64_BN), (unsigned)((op.M + F64_BM - 1) / F64_BM), (unsigned)op.batch);
+  const int64_t tiles64 = ((op.N + F64_BN - 1) / F64_BN) * ((op.M + F64_BM - 1) / F64_BM) * op.batch;
   note_launch();
+  if constexpr (std::is_same<Epi, EpiStore>::value) {
+    if (tiles64 < F64_SMALL_LAUNCH) {
+      dim3 grid((unsigned)((op.N + 31) / 32), (unsigned)((op.M + 31) / 32), (unsigned)op.batch);
+      k_gemm_f64<A_KMAJOR, B_NMAJOR, Epi, 32><<<grid, 64, 0, st>>>(op, epi);
+      return cudaGetLastError();
+    }
+  }
+  dim3 grid((unsigned)((op.N + F64_BN - 1) / F64_BN), (unsigned)((op.M + F64_BM - 1) / F64_BM), (unsigned)op.batch);
   k_gemm_f64<A_KMAJOR, B_NMAJOR, Epi><<<grid, F64_THREADS, 0, st>>>(op, epi);
   return cudaGetLastError();
 }

@@ -18,44 +18,57 @@ namespace ibmi {
 
 // Factors the jb x jb diagonal tile T (lower part, row-major, ld) in place:
 // T = L L^T, and writes L^{-1} (jb x jb, ld jb) to linv.  One CTA of 32 x 32
-// threads per block of the batch.  A non-positive or non-finite pivot records
-// NOT_SPD (set z, global pivot lo_z + row0 + j) and is replaced by 1 so the
-// factorisation finishes.
+// threads per block of the batch.  FP64 latency is what bounds this kernel on
+// GB300, so each pivot takes one rsqrt (sqrt(d) = d rsqrt(d); the column is
+// scaled by rsqrt(d)), computed by the thread that finishes the pivot's update
+// in the previous step, which leaves two barriers per step.  L^{-1} is built
+// column by column, one warp per column (lane = row), by right-looking
+// substitution.  A non-positive or non-finite pivot records NOT_SPD (set z,
+// global pivot lo_z + row0 + j) and is replaced by 1 so the factorisation
+// finishes.
 __global__ void __launch_bounds__(1024) k_potrf_tile(double* T, int64_t ld, int64_t zT, int jb, double* linv,
                                                      int64_t zL, DevStatus* st, const int64_t* dlo, int64_t row0) {
   __shared__ double L[CHOL_NB][CHOL_NB + 1];
   __shared__ double X[CHOL_NB][CHOL_NB + 1];
+  __shared__ double rd[CHOL_NB];   // rsqrt of the pivots
   const int z = blockIdx.z;
   T += z * zT;
   linv += z * zL;
   const int c = threadIdx.x, r = threadIdx.y;
+  auto pivot = [&](double d, int j) -> double {   // returns sqrt(d), sets rd[j]
+    if (!(d > 0.0) || !isfinite(d)) {
+      if (atomicCAS(&st->code, 0, (int)IBMI_ERR_NOT_SPD) == 0) {
+        st->block = z;
+        st->pivot = dlo[z] + row0 + j;
+      }
+      d = 1.0;
+    }
+    const double q = rsqrt(d);
+    rd[j] = q;
+    return d * q;
+  };
   L[r][c] = (r < jb && c <= r) ? T[r * ld + c] : 0.0;
+  if (r == 0 && c == 0) L[0][0] = pivot(T[0], 0);
   __syncthreads();
   for (int j = 0; j < jb; ++j) {
-    if (r == j && c == j) {
-      double d = L[j][j];
-      if (!(d > 0.0) || !isfinite(d)) {
-        if (atomicCAS(&st->code, 0, (int)IBMI_ERR_NOT_SPD) == 0) {
-          st->block = z;
-          st->pivot = dlo[z] + row0 + j;
-        }
-        d = 1.0;
-      }
-      L[j][j] = sqrt(d);
+    if (c == j && r > j && r < jb) L[r][j] *= rd[j];
+    __syncthreads();
+    if (c > j && r >= c && r < jb) {
+      double v = L[r][c] - L[r][j] * L[c][j];
+      if (r == j + 1 && c == j + 1) v = pivot(v, j + 1);
+      L[r][c] = v;
     }
-    __syncthreads();
-    if (c == j && r > j && r < jb) L[r][j] /= L[j][j];
-    __syncthreads();
-    if (c > j && r >= c && r < jb) L[r][c] -= L[r][j] * L[c][j];
     __syncthreads();
   }
-  // X = L^{-1} by forward substitution, one column per thread of the first row.
-  if (r == 0 && c < jb) {
-    for (int i = 0; i < jb; ++i) {
-      double s = (i == c) ? 1.0 : 0.0;
-      for (int t = c; t < i; ++t) s -= L[i][t] * X[t][c];
-      X[i][c] = (i >= c) ? s / L[i][i] : 0.0;
+  {  // X = L^{-1}: warp w owns column w; x_t = acc_t rd[t] once rows < t are done
+    const int w = r, i = c;
+    double acc = (i == w) ? 1.0 : 0.0, xi = 0.0;
+    for (int t = w; t < jb; ++t) {
+      const double xt = __shfl_sync(0xffffffffu, acc * rd[t], t);
+      if (i == t) xi = xt;
+      if (i > t) acc -= L[i][t] * xt;
     }
+    if (i < jb && w < jb) X[i][w] = (i >= w) ? xi : 0.0;
   }
   __syncthreads();
   if (r < jb && c < jb) {
@@ -122,10 +135,9 @@ ibmi_status invariants_all(ibmi_plan_s* P, const double* A, int64_t lda, bool fu
   const int64_t p = P->d.p, mmax = P->mmax;
   const int K = (int)P->lo.size();
   const int64_t ncols = full_w ? p : mmax;
-  const int64_t zL = mmax * mmax, zLi = mmax * CHOL_NB, zR = mmax * ncols, zT = (int64_t)CHOL_NB * ncols;
+  const int64_t zL = mmax * mmax, zLi = mmax * CHOL_NB, zR = mmax * ncols;
   double* Lw = P->bat_L;
   double* R = P->bat_R;
-  double* tmp = P->bat_tmp;
   double flops = 0.0;
   for (int k = 0; k < K; ++k) {
     const double m = (double)(P->hi[k] - P->lo[k]);
@@ -166,37 +178,43 @@ ibmi_status invariants_all(ibmi_plan_s* P, const double* A, int64_t lda, bool fu
   note_launch();
   k_bat_rhs<<<dim3(nblk(mmax * ncols), 1, K), 256, 0, st>>>(A, lda, P->dlo, P->dm, mmax, ncols, full_w ? 1 : 0, R);
   IBMI_CUDA_TRY(cudaGetLastError());
+  // Both triangular solves work in place: the diagonal-block product reads
+  // rows j0..j0+jb of one column tile and writes the same tile (one CTA owns
+  // all jb rows of it, jb <= 32 <= the tile height, and reads its whole K
+  // before writing).
+  static_assert(CHOL_NB <= 32, "in-place diagonal-block products need jb within one tile row");
   for (int64_t j0 = 0; j0 < mmax; j0 += CHOL_NB) {
     const int jb = (int)std::min<int64_t>(CHOL_NB, mmax - j0);
     const double* Li = P->bat_linv + j0 * CHOL_NB;
-    {  // tmp = L_jj^{-1} R[j0:j0+jb, :]
-      F64Operands op = bat(F64Operands{Li, jb, id, id, R + j0 * ncols, ncols, id, id, jb, ncols, jb}, zLi, zR);
-      IBMI_CUDA_TRY((launch_gemm_f64<true, true>(op, EpiStore{tmp, ncols, 1.0, 0.0, zT}, st)));
+    // With R = I (A_I^{-1} only) the forward solve builds L^{-1}, which is
+    // lower triangular: rows j0.. of R are still zero right of column j0 + jb.
+    const int64_t nc = full_w ? ncols : std::min<int64_t>(ncols, j0 + jb);
+    double* Rj = R + j0 * ncols;
+    {  // R[j0:j0+jb, :nc] = L_jj^{-1} R[j0:j0+jb, :nc]
+      F64Operands op = bat(F64Operands{Li, jb, id, id, Rj, ncols, id, id, jb, nc, jb}, zLi, zR);
+      IBMI_CUDA_TRY((launch_gemm_f64<true, true>(op, EpiStore{Rj, ncols, 1.0, 0.0, zR}, st)));
     }
     const int64_t rest = mmax - j0 - jb;
-    if (rest > 0) {  // R[j0+jb:, :] -= L[j0+jb:, j0:j0+jb] tmp
-      F64Operands op = bat(F64Operands{Lw + (j0 + jb) * mmax + j0, mmax, id, id, tmp, ncols, id, id, rest, ncols, jb},
-                           zL, zT);
+    if (rest > 0) {  // R[j0+jb:, :nc] -= L[j0+jb:, j0:j0+jb] R[j0:j0+jb, :nc]
+      F64Operands op = bat(F64Operands{Lw + (j0 + jb) * mmax + j0, mmax, id, id, Rj, ncols, id, id, rest, nc, jb},
+                           zL, zR);
       IBMI_CUDA_TRY((launch_gemm_f64<true, true>(op, EpiStore{R + (j0 + jb) * ncols, ncols, -1.0, 1.0, zR}, st)));
     }
-    IBMI_CUDA_TRY(cudaMemcpy2DAsync(R + j0 * ncols, sizeof(double) * zR, tmp, sizeof(double) * zT,
-                                    sizeof(double) * jb * ncols, K, cudaMemcpyDeviceToDevice, st));
   }
   const int64_t nbk = (mmax + CHOL_NB - 1) / CHOL_NB;
   for (int64_t b = nbk - 1; b >= 0; --b) {
     const int64_t j0 = b * CHOL_NB;
     const int jb = (int)std::min<int64_t>(CHOL_NB, mmax - j0);
     const double* Li = P->bat_linv + j0 * CHOL_NB;
-    {  // tmp = L_jj^{-T} R[j0:j0+jb, :]
-      F64Operands op = bat(F64Operands{Li, jb, id, id, R + j0 * ncols, ncols, id, id, jb, ncols, jb}, zLi, zR);
-      IBMI_CUDA_TRY((launch_gemm_f64<false, true>(op, EpiStore{tmp, ncols, 1.0, 0.0, zT}, st)));
+    double* Rj = R + j0 * ncols;
+    {  // R[j0:j0+jb, :] = L_jj^{-T} R[j0:j0+jb, :]
+      F64Operands op = bat(F64Operands{Li, jb, id, id, Rj, ncols, id, id, jb, ncols, jb}, zLi, zR);
+      IBMI_CUDA_TRY((launch_gemm_f64<false, true>(op, EpiStore{Rj, ncols, 1.0, 0.0, zR}, st)));
     }
-    if (j0 > 0) {  // R[0:j0, :] -= L[j0:j0+jb, 0:j0]^T tmp
-      F64Operands op = bat(F64Operands{Lw + j0 * mmax, mmax, id, id, tmp, ncols, id, id, j0, ncols, jb}, zL, zT);
+    if (j0 > 0) {  // R[0:j0, :] -= L[j0:j0+jb, 0:j0]^T R[j0:j0+jb, :]
+      F64Operands op = bat(F64Operands{Lw + j0 * mmax, mmax, id, id, Rj, ncols, id, id, j0, ncols, jb}, zL, zR);
       IBMI_CUDA_TRY((launch_gemm_f64<false, true>(op, EpiStore{R, ncols, -1.0, 1.0, zR}, st)));
     }
-    IBMI_CUDA_TRY(cudaMemcpy2DAsync(R + j0 * ncols, sizeof(double) * zR, tmp, sizeof(double) * zT,
-                                    sizeof(double) * jb * ncols, K, cudaMemcpyDeviceToDevice, st));
   }
   const int64_t nout = std::max(mmax * mmax, full_w ? mmax * p : 0);
   note_launch();

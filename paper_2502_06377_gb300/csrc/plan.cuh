@@ -20,7 +20,6 @@ struct ibmi_plan_s {
   double* bat_L = nullptr;       // K x mmax x mmax Cholesky factors
   double* bat_R = nullptr;       // K x mmax x ncols right-hand sides / solutions
   double* bat_linv = nullptr;    // K x mmax x 32 inverted diagonal tiles
-  double* bat_tmp = nullptr;     // K x 32 x ncols
   int64_t* dlo = nullptr;        // device copies of lo_k, m_k and of the pool offsets
   int64_t* dm = nullptr;         // of A_I^{-1} and W for each set
   int64_t* doff_ainv = nullptr;
