@@ -27,6 +27,10 @@ struct F64Operands {
   int64_t M, N, K;
   int64_t zA = 0, zB = 0;   // element offset of operand z of a batch (blockIdx.z)
   int batch = 1;
+  // Triangular K: opA(i, l) = 0 for l < i and opB(l, j) = 0 for l < j (e.g.
+  // Y^T Y with Y lower triangular), so a tile starts its K loop at
+  // max(first row, first column), rounded down to the K block.
+  bool tri_k = false;
 };
 
 template <bool A_KMAJOR, bool B_NMAJOR, class Epi, int T = F64_BM>
@@ -46,7 +50,8 @@ k_gemm_f64(F64Operands op, Epi epi) {
 #pragma unroll
     for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
 
-  for (int64_t l0 = 0; l0 < op.K; l0 += F64_BK) {
+  const int64_t lstart = op.tri_k ? (i0 > j0 ? i0 : j0) / F64_BK * F64_BK : 0;
+  for (int64_t l0 = lstart; l0 < op.K; l0 += F64_BK) {
     // A tile: T x 16 values.
 #pragma unroll
     for (int t = 0; t < T * F64_BK / NT; ++t) {

@@ -174,7 +174,7 @@ ibmi_status invariants_all(ibmi_plan_s* P, const double* A, int64_t lda, bool fu
       IBMI_CUDA_TRY((launch_gemm_f64<true, false>(op, EpiStore{panel + jb, mmax, -1.0, 1.0, zL}, st)));
     }
   }
-  // R <- L^{-T} L^{-1} R
+  // R <- L^{-T} L^{-1} R (full_w); A_I^{-1} = L^{-T} L^{-1} otherwise
   note_launch();
   k_bat_rhs<<<dim3(nblk(mmax * ncols), 1, K), 256, 0, st>>>(A, lda, P->dlo, P->dm, mmax, ncols, full_w ? 1 : 0, R);
   IBMI_CUDA_TRY(cudaGetLastError());
@@ -201,24 +201,34 @@ ibmi_status invariants_all(ibmi_plan_s* P, const double* A, int64_t lda, bool fu
       IBMI_CUDA_TRY((launch_gemm_f64<true, true>(op, EpiStore{R + (j0 + jb) * ncols, ncols, -1.0, 1.0, zR}, st)));
     }
   }
-  const int64_t nbk = (mmax + CHOL_NB - 1) / CHOL_NB;
-  for (int64_t b = nbk - 1; b >= 0; --b) {
-    const int64_t j0 = b * CHOL_NB;
-    const int jb = (int)std::min<int64_t>(CHOL_NB, mmax - j0);
-    const double* Li = P->bat_linv + j0 * CHOL_NB;
-    double* Rj = R + j0 * ncols;
-    {  // R[j0:j0+jb, :] = L_jj^{-T} R[j0:j0+jb, :]
-      F64Operands op = bat(F64Operands{Li, jb, id, id, Rj, ncols, id, id, jb, ncols, jb}, zLi, zR);
-      IBMI_CUDA_TRY((launch_gemm_f64<false, true>(op, EpiStore{Rj, ncols, 1.0, 0.0, zR}, st)));
+  double* X = R;   // the solutions
+  if (full_w) {
+    const int64_t nbk = (mmax + CHOL_NB - 1) / CHOL_NB;
+    for (int64_t b = nbk - 1; b >= 0; --b) {
+      const int64_t j0 = b * CHOL_NB;
+      const int jb = (int)std::min<int64_t>(CHOL_NB, mmax - j0);
+      const double* Li = P->bat_linv + j0 * CHOL_NB;
+      double* Rj = R + j0 * ncols;
+      {  // R[j0:j0+jb, :] = L_jj^{-T} R[j0:j0+jb, :]
+        F64Operands op = bat(F64Operands{Li, jb, id, id, Rj, ncols, id, id, jb, ncols, jb}, zLi, zR);
+        IBMI_CUDA_TRY((launch_gemm_f64<false, true>(op, EpiStore{Rj, ncols, 1.0, 0.0, zR}, st)));
+      }
+      if (j0 > 0) {  // R[0:j0, :] -= L[j0:j0+jb, 0:j0]^T R[j0:j0+jb, :]
+        F64Operands op = bat(F64Operands{Lw + j0 * mmax, mmax, id, id, Rj, ncols, id, id, j0, ncols, jb}, zL, zR);
+        IBMI_CUDA_TRY((launch_gemm_f64<false, true>(op, EpiStore{R, ncols, -1.0, 1.0, zR}, st)));
+      }
     }
-    if (j0 > 0) {  // R[0:j0, :] -= L[j0:j0+jb, 0:j0]^T R[j0:j0+jb, :]
-      F64Operands op = bat(F64Operands{Lw + j0 * mmax, mmax, id, id, Rj, ncols, id, id, j0, ncols, jb}, zL, zR);
-      IBMI_CUDA_TRY((launch_gemm_f64<false, true>(op, EpiStore{R, ncols, -1.0, 1.0, zR}, st)));
-    }
+  } else {
+    // R holds Y = L^{-1}; A_I^{-1} = Y^T Y in one product (into the buffer of L,
+    // no longer needed), each tile summing only k >= max(i, j).
+    F64Operands op = bat(F64Operands{R, ncols, id, id, R, ncols, id, id, mmax, mmax, mmax}, zR, zR);
+    op.tri_k = true;
+    IBMI_CUDA_TRY((launch_gemm_f64<false, true>(op, EpiStore{Lw, mmax, 1.0, 0.0, zL}, st)));
+    X = Lw;
   }
   const int64_t nout = std::max(mmax * mmax, full_w ? mmax * p : 0);
   note_launch();
-  k_bat_extract<<<dim3(nblk(nout), 1, K), 256, 0, st>>>(R, P->dlo, P->dm, mmax, ncols, full_w ? 1 : 0, P->pool,
+  k_bat_extract<<<dim3(nblk(nout), 1, K), 256, 0, st>>>(X, P->dlo, P->dm, mmax, ncols, full_w ? 1 : 0, P->pool,
                                                          P->doff_ainv, P->doff_w, p);
   IBMI_CUDA_TRY(cudaGetLastError());
   return IBMI_OK;
