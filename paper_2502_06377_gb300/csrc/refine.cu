@@ -195,13 +195,15 @@ __device__ __forceinline__ double pow2i(int k) {
 // (groups 0..4 and 5..qmax, each below 2^59), so only the final conversion and
 // scaling round.
 __device__ __forceinline__ double oz_value(const int* T, int64_t plane, int64_t idx, int qmax, int e) {
+  // all group loads issued together (predicated, no early exit)
+  int t[10];
+#pragma unroll
+  for (int q = 0; q < 10; ++q) t[q] = q <= qmax ? T[(int64_t)q * plane + idx] : 0;
   long long hi = 0, lo = 0;
 #pragma unroll
   for (int q = 0; q < 10; ++q) {
-    if (q > qmax) break;
-    const long long t = T[(int64_t)q * plane + idx];
-    if (q < 5) hi += t * (1ll << (7 * (4 - q)));
-    else lo += t * (1ll << (7 * (9 - q)));
+    if (q < 5) hi += (long long)t[q] * (1ll << (7 * (4 - q)));
+    else lo += (long long)t[q] * (1ll << (7 * (9 - q)));
   }
   // sum = hi 2^-28 + lo 2^-63
   return (double)hi * pow2i(e - 28) + (double)lo * pow2i(e - 63);
