@@ -415,6 +415,7 @@ static ibmi_status digit_gemm(RefineState* R, const DigitGemm& g, cudaStream_t s
         const int k1 = std::min(g.kt1, k0 + chunk_tiles);
         // K tiles [k0, k1): an empty first range plus [k0, k1)
         tc::Tiles t{g.M, 0, 0, grid_n, 0, 0, k0, k1, 1, R->err};
+        t.pdl = 1;   // digit planes are written only by the slicing kernels
         int* Tq = R->T + (int64_t)q * p * ldp;
         EpiOzAcc epi{{}, Tq, ldp, g.M, g.N, first ? 1 : 0};
         ProfScope ps(g.kclass, st, 2.0 * (double)g.M * g.N * (double)(k1 - k0) * tc::BK);

@@ -58,7 +58,16 @@ struct Tiles {
   int* err;         // error word (0 = ok)
   int grid_n = 0;   // N tiles, M tiles (filled in by launch())
   int grid_m = 0;
+  // Programmatic dependent launch: the kernel may start while the previous
+  // kernel on the stream (another k_tc_gemm that set this) finishes.  Only
+  // for launches whose operands no k_tc_gemm writes: the epilogue waits for
+  // the previous grid before its first global access, then lets the next
+  // launch begin.
+  int pdl = 0;
 };
+
+__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 // Work unit -> output tile, split index and K-tile range: unit u is tile
 // u mod (grid_n grid_m) of K split u / (grid_n grid_m).
@@ -352,6 +361,10 @@ __global__ void __launch_bounds__(THREADS, Cfg<S, BN>::CTAS_PER_SM) k_tc_gemm(co
   } else {  // epilogue warps 2..5
     const int q = warp & 3;
     const int row = q * 32 + lane;
+    if (t.pdl) {
+      grid_dependency_wait();   // the previous grid's writes are complete and visible
+      if (warp == 2 && lane == 0) grid_launch_dependents();
+    }
     Epi e = epi;
     float* stage = (float*)(smem + C::STAGES * C::STAGE_BYTES + 256) + q * 32 * 17;   // warp_tile epilogues only
     int local = 0;
@@ -455,8 +468,21 @@ cudaError_t launch(const Maps& maps, const Tiles& t0, int grid_n, int grid_m, co
   const int grid = (int)std::min<int64_t>(total, (int64_t)resident_ctas<S, BN>());
   if (grid_used) *grid_used = grid;
   note_launch();
-  k_tc_gemm<S, BN, Epi><<<grid, THREADS, smem_bytes, st>>>(maps, t, epi);
-  return cudaGetLastError();
+  if (!t.pdl) {
+    k_tc_gemm<S, BN, Epi><<<grid, THREADS, smem_bytes, st>>>(maps, t, epi);
+    return cudaGetLastError();
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(THREADS);
+  cfg.dynamicSmemBytes = smem_bytes;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_tc_gemm<S, BN, Epi>, maps, t, epi);
 }
 
 }  // namespace tc
