@@ -272,7 +272,8 @@ ibmi_status mixed_create(ibmi_plan_s* P) {
     for (int k = 0; k < K; ++k)
       if (!tc::make_map_bf16(&M->mapW[s][k], M->Ws[s][k], P->hi[k] - P->lo[k], p, ldp, 128)) return IBMI_ERR_CUDA;
   }
-  return refine_create(&M->ref, p, M->err);
+  IBMI_TRY(refine_create(&M->ref, p, M->err));
+  return refine_plan_w(&M->ref, P->lo, P->hi);
 }
 
 void mixed_destroy(ibmi_plan_s* P) {
@@ -387,9 +388,14 @@ ibmi_status mixed_run(ibmi_plan_s* P, const double* A, int64_t lda, double* H, i
     IBMI_TRY(invariants_all(P, A, lda, false, st));
     if (d.init == IBMI_INIT_IDENTITY) IBMI_TRY(set_identity(H, ldh, p, st));
     IBMI_TRY(refine_set_matrix(R, A, lda, st));
-    for (int k = 0; k < K; ++k)
-      IBMI_TRY(refine_form_w(R, P->ainv[k], P->hi[k] - P->lo[k], P->lo[k], P->hi[k], M->Ws[0][k], M->Ws[1][k],
-                             M->Ws[2][k], st));
+    if (R->w_rows > 0) {
+      std::vector<const double*> ainv(P->ainv.begin(), P->ainv.end());
+      IBMI_TRY(refine_form_w_all(R, ainv, P->lo, P->hi, M->Ws[0].data(), M->Ws[1].data(), M->Ws[2].data(), st));
+    } else {
+      for (int k = 0; k < K; ++k)
+        IBMI_TRY(refine_form_w(R, P->ainv[k], P->hi[k] - P->lo[k], P->lo[k], P->hi[k], M->Ws[0][k], M->Ws[1][k],
+                               M->Ws[2][k], st));
+    }
     return mixed_prepare(P, H, ldh, st);
   }));
   *flops += fplan;

@@ -351,6 +351,9 @@ ibmi_status refine_create(RefineState* R, int64_t p, int* err) {
 void refine_destroy(RefineState* R) {
   cudaFree(R->pool);
   R->pool = nullptr;
+  cudaFree(R->wpool);
+  R->wpool = nullptr;
+  R->w_rows = 0;
 }
 
 static ibmi_status slice_digits(RefineState* R, const double* X, int64_t ldx, __nv_bfloat16* const* dst, int nslices,
@@ -435,14 +438,15 @@ static ibmi_status pair_products(RefineState* R, const CUtensorMap* ma, int nsa,
 
 // W = A_I^{-1} A_{I,:} from digit products, written as BF16 hi/lo (zero on
 // the columns of I and on the padding).
-__global__ void k_oz_wcombine(const int* T, int64_t m, int64_t p, int64_t ldp, const int* ea, const int* eb, int qmax,
-                              int64_t lo, int64_t hi, __nv_bfloat16* W0, __nv_bfloat16* W1, __nv_bfloat16* W2) {
+__global__ void k_oz_wcombine(const int* T, int64_t plane, int64_t m, int64_t p, int64_t ldp, const int* ea,
+                              const int* eb, int qmax, int64_t lo, int64_t hi, __nv_bfloat16* W0, __nv_bfloat16* W1,
+                              __nv_bfloat16* W2) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= m * ldp) return;
   const int64_t i = idx / ldp, j = idx - i * ldp;
   float w = 0.f;
   if (j < p && (j < lo || j >= hi)) {
-    w = (float)oz_value(T, p * ldp, idx, qmax, ea[i] + eb[j] - 12);
+    w = (float)oz_value(T, plane, idx, qmax, ea[i] + eb[j] - 12);
   }
   const __nv_bfloat16 a = __float2bfloat16_rn(w);
   const float r = w - __bfloat162float(a);
@@ -465,7 +469,93 @@ ibmi_status refine_form_w(RefineState* R, const double* Ainv, int64_t m, int64_t
                                    (int)((hi + tc::BK - 1) / tc::BK), QW, IBMI_K_INVARIANTS_TC}, st));
   ProfScope ps(IBMI_K_OTHER, st, 0.0);
   note_launch();
-  k_oz_wcombine<<<nblk(m * ldp), 256, 0, st>>>(R->T, m, p, ldp, R->expX, R->expA, QW, lo, hi, W0, W1, W2);
+  k_oz_wcombine<<<nblk(m * ldp), 256, 0, st>>>(R->T, p * ldp, m, p, ldp, R->expX, R->expA, QW, lo, hi, W0, W1, W2);
+  IBMI_CUDA_TRY(cudaGetLastError());
+  return IBMI_OK;
+}
+
+ibmi_status refine_plan_w(RefineState* R, const std::vector<int64_t>& lo, const std::vector<int64_t>& hi) {
+  const int64_t p = R->p, ldp = R->ldp;
+  const int K = (int)lo.size();
+  R->w_rows = 0;
+  R->w_off.assign(K, 0);
+  int64_t rows = 0;
+  for (int k = 0; k < K; ++k) {
+    const int64_t m = hi[k] - lo[k];
+    const int64_t kt = (hi[k] + tc::BK - 1) / tc::BK - lo[k] / tc::BK;
+    if (kt * tc::BK > OZ_KCHUNK) return IBMI_OK;   // exactness bound per accumulation: set by set
+    R->w_off[k] = rows;
+    rows += (m + 127) / 128 * 128;
+  }
+  const size_t xregion = (size_t)((uint8_t*)R->Xo[OZ_SX - 1] - (uint8_t*)R->Xo[0]) + sizeof(__nv_bfloat16) * p * ldp;
+  if (5 * sizeof(__nv_bfloat16) * (size_t)rows * ldp > xregion) return IBMI_OK;
+  if (5 * (size_t)rows * ldp > (size_t)(OZ_QMAX + 1) * p * ldp) return IBMI_OK;
+  const int tiles = (int)(rows / 128);
+  if (cudaMalloc(&R->wpool, sizeof(int) * rows + sizeof(int2) * tiles + 256) != cudaSuccess) {
+    cudaGetLastError();
+    return IBMI_ERR_OOM;
+  }
+  R->expW = (int*)R->wpool;
+  R->w_kr = (int2*)((uint8_t*)R->wpool + (sizeof(int) * rows + 255) / 256 * 256);
+  std::vector<int2> kr(tiles);
+  for (int k = 0; k < K; ++k) {
+    const int64_t m = hi[k] - lo[k];
+    for (int64_t t = R->w_off[k] / 128; t < (R->w_off[k] + m + 127) / 128; ++t)
+      kr[t] = make_int2((int)(lo[k] / tc::BK), (int)((hi[k] + tc::BK - 1) / tc::BK));
+  }
+  IBMI_CUDA_TRY(cudaMemcpy(R->w_kr, kr.data(), sizeof(int2) * tiles, cudaMemcpyHostToDevice));
+  for (int s = 0; s < 5; ++s)
+    if (!tc::make_map_bf16(&R->mXw[s], R->Xo[0] + (int64_t)s * rows * ldp, rows, p, ldp, 128)) return IBMI_ERR_CUDA;
+  R->w_rows = rows;
+  return IBMI_OK;
+}
+
+ibmi_status refine_form_w_all(RefineState* R, const std::vector<const double*>& Ainv, const std::vector<int64_t>& lo,
+                              const std::vector<int64_t>& hi, __nv_bfloat16* const* W0, __nv_bfloat16* const* W1,
+                              __nv_bfloat16* const* W2, cudaStream_t st) {
+  const int64_t p = R->p, ldp = R->ldp, rows = R->w_rows;
+  const int K = (int)lo.size();
+  constexpr int NW_A = 5, NW_B = 4, QW = 4;   // 34-bit A_I^{-1} digits, 27-bit A digits
+  if (rows == 0) return IBMI_ERR_INVALID_ARG;
+  {
+    ProfScope ps(IBMI_K_OTHER, st, 0.0);
+    for (int k = 0; k < K; ++k) {   // A_I^{-1} at columns [lo, hi) of set k's slot
+      const int64_t m = hi[k] - lo[k];
+      __nv_bfloat16* dst[5];
+      for (int s = 0; s < NW_A; ++s) dst[s] = R->Xo[0] + (int64_t)s * rows * ldp + R->w_off[k] * ldp;
+      IBMI_TRY(slice_digits(R, Ainv[k], m, dst, NW_A, R->expW + R->w_off[k], st, m, m, lo[k]));
+    }
+  }
+  double flops = 0.0;
+  for (int k = 0; k < K; ++k)
+    flops += 2.0 * (double)((hi[k] - lo[k] + 127) / 128 * 128) * p *
+             (double)(((hi[k] + tc::BK - 1) / tc::BK - lo[k] / tc::BK) * tc::BK);
+  const int grid_n = (int)((p + OZ_BN - 1) / OZ_BN), grid_m = (int)(rows / 128);
+  for (int q = 0; q <= QW; ++q) {
+    bool first = true;
+    for (int s = 0; s <= q; ++s) {
+      const int u = q - s;
+      if (s >= NW_A || u >= NW_B) continue;
+      tc::Maps maps;
+      maps.a[0] = R->mXw[s];
+      maps.b[0] = R->mAo[u];
+      tc::Tiles t{rows, 0, 0, grid_n, 0, 1 << 29, 0, 0, 1, R->err};
+      t.mkr = R->w_kr;
+      t.pdl = 1;
+      EpiOzAcc epi{{}, R->T + (int64_t)q * rows * ldp, ldp, rows, p, first ? 1 : 0};
+      ProfScope ps(IBMI_K_INVARIANTS_TC, st, flops);
+      IBMI_CUDA_TRY((tc::launch<1, OZ_BN>(maps, t, grid_n, grid_m, epi, st)));
+      first = false;
+    }
+  }
+  ProfScope ps(IBMI_K_OTHER, st, 0.0);
+  for (int k = 0; k < K; ++k) {
+    const int64_t m = hi[k] - lo[k];
+    note_launch();
+    k_oz_wcombine<<<nblk(m * ldp), 256, 0, st>>>(R->T + R->w_off[k] * ldp, rows * ldp, m, p, ldp,
+                                                 R->expW + R->w_off[k], R->expA, QW, lo[k], hi[k], W0[k], W1[k],
+                                                 W2[k]);
+  }
   IBMI_CUDA_TRY(cudaGetLastError());
   return IBMI_OK;
 }

@@ -2,6 +2,8 @@
 #pragma once
 #include <cuda_bf16.h>
 
+#include <vector>
+
 #include "tc_gemm.cuh"
 
 namespace ibmi {
@@ -41,6 +43,15 @@ struct RefineState {
   int* err = nullptr;
   CUtensorMap mAo[OZ_SA], mXo[OZ_S], mQo[NS_S], mAf[2];
   void* pool = nullptr;
+  // W of all sets in one pass (refine_plan_w): set k's rows sit in a slot of
+  // whole 128-row tiles starting at row w_off[k] of a stacked view of the X
+  // digit region (5 planes of w_rows rows) and of the T region.
+  int64_t w_rows = 0;              // 0: W is formed set by set
+  std::vector<int64_t> w_off;
+  int* expW = nullptr;             // row exponents of the stacked A_I^{-1}
+  int2* w_kr = nullptr;            // K-tile range of every 128-row tile
+  CUtensorMap mXw[5];
+  void* wpool = nullptr;
 };
 
 ibmi_status refine_create(RefineState* R, int64_t p, int* err);
@@ -65,6 +76,19 @@ ibmi_status refine_ns_update(RefineState* R, double* X, int64_t ldx, cudaStream_
 // row pitch ldp.  Needs refine_set_matrix first; uses the X digit planes.
 ibmi_status refine_form_w(RefineState* R, const double* Ainv, int64_t m, int64_t lo, int64_t hi, __nv_bfloat16* W0,
                           __nv_bfloat16* W1, __nv_bfloat16* W2, cudaStream_t st);
+
+// Prepares the one-pass formation of W for the sets [lo_k, hi_k): the stacked
+// view fits when 5 slots of sum_k ceil(m_k/128)*128 rows fit in the X digit
+// and T regions and every set spans at most 4096 columns; otherwise W is
+// formed set by set (w_rows stays 0).
+ibmi_status refine_plan_w(RefineState* R, const std::vector<int64_t>& lo, const std::vector<int64_t>& hi);
+
+// W_k for every set k at once (needs refine_plan_w with w_rows > 0 and
+// refine_set_matrix): the same digit products as refine_form_w, 14 launches
+// in all instead of 14 per set.
+ibmi_status refine_form_w_all(RefineState* R, const std::vector<const double*>& Ainv, const std::vector<int64_t>& lo,
+                              const std::vector<int64_t>& hi, __nv_bfloat16* const* W0, __nv_bfloat16* const* W1,
+                              __nv_bfloat16* const* W2, cudaStream_t st);
 
 // The same two residuals split into their kernels (no host synchronisation,
 // so they can be captured in a CUDA graph) and the read of the value

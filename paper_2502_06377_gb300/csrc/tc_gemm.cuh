@@ -64,6 +64,10 @@ struct Tiles {
   // the previous grid before its first global access, then lets the next
   // launch begin.
   int pdl = 0;
+  // Per 128-row tile K-tile ranges [x, y) (device array of grid_m entries;
+  // splits == 1, kt0_end >= every y): rows of different problems stacked in
+  // one launch, each with its own K range.
+  const int2* mkr = nullptr;
 };
 
 __device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
@@ -79,6 +83,12 @@ __device__ __forceinline__ Unit unit_of(const Tiles& t, int u, int nk) {
   Unit r;
   r.tile = u;
   r.z = u / (t.grid_n * t.grid_m);
+  if (t.mkr) {
+    const int2 kr = t.mkr[(u / t.grid_n) % t.grid_m];
+    r.kb = kr.x;
+    r.nk = kr.y - kr.x;
+    return r;
+  }
   r.kb = (int)((int64_t)nk * r.z / t.splits);
   r.nk = (int)((int64_t)nk * (r.z + 1) / t.splits) - r.kb;
   return r;
