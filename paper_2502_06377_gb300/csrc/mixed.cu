@@ -192,45 +192,61 @@ __global__ void k_reslice_h(const float* Hf, int64_t n, __nv_bfloat16* s0, __nv_
   split3(Hf[idx], s0[idx], s1[idx], s2[idx]);
 }
 
-// a3 epilogue: X = -acc for rows i < m of the set and columns j in I^c;
-// written to H[lo+i, j] (16 consecutive columns per thread) and to H[j, lo+i]
-// (the 32 lanes of a warp hold consecutive i: coalesced).
+// a3 epilogue: X = -acc for rows i < m of the set and columns j in I^c,
+// written to H[lo+i, j] and to H[j, lo+i].  The warp's 32 x 16 block comes
+// through shared memory: the transposed copy goes out lane = row (32
+// consecutive columns of H per store), the direct copy lane = (row 2k +
+// lane/16, column lane%16) (two 16-wide row pieces per store).
 struct EpiTcSweepX : tc::EpiBase {
   float* Hf; __nv_bfloat16* H0; __nv_bfloat16* H1; __nv_bfloat16* H2;
   int64_t ldp, lo, hi, p, m;
-  __device__ __forceinline__ void operator()(int64_t i, int64_t j0, int, const float (&v)[16]) const {
-    if (i >= m) return;
-    const int64_t r = lo + i;
-#pragma unroll
-    for (int c = 0; c < 16; ++c) {
-      const int64_t j = j0 + c;
-      if (j >= p || (j >= lo && j < hi)) continue;
-      const float x = -v[c];
-      __nv_bfloat16 a, b, d;
-      split3(x, a, b, d);
-      Hf[r * ldp + j] = x;
-      H0[r * ldp + j] = a;
-      H1[r * ldp + j] = b;
-      Hf[j * ldp + r] = x;
-      H0[j * ldp + r] = a;
-      H1[j * ldp + r] = b;
-      if (H2) {   // third slice only while the sweep uses three
-        H2[r * ldp + j] = d;
-        H2[j * ldp + r] = d;
+  __device__ __forceinline__ void put(int64_t idx, float x) const {
+    __nv_bfloat16 a, b, d;
+    split3(x, a, b, d);
+    Hf[idx] = x;
+    H0[idx] = a;
+    H1[idx] = b;
+    if (H2) H2[idx] = d;   // third slice only while the sweep uses three
+  }
+  __device__ __forceinline__ void warp_tile(int64_t row0, int64_t j0, int, const float* __restrict__ stage,
+                                            int lane) const {
+    {  // H[j, lo + i]: lane = row i
+      const int64_t i = row0 + lane;
+      if (i < m) {
+#pragma unroll 4
+        for (int c = 0; c < 16; ++c) {
+          const int64_t j = j0 + c;
+          if (j < p && (j < lo || j >= hi)) put(j * ldp + lo + i, -stage[lane * 17 + c]);
+        }
       }
+    }
+    const int c = lane & 15;
+    const int64_t j = j0 + c;
+    if (j >= p || (j >= lo && j < hi)) return;
+#pragma unroll 4
+    for (int k = 0; k < 16; ++k) {   // H[lo + i, j]: lane = (row, column)
+      const int r = 2 * k + (lane >> 4);
+      const int64_t i = row0 + r;
+      if (i < m) put((lo + i) * ldp + j, -stage[r * 17 + c]);
     }
   }
 };
 
-// a4 epilogue: split-K partial of X W^T, rows/cols < m.
+// a4 epilogue: split-K partial of X W^T, rows/cols < m, through shared memory
+// so that each store covers 16 consecutive columns of two rows.
 struct EpiTcPartial : tc::EpiBase {
   float* Spart; int64_t m;
-  __device__ __forceinline__ void operator()(int64_t i, int64_t j0, int z, const float (&v)[16]) const {
-    if (i >= m) return;
-    float* o = Spart + (int64_t)z * m * m + i * m;
-#pragma unroll
-    for (int c = 0; c < 16; ++c)
-      if (j0 + c < m) o[j0 + c] = v[c];
+  __device__ __forceinline__ void warp_tile(int64_t row0, int64_t j0, int z, const float* __restrict__ stage,
+                                            int lane) const {
+    const int c = lane & 15;
+    if (j0 + c >= m) return;
+    float* o = Spart + (int64_t)z * m * m + j0 + c;
+#pragma unroll 4
+    for (int k = 0; k < 16; ++k) {
+      const int r = 2 * k + (lane >> 4);
+      const int64_t i = row0 + r;
+      if (i < m) o[i * m] = stage[r * 17 + c];
+    }
   }
 };
 
