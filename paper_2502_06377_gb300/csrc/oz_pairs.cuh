@@ -1,0 +1,223 @@
+// All slice-pair products of one error-free sliced product in a single
+// persistent tcgen05 launch (internal).
+//
+// T_q += D_s(X) D_u(B)^T for every pair (s, u) of a list, in list order, each
+// pair an exact FP32 accumulation in TMEM per K chunk (<= 4096 terms) that the
+// epilogue adds in int32 into the digit-group plane T_q.  CTA c owns output
+// tiles c, c + gridDim.x, ... for every pair, so all read-modify-writes of a
+// tile come from one CTA in list order (no races), and the epilogue of one
+// pair's last tile runs under the MMAs of the next pair's first tile: the
+// pipeline fill, launch gap and exposed last epilogue of one launch per pair
+// are gone.  Roles as in k_tc_gemm: warp 0 TMA producer, warp 1 MMA issuer,
+// warps 2-5 epilogue through a shared-memory stage (row-coalesced int4).
+#pragma once
+#include "tc_gemm.cuh"
+
+namespace ibmi {
+namespace tc {
+
+constexpr int OZP_MAX_A = 10, OZP_MAX_B = 8, OZP_MAX_PAIRS = 64;
+
+struct OzPairMaps {
+  CUtensorMap a[OZP_MAX_A];   // digit planes of the left operand (rows i), 128-row boxes
+  CUtensorMap b[OZP_MAX_B];   // digit planes of the right operand (rows j), BN-row boxes
+};
+
+struct OzPairArgs {
+  int n;                                   // pairs
+  int8_t s[OZP_MAX_PAIRS], u[OZP_MAX_PAIRS], q[OZP_MAX_PAIRS], first[OZP_MAX_PAIRS];
+  int grid_n, tiles;                       // N tiles; tiles = grid_m * grid_n
+  int kt_total, chunk;                     // K tiles; K tiles per exact accumulation
+  int* T;                                  // group planes: T + q * plane, row pitch ldt
+  int64_t plane, ldt, M, N;
+  int* err;
+};
+
+template <int BN>
+__global__ void __launch_bounds__(THREADS, 1) k_oz_pairs(const __grid_constant__ OzPairMaps maps,
+                                                         const __grid_constant__ OzPairArgs g) {
+  using C = Cfg<1, BN>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* tiles = smem;
+  uint64_t* full = (uint64_t*)(smem + C::STAGES * C::STAGE_BYTES);
+  uint64_t* empty = full + C::STAGES;
+  uint64_t* accf = empty + C::STAGES;
+  uint64_t* acce = accf + 2;
+  uint32_t* tmem_slot = (uint32_t*)(acce + 2);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nchunks = (g.kt_total + g.chunk - 1) / g.chunk;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < C::STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&accf[b], 1);
+      mbar_init(&acce[b], 4);
+    }
+    fence_barrier_init();
+  }
+  if (warp == 1) tmem_alloc(tmem_slot, C::TMEM_COLS);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {  // TMA producer
+      int kc = 0;
+      bool ok = true;
+      for (int pi = 0; ok && pi < g.n; ++pi)
+        for (int ci = 0; ok && ci < nchunks; ++ci)
+          for (int tt = blockIdx.x; ok && tt < g.tiles; tt += gridDim.x) {
+            const int mt = tt / g.grid_n, ntl = tt - mt * g.grid_n;
+            const int kb = ci * g.chunk, nk = min(g.chunk, g.kt_total - kb);
+            const CUtensorMap* ma = &maps.a[g.s[pi]];
+            const CUtensorMap* mb = &maps.b[g.u[pi]];
+            for (int it = 0; it < nk; ++it, ++kc) {
+              const int st = kc % C::STAGES;
+              const uint32_t ph = (uint32_t)(kc / C::STAGES) & 1u;
+              if (!mbar_wait(&empty[st], ph ^ 1u, g.err)) { ok = false; break; }
+              const int kx = (kb + it) * BK;
+              uint8_t* sa = tiles + st * C::STAGE_BYTES;
+              mbar_expect_tx(&full[st], C::STAGE_BYTES);
+              tma_load_2d(sa, ma, &full[st], kx, mt * BM);
+              tma_load_2d(sa + C::A_BYTES, mb, &full[st], kx, ntl * BN);
+            }
+          }
+      if (*(volatile int*)g.err != 0) {   // error exit: wait (bounded) for copies in flight
+        for (int k = kc - C::STAGES < 0 ? 0 : kc - C::STAGES; k < kc; ++k) {
+          const int st = k % C::STAGES;
+          const uint32_t ph = (uint32_t)(k / C::STAGES) & 1u;
+          const uint64_t t0 = globaltimer();
+          while (!mbar_try_wait(&full[st], ph) && globaltimer() - t0 < 1000000000ull) {
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {  // MMA issuer
+      constexpr uint32_t idesc = idesc_bf16(BM, BN);
+      int kc = 0, local = 0;
+      bool ok = true;
+      for (int pi = 0; ok && pi < g.n; ++pi)
+        for (int ci = 0; ok && ci < nchunks; ++ci)
+          for (int tt = blockIdx.x; ok && tt < g.tiles; tt += gridDim.x, ++local) {
+            const int nk = min(g.chunk, g.kt_total - ci * g.chunk);
+            const int buf = local & 1;
+            const uint32_t use = (uint32_t)(local >> 1);
+            if (!mbar_wait(&acce[buf], (use & 1u) ^ 1u, g.err)) { ok = false; break; }
+            tc_fence_after();
+            const uint32_t dacc = tmem + (uint32_t)(buf * BN);
+            for (int it = 0; it < nk; ++it, ++kc) {
+              const int st = kc % C::STAGES;
+              const uint32_t ph = (uint32_t)(kc / C::STAGES) & 1u;
+              if (!mbar_wait(&full[st], ph, g.err)) { ok = false; break; }
+              tc_fence_after();
+              const uint32_t sa = smem_u32(tiles + st * C::STAGE_BYTES);
+              const uint32_t sb = sa + C::A_BYTES;
+#pragma unroll
+              for (int kk = 0; kk < BK / 16; ++kk)
+                mma_bf16(dacc, sdesc_sw128(sa + kk * 32), sdesc_sw128(sb + kk * 32), idesc, (it | kk) != 0 ? 1u : 0u);
+              mma_commit(&empty[st]);
+            }
+            mma_commit(&accf[buf]);
+          }
+    }
+  } else {  // epilogue warps 2..5
+    const int qw = warp & 3;
+    float* stage = (float*)(smem + C::STAGES * C::STAGE_BYTES + 256) + qw * 32 * 17;
+    const int c4 = (lane & 3) * 4, r0 = lane >> 2;
+    int local = 0;
+    bool ok = true;
+    for (int pi = 0; ok && pi < g.n; ++pi)
+      for (int ci = 0; ok && ci < nchunks; ++ci)
+        for (int tt = blockIdx.x; ok && tt < g.tiles; tt += gridDim.x, ++local) {
+          const int mt = tt / g.grid_n, ntl = tt - mt * g.grid_n;
+          const int buf = local & 1;
+          const uint32_t use = (uint32_t)(local >> 1);
+          if (!mbar_wait(&accf[buf], use & 1u, g.err)) { ok = false; break; }
+          tc_fence_after();
+          int* Tq = g.T + (int64_t)g.q[pi] * g.plane;
+          const bool first = g.first[pi] && ci == 0;
+          const int64_t row0 = (int64_t)mt * BM + qw * 32;
+#pragma unroll 1
+          for (int c = 0; c < BN; c += 16) {
+            float v[16];
+            tmem_ld16(tmem + ((uint32_t)(qw * 32) << 16) + (uint32_t)(buf * BN + c), v);
+#pragma unroll
+            for (int k = 0; k < 16; ++k) stage[lane * 17 + k] = v[k];
+            __syncwarp();
+            // lane = (row 8k + lane/4, columns 4(lane%4)..+3): all staged values,
+            // then all loads, then all stores
+            const int64_t j0 = (int64_t)ntl * BN + c;
+            int4 a[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              const float* sv = stage + (8 * k + r0) * 17 + c4;
+              a[k] = make_int4(__float2int_rn(sv[0]), __float2int_rn(sv[1]), __float2int_rn(sv[2]),
+                               __float2int_rn(sv[3]));
+            }
+            __syncwarp();
+            int* t0 = Tq + (row0 + r0) * g.ldt + j0 + c4;
+            if (j0 + c4 + 4 <= g.N) {
+              int4 o[4];
+#pragma unroll
+              for (int k = 0; k < 4; ++k)
+                o[k] = (first || row0 + 8 * k + r0 >= g.M) ? make_int4(0, 0, 0, 0)
+                                                            : *reinterpret_cast<const int4*>(t0 + 8 * k * g.ldt);
+#pragma unroll
+              for (int k = 0; k < 4; ++k) {
+                if (row0 + 8 * k + r0 >= g.M) continue;
+                o[k].x += a[k].x;
+                o[k].y += a[k].y;
+                o[k].z += a[k].z;
+                o[k].w += a[k].w;
+                *reinterpret_cast<int4*>(t0 + 8 * k * g.ldt) = o[k];
+              }
+            } else {
+#pragma unroll
+              for (int k = 0; k < 4; ++k) {
+                if (row0 + 8 * k + r0 >= g.M) continue;
+                int* t = t0 + 8 * k * g.ldt;
+                const int vv[4] = {a[k].x, a[k].y, a[k].z, a[k].w};
+                for (int uu = 0; uu < 4 && j0 + c4 + uu < g.N; ++uu) t[uu] = (first ? 0 : t[uu]) + vv[uu];
+              }
+            }
+          }
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&acce[buf]);
+        }
+  }
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, C::TMEM_COLS);
+  }
+}
+
+// Launches k_oz_pairs on min(tiles, SMs) persistent CTAs.
+template <int BN>
+cudaError_t launch_oz_pairs(const OzPairMaps& maps, const OzPairArgs& g, cudaStream_t st) {
+  using C = Cfg<1, BN>;
+  constexpr uint32_t smem_bytes = C::SMEM + STAGE_TILE_BYTES;
+  static_assert(smem_bytes <= 227 * 1024, "shared memory per CTA");
+  static_assert(C::CTAS_PER_SM == 1, "one CTA per SM");
+  static std::atomic<bool> attr_set{false};
+  if (!attr_set.load(std::memory_order_acquire)) {
+    cudaError_t e = cudaFuncSetAttribute(k_oz_pairs<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+    if (e != cudaSuccess) return e;
+    attr_set.store(true, std::memory_order_release);
+  }
+  if (g.n <= 0 || g.tiles <= 0 || g.kt_total <= 0) return cudaSuccess;
+  const int grid = std::min(g.tiles, resident_ctas<1, BN>());
+  note_launch();
+  k_oz_pairs<BN><<<grid, THREADS, smem_bytes, st>>>(maps, g);
+  return cudaGetLastError();
+}
+
+}  // namespace tc
+}  // namespace ibmi

@@ -3,6 +3,7 @@
 #include <math.h>
 
 #include "refine.cuh"
+#include "oz_pairs.cuh"
 
 namespace ibmi {
 
@@ -430,10 +431,44 @@ static ibmi_status digit_gemm(RefineState* R, const DigitGemm& g, cudaStream_t s
   return IBMI_OK;
 }
 
+// All pairs (s, u) with s + u <= qmax of a p x p x p sliced product in one
+// persistent launch (k_oz_pairs), in group order so that the first pair of
+// each group stores and the others add.
 static ibmi_status pair_products(RefineState* R, const CUtensorMap* ma, int nsa, const CUtensorMap* mb, int nsb,
                                  int qmax, int kclass, cudaStream_t st) {
-  const int nkt = (int)((R->p + tc::BK - 1) / tc::BK);
-  return digit_gemm(R, DigitGemm{ma, nsa, mb, nsb, R->p, R->p, 0, nkt, qmax, kclass}, st);
+  const int64_t p = R->p, ldp = R->ldp;
+  tc::OzPairMaps maps;
+  for (int s = 0; s < nsa; ++s) maps.a[s] = ma[s];
+  for (int u = 0; u < nsb; ++u) maps.b[u] = mb[u];
+  tc::OzPairArgs g{};
+  int n = 0;
+  for (int q = 0; q <= qmax; ++q) {
+    bool first = true;
+    for (int s = 0; s <= q; ++s) {
+      const int u = q - s;
+      if (s >= nsa || u >= nsb) continue;
+      g.s[n] = (int8_t)s;
+      g.u[n] = (int8_t)u;
+      g.q[n] = (int8_t)q;
+      g.first[n] = first ? 1 : 0;
+      first = false;
+      ++n;
+    }
+  }
+  g.n = n;
+  g.grid_n = (int)((p + OZ_BN - 1) / OZ_BN);
+  g.tiles = g.grid_n * (int)((p + 127) / 128);
+  g.kt_total = (int)((p + tc::BK - 1) / tc::BK);
+  g.chunk = OZ_KCHUNK / tc::BK;
+  g.T = R->T;
+  g.plane = p * ldp;
+  g.ldt = ldp;
+  g.M = p;
+  g.N = p;
+  g.err = R->err;
+  ProfScope ps(kclass, st, 2.0 * n * (double)p * p * (double)g.kt_total * tc::BK);
+  IBMI_CUDA_TRY(tc::launch_oz_pairs<OZ_BN>(maps, g, st));
+  return IBMI_OK;
 }
 
 // W = A_I^{-1} A_{I,:} from digit products, written as BF16 hi/lo (zero on
