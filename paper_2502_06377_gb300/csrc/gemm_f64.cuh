@@ -31,6 +31,9 @@ struct F64Operands {
   // Y^T Y with Y lower triangular), so a tile starts its K loop at
   // max(first row, first column), rounded down to the K block.
   bool tri_k = false;
+  // Symmetric result: tiles entirely above the diagonal are skipped (the
+  // consumer reads element (i, j) with j > i from (j, i)).
+  bool lower_tiles = false;
 };
 
 template <bool A_KMAJOR, bool B_NMAJOR, class Epi, int T = F64_BM>
@@ -42,6 +45,7 @@ k_gemm_f64(F64Operands op, Epi epi) {
   __shared__ double Bs[F64_BK][T + 1];
   const int tx = threadIdx.x % Q, ty = threadIdx.x / Q;
   const int64_t i0 = (int64_t)blockIdx.y * T, j0 = (int64_t)blockIdx.x * T;
+  if (op.lower_tiles && j0 >= i0 + T) return;
   op.A += blockIdx.z * op.zA;
   op.B += blockIdx.z * op.zB;
   double acc[4][4];
@@ -191,7 +195,9 @@ inline cudaError_t launch_gemm_f64(const F64Operands& op, const Epi& epi, cudaSt
   const int64_t tiles64 = ((op.N + F64_BN - 1) / F64_BN) * ((op.M + F64_BM - 1) / F64_BM) * op.batch;
   note_launch();
   if constexpr (std::is_same<Epi, EpiStore>::value) {
-    if (tiles64 < F64_SMALL_LAUNCH) {
+    // triangular K: a 64 x 64 tile at the start of the diagonal sums all of K
+    // on one SM; 32 x 32 tiles quarter that critical path
+    if (tiles64 < F64_SMALL_LAUNCH || op.tri_k) {
       dim3 grid((unsigned)((op.N + 31) / 32), (unsigned)((op.M + 31) / 32), (unsigned)op.batch);
       k_gemm_f64<A_KMAJOR, B_NMAJOR, Epi, 32><<<grid, 64, 0, st>>>(op, epi);
       return cudaGetLastError();

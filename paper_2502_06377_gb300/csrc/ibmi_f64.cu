@@ -111,9 +111,11 @@ __global__ void k_bat_rhs(const double* A, int64_t lda, const int64_t* dlo, cons
 
 // Scatter of the solutions: A_I^{-1} (symmetrised) and, for full_w, W with
 // zero columns on I.  Offsets of the per-set outputs come from doff_*.
+// lower_only: R holds A_I^{-1} on and below the diagonal only; the upper
+// triangle is mirrored from it.
 __global__ void k_bat_extract(const double* R, const int64_t* dlo, const int64_t* dm, int64_t mmax, int64_t ncols,
-                              int full_w, double* base, const int64_t* doff_ainv, const int64_t* doff_w,
-                              int64_t p) {
+                              int full_w, int lower_only, double* base, const int64_t* doff_ainv,
+                              const int64_t* doff_w, int64_t p) {
   const int z = blockIdx.z;
   const int64_t lo = dlo[z], m = dm[z];
   const double* Rz = R + z * mmax * ncols;
@@ -121,7 +123,10 @@ __global__ void k_bat_extract(const double* R, const int64_t* dlo, const int64_t
   if (idx < m * m) {
     int64_t i = idx / m, j = idx - i * m;
     const int64_t cj = full_w ? lo + j : j, ci = full_w ? lo + i : i;
-    base[doff_ainv[z] + idx] = 0.5 * (Rz[i * ncols + cj] + Rz[j * ncols + ci]);
+    if (lower_only)
+      base[doff_ainv[z] + idx] = i >= j ? Rz[i * ncols + j] : Rz[j * ncols + i];
+    else
+      base[doff_ainv[z] + idx] = 0.5 * (Rz[i * ncols + cj] + Rz[j * ncols + ci]);
   }
   if (full_w && idx < m * p) {
     int64_t i = idx / p, c = idx - i * p;
@@ -223,13 +228,14 @@ ibmi_status invariants_all(ibmi_plan_s* P, const double* A, int64_t lda, bool fu
     // no longer needed), each tile summing only k >= max(i, j).
     F64Operands op = bat(F64Operands{R, ncols, id, id, R, ncols, id, id, mmax, mmax, mmax}, zR, zR);
     op.tri_k = true;
+    op.lower_tiles = true;
     IBMI_CUDA_TRY((launch_gemm_f64<false, true>(op, EpiStore{Lw, mmax, 1.0, 0.0, zL}, st)));
     X = Lw;
   }
   const int64_t nout = std::max(mmax * mmax, full_w ? mmax * p : 0);
   note_launch();
-  k_bat_extract<<<dim3(nblk(nout), 1, K), 256, 0, st>>>(X, P->dlo, P->dm, mmax, ncols, full_w ? 1 : 0, P->pool,
-                                                         P->doff_ainv, P->doff_w, p);
+  k_bat_extract<<<dim3(nblk(nout), 1, K), 256, 0, st>>>(X, P->dlo, P->dm, mmax, ncols, full_w ? 1 : 0,
+                                                         full_w ? 0 : 1, P->pool, P->doff_ainv, P->doff_w, p);
   IBMI_CUDA_TRY(cudaGetLastError());
   return IBMI_OK;
 }

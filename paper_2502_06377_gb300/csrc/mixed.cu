@@ -147,35 +147,35 @@ __device__ __forceinline__ void split3(float x, __nv_bfloat16& a, __nv_bfloat16&
 }
 
 // FP64 H (ldh) -> FP32 master + BF16 hi/lo (ldp)
+// Elementwise kernels run on 2-D grids: row = blockIdx.y, column =
+// blockIdx.x * 256 + threadIdx.x (no 64-bit index division).
 __global__ void k_import_h(const double* H, int64_t ldh, int64_t p, int64_t ldp, float* Hf, __nv_bfloat16* s0,
                            __nv_bfloat16* s1, __nv_bfloat16* s2) {
-  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= p * ldp) return;
-  int64_t i = idx / ldp, c = idx - i * ldp;
+  const int64_t i = blockIdx.y, c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ldp) return;
+  const int64_t idx = i * ldp + c;
   float x = c < p ? (float)H[i * ldh + c] : 0.f;
   Hf[idx] = x;
   split3(x, s0[idx], s1[idx], s2[idx]);
 }
 
 __global__ void k_export_h(const float* Hf, int64_t ldp, int64_t p, double* H, int64_t ldh) {
-  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= p * p) return;
-  int64_t i = idx / p, c = idx - i * p;
+  const int64_t i = blockIdx.y, c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= p) return;
   H[i * ldh + c] = (double)Hf[i * ldp + c];
 }
 
 // a4 finish: H[I, I] = A_I^{-1} - (P + P^T)/2 with P = sum of the split-K partials.
 __global__ void k_mixed_sym(const float* Spart, int splits, int64_t m, const double* Ainv, int64_t lo, int64_t ldp,
                             float* Hf, __nv_bfloat16* s0, __nv_bfloat16* s1, __nv_bfloat16* s2) {
-  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= m * m) return;
-  int64_t i = idx / m, j = idx - i * m;
+  const int64_t i = blockIdx.y, j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= m) return;
   float a = 0.f, b = 0.f;
   for (int z = 0; z < splits; ++z) {
     a += Spart[(int64_t)z * m * m + i * m + j];
     b += Spart[(int64_t)z * m * m + j * m + i];
   }
-  float x = (float)(Ainv[idx] - 0.5 * ((double)a + (double)b));
+  float x = (float)(Ainv[i * m + j] - 0.5 * ((double)a + (double)b));
   int64_t o = (lo + i) * ldp + lo + j;
   Hf[o] = x;
   __nv_bfloat16 t0, t1, t2;
@@ -183,6 +183,10 @@ __global__ void k_mixed_sym(const float* Spart, int splits, int64_t m, const dou
   s0[o] = t0;
   s1[o] = t1;
   if (s2) s2[o] = t2;
+}
+
+static inline dim3 grid2(int64_t cols, int64_t rows) {
+  return dim3((unsigned)((cols + 255) / 256), (unsigned)rows);
 }
 
 // All three slices of H from the FP32 master (entering the three-slice sweep).
@@ -307,7 +311,7 @@ ibmi_status mixed_prepare(ibmi_plan_s* P, const double* H, int64_t ldh, cudaStre
   const int64_t p = P->d.p, ldp = M->ldp;
   ProfScope ps(IBMI_K_OTHER, st, 0.0);
   note_launch();
-  k_import_h<<<nblk(p * ldp), 256, 0, st>>>(H, ldh, p, ldp, M->Hf, M->Hs[0], M->Hs[1], M->Hs[2]);
+  k_import_h<<<grid2(ldp, p), 256, 0, st>>>(H, ldh, p, ldp, M->Hf, M->Hs[0], M->Hs[1], M->Hs[2]);
   IBMI_CUDA_TRY(cudaGetLastError());
   return IBMI_OK;
 }
@@ -349,7 +353,7 @@ ibmi_status mixed_sweep_step(ibmi_plan_s* P, int k, cudaStream_t st) {
     if (S == 2) IBMI_CUDA_TRY((tc::launch<2, MX_BN>(maps, t, ntn, (int)((m + 127) / 128), epi, st)));
     else IBMI_CUDA_TRY((tc::launch<3, MX_BN>(maps, t, ntn, (int)((m + 127) / 128), epi, st)));
     note_launch();
-    k_mixed_sym<<<nblk(m * m), 256, 0, st>>>(M->Spart, splits, m, P->ainv[k], lo, M->ldp, M->Hf, M->Hs[0],
+    k_mixed_sym<<<grid2(m, m), 256, 0, st>>>(M->Spart, splits, m, P->ainv[k], lo, M->ldp, M->Hf, M->Hs[0],
                                              M->Hs[1], S == 3 ? M->Hs[2] : nullptr);
     IBMI_CUDA_TRY(cudaGetLastError());
   }
@@ -360,7 +364,7 @@ static ibmi_status mixed_export_launch(ibmi_plan_s* P, double* H, int64_t ldh, c
   MixedState* M = MS(P);
   const int64_t p = P->d.p;
   note_launch();
-  k_export_h<<<nblk(p * p), 256, 0, st>>>(M->Hf, M->ldp, p, H, ldh);
+  k_export_h<<<grid2(p, p), 256, 0, st>>>(M->Hf, M->ldp, p, H, ldh);
   IBMI_CUDA_TRY(cudaGetLastError());
   return IBMI_OK;
 }

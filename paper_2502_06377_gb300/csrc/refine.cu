@@ -103,13 +103,19 @@ __global__ void k_oz_slices(const double* X, int64_t ldx, int64_t ncols, int64_t
 
 __global__ void k_fsplit2(const double* X, int64_t ldx, int64_t p, int64_t ldp, __nv_bfloat16* s0,
                           __nv_bfloat16* s1) {
-  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= p * ldp) return;
-  int64_t i = idx / ldp, c = idx - i * ldp;
+  const int64_t i = blockIdx.y, c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ldp) return;
+  const int64_t idx = i * ldp + c;
   float x = c < p ? (float)X[i * ldx + c] : 0.f;
   __nv_bfloat16 h = __float2bfloat16_rn(x);
   s0[idx] = h;
   s1[idx] = __float2bfloat16_rn(x - __bfloat162float(h));
+}
+
+// 2-D grids for the elementwise kernels: row = blockIdx.y, column =
+// blockIdx.x * 256 + threadIdx.x (no 64-bit index division).
+static inline dim3 grid2(int64_t cols, int64_t rows) {
+  return dim3((unsigned)((cols + 255) / 256), (unsigned)rows);
 }
 
 // ---------------------------------------------------------- epilogues ----
@@ -214,17 +220,13 @@ __device__ __forceinline__ double oz_value(const int* T, int64_t plane, int64_t 
 // sum Q^2 per CTA.
 __global__ void k_oz_combine(const int* T, int64_t p, int64_t ldp, const int* ex, const int* ea, int qmax,
                              double* Q, double* partials) {
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t i = blockIdx.y, j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   double sq = 0.0;
-  if (idx < p * ldp) {
-    const int64_t i = idx / ldp, j = idx - i * ldp;
-    double q = 0.0;
-    if (j < p) {
-      const double c = oz_value(T, p * ldp, idx, qmax, ex[i] + ea[j] - 12);
-      q = (i == j ? 1.0 : 0.0) - c;
-      sq = q * q;
-      Q[i * p + j] = q;
-    }
+  if (j < p) {
+    const double c = oz_value(T, p * ldp, i * ldp + j, qmax, ex[i] + ea[j] - 12);
+    const double q = (i == j ? 1.0 : 0.0) - c;
+    sq = q * q;
+    Q[i * p + j] = q;
   }
   __shared__ double red[8];
   for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
@@ -233,7 +235,7 @@ __global__ void k_oz_combine(const int* T, int64_t p, int64_t ldp, const int* ex
   if (threadIdx.x == 0) {
     double t = 0.0;
     for (int w = 0; w < (int)(blockDim.x / 32); ++w) t += red[w];
-    partials[blockIdx.x] = t;
+    partials[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = t;
   }
 }
 
@@ -254,17 +256,24 @@ __global__ void k_sum_partials(const double* partials, int64_t n, int64_t p, dou
 // Newton-Schulz update: Xn = X + 2^{e_i + g_j - 12} sum_{q <= qmax} T_q 2^{-7q}.
 __global__ void k_oz_update(const int* T, int64_t p, int64_t ldp, const int* ex, const int* eq, int qmax,
                             const double* X, int64_t ldx, double* Xn) {
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= p * p) return;
-  const int64_t i = idx / p, j = idx - i * p;
-  Xn[idx] = X[i * ldx + j] + oz_value(T, p * ldp, i * ldp + j, qmax, ex[i] + eq[j] - 12);
+  const int64_t i = blockIdx.y, j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= p) return;
+  Xn[i * p + j] = X[i * ldx + j] + oz_value(T, p * ldp, i * ldp + j, qmax, ex[i] + eq[j] - 12);
 }
 
+// X = (Xn + Xn^T) / 2 by 32 x 32 tiles through shared memory (both the tile
+// and its mirror read row-wise).
 __global__ void k_sym_into(const double* Xn, int64_t p, double* X, int64_t ldx) {
-  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= p * p) return;
-  int64_t i = idx / p, j = idx - i * p;
-  X[i * ldx + j] = 0.5 * (Xn[i * p + j] + Xn[j * p + i]);
+  __shared__ double a[32][33], b[32][33];
+  const int64_t I0 = (int64_t)blockIdx.y * 32, J0 = (int64_t)blockIdx.x * 32;
+  const int tx = threadIdx.x;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    a[r][tx] = (I0 + r < p && J0 + tx < p) ? Xn[(I0 + r) * p + J0 + tx] : 0.0;
+    b[r][tx] = (J0 + r < p && I0 + tx < p) ? Xn[(J0 + r) * p + I0 + tx] : 0.0;
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y)
+    if (I0 + r < p && J0 + tx < p) X[(I0 + r) * ldx + J0 + tx] = 0.5 * (a[r][tx] + b[tx][r]);
 }
 
 // Power iteration on the dense Q (p x p, row pitch p): y = Q v, one warp per row.
@@ -319,7 +328,7 @@ ibmi_status refine_create(RefineState* R, int64_t p, int* err) {
   const int64_t ldp = R->ldp;
   const size_t plane16 = sizeof(__nv_bfloat16) * p * ldp;
   const int64_t tiles = ((p + 127) / 128) * ((p + RF_BN - 1) / RF_BN);
-  R->n_partials = std::max<int64_t>(tiles * 4, (p * ldp + 255) / 256) + 8;
+  R->n_partials = std::max<int64_t>(tiles * 4, p * ((p + 255) / 256)) + 8;
   size_t bytes = plane16 * (OZ_SA + OZ_SX + NS_S + 2) + sizeof(int) * (size_t)(OZ_QMAX + 1) * p * ldp +
                  sizeof(double) * p * p + sizeof(double) * R->n_partials + 3 * sizeof(int) * p +
                  sizeof(double) * (2 * p + 8) + 64 * 256;
@@ -373,7 +382,7 @@ ibmi_status refine_set_matrix(RefineState* R, const double* A, int64_t lda, cuda
   ProfScope ps(IBMI_K_OTHER, st, 0.0);
   IBMI_TRY(slice_digits(R, A, lda, R->Ao, OZ_SA, R->expA, st));
   note_launch();
-  k_fsplit2<<<nblk(R->p * R->ldp), 256, 0, st>>>(A, lda, R->p, R->ldp, R->Af[0], R->Af[1]);
+  k_fsplit2<<<grid2(R->ldp, R->p), 256, 0, st>>>(A, lda, R->p, R->ldp, R->Af[0], R->Af[1]);
   IBMI_CUDA_TRY(cudaGetLastError());
   return IBMI_OK;
 }
@@ -476,9 +485,9 @@ static ibmi_status pair_products(RefineState* R, const CUtensorMap* ma, int nsa,
 __global__ void k_oz_wcombine(const int* T, int64_t plane, int64_t m, int64_t p, int64_t ldp, const int* ea,
                               const int* eb, int qmax, int64_t lo, int64_t hi, __nv_bfloat16* W0, __nv_bfloat16* W1,
                               __nv_bfloat16* W2) {
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= m * ldp) return;
-  const int64_t i = idx / ldp, j = idx - i * ldp;
+  const int64_t i = blockIdx.y, j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= ldp) return;
+  const int64_t idx = i * ldp + j;
   float w = 0.f;
   if (j < p && (j < lo || j >= hi)) {
     w = (float)oz_value(T, plane, idx, qmax, ea[i] + eb[j] - 12);
@@ -504,7 +513,7 @@ ibmi_status refine_form_w(RefineState* R, const double* Ainv, int64_t m, int64_t
                                    (int)((hi + tc::BK - 1) / tc::BK), QW, IBMI_K_INVARIANTS_TC}, st));
   ProfScope ps(IBMI_K_OTHER, st, 0.0);
   note_launch();
-  k_oz_wcombine<<<nblk(m * ldp), 256, 0, st>>>(R->T, p * ldp, m, p, ldp, R->expX, R->expA, QW, lo, hi, W0, W1, W2);
+  k_oz_wcombine<<<grid2(ldp, m), 256, 0, st>>>(R->T, p * ldp, m, p, ldp, R->expX, R->expA, QW, lo, hi, W0, W1, W2);
   IBMI_CUDA_TRY(cudaGetLastError());
   return IBMI_OK;
 }
@@ -587,7 +596,7 @@ ibmi_status refine_form_w_all(RefineState* R, const std::vector<const double*>& 
   for (int k = 0; k < K; ++k) {
     const int64_t m = hi[k] - lo[k];
     note_launch();
-    k_oz_wcombine<<<nblk(m * ldp), 256, 0, st>>>(R->T + R->w_off[k] * ldp, rows * ldp, m, p, ldp,
+    k_oz_wcombine<<<grid2(ldp, m), 256, 0, st>>>(R->T + R->w_off[k] * ldp, rows * ldp, m, p, ldp,
                                                  R->expW + R->w_off[k], R->expA, QW, lo[k], hi[k], W0[k], W1[k],
                                                  W2[k]);
   }
@@ -634,9 +643,10 @@ ibmi_status refine_residual_launch(RefineState* R, const double* X, int64_t ldx,
   IBMI_TRY(pair_products(R, R->mXo, OZ_SX, R->mAo, OZ_SA, OZ_QMAX, IBMI_K_RESIDUAL, st));
   {
     ProfScope ps(IBMI_K_OTHER, st, 0.0);
-    const unsigned nb = nblk(p * ldp);
+    const dim3 gc = grid2(p, p);
+    const int64_t nb = (int64_t)gc.x * gc.y;
     note_launch();
-    k_oz_combine<<<nb, 256, 0, st>>>(R->T, p, ldp, R->expX, R->expA, OZ_QMAX, R->Xn, R->partials);
+    k_oz_combine<<<gc, 256, 0, st>>>(R->T, p, ldp, R->expX, R->expA, OZ_QMAX, R->Xn, R->partials);
     IBMI_CUDA_TRY(cudaGetLastError());
     note_launch();
     k_sum_partials<<<1, 1024, 0, st>>>(R->partials, nb, p, R->dout);
@@ -654,10 +664,10 @@ ibmi_status refine_ns_update(RefineState* R, double* X, int64_t ldx, cudaStream_
   IBMI_TRY(pair_products(R, R->mXo, NS_S, R->mQo, NS_S, NS_S - 1, IBMI_K_NS, st));
   ProfScope ps(IBMI_K_OTHER, st, 0.0);
   note_launch();
-  k_oz_update<<<nblk(p * p), 256, 0, st>>>(R->T, p, ldp, R->expX, R->expQ, NS_S - 1, X, ldx, R->Xn);
+  k_oz_update<<<grid2(p, p), 256, 0, st>>>(R->T, p, ldp, R->expX, R->expQ, NS_S - 1, X, ldx, R->Xn);
   IBMI_CUDA_TRY(cudaGetLastError());
   note_launch();
-  k_sym_into<<<nblk(p * p), 256, 0, st>>>(R->Xn, p, X, ldx);
+  k_sym_into<<<dim3((unsigned)((p + 31) / 32), (unsigned)((p + 31) / 32)), dim3(32, 8), 0, st>>>(R->Xn, p, X, ldx);
   IBMI_CUDA_TRY(cudaGetLastError());
   return IBMI_OK;
 }
