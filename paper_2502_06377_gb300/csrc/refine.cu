@@ -634,19 +634,21 @@ ibmi_status refine_residual(RefineState* R, const double* X, int64_t ldx, cudaSt
   return read_scalar(R, st, rho);
 }
 
-ibmi_status refine_residual_launch(RefineState* R, const double* X, int64_t ldx, cudaStream_t st) {
+ibmi_status refine_residual_launch(RefineState* R, const double* X, int64_t ldx, cudaStream_t st, int qmax) {
   const int64_t p = R->p, ldp = R->ldp;
+  if (qmax < NS_S - 1 || qmax > OZ_QMAX) return IBMI_ERR_INVALID_ARG;
+  const int nsx = std::min(OZ_SX, qmax + 1);   // digits of X that groups <= qmax use
   {
     ProfScope ps(IBMI_K_OTHER, st, 0.0);
-    IBMI_TRY(slice_digits(R, X, ldx, R->Xo, OZ_SX, R->expX, st));
+    IBMI_TRY(slice_digits(R, X, ldx, R->Xo, nsx, R->expX, st));
   }
-  IBMI_TRY(pair_products(R, R->mXo, OZ_SX, R->mAo, OZ_SA, OZ_QMAX, IBMI_K_RESIDUAL, st));
+  IBMI_TRY(pair_products(R, R->mXo, nsx, R->mAo, OZ_SA, qmax, IBMI_K_RESIDUAL, st));
   {
     ProfScope ps(IBMI_K_OTHER, st, 0.0);
     const dim3 gc = grid2(p, p);
     const int64_t nb = (int64_t)gc.x * gc.y;
     note_launch();
-    k_oz_combine<<<gc, 256, 0, st>>>(R->T, p, ldp, R->expX, R->expA, OZ_QMAX, R->Xn, R->partials);
+    k_oz_combine<<<gc, 256, 0, st>>>(R->T, p, ldp, R->expX, R->expA, qmax, R->Xn, R->partials);
     IBMI_CUDA_TRY(cudaGetLastError());
     note_launch();
     k_sum_partials<<<1, 1024, 0, st>>>(R->partials, nb, p, R->dout);

@@ -93,7 +93,13 @@ ibmi_status refine_form_w_all(RefineState* R, const std::vector<const double*>& 
 // The same two residuals split into their kernels (no host synchronisation,
 // so they can be captured in a CUDA graph) and the read of the value
 // (synchronises the stream, reports a bounded-wait expiry as IBMI_ERR_TIMEOUT).
-ibmi_status refine_residual_launch(RefineState* R, const double* X, int64_t ldx, cudaStream_t st);
+// qmax < OZ_QMAX keeps only digit groups q <= qmax (qmax + 1 digits of X,
+// (qmax + 1)(qmax + 2)/2 pair products for qmax <= 7): Q then carries an
+// absolute error of about 2^(e_X + e_A - 7 (qmax + 1)) sqrt(p), for a
+// Newton-Schulz step that does not need FP64 accuracy (qmax >= 4, so that the
+// update still finds its five digits of X).
+ibmi_status refine_residual_launch(RefineState* R, const double* X, int64_t ldx, cudaStream_t st,
+                                   int qmax = OZ_QMAX);
 ibmi_status refine_cheap_residual_launch(RefineState* R, const CUtensorMap* mapH2, cudaStream_t st);
 ibmi_status refine_read(RefineState* R, cudaStream_t st, double* rho);
 
