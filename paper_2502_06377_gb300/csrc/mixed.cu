@@ -76,12 +76,14 @@ struct MixedState {
   bool graphs = false;
   const double* gA = nullptr;
   const double* gH = nullptr;
-  PhaseGraph g_setup, g_sweep[2], g_cheap, g_reslice, g_export_resid, g_export_resid_ns0, g_resid, g_update, g_radius;
+  PhaseGraph g_setup, g_sweep[2], g_cheap, g_reslice, g_export_resid, g_export_resid_ns0, g_resid, g_resid_q8, g_update,
+      g_radius;
 };
 
 static void drop_graphs(MixedState* M) {
   for (PhaseGraph* g : {&M->g_setup, &M->g_sweep[0], &M->g_sweep[1], &M->g_cheap, &M->g_reslice,
-                        &M->g_export_resid, &M->g_export_resid_ns0, &M->g_resid, &M->g_update, &M->g_radius}) {
+                        &M->g_export_resid, &M->g_export_resid_ns0, &M->g_resid, &M->g_resid_q8, &M->g_update,
+                        &M->g_radius}) {
     if (g->exec) cudaGraphExecDestroy(g->exec);
     *g = PhaseGraph{};
   }
@@ -526,6 +528,17 @@ ibmi_status mixed_run(ibmi_plan_s* P, const double* A, int64_t lda, double* H, i
       *flops += fr * kNs0Pairs / 52.0;
       IBMI_TRY(refine_read(R, st, &rho));
       if (rho <= d.tol) IBMI_TRY(accurate(&rho));   // certify with the full residual
+    } else if (prev * prev > 1e3 * d.tol) {
+      // rho is about prev^2 here, far above tol: groups q <= 8 (44 pairs) are
+      // enough for a step that another step will follow
+      IBMI_TRY(graph_or_run(M, &M->g_resid_q8, st, [&]() { return refine_residual_launch(R, H, ldh, st, 8); }));
+      *flops += fr * 44.0 / 52.0;
+      IBMI_TRY(refine_read(R, st, &rho));
+      if (rho <= d.tol) {   // certify with the full residual
+        IBMI_TRY(graph_or_run(M, &M->g_resid, st, [&]() { return refine_residual_launch(R, H, ldh, st); }));
+        *flops += fr;
+        IBMI_TRY(refine_read(R, st, &rho));
+      }
     } else {
       IBMI_TRY(graph_or_run(M, &M->g_resid, st, [&]() { return refine_residual_launch(R, H, ldh, st); }));
       *flops += fr;
