@@ -3,6 +3,7 @@
 #include <math.h>
 
 #include "refine.cuh"
+#include "oz_round.h"
 #include "oz_pairs.cuh"
 
 namespace ibmi {
@@ -25,20 +26,25 @@ __global__ void k_oz_slices(const double* X, int64_t ldx, int64_t ncols, int64_t
                             int nslices, int* expo) {
   const int64_t i = blockIdx.x;
   const double* row = X + i * ldx;
-  double mx = 0.0;
-  for (int64_t c = threadIdx.x; c < ncols; c += blockDim.x) mx = fmax(mx, fabs(row[c]));
-  __shared__ double red[32];
-  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  // row maximum of |x| on the bit patterns (integer order = order of |x|)
+  unsigned long long mx = 0;
+  for (int64_t c = threadIdx.x; c < ncols; c += blockDim.x) mx = max(mx, (unsigned long long)ozr_abs_bits(row[c]));
+  __shared__ unsigned long long red[32];
+  for (int o = 16; o > 0; o >>= 1) mx = max(mx, (unsigned long long)__shfl_xor_sync(0xffffffffu, mx, o));
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
   __syncthreads();
   if (threadIdx.x < 32) {
-    double v = threadIdx.x < blockDim.x / 32 ? red[threadIdx.x] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    unsigned long long v = threadIdx.x < blockDim.x / 32 ? red[threadIdx.x] : 0ull;
+    for (int o = 16; o > 0; o >>= 1) v = max(v, (unsigned long long)__shfl_xor_sync(0xffffffffu, v, o));
     if (threadIdx.x == 0) red[0] = v;
   }
   __syncthreads();
-  int e = 0;
-  if (red[0] > 0.0) frexp(red[0], &e);   // red[0] = f 2^e, f in [0.5, 1)
+  int e = 0;   // max = f 2^e, f in [0.5, 1)
+  if (red[0] != 0) {
+    const int ef = (int)(red[0] >> 52);
+    if (ef != 0) e = ef - 1022;
+    else frexp(ozr_bits_to_double(red[0]), &e);   // subnormal maximum
+  }
   if (threadIdx.x == 0) expo[i] = e;
   // F = rint(x 2^{55-e}) and Flo = the remainder carried 14 bits further,
   // from the bit pattern of x with integer operations only (no FP64 ALU).
@@ -212,8 +218,10 @@ __device__ __forceinline__ double oz_value(const int* T, int64_t plane, int64_t 
     if (q < 5) hi += (long long)t[q] * (1ll << (7 * (4 - q)));
     else lo += (long long)t[q] * (1ll << (7 * (9 - q)));
   }
-  // sum = hi 2^-28 + lo 2^-63
-  return (double)hi * pow2i(e - 28) + (double)lo * pow2i(e - 63);
+  // sum = (hi 2^35 + lo) 2^(e-63), rounded once, with integer operations
+  bool ok;
+  const double v = ozr_round(hi, lo, e - 63, &ok);
+  return ok ? v : (double)hi * pow2i(e - 28) + (double)lo * pow2i(e - 63);
 }
 
 // C = 2^{e_i + f_j - 12} sum_q T_q 2^{-7q};  Q = I - C (FP64, ld p);
@@ -221,16 +229,19 @@ __device__ __forceinline__ double oz_value(const int* T, int64_t plane, int64_t 
 __global__ void k_oz_combine(const int* T, int64_t p, int64_t ldp, const int* ex, const int* ea, int qmax,
                              double* Q, double* partials) {
   const int64_t i = blockIdx.y, j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  double sq = 0.0;
+  float sq = 0.f;
   if (j < p) {
     const double c = oz_value(T, p * ldp, i * ldp + j, qmax, ex[i] + ea[j] - 12);
-    const double q = (i == j ? 1.0 : 0.0) - c;
-    sq = q * q;
+    // off the diagonal Q = -c is a sign flip; the squares for rho need only
+    // float precision (FP64 arithmetic is scarce on this GPU)
+    const double q = i == j ? 1.0 - c : ozr_bits_to_double(ozr_double_to_bits(c) ^ 0x8000000000000000ull);
+    const float qf = ozr_to_float(q);
+    sq = qf * qf;
     Q[i * p + j] = q;
   }
   __shared__ double red[8];
   for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sq;
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (double)sq;
   __syncthreads();
   if (threadIdx.x == 0) {
     double t = 0.0;
@@ -490,7 +501,7 @@ __global__ void k_oz_wcombine(const int* T, int64_t plane, int64_t m, int64_t p,
   const int64_t idx = i * ldp + j;
   float w = 0.f;
   if (j < p && (j < lo || j >= hi)) {
-    w = (float)oz_value(T, plane, idx, qmax, ea[i] + eb[j] - 12);
+    w = ozr_to_float(oz_value(T, plane, idx, qmax, ea[i] + eb[j] - 12));
   }
   const __nv_bfloat16 a = __float2bfloat16_rn(w);
   const float r = w - __bfloat162float(a);
