@@ -269,10 +269,14 @@ ibmi_status mixed_create(ibmi_plan_s* P) {
   P->mixed = M;
   M->ldp = (p + 63) / 64 * 64;
   const int64_t ldp = M->ldp;
-  // a4 split-K factor: fill ~one wave of 148 SMs with ceil(m/128)^2 tiles
+  // a4 split-K factor: fill one round of the SMs with ceil(m/128)^2 tiles
   int64_t tiles2 = ((P->mmax + 127) / 128) * ((P->mmax + MX_BN - 1) / MX_BN);
   int kt = (int)((p + tc::BK - 1) / tc::BK);
-  M->splits_max = (int)std::max<int64_t>(1, std::min<int64_t>(std::max<int64_t>(1, 148 / tiles2), kt / 4 > 0 ? kt / 4 : 1));
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (sms <= 0) sms = 148;
+  M->splits_max = (int)std::max<int64_t>(1, std::min<int64_t>(std::max<int64_t>(1, sms / tiles2), kt / 4 > 0 ? kt / 4 : 1));
   size_t bytes = sizeof(float) * p * ldp + 3 * sizeof(__nv_bfloat16) * p * ldp + 512 +
                  sizeof(float) * (size_t)M->splits_max * P->mmax * P->mmax + 256;
   for (int k = 0; k < K; ++k) bytes += 3 * sizeof(__nv_bfloat16) * (P->hi[k] - P->lo[k]) * ldp + 768;
