@@ -230,13 +230,14 @@ def run_serve(args):
     pool_reqs = trace[:48]
     pool = [r.matrix(seed=100 + i) for i, r in enumerate(pool_reqs)]
     srv = ibmi.Server(64 << 30, workers=16)
-    # warm-up: one request of every pool entry (plans, tensor maps)
-    ids = [(srv.submit(A), A.shape[0]) for A in pool]
-    for rid, p in ids:
-        while srv.poll(rid, p)[0] == ibmi.IBMI_NOT_READY:
-            time.sleep(0.001)
-    srv.close()
-    srv = ibmi.Server(64 << 30, workers=16)
+    # warm-up on the same server: every pool entry a few times, so that each
+    # worker holds the plans (and captured graphs) of the sizes it serves
+    for _ in range(max(1, args.warmup)):
+        ids = [(srv.submit(A), A.shape[0]) for A in pool]
+        for rid, p in ids:
+            while srv.poll(rid, p)[0] == ibmi.IBMI_NOT_READY:
+                time.sleep(0.001)
+    srv.reset_stats()
     t0 = time.perf_counter()
     sub = []
     for i, r in enumerate(trace):

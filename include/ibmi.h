@@ -195,8 +195,9 @@ ibmi_status ibmi_batch_release(void);
 
 /* Continuous-batching server.  Requests (host matrices) are queued; a request
  * is admitted when its device bytes (A, H and padded staging, 16 (p^2 + pb^2)
- * bytes) fit in three quarters of hbm_budget beside the admitted ones (the
- * last quarter caps the workers' plan caches); admitted requests run as soon
+ * bytes) fit in a quarter of hbm_budget beside the admitted ones (the other
+ * three quarters cap the workers' plan caches, least recently used plans
+ * going first); admitted requests run as soon
  * as a worker is free, overlapping on the device with the others; finishing
  * frees their bytes for the next ones in arrival order.  ibmi_serve_submit
  * copies A (p x p, lda); IBMI_ERR_BUDGET if one request alone exceeds the
@@ -214,6 +215,10 @@ ibmi_status ibmi_serve_poll(ibmi_server_t server, uint64_t request, double* H_ho
 ibmi_status ibmi_serve_cancel(ibmi_server_t server, uint64_t request);
 ibmi_status ibmi_serve_stats(ibmi_server_t server, double* p50_s, double* p99_s, double* inverses_per_s,
                              int64_t* completed, uint64_t* bytes_in_use);
+/* Forgets the latencies and completion counts gathered so far (for example
+ * after a warm-up that created the workers' plans); requests in flight are
+ * counted when they finish. */
+ibmi_status ibmi_serve_stats_reset(ibmi_server_t server);
 ibmi_status ibmi_serve_destroy(ibmi_server_t server);
 
 /* Kernel profiling, for the benchmark's roofline figures.  While enabled, the

@@ -233,6 +233,10 @@ class Server:
         return {"p50_s": p50.value, "p99_s": p99.value, "inverses_per_s": ips.value, "completed": n.value,
                 "bytes_in_use": used.value}
 
+    def reset_stats(self):
+        """Forget the latencies and counts so far (e.g. after a warm-up)."""
+        self._lib.ibmi_serve_stats_reset(self.handle)
+
     def close(self):
         if getattr(self, "handle", None):
             self._lib.ibmi_serve_destroy(self.handle)

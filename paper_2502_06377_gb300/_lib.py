@@ -121,5 +121,6 @@ _SIGS.update({
     "ibmi_serve_poll": (C.c_int, [C.c_void_p, C.c_uint64, C.c_void_p, C.c_int64, C.POINTER(ibmi_result)]),
     "ibmi_serve_cancel": (C.c_int, [C.c_void_p, C.c_uint64]),
     "ibmi_serve_stats": (C.c_int, [C.c_void_p, _D, _D, _D, C.POINTER(C.c_int64), C.POINTER(C.c_uint64)]),
+    "ibmi_serve_stats_reset": (C.c_int, [C.c_void_p]),
     "ibmi_serve_destroy": (C.c_int, [C.c_void_p]),
 })

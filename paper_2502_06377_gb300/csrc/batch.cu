@@ -88,8 +88,14 @@ static ibmi_plan_desc desc_for(const Shape& s, const ibmi_batch_opts& o) {
 struct Worker {
   int device = 0;
   cudaStream_t stream = nullptr;
-  std::map<std::pair<Shape, int>, ibmi_plan_t> plans;   // by (partition, precision)
+  struct Cached {
+    ibmi_plan_t plan;
+    size_t bytes;
+    uint64_t last_use;
+  };
+  std::map<std::pair<Shape, int>, Cached> plans;   // by (partition, precision)
   size_t plan_bytes = 0;
+  uint64_t clock = 0;
 
   ibmi_status init(int dev) {
     device = dev;
@@ -98,9 +104,20 @@ struct Worker {
     return IBMI_OK;
   }
   void release_plans() {
-    for (auto& kv : plans) ibmi_plan_destroy(kv.second);
+    for (auto& kv : plans) ibmi_plan_destroy(kv.second.plan);
     plans.clear();
     plan_bytes = 0;
+  }
+  // Frees least recently used plans until `need` more bytes fit in `cap`.
+  void evict_for(size_t need, size_t cap) {
+    while (!plans.empty() && plan_bytes + need > cap) {
+      auto lru = plans.begin();
+      for (auto it = plans.begin(); it != plans.end(); ++it)
+        if (it->second.last_use < lru->second.last_use) lru = it;
+      ibmi_plan_destroy(lru->second.plan);
+      plan_bytes -= lru->second.bytes;
+      plans.erase(lru);
+    }
   }
   void destroy() {
     cudaSetDevice(device);
@@ -111,7 +128,8 @@ struct Worker {
     auto it = plans.find({s, o.precision});
     if (it != plans.end()) {
       // stopping parameters may differ from call to call
-      ibmi_plan_t P = it->second;
+      it->second.last_use = ++clock;
+      ibmi_plan_t P = it->second.plan;
       const ibmi_plan_desc d = desc_for(s, o);
       P->d.tol = d.tol;
       P->d.max_sweeps = d.max_sweeps;
@@ -123,7 +141,7 @@ struct Worker {
     }
     ibmi_plan_desc d = desc_for(s, o);
     const size_t need = ibmi_plan_bytes(&d) + 16 * (size_t)s.p * s.p;
-    if (max_plan_bytes && plan_bytes + need > max_plan_bytes) release_plans();
+    if (max_plan_bytes) evict_for(need, max_plan_bytes);
     ibmi_plan_t P = nullptr;
     IBMI_TRY(ibmi_plan(&d, &P));
     if (cudaMalloc(&P->dA, sizeof(double) * s.p * s.p) != cudaSuccess ||
@@ -133,7 +151,7 @@ struct Worker {
       return IBMI_ERR_OOM;
     }
     if (o.precision == IBMI_MIXED) mixed_enable_graphs(P, o.graphs != 0);
-    plans[{s, o.precision}] = P;
+    plans[{s, o.precision}] = Cached{P, need, ++clock};
     plan_bytes += need;
     *out = P;
     return IBMI_OK;
@@ -266,7 +284,7 @@ struct Request {
 struct ibmi_server_impl {
   ibmi_batch_opts opts{};
   size_t budget = 0;       // total device bytes the server may hold
-  size_t req_budget = 0;   // part of it for admitted requests (the rest caps the plan caches)
+  size_t req_budget = 0;   // part of it for admitted requests (a quarter; the rest caps the plan caches)
   size_t in_use = 0;
   int device = 0;
   std::mutex mu;
@@ -488,7 +506,7 @@ ibmi_status ibmi_serve_create(size_t hbm_budget, const ibmi_batch_opts* opts, ib
   if (opts) S->opts = *opts; else ibmi_batch_opts_init(&S->opts);
   if (S->opts.workers < 1 || S->opts.workers > 64) { delete S; return IBMI_ERR_INVALID_ARG; }
   S->budget = hbm_budget;
-  S->req_budget = hbm_budget - hbm_budget / 4;
+  S->req_budget = hbm_budget / 4;
   cudaGetDevice(&S->device);
   S->workers.resize(S->opts.workers);
   for (auto& w : S->workers) {
@@ -560,6 +578,15 @@ ibmi_status ibmi_serve_cancel(ibmi_server_t h, uint64_t req) {
     return IBMI_OK;
   }
   return r->state == 3 ? IBMI_OK : IBMI_NOT_READY;   // admitted or finished: runs to completion
+}
+
+ibmi_status ibmi_serve_stats_reset(ibmi_server_t h) {
+  auto* S = (ibmi_server_impl*)h;
+  if (!S) return IBMI_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(S->mu);
+  S->latencies.clear();
+  S->completed = 0;
+  return IBMI_OK;
 }
 
 ibmi_status ibmi_serve_stats(ibmi_server_t h, double* p50, double* p99, double* inv_per_s, int64_t* completed,

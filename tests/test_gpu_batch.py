@@ -141,7 +141,7 @@ def test_serve_admission_respects_budget(ibmi, batch):
     mats, _ = batch
     p = 512
     per_req = 16 * (p * p + p * p)              # bytes charged per request of order 512
-    budget = int(per_req * 2.5 / 0.75)          # room for two admitted requests
+    budget = int(per_req * 2.5 / 0.25)          # a quarter of it admits two requests
     srv = ibmi.Server(budget, workers=8)
     big = [A for A in mats if A.shape[0] == p][:1] * 8
     if not big:
@@ -163,7 +163,7 @@ def test_serve_admission_respects_budget(ibmi, batch):
 
 def test_serve_cancel_and_budget_reject(ibmi, batch):
     mats, _ = batch
-    srv = ibmi.Server(64 << 20, workers=1)    # 64 MB: one small request at a time
+    srv = ibmi.Server(64 << 20, workers=1)    # 64 MB, 16 MB of it for requests
     with pytest.raises(ibmi.IbmiError) as e:
         srv.submit(np.eye(2048))                # 2048^2 * 32 bytes > budget
     assert e.value.status == ibmi.IBMI_ERR_BUDGET
