@@ -20,7 +20,10 @@
  * Conventions for every entry point:
  *   - Matrices are dense, row-major, FP64, with a leading dimension ld >= p
  *     (in elements).  Since A and H are symmetric, row- and column-major agree.
- *   - A is read-only.  H is owned by the caller and written in full.
+ *   - A is read-only, and only its lower triangle (i >= j) is read: the
+ *     strict upper triangle may hold anything (ibmi_residual_noalloc, which
+ *     allocates nothing, is the exception and reads A in full).  H is owned by
+ *     the caller and written in full.
  *   - Device pointers must be CUDA device memory of the current device;
  *     "_host" variants take host memory and copy inside the call.
  *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).

@@ -411,6 +411,7 @@ size_t ibmi_plan_bytes(const ibmi_plan_desc* d) {
   const double p = (double)d->p, K = (double)d->K;
   const double m = std::min(p, p / K + 2.0 * (double)d->h);
   double b = 8.0 * (K * m * m + m * m + p * p / 4096.0 + 64.0);              // A_I^{-1}, S, partials
+  b += 8.0 * p * p;                                                          // A from its lower triangle
   const double ncols = d->precision == IBMI_MIXED ? m : p;
   b += 8.0 * K * (m * m + m * ncols + 32.0 * m);                             // batched factorisation
   if (d->precision == IBMI_MIXED) {

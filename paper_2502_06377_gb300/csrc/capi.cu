@@ -98,6 +98,10 @@ static ibmi_status invert_impl(ibmi_plan_s* P, const double* A, int64_t lda, dou
   const ibmi_plan_desc& d = P->d;
   const double sqrtp = sqrt((double)p);
   double flops = 0.0;
+  // only A's lower triangle is read: the solve runs on its symmetric copy
+  IBMI_TRY(sym_from_lower(A, lda, p, P->dAs, p, st));
+  A = P->dAs;
+  lda = p;
   const bool mixed = d.precision == IBMI_MIXED;
   if (mixed) {
     ibmi_status s = mixed_run(P, A, lda, H, ldh, st, res, &flops);
@@ -249,6 +253,12 @@ ibmi_status ibmi_plan(const ibmi_plan_desc* desc, ibmi_plan_t* out) {
     return IBMI_ERR_OOM;
   }
   P->pool_bytes = total;
+  if (cudaMalloc(&P->dAs, sizeof(double) * (size_t)d.p * d.p) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(P->pool);
+    delete P;
+    return IBMI_ERR_OOM;
+  }
   double* q = P->pool;
   std::vector<int64_t> hoff_ainv(d.K), hoff_w(d.K, 0), hm(d.K);
   for (int k = 0; k < d.K; ++k) {
@@ -309,6 +319,7 @@ ibmi_status ibmi_plan_destroy(ibmi_plan_t P) {
   cudaFree(P->nsX);
   cudaFree(P->pe);
   cudaFree(P->dA);
+  cudaFree(P->dAs);
   cudaFree(P->dH);
   delete P;
   return IBMI_OK;
@@ -380,8 +391,10 @@ ibmi_status ibmi_residual(const double* A, int64_t lda, const double* H, int64_t
   cudaStream_t st = (cudaStream_t)stream;
   const int64_t n = gemm_f64_ctas(p, p);
   double* buf = nullptr;
-  IBMI_CUDA_TRY(cudaMallocAsync(&buf, sizeof(double) * (n + 2), st));
-  ibmi_status s = residual_f64_dev(A, lda, H, ldh, p, buf, n, buf + n, st);
+  IBMI_CUDA_TRY(cudaMallocAsync(&buf, sizeof(double) * (n + 2 + p * p), st));
+  double* As = buf + n + 2;   // A from its lower triangle
+  ibmi_status s = sym_from_lower(A, lda, p, As, p, st);
+  if (s == IBMI_OK) s = residual_f64_dev(As, p, H, ldh, p, buf, n, buf + n, st);
   double v[2] = {NAN, NAN};
   if (s == IBMI_OK) {
     cudaMemcpyAsync(v, buf + n, sizeof(v), cudaMemcpyDeviceToHost, st);
@@ -400,12 +413,20 @@ ibmi_status ibmi_residual_tc(const double* A, int64_t lda, const double* H, int6
   int* err = nullptr;
   IBMI_CUDA_TRY(cudaMalloc(&err, sizeof(int)));
   IBMI_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
+  double* As = nullptr;   // A from its lower triangle
+  if (cudaMalloc(&As, sizeof(double) * p * p) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(err);
+    return IBMI_ERR_OOM;
+  }
   RefineState R;
-  ibmi_status s = refine_create(&R, p, err);
-  if (s == IBMI_OK) s = refine_set_matrix(&R, A, lda, st);
+  ibmi_status s = sym_from_lower(A, lda, p, As, p, st);
+  if (s == IBMI_OK) s = refine_create(&R, p, err);
+  if (s == IBMI_OK) s = refine_set_matrix(&R, As, p, st);
   if (s == IBMI_OK) s = refine_residual(&R, H, ldh, st, out);
   cudaStreamSynchronize(st);
   refine_destroy(&R);
+  cudaFree(As);
   cudaFree(err);
   return s;
 }
@@ -427,6 +448,21 @@ ibmi_status ibmi_refine(const double* A, int64_t lda, double* X, int64_t ldx, in
   auto t0 = std::chrono::steady_clock::now();
   const double fr = 2.0 * (double)p * p * p;
   ibmi_status s = IBMI_NOT_CONVERGED;
+  double* As = nullptr;   // A from its lower triangle
+  if (cudaMalloc(&As, sizeof(double) * p * p) != cudaSuccess) {
+    cudaGetLastError();
+    return (ibmi_status)(res->status = IBMI_ERR_OOM);
+  }
+  struct FreeOnExit {
+    double* q;
+    ~FreeOnExit() { cudaFree(q); }   // synchronises the device first
+  } keep{As};
+  {
+    const ibmi_status e = sym_from_lower(A, lda, p, As, p, st);
+    if (e != IBMI_OK) return (ibmi_status)(res->status = e);
+  }
+  A = As;
+  lda = p;
   if (precision == IBMI_MIXED) {
     int* err = nullptr;
     IBMI_CUDA_TRY(cudaMalloc(&err, sizeof(int)));

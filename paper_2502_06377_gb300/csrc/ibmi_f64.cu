@@ -435,6 +435,39 @@ __global__ void k_set_identity(double* H, int64_t ldh, int64_t p) {
   H[i * ldh + j] = (i == j) ? 1.0 : 0.0;
 }
 
+// S = A with the strict upper triangle taken from the lower one: only
+// elements A[i][j] with i >= j are read.  32 x 32 tiles through shared memory;
+// a tile above the diagonal is the transpose of its mirror below it.
+__global__ void k_sym_from_lower(const double* A, int64_t lda, int64_t p, double* S, int64_t lds) {
+  __shared__ double t[32][33];
+  const int64_t I0 = (int64_t)blockIdx.y * 32, J0 = (int64_t)blockIdx.x * 32;
+  const bool upper = J0 > I0;
+  const int64_t R0 = upper ? J0 : I0, C0 = upper ? I0 : J0;   // source tile, on or below the diagonal
+  const int tx = threadIdx.x;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int64_t i = R0 + r, j = C0 + tx;
+    t[r][tx] = (i < p && j < p && i >= j) ? A[i * lda + j] : 0.0;
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int64_t i = I0 + r, j = J0 + tx;
+    if (i >= p || j >= p) continue;
+    double v;
+    if (upper) v = t[tx][r];                      // S[i][j] = A[j][i]
+    else if (I0 > J0) v = t[r][tx];
+    else v = r >= tx ? t[r][tx] : t[tx][r];       // diagonal tile
+    S[i * lds + j] = v;
+  }
+}
+
+ibmi_status sym_from_lower(const double* A, int64_t lda, int64_t p, double* S, int64_t lds, cudaStream_t st) {
+  const unsigned nt = (unsigned)((p + 31) / 32);
+  note_launch();
+  k_sym_from_lower<<<dim3(nt, nt), dim3(32, 8), 0, st>>>(A, lda, p, S, lds);
+  IBMI_CUDA_TRY(cudaGetLastError());
+  return IBMI_OK;
+}
+
 ibmi_status set_identity(double* H, int64_t ldh, int64_t p, cudaStream_t st) {
   note_launch();
   k_set_identity<<<nblk(p * p), 256, 0, st>>>(H, ldh, p);

@@ -38,6 +38,7 @@ struct ibmi_plan_s {
   double* nsX = nullptr;
   // host-variant staging (allocated on first use)
   double* dA = nullptr;
+  double* dAs = nullptr;         // p x p: A symmetrised from its lower triangle (every solve)
   double* dH = nullptr;
   // mixed-precision state (allocated at plan time when precision == MIXED)
   void* mixed = nullptr;
@@ -88,6 +89,10 @@ ibmi_status ns_step_f64(ibmi_plan_s* P, const double* A, int64_t lda, double* X,
                         cudaStream_t st);
 
 ibmi_status set_identity(double* H, int64_t ldh, int64_t p, cudaStream_t st);
+
+// S (ld lds) = the symmetric matrix whose lower triangle is A's; the strict
+// upper triangle of A is never read.
+ibmi_status sym_from_lower(const double* A, int64_t lda, int64_t p, double* S, int64_t lds, cudaStream_t st);
 
 // eq. error on the last set: ||(H A)[I_K, I_K^c]||_2 (FP64 GEMM, then power
 // iteration on B^T B); host value in *out (syncs the stream).
