@@ -49,6 +49,8 @@ constexpr int MX_BN = 128;   // N tile of the sweep products
 constexpr int kRadiusIters = 40;            // power-iteration steps of the radius estimate
 constexpr int kNs0Groups = 7;               // digit groups of the first Newton-Schulz residual
 constexpr double kNs0Pairs = 36.0;          // its pair products (all pairs of groups 0..7)
+constexpr double kEarlyHandOver = 0.6;      // radius below which slow sweeps hand over early
+constexpr int64_t kEarlyMinOrder = 2048;    // smallest order for that test
 constexpr double kRadiusHandOver = 0.5;     // hand over to Newton-Schulz below this radius
 
 // One captured phase: the executable graph and its kernel-node count (added
@@ -437,6 +439,10 @@ ibmi_status mixed_run(ibmi_plan_s* P, const double* A, int64_t lda, double* H, i
   }
   M->level = 0;
   double pending = NAN;   // accurate residual of the current H when it was just taken
+  double next_radius_test = INFINITY;   // slow convergence: rho below which the radius is measured again
+  // sweeps whose cost matches about two tail steps (time ratio of a step to a
+  // sweep ~ 8.4 fr / fs, from the measured rates of the two kinds of product)
+  const double slow_sweeps = 2.0 * 8.4 * fr / std::max(fs, 1.0);
   int r = 0, stalled = 0;
   double best = INFINITY;
   CheckCadence cad;
@@ -450,47 +456,37 @@ ibmi_status mixed_run(ibmi_plan_s* P, const double* A, int64_t lda, double* H, i
     *flops += fr;
     return refine_read(R, st, acc);
   };
-  while (true) {
-    ++r;
-    IBMI_TRY(graph_or_run(M, &M->g_sweep[M->level], st, [&]() -> ibmi_status {
-      for (int k = 0; k < K; ++k) IBMI_TRY(mixed_sweep_step(P, k, st));
-      return IBMI_OK;
-    }));
-    *flops += fs;
-    res->sweeps = r;
-    if (r < cad.next && r < d.max_sweeps) continue;
-    double rho;
-    IBMI_TRY(graph_or_run(M, &M->g_cheap, st, [&]() { return refine_cheap_residual_launch(R, M->mapH, st); }));
-    IBMI_TRY(refine_read(R, st, &rho));
-    *flops += fr;
-    res->resid_f = rho;
-    if (!isfinite(rho)) return IBMI_ERR_NONFINITE;
-    if (d.ns_theta > 0.0 && rho * sqrtp <= d.ns_theta) break;
-    // The sweep products have an accuracy floor (two BF16 slices: about
-    // kappa(A) * 1e-5 in rho).  When the residual stops falling (three checks
-    // without a 5% gain) the sweep first moves to three slices (24-bit
-    // operands, six products); if it stalls there too, the Newton-Schulz
-    // tail is tried when ||I - A H||_F is within 8 theta or the measured
-    // spectral radius of I - X A is at most 1/2 (it stops if a step does not
-    // help); otherwise the sweeps go on.
-    stalled = rho > 0.95 * best ? stalled + 1 : 0;
-    best = fmin(best, rho);
-    if (d.ns_theta > 0.0 && stalled >= 3) {
-      if (M->level == 0) {
-        M->level = 1;
-        stalled = 0;
-        best = INFINITY;
-        IBMI_TRY(graph_or_run(M, &M->g_reslice, st, [&]() -> ibmi_status {
-          note_launch();
-          k_reslice_h<<<nblk(p * M->ldp), 256, 0, st>>>(M->Hf, p * M->ldp, M->Hs[0], M->Hs[1], M->Hs[2]);
-          IBMI_CUDA_TRY(cudaGetLastError());
-          return IBMI_OK;
-        }));
-      } else if (rho * sqrtp <= 8.0 * d.ns_theta) {
-        break;
-      } else {
-        // ||I - A H||_F bounds the spectral radius of I - X A that
-        // eq. newton needs from above, often by far; measure the radius.
+  // Sweeps, then the Newton-Schulz tail; a tail entered early that fails
+  // returns here.
+  for (;;) {
+    bool early = false, resume = false;
+    pending = NAN;
+    while (true) {
+      ++r;
+      IBMI_TRY(graph_or_run(M, &M->g_sweep[M->level], st, [&]() -> ibmi_status {
+        for (int k = 0; k < K; ++k) IBMI_TRY(mixed_sweep_step(P, k, st));
+        return IBMI_OK;
+      }));
+      *flops += fs;
+      res->sweeps = r;
+      if (r < cad.next && r < d.max_sweeps) continue;
+      double rho;
+      IBMI_TRY(graph_or_run(M, &M->g_cheap, st, [&]() { return refine_cheap_residual_launch(R, M->mapH, st); }));
+      IBMI_TRY(refine_read(R, st, &rho));
+      *flops += fr;
+      res->resid_f = rho;
+      if (!isfinite(rho)) return IBMI_ERR_NONFINITE;
+      if (d.ns_theta > 0.0 && rho * sqrtp <= d.ns_theta) break;
+      // Slow convergence: eq. newton needs only the spectral radius of I - X A
+      // below 1, which ||I - A H||_F bounds loosely.  Once that norm is within
+      // 16 theta and the sweeps still predicted to reach theta cost more than
+      // about two Newton-Schulz steps, measure the radius and hand over at
+      // <= 0.6; otherwise test again after rho has halved.  A tail started this
+      // way that fails returns to the sweeps (their state is untouched).  Below
+      // order 2048 launch latency, not arithmetic, sets both costs and the
+      // test (about 80 small launches) does not pay.
+      if (d.ns_theta > 0.0 && p >= kEarlyMinOrder && rho * sqrtp <= 16.0 * d.ns_theta &&
+          rho <= next_radius_test && cad.sweeps_to(rho, d.ns_theta / sqrtp) > slow_sweeps) {
         double acc, rad;
         IBMI_TRY(accurate(&acc));
         res->resid_f = acc;
@@ -498,64 +494,112 @@ ibmi_status mixed_run(ibmi_plan_s* P, const double* A, int64_t lda, double* H, i
         IBMI_TRY(graph_or_run(M, &M->g_radius, st, [&]() { return refine_q_radius_launch(R, kRadiusIters, st); }));
         *flops += 2.0 * kRadiusIters * (double)p * p;
         IBMI_TRY(refine_q_radius_read(R, st, &rad));
-        if (rad <= kRadiusHandOver) {
+        next_radius_test = 0.5 * rho;
+        if (rad <= kEarlyHandOver) {
           pending = acc;
+          early = true;
           break;
         }
-        stalled = 0;
       }
+      // The sweep products have an accuracy floor (two BF16 slices: about
+      // kappa(A) * 1e-5 in rho).  When the residual stops falling (three checks
+      // without a 5% gain) the sweep first moves to three slices (24-bit
+      // operands, six products); if it stalls there too, the Newton-Schulz
+      // tail is tried when ||I - A H||_F is within 8 theta or the measured
+      // spectral radius of I - X A is at most 1/2 (it stops if a step does not
+      // help); otherwise the sweeps go on.
+      stalled = rho > 0.95 * best ? stalled + 1 : 0;
+      best = fmin(best, rho);
+      if (d.ns_theta > 0.0 && stalled >= 3) {
+        if (M->level == 0) {
+          M->level = 1;
+          stalled = 0;
+          best = INFINITY;
+          IBMI_TRY(graph_or_run(M, &M->g_reslice, st, [&]() -> ibmi_status {
+            note_launch();
+            k_reslice_h<<<nblk(p * M->ldp), 256, 0, st>>>(M->Hf, p * M->ldp, M->Hs[0], M->Hs[1], M->Hs[2]);
+            IBMI_CUDA_TRY(cudaGetLastError());
+            return IBMI_OK;
+          }));
+        } else if (rho * sqrtp <= 8.0 * d.ns_theta) {
+          break;
+        } else {
+          // ||I - A H||_F bounds the spectral radius of I - X A that
+          // eq. newton needs from above, often by far; measure the radius.
+          double acc, rad;
+          IBMI_TRY(accurate(&acc));
+          res->resid_f = acc;
+          if (acc <= d.tol) return IBMI_OK;
+          IBMI_TRY(graph_or_run(M, &M->g_radius, st, [&]() { return refine_q_radius_launch(R, kRadiusIters, st); }));
+          *flops += 2.0 * kRadiusIters * (double)p * p;
+          IBMI_TRY(refine_q_radius_read(R, st, &rad));
+          if (rad <= kRadiusHandOver) {
+            pending = acc;
+            break;
+          }
+          stalled = 0;
+        }
+      }
+      if (rho <= d.tol || r >= d.max_sweeps) {
+        // BF16x3 cannot certify tol: confirm with the FP64-accurate residual
+        double acc;
+        IBMI_TRY(accurate(&acc));
+        res->resid_f = acc;
+        if (acc <= d.tol) return IBMI_OK;
+        if (r >= d.max_sweeps) return IBMI_NOT_CONVERGED;
+      }
+      cad.after(r, rho, target);
     }
-    if (rho <= d.tol || r >= d.max_sweeps) {
-      // BF16x3 cannot certify tol: confirm with the FP64-accurate residual
-      double acc;
-      IBMI_TRY(accurate(&acc));
-      res->resid_f = acc;
-      if (acc <= d.tol) return IBMI_OK;
-      if (r >= d.max_sweeps) return IBMI_NOT_CONVERGED;
-    }
-    cad.after(r, rho, target);
-  }
-  double prev = INFINITY;
-  for (int s = 0;; ++s) {
-    double rho;
-    if (s == 0 && !isnan(pending)) {
-      rho = pending;
-    } else if (s == 0) {
-      // The first step's residual only has to be small against rho^2 / kappa:
-      // Newton-Schulz corrects the error of one step in the next, and the
-      // residual that certifies tol is always the full one.  Digit groups
-      // q <= 7 (36 of 52 pair products) leave about 2^-56 of |X| |A| sqrt(p).
-      IBMI_TRY(graph_or_run(M, &M->g_export_resid_ns0, st, [&]() -> ibmi_status {
-        IBMI_TRY(mixed_export_launch(P, H, ldh, st));
-        return refine_residual_launch(R, H, ldh, st, kNs0Groups);
-      }));
-      *flops += fr * kNs0Pairs / 52.0;
-      IBMI_TRY(refine_read(R, st, &rho));
-      if (rho <= d.tol) IBMI_TRY(accurate(&rho));   // certify with the full residual
-    } else if (prev * prev > 1e3 * d.tol) {
-      // rho is about prev^2 here, far above tol: groups q <= 8 (44 pairs) are
-      // enough for a step that another step will follow
-      IBMI_TRY(graph_or_run(M, &M->g_resid_q8, st, [&]() { return refine_residual_launch(R, H, ldh, st, 8); }));
-      *flops += fr * 44.0 / 52.0;
-      IBMI_TRY(refine_read(R, st, &rho));
-      if (rho <= d.tol) {   // certify with the full residual
+    double prev = INFINITY;
+    for (int s = 0;; ++s) {
+      double rho;
+      if (s == 0 && !isnan(pending)) {
+        rho = pending;
+      } else if (s == 0) {
+        // The first step's residual only has to be small against rho^2 / kappa:
+        // Newton-Schulz corrects the error of one step in the next, and the
+        // residual that certifies tol is always the full one.  Digit groups
+        // q <= 7 (36 of 52 pair products) leave about 2^-56 of |X| |A| sqrt(p).
+        IBMI_TRY(graph_or_run(M, &M->g_export_resid_ns0, st, [&]() -> ibmi_status {
+          IBMI_TRY(mixed_export_launch(P, H, ldh, st));
+          return refine_residual_launch(R, H, ldh, st, kNs0Groups);
+        }));
+        *flops += fr * kNs0Pairs / 52.0;
+        IBMI_TRY(refine_read(R, st, &rho));
+        if (rho <= d.tol) IBMI_TRY(accurate(&rho));   // certify with the full residual
+      } else if (prev * prev > 1e3 * d.tol) {
+        // rho is about prev^2 here, far above tol: groups q <= 8 (44 pairs) are
+        // enough for a step that another step will follow
+        IBMI_TRY(graph_or_run(M, &M->g_resid_q8, st, [&]() { return refine_residual_launch(R, H, ldh, st, 8); }));
+        *flops += fr * 44.0 / 52.0;
+        IBMI_TRY(refine_read(R, st, &rho));
+        if (rho <= d.tol) {   // certify with the full residual
+          IBMI_TRY(graph_or_run(M, &M->g_resid, st, [&]() { return refine_residual_launch(R, H, ldh, st); }));
+          *flops += fr;
+          IBMI_TRY(refine_read(R, st, &rho));
+        }
+      } else {
         IBMI_TRY(graph_or_run(M, &M->g_resid, st, [&]() { return refine_residual_launch(R, H, ldh, st); }));
         *flops += fr;
         IBMI_TRY(refine_read(R, st, &rho));
       }
-    } else {
-      IBMI_TRY(graph_or_run(M, &M->g_resid, st, [&]() { return refine_residual_launch(R, H, ldh, st); }));
+      res->resid_f = rho;
+      if (!isfinite(rho)) return IBMI_ERR_NONFINITE;
+      if (rho <= d.tol) return IBMI_OK;
+      if (s >= d.ns_max || !(rho < prev)) {
+        if (early && r < d.max_sweeps) {   // back to the sweeps
+          resume = true;
+          break;
+        }
+        return IBMI_NOT_CONVERGED;
+      }
+      prev = rho;
+      IBMI_TRY(graph_or_run(M, &M->g_update, st, [&]() { return refine_ns_update(R, H, ldh, st); }));
       *flops += fr;
-      IBMI_TRY(refine_read(R, st, &rho));
+      res->ns_steps = s + 1;
     }
-    res->resid_f = rho;
-    if (!isfinite(rho)) return IBMI_ERR_NONFINITE;
-    if (rho <= d.tol) return IBMI_OK;
-    if (s >= d.ns_max || !(rho < prev)) return IBMI_NOT_CONVERGED;
-    prev = rho;
-    IBMI_TRY(graph_or_run(M, &M->g_update, st, [&]() { return refine_ns_update(R, H, ldh, st); }));
-    *flops += fr;
-    res->ns_steps = s + 1;
+    if (!resume) return IBMI_NOT_CONVERGED;   // not reached: the tail returns
+    cad.next = r + 1;   // the next radius test waits for rho to halve (set at the test)
   }
 }
 

@@ -57,16 +57,23 @@ struct CheckCadence {
   int next = 1;
   int last_r = 0;
   double last_rho = 0.0;
+  double f = 0.0;   // contraction per sweep between the last two tests (0: unknown)
   void after(int r, double rho, double target) {
     int gap = gmin;
-    if (last_r > 0 && rho > 0.0 && last_rho > rho && target > 0.0 && rho > target) {
-      const double f = pow(rho / last_rho, 1.0 / (double)(r - last_r));
+    if (last_r > 0 && rho > 0.0 && last_rho > rho) f = pow(rho / last_rho, 1.0 / (double)(r - last_r));
+    else f = 0.0;
+    if (f > 0.0 && target > 0.0 && rho > target) {
       const double need = log(target / rho) / log(f);
       gap = (int)std::max<double>(gmin, std::min<double>(8.0, floor(0.5 * need)));
     }
     last_r = r;
     last_rho = rho;
     next = r + gap;
+  }
+  // Sweeps predicted to take rho down to target (infinity if unknown).
+  double sweeps_to(double rho, double target) const {
+    if (!(f > 0.0 && f < 1.0) || rho <= target) return f > 0.0 && f < 1.0 ? 0.0 : INFINITY;
+    return log(target / rho) / log(f);
   }
 };
 

@@ -8,7 +8,6 @@
 
 namespace ibmi {
 
-static inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
 // ------------------------------------------------------------ slicing ----
 
