@@ -14,7 +14,8 @@ import numpy as np
 from . import _lib
 from ._lib import (IBMI_FP64, IBMI_MIXED, IBMI_INIT_IDENTITY, IBMI_INIT_USER,  # noqa: F401
                    IBMI_STOP_RESID_F, IBMI_STOP_PAPER_EST, IBMI_OK, IBMI_NOT_CONVERGED,
-                   IBMI_ERR_NOT_SPD, IBMI_ERR_INVALID_ARG, ibmi_plan_desc, ibmi_result)
+                   IBMI_ERR_NOT_SPD, IBMI_ERR_INVALID_ARG, IBMI_ERR_NONFINITE, IBMI_ERR_OOM,
+                   IBMI_ERR_TIMEOUT, IBMI_ERR_CUDA, ibmi_plan_desc, ibmi_result)
 
 
 class IbmiError(RuntimeError):

@@ -39,12 +39,13 @@ __global__ void k_oz_slices(const double* X, int64_t ldx, int64_t ncols, int64_t
   }
   __syncthreads();
   int e = 0;   // max = f 2^e, f in [0.5, 1)
-  if (red[0] != 0) {
+  const bool nonfinite = (red[0] >> 52) == 0x7ff;   // an Inf or NaN in the row
+  if (red[0] != 0 && !nonfinite) {
     const int ef = (int)(red[0] >> 52);
     if (ef != 0) e = ef - 1022;
     else frexp(ozr_bits_to_double(red[0]), &e);   // subnormal maximum
   }
-  if (threadIdx.x == 0) expo[i] = e;
+  if (threadIdx.x == 0) expo[i] = nonfinite ? OZ_NONFINITE_EXP : e;
   // F = rint(x 2^{55-e}) and Flo = the remainder carried 14 bits further,
   // from the bit pattern of x with integer operations only (no FP64 ALU).
   for (int64_t c = threadIdx.x; c < ldp; c += blockDim.x) {
@@ -53,7 +54,7 @@ __global__ void k_oz_slices(const double* X, int64_t ldx, int64_t ncols, int64_t
       const unsigned long long bits = (unsigned long long)__double_as_longlong(row[c - c0]);
       const int ex = (int)((bits >> 52) & 0x7ff);
       const bool neg = (bits >> 63) != 0;
-      if (ex != 0) {   // zeros and subnormals are far below 2^(e-69)
+      if (ex != 0 && !nonfinite) {   // zeros and subnormals are far below 2^(e-69)
         const unsigned long long m = (bits & 0xfffffffffffffull) | 0x10000000000000ull;   // 53-bit significand
         const int sh = ex - 1075 + 55 - e;   // x 2^{55-e} = m 2^sh, sh <= 2 because |x| < 2^e
         long long qq = 0, lo14 = 0;
@@ -217,6 +218,7 @@ __device__ __forceinline__ double oz_value(const int* T, int64_t plane, int64_t 
     if (q < 5) hi += (long long)t[q] * (1ll << (7 * (4 - q)));
     else lo += (long long)t[q] * (1ll << (7 * (9 - q)));
   }
+  if (e >= OZ_NONFINITE_EXP / 2) return __longlong_as_double(0x7ff8000000000000ll);   // a non-finite operand row
   // sum = (hi 2^35 + lo) 2^(e-63), rounded once, with integer operations
   bool ok;
   const double v = ozr_round(hi, lo, e - 63, &ok);

@@ -22,6 +22,8 @@ constexpr int OZ_SX = 10;       // digits of the iterate
 constexpr int OZ_SA = 8;        // digits of A
 constexpr int OZ_QMAX = 9;      // highest digit group kept (52 pair products)
 constexpr int OZ_KCHUNK = 4096; // exactness bound on K per accumulation
+constexpr int OZ_NONFINITE_EXP = 1 << 20;   // row exponent marking an Inf or NaN in the row: every
+                                            // value recombined from it is NaN
 constexpr int NS_S = 5;         // digit slices of the Newton-Schulz update operands (34 bits,
                                 // digit groups q <= 4: 15 exact pair products)
 

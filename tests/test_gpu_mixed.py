@@ -165,3 +165,38 @@ def test_mixed_floor_hands_over_by_radius(ibmi, ell):
     assert O.residual_f(A, H) <= 1e-10
     inv = np.linalg.inv(A)
     assert np.abs(H - inv).max() <= 1e-6 * np.abs(inv).max()
+
+
+def test_mixed_not_spd_reported_like_oracle(ibmi):
+    p = 200
+    A = wl.random_spd(p, 6, 1.0, 1e2)
+    A[150, 150] = -5.0
+    s, res, _ = run(ibmi, A, K=2, h=10, tol=1e-10, ns_theta=0.5)
+    ref = O.ibmi(A, O.partition(p, 2, 10), tol=1e-10)
+    assert s == ibmi.IBMI_ERR_NOT_SPD and ref.status == "not_spd"
+    assert res["bad_block"] == ref.bad_block and res["bad_pivot"] == ref.bad_pivot
+
+
+def test_mixed_nonfinite_reported(ibmi):
+    """A NaN outside every diagonal block reaches H through W and the sweeps
+    and is reported as IBMI_ERR_NONFINITE (never as a converged result)."""
+    p = 256
+    A = matern(p, 31)
+    A[250, 3] = A[3, 250] = np.nan        # sets [0, 128) and [128, 256): off-block
+    s, res, _ = run(ibmi, A, K=2, h=0, tol=1e-10, ns_theta=0.5)
+    assert s == ibmi.IBMI_ERR_NONFINITE
+
+
+def test_sliced_residual_propagates_nonfinite(ibmi):
+    """An Inf or NaN in H (or A) makes the FP64-accurate sliced residual NaN
+    instead of a finite value from meaningless digits."""
+    p = 200
+    A = matern(p, 33)
+    H = np.linalg.inv(A)
+    for bad in (np.nan, np.inf):
+        Hb = H.copy()
+        Hb[17, 5] = Hb[5, 17] = bad
+        v = ibmi.ibmi_residual_tc(torch.from_numpy(A).cuda(), torch.from_numpy(Hb).cuda())
+        assert not np.isfinite(v)
+    v = ibmi.ibmi_residual_tc(torch.from_numpy(A).cuda(), torch.from_numpy(H).cuda())
+    assert np.isfinite(v) and v < 1e-12
