@@ -34,7 +34,7 @@ struct OzPairArgs {
 };
 
 template <int BN>
-__global__ void __launch_bounds__(THREADS, 1) k_oz_pairs(const __grid_constant__ OzPairMaps maps,
+__global__ void __launch_bounds__(THREADS, Cfg<1, BN>::CTAS_PER_SM) k_oz_pairs(const __grid_constant__ OzPairMaps maps,
                                                          const __grid_constant__ OzPairArgs g) {
   using C = Cfg<1, BN>;
   extern __shared__ uint8_t smem_raw[];
@@ -205,7 +205,7 @@ cudaError_t launch_oz_pairs(const OzPairMaps& maps, const OzPairArgs& g, cudaStr
   using C = Cfg<1, BN>;
   constexpr uint32_t smem_bytes = C::SMEM + STAGE_TILE_BYTES;
   static_assert(smem_bytes <= 227 * 1024, "shared memory per CTA");
-  static_assert(C::CTAS_PER_SM == 1, "one CTA per SM");
+  static_assert(C::CTAS_PER_SM * (smem_bytes + 1024) <= 228 * 1024, "shared memory of the CTAs on an SM");
   static std::atomic<bool> attr_set{false};
   if (!attr_set.load(std::memory_order_acquire)) {
     cudaError_t e = cudaFuncSetAttribute(k_oz_pairs<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);

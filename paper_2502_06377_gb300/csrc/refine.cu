@@ -2,6 +2,8 @@
 // Newton-Schulz update of eq. newton, for the mixed-precision path.
 #include <math.h>
 
+#include <type_traits>
+
 #include "refine.cuh"
 #include "oz_round.h"
 #include "oz_pairs.cuh"
@@ -330,8 +332,21 @@ __global__ void k_q_normalize(const double* y, int64_t p, double* v, double* est
 // --------------------------------------------------------------- host ----
 
 static constexpr int RF_BN = 128;   // N tile of the BF16x3 residual
-static constexpr int OZ_BN = 224;   // N tile of the digit-pair GEMMs (128 x 224 per CTA: p = 4096 gives
-                                    // 608 tiles, four full rounds of 152 SMs)
+// N tile of the digit-pair GEMMs by order: 224 for large p (p = 4096 gives 608
+// tiles of 128 x 224, four full rounds of 152 SMs, one CTA per SM); 128 and
+// 64 for smaller p, where 224-wide tiles would be mostly padding and two
+// CTAs fit on an SM (more matrices of a batch run side by side).
+static int oz_bn_for(int64_t p) { return p > 1536 ? 224 : (p > 384 ? 128 : 64); }
+
+// Calls f(std::integral_constant<int, BN>) for the tile width of R.
+template <class F>
+static ibmi_status with_bn(const RefineState* R, F&& f) {
+  switch (R->bn) {
+    case 224: return f(std::integral_constant<int, 224>{});
+    case 128: return f(std::integral_constant<int, 128>{});
+    default: return f(std::integral_constant<int, 64>{});
+  }
+}
 
 ibmi_status refine_create(RefineState* R, int64_t p, int* err) {
   R->p = p;
@@ -363,9 +378,10 @@ ibmi_status refine_create(RefineState* R, int64_t p, int* err) {
   R->expQ = (int*)take(sizeof(int) * p);
   R->pv = (double*)take(sizeof(double) * (2 * p + 8));
   bool ok = true;
-  for (int s = 0; s < OZ_SA; ++s) ok &= tc::make_map_bf16(&R->mAo[s], R->Ao[s], p, p, ldp, OZ_BN);
+  R->bn = oz_bn_for(p);
+  for (int s = 0; s < OZ_SA; ++s) ok &= tc::make_map_bf16(&R->mAo[s], R->Ao[s], p, p, ldp, R->bn);
   for (int s = 0; s < OZ_SX; ++s) ok &= tc::make_map_bf16(&R->mXo[s], R->Xo[s], p, p, ldp, 128);
-  for (int s = 0; s < NS_S; ++s) ok &= tc::make_map_bf16(&R->mQo[s], R->Qo[s], p, p, ldp, OZ_BN);
+  for (int s = 0; s < NS_S; ++s) ok &= tc::make_map_bf16(&R->mQo[s], R->Qo[s], p, p, ldp, R->bn);
   for (int s = 0; s < 2; ++s) ok &= tc::make_map_bf16(&R->mAf[s], R->Af[s], p, p, ldp, RF_BN);
   return ok ? IBMI_OK : IBMI_ERR_CUDA;
 }
@@ -427,7 +443,8 @@ struct DigitGemm {
 static ibmi_status digit_gemm(RefineState* R, const DigitGemm& g, cudaStream_t st) {
   const int64_t p = R->p, ldp = R->ldp;
   const int chunk_tiles = OZ_KCHUNK / tc::BK;
-  const int grid_n = (int)((g.N + OZ_BN - 1) / OZ_BN), grid_m = (int)((g.M + 127) / 128);
+  const int BNr = R->bn;
+  const int grid_n = (int)((g.N + BNr - 1) / BNr), grid_m = (int)((g.M + 127) / 128);
   for (int q = 0; q <= g.qmax; ++q) {
     bool first = true;
     for (int s = 0; s <= q; ++s) {
@@ -444,7 +461,10 @@ static ibmi_status digit_gemm(RefineState* R, const DigitGemm& g, cudaStream_t s
         int* Tq = R->T + (int64_t)q * p * ldp;
         EpiOzAcc epi{{}, Tq, ldp, g.M, g.N, first ? 1 : 0};
         ProfScope ps(g.kclass, st, 2.0 * (double)g.M * g.N * (double)(k1 - k0) * tc::BK);
-        IBMI_CUDA_TRY((tc::launch<1, OZ_BN>(maps, t, grid_n, grid_m, epi, st)));
+        IBMI_TRY(with_bn(R, [&](auto bn) -> ibmi_status {
+          IBMI_CUDA_TRY((tc::launch<1, decltype(bn)::value>(maps, t, grid_n, grid_m, epi, st)));
+          return IBMI_OK;
+        }));
         first = false;
       }
     }
@@ -477,7 +497,7 @@ static ibmi_status pair_products(RefineState* R, const CUtensorMap* ma, int nsa,
     }
   }
   g.n = n;
-  g.grid_n = (int)((p + OZ_BN - 1) / OZ_BN);
+  g.grid_n = (int)((p + R->bn - 1) / R->bn);
   g.tiles = g.grid_n * (int)((p + 127) / 128);
   g.kt_total = (int)((p + tc::BK - 1) / tc::BK);
   g.chunk = OZ_KCHUNK / tc::BK;
@@ -488,8 +508,10 @@ static ibmi_status pair_products(RefineState* R, const CUtensorMap* ma, int nsa,
   g.N = p;
   g.err = R->err;
   ProfScope ps(kclass, st, 2.0 * n * (double)p * p * (double)g.kt_total * tc::BK);
-  IBMI_CUDA_TRY(tc::launch_oz_pairs<OZ_BN>(maps, g, st));
-  return IBMI_OK;
+  return with_bn(R, [&](auto bn) -> ibmi_status {
+    IBMI_CUDA_TRY(tc::launch_oz_pairs<decltype(bn)::value>(maps, g, st));
+    return IBMI_OK;
+  });
 }
 
 // W = A_I^{-1} A_{I,:} from digit products, written as BF16 hi/lo (zero on
@@ -586,7 +608,7 @@ ibmi_status refine_form_w_all(RefineState* R, const std::vector<const double*>& 
   for (int k = 0; k < K; ++k)
     flops += 2.0 * (double)((hi[k] - lo[k] + 127) / 128 * 128) * p *
              (double)(((hi[k] + tc::BK - 1) / tc::BK - lo[k] / tc::BK) * tc::BK);
-  const int grid_n = (int)((p + OZ_BN - 1) / OZ_BN), grid_m = (int)(rows / 128);
+  const int grid_n = (int)((p + R->bn - 1) / R->bn), grid_m = (int)(rows / 128);
   for (int q = 0; q <= QW; ++q) {
     bool first = true;
     for (int s = 0; s <= q; ++s) {
@@ -600,7 +622,10 @@ ibmi_status refine_form_w_all(RefineState* R, const std::vector<const double*>& 
       t.pdl = 1;
       EpiOzAcc epi{{}, R->T + (int64_t)q * rows * ldp, ldp, rows, p, first ? 1 : 0};
       ProfScope ps(IBMI_K_INVARIANTS_TC, st, flops);
-      IBMI_CUDA_TRY((tc::launch<1, OZ_BN>(maps, t, grid_n, grid_m, epi, st)));
+      IBMI_TRY(with_bn(R, [&](auto bn) -> ibmi_status {
+        IBMI_CUDA_TRY((tc::launch<1, decltype(bn)::value>(maps, t, grid_n, grid_m, epi, st)));
+        return IBMI_OK;
+      }));
       first = false;
     }
   }

@@ -29,6 +29,7 @@ constexpr int NS_S = 5;         // digit slices of the Newton-Schulz update oper
 
 struct RefineState {
   int64_t p = 0, ldp = 0;
+  int bn = 224;                   // N tile of the digit-pair products (by order; see refine_create)
   __nv_bfloat16* Ao[OZ_SA] = {};  // digit slices of A (rows), p x ldp
   __nv_bfloat16* Xo[OZ_S] = {};   // digit slices of the iterate X
   int* expA = nullptr;            // row exponents

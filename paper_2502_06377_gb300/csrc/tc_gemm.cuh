@@ -461,7 +461,7 @@ cudaError_t launch(const Maps& maps, const Tiles& t0, int grid_n, int grid_m, co
   using C = Cfg<S, BN>;
   constexpr uint32_t smem_bytes = C::SMEM + (has_warp_tile<Epi>::value ? STAGE_TILE_BYTES : 0u);
   static_assert(smem_bytes <= 227 * 1024, "shared memory per CTA");
-  static_assert(!has_warp_tile<Epi>::value || C::CTAS_PER_SM == 1, "staging sized for one CTA per SM");
+  static_assert(C::CTAS_PER_SM * (smem_bytes + 1024) <= 228 * 1024, "shared memory of the CTAs on an SM");
   static std::atomic<bool> attr_set{false};
   if (!attr_set.load(std::memory_order_acquire)) {
     cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<S, BN, Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize,
