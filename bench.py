@@ -330,7 +330,7 @@ def main():
     prec = ibmi.IBMI_MIXED if args.precision == "mixed" else ibmi.IBMI_FP64
     kw = dict(tol=TOL, max_sweeps=500, precision=prec)
     if prec == ibmi.IBMI_MIXED:
-        kw.update(ns_theta=0.5, ns_max=8, check_every=1)
+        kw.update(ns_theta=0.9, ns_max=8, check_every=1)
     else:
         kw.update(check_every=1)
     plan = ibmi.ibmi_plan(P, K=K_SETS, h=H_OV, **kw)

@@ -77,7 +77,10 @@ static ibmi_plan_desc desc_for(const Shape& s, const ibmi_batch_opts& o) {
   d.tol = o.tol;
   d.max_sweeps = o.max_sweeps;
   d.check_every = 1;
-  d.ns_theta = o.precision == IBMI_MIXED ? o.ns_theta : 0.0;
+  // hand-over: for small orders a sweep costs about as much as a tail step
+  // (both launch-latency bound), so the tail starts earlier; an unfinished
+  // tail returns to the sweeps
+  d.ns_theta = o.precision != IBMI_MIXED ? 0.0 : (o.ns_theta > 0.0 ? o.ns_theta : (s.p <= 1024 ? 2.0 : 0.9));
   d.ns_max = o.ns_max;
   return d;
 }
@@ -399,7 +402,7 @@ void ibmi_batch_opts_init(ibmi_batch_opts* o) {
   o->precision = IBMI_MIXED;
   o->tol = 1e-10;
   o->max_sweeps = 500;
-  o->ns_theta = 0.5;
+  o->ns_theta = 0.0;   // by order
   o->ns_max = 8;
   o->workers = 8;
   o->autotune = 1;

@@ -440,6 +440,8 @@ ibmi_status mixed_run(ibmi_plan_s* P, const double* A, int64_t lda, double* H, i
   M->level = 0;
   double pending = NAN;   // accurate residual of the current H when it was just taken
   double next_radius_test = INFINITY;   // slow convergence: rho below which the radius is measured again
+  double handover_below = INFINITY;     // after a failed tail: rho below which the next hand-over may come
+  double handover_rho = 0.0;            // rho of the stop test that handed over
   // sweeps whose cost matches about two tail steps (time ratio of a step to a
   // sweep ~ 8.4 fr / fs, from the measured rates of the two kinds of product)
   const double slow_sweeps = 2.0 * 8.4 * fr / std::max(fs, 1.0);
@@ -476,7 +478,11 @@ ibmi_status mixed_run(ibmi_plan_s* P, const double* A, int64_t lda, double* H, i
       *flops += fr;
       res->resid_f = rho;
       if (!isfinite(rho)) return IBMI_ERR_NONFINITE;
-      if (d.ns_theta > 0.0 && rho * sqrtp <= d.ns_theta) break;
+      if (d.ns_theta > 0.0 && rho * sqrtp <= d.ns_theta && rho <= handover_below) {
+        early = true;   // a failing tail returns to the sweeps
+        handover_rho = rho;
+        break;
+      }
       // Slow convergence: eq. newton needs only the spectral radius of I - X A
       // below 1, which ||I - A H||_F bounds loosely.  Once that norm is within
       // 16 theta and the sweeps still predicted to reach theta cost more than
@@ -498,6 +504,7 @@ ibmi_status mixed_run(ibmi_plan_s* P, const double* A, int64_t lda, double* H, i
         if (rad <= kEarlyHandOver) {
           pending = acc;
           early = true;
+          handover_rho = rho;
           break;
         }
       }
@@ -599,7 +606,10 @@ ibmi_status mixed_run(ibmi_plan_s* P, const double* A, int64_t lda, double* H, i
       res->ns_steps = s + 1;
     }
     if (!resume) return IBMI_NOT_CONVERGED;   // not reached: the tail returns
-    cad.next = r + 1;   // the next radius test waits for rho to halve (set at the test)
+    // the next hand-over waits for rho to halve (the radius test's own
+    // threshold was set when it ran)
+    handover_below = 0.5 * handover_rho;
+    cad.next = r + 1;
   }
 }
 
