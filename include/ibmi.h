@@ -168,7 +168,7 @@ typedef struct ibmi_batch_opts {
   double tol;          /* default 1e-10 (rho_F)                                */
   int32_t max_sweeps;  /* default 500                                          */
   double ns_theta;     /* Newton-Schulz hand-over (mixed); default 0: by order,
-                          2.0 up to p = 1024, 0.9 above                       */
+                          3.0 up to p = 1024, 0.9 above                       */
   int32_t ns_max;      /* default 8                                            */
   int32_t workers;     /* concurrent streams, 1..64, default 8                 */
   int32_t autotune;    /* 1 (default): tune (K, h) per size bucket              */

@@ -80,7 +80,7 @@ static ibmi_plan_desc desc_for(const Shape& s, const ibmi_batch_opts& o) {
   // hand-over: for small orders a sweep costs about as much as a tail step
   // (both launch-latency bound), so the tail starts earlier; an unfinished
   // tail returns to the sweeps
-  d.ns_theta = o.precision != IBMI_MIXED ? 0.0 : (o.ns_theta > 0.0 ? o.ns_theta : (s.p <= 1024 ? 2.0 : 0.9));
+  d.ns_theta = o.precision != IBMI_MIXED ? 0.0 : (o.ns_theta > 0.0 ? o.ns_theta : (s.p <= 1024 ? 3.0 : 0.9));
   d.ns_max = o.ns_max;
   return d;
 }
