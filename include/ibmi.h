@@ -83,7 +83,8 @@ typedef struct ibmi_plan_desc {
   int64_t h;               /* overlap half-width for the default layout (see below)        */
   const int64_t* lo;       /* optional explicit sets: K ascending starts (host, copied) ... */
   const int64_t* hi;       /* ... and ends; NULL = default layout                           */
-  int32_t precision;       /* ibmi_precision                                                */
+  int32_t precision;       /* ibmi_precision (with a single set, K = 1, H = A^{-1} is the
+                              FP64 block inverse for either precision)                 */
   double tol;              /* stop tolerance (default 1e-10)                                */
   int32_t max_sweeps;      /* sweep cap (default 500, the cap used in Section 5)           */
   int32_t stop_rule;       /* ibmi_stop_rule                                                */

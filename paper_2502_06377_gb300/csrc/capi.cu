@@ -102,7 +102,9 @@ static ibmi_status invert_impl(ibmi_plan_s* P, const double* A, int64_t lda, dou
   IBMI_TRY(sym_from_lower(A, lda, p, P->dAs, p, st));
   A = P->dAs;
   lda = p;
-  const bool mixed = d.precision == IBMI_MIXED;
+  // one set is the whole matrix: H = A^{-1} from the FP64 block inverse,
+  // whatever the precision
+  const bool mixed = d.precision == IBMI_MIXED && K > 1;
   if (mixed) {
     ibmi_status s = mixed_run(P, A, lda, H, ldh, st, res, &flops);
     res->flops = flops;
@@ -110,7 +112,7 @@ static ibmi_status invert_impl(ibmi_plan_s* P, const double* A, int64_t lda, dou
   }
   // a2: invariants
   IBMI_CUDA_TRY(cudaMemsetAsync(P->dstatus, 0, sizeof(DevStatus), st));
-  IBMI_TRY(invariants_all(P, A, lda, true, st));
+  IBMI_TRY(invariants_all(P, A, lda, K > 1, st));   // one set needs no W (its sweep sets H = A^{-1})
   flops += flops_plan(P);
   DevStatus hs;
   IBMI_CUDA_TRY(cudaMemcpyAsync(&hs, P->dstatus, sizeof(hs), cudaMemcpyDeviceToHost, st));
@@ -218,7 +220,6 @@ ibmi_status ibmi_plan(const ibmi_plan_desc* desc, ibmi_plan_t* out) {
     return IBMI_ERR_INVALID_ARG;
   }
   if (d.init != IBMI_INIT_IDENTITY && d.init != IBMI_INIT_USER) return IBMI_ERR_INVALID_ARG;
-  if (d.precision == IBMI_MIXED && d.K < 2) return IBMI_ERR_INVALID_ARG;   // nothing to sweep
   if (d.max_sweeps < 1 || d.check_every < 1 || d.ns_max < 0 || !(d.tol >= 0.0) || !(d.ns_theta >= 0.0))
     return IBMI_ERR_INVALID_ARG;
   ibmi_plan_s* P = new ibmi_plan_s();
@@ -301,7 +302,7 @@ ibmi_status ibmi_plan(const ibmi_plan_desc* desc, ibmi_plan_t* out) {
     ibmi_plan_destroy(P);
     return IBMI_ERR_CUDA;
   }
-  if (d.precision == IBMI_MIXED) {
+  if (d.precision == IBMI_MIXED && P->lo.size() > 1) {   // one set: the FP64 block inverse is H
     ibmi_status s = mixed_create(P);
     if (s != IBMI_OK) { ibmi_plan_destroy(P); return s; }
   }

@@ -330,7 +330,7 @@ ibmi_status mixed_sweep_step(ibmi_plan_s* P, int k, cudaStream_t st) {
   MixedState* M = MS(P);
   const int64_t p = P->d.p, lo = P->lo[k], hi = P->hi[k], m = hi - lo, n = p - m;
   const tc::TileRanges kr = tc::complement_tiles(lo, hi, p, tc::BK);
-  if (n == 0) return IBMI_ERR_INVALID_ARG;   // K = 1 is served by the FP64 path
+  if (n == 0) return IBMI_ERR_INVALID_ARG;   // K = 1 never gets here (the FP64 path serves it)
   // a3: X = -W T; A operand = W slices (rows of the set), B = H slices (rows j).
   const int S = M->level == 0 ? 2 : 3;
   const double mult = S == 2 ? 3.0 : 6.0;   // slice products per product

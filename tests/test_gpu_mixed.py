@@ -200,3 +200,14 @@ def test_sliced_residual_propagates_nonfinite(ibmi):
         assert not np.isfinite(v)
     v = ibmi.ibmi_residual_tc(torch.from_numpy(A).cuda(), torch.from_numpy(H).cuda())
     assert np.isfinite(v) and v < 1e-12
+
+
+def test_mixed_single_set_is_direct_inverse(ibmi):
+    """One set covering the matrix: the block inverse is the answer, for a
+    mixed-precision plan as for an FP64 one."""
+    p = 160
+    A = matern(p, 35)
+    s, res, H = run(ibmi, A, K=1, tol=1e-12)
+    assert s == ibmi.IBMI_OK and res["sweeps"] == 1
+    inv = np.linalg.inv(A)
+    assert np.abs(H - inv).max() <= 1e-12 * np.abs(inv).max()
