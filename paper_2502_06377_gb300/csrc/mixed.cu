@@ -379,19 +379,6 @@ static ibmi_status mixed_export_launch(ibmi_plan_s* P, double* H, int64_t ldh, c
   return IBMI_OK;
 }
 
-ibmi_status mixed_export(ibmi_plan_s* P, double* H, int64_t ldh, cudaStream_t st) {
-  MixedState* M = MS(P);
-  IBMI_TRY(mixed_export_launch(P, H, ldh, st));
-  int herr = 0;
-  IBMI_CUDA_TRY(cudaMemcpyAsync(&herr, M->err, sizeof(int), cudaMemcpyDeviceToHost, st));
-  IBMI_CUDA_TRY(cudaStreamSynchronize(st));
-  if (herr != 0) {
-    set_last_error("tcgen05 kernel: bounded wait expired");
-    return IBMI_ERR_TIMEOUT;
-  }
-  return IBMI_OK;
-}
-
 ibmi_status mixed_run(ibmi_plan_s* P, const double* A, int64_t lda, double* H, int64_t ldh, cudaStream_t st,
                       ibmi_result* res, double* flops) {
   MixedState* M = MS(P);

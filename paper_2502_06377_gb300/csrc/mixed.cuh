@@ -9,8 +9,6 @@ void mixed_destroy(ibmi_plan_s* P);
 ibmi_status mixed_prepare(ibmi_plan_s* P, const double* H, int64_t ldh, cudaStream_t st);
 // a3 + a4 for set k on the mixed-precision iterate.
 ibmi_status mixed_sweep_step(ibmi_plan_s* P, int k, cudaStream_t st);
-// Writes the mixed iterate into the caller's FP64 H.
-ibmi_status mixed_export(ibmi_plan_s* P, double* H, int64_t ldh, cudaStream_t st);
 // The whole mixed pipeline: FP64 block factorisations and W on tensor cores,
 // sweeps (tcgen05 BF16 slices), hand-over test on a BF16x3 residual, then the
 // Newton-Schulz tail with FP64-accurate residuals (sliced error-free

@@ -711,11 +711,6 @@ ibmi_status refine_ns_update(RefineState* R, double* X, int64_t ldx, cudaStream_
   return IBMI_OK;
 }
 
-ibmi_status refine_cheap_residual(RefineState* R, const CUtensorMap* mapH2, cudaStream_t st, double* rho) {
-  IBMI_TRY(refine_cheap_residual_launch(R, mapH2, st));
-  return read_scalar(R, st, rho);
-}
-
 ibmi_status refine_cheap_residual_launch(RefineState* R, const CUtensorMap* mapH2, cudaStream_t st) {
   const int64_t p = R->p;
   tc::Maps maps;

@@ -103,6 +103,9 @@ ibmi_status refine_form_w_all(RefineState* R, const std::vector<const double*>& 
 // update still finds its five digits of X).
 ibmi_status refine_residual_launch(RefineState* R, const double* X, int64_t ldx, cudaStream_t st,
                                    int qmax = OZ_QMAX);
+// ||I - H A||_F / sqrt(p) from BF16x3 products, for H given by its BF16 hi/lo
+// slice maps (about 5 significant digits; the stop test of the sweeps and the
+// hand-over to Newton-Schulz); value read by refine_read.
 ibmi_status refine_cheap_residual_launch(RefineState* R, const CUtensorMap* mapH2, cudaStream_t st);
 ibmi_status refine_read(RefineState* R, cudaStream_t st, double* rho);
 
@@ -116,9 +119,5 @@ ibmi_status refine_read(RefineState* R, cudaStream_t st, double* rho);
 ibmi_status refine_q_radius_launch(RefineState* R, int iters, cudaStream_t st);
 ibmi_status refine_q_radius_read(RefineState* R, cudaStream_t st, double* radius);
 
-// ||I - H A||_F / sqrt(p) from BF16x3 products, for H given by its BF16 hi/lo
-// slice maps (about 5 significant digits; used to decide the hand-over to
-// Newton-Schulz).  Host value in *rho.
-ibmi_status refine_cheap_residual(RefineState* R, const CUtensorMap* mapH2, cudaStream_t st, double* rho);
 
 }  // namespace ibmi
