@@ -75,3 +75,26 @@ def test_batched_reads_lower_triangle_only(ibmi):
     assert outs[0][:2] == outs[1][:2]
     for a, b in zip(outs[0][2], outs[1][2]):
         assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_padded_leading_dimensions(ibmi, precision):
+    """A and H stored with row pitches above p give the bits of contiguous
+    storage (padding untouched in H, ignored in A)."""
+    p, lda, ldh = 301, 301 + 37, 301 + 5
+    A, _ = _pair(p, seed=9)
+    prec = ibmi.IBMI_MIXED if precision == "mixed" else ibmi.IBMI_FP64
+    kw = dict(K=3, h=9, precision=prec, tol=1e-10, max_sweeps=200, ns_theta=0.9 if prec == ibmi.IBMI_MIXED else 0.0)
+    dA = torch.from_numpy(A).cuda()
+    dH = torch.empty_like(dA)
+    plan = ibmi.ibmi_plan(p, **kw)
+    s0, r0 = ibmi.ibmi_invert(plan, dA, dH)
+    Apad = torch.full((p, lda), float("nan"), dtype=torch.float64, device="cuda")
+    Apad[:, :p] = dA
+    Hpad = torch.full((p, ldh), -7.0, dtype=torch.float64, device="cuda")
+    s1, r1 = ibmi.ibmi_invert(plan, Apad[:, :p], Hpad[:, :p])
+    torch.cuda.synchronize()
+    plan.close()
+    assert (s0, r0["sweeps"], r0["ns_steps"]) == (s1, r1["sweeps"], r1["ns_steps"])
+    assert np.array_equal(dH.cpu().numpy(), Hpad[:, :p].cpu().numpy())
+    assert torch.all(Hpad[:, p:] == -7.0)
