@@ -136,7 +136,8 @@ __global__ void k_bat_extract(const double* R, const int64_t* dlo, const int64_t
 
 static inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
-ibmi_status invariants_all(ibmi_plan_s* P, const double* A, int64_t lda, bool full_w, cudaStream_t st) {
+ibmi_status invariants_all(ibmi_plan_s* P, const double* A, int64_t lda, bool full_w, cudaStream_t st,
+                           bool leave_y) {
   const int64_t p = P->d.p, mmax = P->mmax;
   const int K = (int)P->lo.size();
   const int64_t ncols = full_w ? p : mmax;
@@ -223,6 +224,8 @@ ibmi_status invariants_all(ibmi_plan_s* P, const double* A, int64_t lda, bool fu
         IBMI_CUDA_TRY((launch_gemm_f64<false, true>(op, EpiStore{R, ncols, -1.0, 1.0, zR}, st)));
       }
     }
+  } else if (leave_y) {
+    return IBMI_OK;   // the caller forms A_I^{-1} = Y^T Y from P->bat_R
   } else {
     // R holds Y = L^{-1}; A_I^{-1} = Y^T Y in one product (into the buffer of L,
     // no longer needed), each tile summing only k >= max(i, j).

@@ -51,6 +51,7 @@ constexpr int kNs0Groups = 7;               // digit groups of the first Newton-
 constexpr double kNs0Pairs = 36.0;          // its pair products (all pairs of groups 0..7)
 constexpr double kEarlyHandOver = 0.6;      // radius below which slow sweeps hand over early
 constexpr int64_t kEarlyMinOrder = 2048;    // smallest order for that test
+constexpr int64_t kTcInverseMinOrder = 1024;   // block order from which Y^T Y runs on the tensor cores
 constexpr double kRadiusHandOver = 0.5;     // hand over to Newton-Schulz below this radius
 
 // One captured phase: the executable graph and its kernel-node count (added
@@ -402,7 +403,14 @@ ibmi_status mixed_run(ibmi_plan_s* P, const double* A, int64_t lda, double* H, i
   IBMI_TRY(graph_or_run(M, &M->g_setup, st, [&]() -> ibmi_status {
     IBMI_CUDA_TRY(cudaMemsetAsync(P->dstatus, 0, sizeof(DevStatus), st));
     IBMI_CUDA_TRY(cudaMemsetAsync(M->err, 0, sizeof(int), st));
-    IBMI_TRY(invariants_all(P, A, lda, false, st));
+    // Large blocks: A_I^{-1} = Y^T Y (Y = L^{-1}) as an exact sliced product
+    // on the tensor cores instead of the FP64 product, which dominates there
+    const bool tc_inverse = P->mmax >= kTcInverseMinOrder;
+    IBMI_TRY(invariants_all(P, A, lda, false, st, tc_inverse));
+    if (tc_inverse)
+      for (int k = 0; k < K; ++k)
+        IBMI_TRY(refine_block_inverse(R, P->bat_R + (int64_t)k * P->mmax * P->mmax, P->mmax, P->hi[k] - P->lo[k],
+                                      P->ainv[k], st));
     if (d.init == IBMI_INIT_IDENTITY) IBMI_TRY(set_identity(H, ldh, p, st));
     IBMI_TRY(refine_set_matrix(R, A, lda, st));
     if (R->w_rows > 0) {

@@ -81,7 +81,10 @@ struct CheckCadence {
 // W = A_I^{-1} A_{I,:} (zero columns on I) -- the mixed path forms W on tensor
 // cores instead.  Non-SPD blocks are reported through plan->dstatus (read by
 // the caller after a stream sync).
-ibmi_status invariants_all(ibmi_plan_s* P, const double* A, int64_t lda, bool full_w, cudaStream_t st);
+// leave_y (with full_w false): stop after the forward solve, leaving Y = L^{-1}
+// of set k in P->bat_R + k * mmax * mmax (row pitch mmax) for the caller.
+ibmi_status invariants_all(ibmi_plan_s* P, const double* A, int64_t lda, bool full_w, cudaStream_t st,
+                           bool leave_y = false);
 
 // a3 + a4 for set k on an FP64 iterate H.
 ibmi_status sweep_step_f64(ibmi_plan_s* P, int k, double* H, int64_t ldh, cudaStream_t st);

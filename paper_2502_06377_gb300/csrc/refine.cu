@@ -290,6 +290,25 @@ __global__ void k_sym_into(const double* Xn, int64_t p, double* X, int64_t ldx) 
     if (I0 + r < p && J0 + tx < p) X[(I0 + r) * ldx + J0 + tx] = 0.5 * (a[r][tx] + b[tx][r]);
 }
 
+// Z = Y^T (m x m; Y row pitch ldy, Z row pitch m), 32 x 32 tiles through shared memory.
+__global__ void k_transpose(const double* Y, int64_t ldy, int64_t m, double* Z) {
+  __shared__ double t[32][33];
+  const int64_t I0 = (int64_t)blockIdx.y * 32, J0 = (int64_t)blockIdx.x * 32;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y)
+    t[r][threadIdx.x] = (I0 + r < m && J0 + threadIdx.x < m) ? Y[(I0 + r) * ldy + J0 + threadIdx.x] : 0.0;
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y)
+    if (J0 + r < m && I0 + threadIdx.x < m) Z[(J0 + r) * m + I0 + threadIdx.x] = t[threadIdx.x][r];
+}
+
+// Ainv[i][j] = 2^{e_i + e_j - 12} sum_{q <= qmax} T_q 2^{-7q} (the product Z Z^T).
+__global__ void k_oz_gram(const int* T, int64_t plane, int64_t ldp, int64_t m, const int* ez, int qmax,
+                          double* Ainv) {
+  const int64_t i = blockIdx.y, j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= m) return;
+  Ainv[i * m + j] = oz_value(T, plane, i * ldp + j, qmax, ez[i] + ez[j] - 12);
+}
+
 // Power iteration on the dense Q (p x p, row pitch p): y = Q v, one warp per row.
 __global__ void k_q_gemv(const double* Q, int64_t p, const double* v, double* y) {
   const int64_t i = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
@@ -382,6 +401,7 @@ ibmi_status refine_create(RefineState* R, int64_t p, int* err) {
   for (int s = 0; s < OZ_SA; ++s) ok &= tc::make_map_bf16(&R->mAo[s], R->Ao[s], p, p, ldp, R->bn);
   for (int s = 0; s < OZ_SX; ++s) ok &= tc::make_map_bf16(&R->mXo[s], R->Xo[s], p, p, ldp, 128);
   for (int s = 0; s < NS_S; ++s) ok &= tc::make_map_bf16(&R->mQo[s], R->Qo[s], p, p, ldp, R->bn);
+  for (int s = 0; s < NS_S; ++s) ok &= tc::make_map_bf16(&R->mXo_b[s], R->Xo[s], p, p, ldp, R->bn);
   for (int s = 0; s < 2; ++s) ok &= tc::make_map_bf16(&R->mAf[s], R->Af[s], p, p, ldp, RF_BN);
   return ok ? IBMI_OK : IBMI_ERR_CUDA;
 }
@@ -656,6 +676,61 @@ ibmi_status refine_q_radius_launch(RefineState* R, int iters, cudaStream_t st) {
     k_q_gemv<<<(unsigned)((p + 7) / 8), 256, 0, st>>>(R->Xn, p, v, y);
     k_q_normalize<<<1, 1024, 0, st>>>(y, p, v, est, 0);
   }
+  IBMI_CUDA_TRY(cudaGetLastError());
+  return IBMI_OK;
+}
+
+ibmi_status refine_block_inverse(RefineState* R, const double* Y, int64_t ldy, int64_t m, double* Ainv,
+                                 cudaStream_t st) {
+  const int64_t p = R->p, ldp = R->ldp;
+  if (m < 1 || m > p) return IBMI_ERR_INVALID_ARG;
+  constexpr int ND = 5, QG = 4;   // 34-bit digits, groups q <= 4
+  double* Z = R->Xn;              // FP64 scratch (p x p)
+  {
+    ProfScope ps(IBMI_K_OTHER, st, 0.0);
+    note_launch();
+    const unsigned nt = (unsigned)((m + 31) / 32);
+    k_transpose<<<dim3(nt, nt), dim3(32, 8), 0, st>>>(Y, ldy, m, Z);
+    IBMI_CUDA_TRY(cudaGetLastError());
+    // rows of Z, zero beyond column m (the last K block reads them)
+    IBMI_TRY(slice_digits(R, Z, m, R->Xo, ND, R->expX, st, m, m, 0));
+  }
+  tc::OzPairMaps maps;
+  for (int d = 0; d < ND; ++d) {
+    maps.a[d] = R->mXo[d];
+    maps.b[d] = R->mXo_b[d];
+  }
+  tc::OzPairArgs g{};
+  int n = 0;
+  for (int q = 0; q <= QG; ++q)
+    for (int a = 0; a <= q; ++a) {
+      g.s[n] = (int8_t)a;
+      g.u[n] = (int8_t)(q - a);
+      g.q[n] = (int8_t)q;
+      g.first[n] = a == 0 ? 1 : 0;
+      ++n;
+    }
+  g.n = n;
+  g.grid_n = (int)((m + R->bn - 1) / R->bn);
+  g.tiles = g.grid_n * (int)((m + 127) / 128);
+  g.kt_total = (int)((m + tc::BK - 1) / tc::BK);
+  g.chunk = OZ_KCHUNK / tc::BK;
+  g.T = R->T;
+  g.plane = p * ldp;
+  g.ldt = ldp;
+  g.M = m;
+  g.N = m;
+  g.err = R->err;
+  {
+    ProfScope ps(IBMI_K_INVARIANTS_TC, st, 2.0 * n * (double)m * m * (double)g.kt_total * tc::BK);
+    IBMI_TRY(with_bn(R, [&](auto bn) -> ibmi_status {
+      IBMI_CUDA_TRY(tc::launch_oz_pairs<decltype(bn)::value>(maps, g, st));
+      return IBMI_OK;
+    }));
+  }
+  ProfScope ps(IBMI_K_OTHER, st, 0.0);
+  note_launch();
+  k_oz_gram<<<grid2(m, m), 256, 0, st>>>(R->T, p * ldp, ldp, m, R->expX, QG, Ainv);
   IBMI_CUDA_TRY(cudaGetLastError());
   return IBMI_OK;
 }

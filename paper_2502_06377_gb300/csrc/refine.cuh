@@ -45,6 +45,7 @@ struct RefineState {
   double* pv = nullptr;           // power-iteration vectors (2 p) and estimate
   int* err = nullptr;
   CUtensorMap mAo[OZ_SA], mXo[OZ_S], mQo[NS_S], mAf[2];
+  CUtensorMap mXo_b[NS_S];        // the first X digit planes with BN-row boxes (as a right operand)
   void* pool = nullptr;
   // W of all sets in one pass (refine_plan_w): set k's rows sit in a slot of
   // whole 128-row tiles starting at row w_off[k] of a stacked view of the X
@@ -79,6 +80,15 @@ ibmi_status refine_ns_update(RefineState* R, double* X, int64_t ldx, cudaStream_
 // row pitch ldp.  Needs refine_set_matrix first; uses the X digit planes.
 ibmi_status refine_form_w(RefineState* R, const double* Ainv, int64_t m, int64_t lo, int64_t hi, __nv_bfloat16* W0,
                           __nv_bfloat16* W1, __nv_bfloat16* W2, cudaStream_t st);
+
+// A_I^{-1} = Y^T Y of one diagonal block from Y = L^{-1} (m x m, row pitch
+// ldy, lower triangular) as an error-free sliced product on tensor cores:
+// five 7-bit digits of each row of Z = Y^T (34 bits), digit groups q <= 4 (15
+// pair products in one all-pairs launch), recombined exactly and rounded once
+// to FP64 into Ainv (m x m, row pitch m).  Borrows the X digit planes and the
+// FP64 scratch.
+ibmi_status refine_block_inverse(RefineState* R, const double* Y, int64_t ldy, int64_t m, double* Ainv,
+                                 cudaStream_t st);
 
 // Prepares the one-pass formation of W for the sets [lo_k, hi_k): the stacked
 // view fits when 5 slots of sum_k ceil(m_k/128)*128 rows fit in the X digit

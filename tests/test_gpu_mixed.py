@@ -211,3 +211,19 @@ def test_mixed_single_set_is_direct_inverse(ibmi):
     assert s == ibmi.IBMI_OK and res["sweeps"] == 1
     inv = np.linalg.inv(A)
     assert np.abs(H - inv).max() <= 1e-12 * np.abs(inv).max()
+
+
+def test_mixed_large_blocks_tensor_core_block_inverse(ibmi):
+    """Blocks of order >= 1024 take A_I^{-1} = Y^T Y from the sliced tensor-core
+    product: the converged inverse is the FP64 one, and fixed-sweep iterates
+    follow the oracle's as closely as with the FP64 block inverse."""
+    p, K, h = 2300, 2, 50
+    A = matern(p, 37)
+    s, res, H = run(ibmi, A, K=K, h=h, tol=1e-10, ns_theta=0.9, max_sweeps=300)
+    assert s == ibmi.IBMI_OK
+    assert O.residual_f(A, H) <= 1e-10
+    inv = np.linalg.inv(A)
+    assert np.abs(H - inv).max() <= 1e-7 * np.abs(inv).max()
+    ref = O.ibmi(A, O.partition(p, K, h), tol=0.0, max_sweeps=2)
+    s, res, H = run(ibmi, A, K=K, h=h, tol=0.0, max_sweeps=2)
+    assert np.linalg.norm(H - ref.h) / np.linalg.norm(ref.h) < 5e-4
