@@ -172,17 +172,18 @@ __global__ void k_export_h(const float* Hf, int64_t ldp, int64_t p, double* H, i
   H[i * ldh + c] = (double)Hf[i * ldp + c];
 }
 
-// a4 finish: H[I, I] = A_I^{-1} - (P + P^T)/2 with P = sum of the split-K partials.
+// a4 finish: H[I, I] = A_I^{-1} - P with P = sum of the split-K partials (its
+// lower triangle, mirrored).
 __global__ void k_mixed_sym(const float* Spart, int splits, int64_t m, const double* Ainv, int64_t lo, int64_t ldp,
                             float* Hf, __nv_bfloat16* s0, __nv_bfloat16* s1, __nv_bfloat16* s2) {
   const int64_t i = blockIdx.y, j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= m) return;
-  float a = 0.f, b = 0.f;
-  for (int z = 0; z < splits; ++z) {
-    a += Spart[(int64_t)z * m * m + i * m + j];
-    b += Spart[(int64_t)z * m * m + j * m + i];
-  }
-  float x = (float)(Ainv[i * m + j] - 0.5 * ((double)a + (double)b));
+  // P is computed on and below the diagonal: element (max, min) serves both
+  // (i, j) and (j, i), so H[I, I] comes out exactly symmetric
+  const int64_t hi_ = i > j ? i : j, lo_ = i > j ? j : i;
+  float a = 0.f;
+  for (int z = 0; z < splits; ++z) a += Spart[(int64_t)z * m * m + hi_ * m + lo_];
+  float x = (float)(Ainv[i * m + j] - (double)a);
   int64_t o = (lo + i) * ldp + lo + j;
   Hf[o] = x;
   __nv_bfloat16 t0, t1, t2;
@@ -272,8 +273,9 @@ ibmi_status mixed_create(ibmi_plan_s* P) {
   P->mixed = M;
   M->ldp = (p + 63) / 64 * 64;
   const int64_t ldp = M->ldp;
-  // a4 split-K factor: fill one round of the SMs with ceil(m/128)^2 tiles
-  int64_t tiles2 = ((P->mmax + 127) / 128) * ((P->mmax + MX_BN - 1) / MX_BN);
+  // a4 split-K factor: fill one round of the SMs with the lower tiles
+  const int64_t tm = (P->mmax + 127) / 128;
+  const int64_t tiles2 = tm * (tm + 1) / 2;   // a4 computes the tiles on and below the diagonal
   int kt = (int)((p + tc::BK - 1) / tc::BK);
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
@@ -359,8 +361,9 @@ ibmi_status mixed_sweep_step(ibmi_plan_s* P, int k, cudaStream_t st) {
     }
     const int ntn = (int)((m + MX_BN - 1) / MX_BN);
     tc::Tiles t{m, lo, 0, ntn, ntn, kr.r0_end, kr.r1_begin, kr.r1_end, splits, M->err};
+    t.lower = 1;   // P is symmetric up to rounding: tiles on and below the diagonal only
     EpiTcPartial epi{{}, M->Spart, m};
-    ProfScope ps(IBMI_K_SWEEP_S, st, mult * 2.0 * m * m * n);
+    ProfScope ps(IBMI_K_SWEEP_S, st, mult * 2.0 * n * (double)(ntn * (ntn + 1) / 2) * MX_BN * MX_BN);
     if (S == 2) IBMI_CUDA_TRY((tc::launch<2, MX_BN>(maps, t, ntn, (int)((m + 127) / 128), epi, st)));
     else IBMI_CUDA_TRY((tc::launch<3, MX_BN>(maps, t, ntn, (int)((m + 127) / 128), epi, st)));
     note_launch();

@@ -68,6 +68,10 @@ struct Tiles {
   // splits == 1, kt0_end >= every y): rows of different problems stacked in
   // one launch, each with its own K range.
   const int2* mkr = nullptr;
+  // Lower tiles only (square tiles, grid_n == grid_m, identity N-tile map):
+  // the units are the tiles on or below the diagonal, for a symmetric result
+  // whose consumer reads element (i, j) with j > i from (j, i).
+  int lower = 0;
 };
 
 __device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
@@ -78,11 +82,21 @@ __device__ __forceinline__ void grid_launch_dependents() { asm volatile("griddep
 struct Unit {
   int tile, z, kb, nk;
 };
-__host__ __device__ inline int unit_count(const Tiles& t) { return t.grid_n * t.grid_m * t.splits; }
+__host__ __device__ inline int tiles_per_split(const Tiles& t) {
+  return t.lower ? t.grid_m * (t.grid_m + 1) / 2 : t.grid_n * t.grid_m;
+}
+__host__ __device__ inline int unit_count(const Tiles& t) { return tiles_per_split(t) * t.splits; }
 __device__ __forceinline__ Unit unit_of(const Tiles& t, int u, int nk) {
   Unit r;
   r.tile = u;
-  r.z = u / (t.grid_n * t.grid_m);
+  r.z = u / tiles_per_split(t);
+  if (t.lower) {   // v-th lower tile: row mt with mt (mt + 1) / 2 <= v, column v - mt (mt + 1) / 2
+    const int v = u - r.z * tiles_per_split(t);
+    int mt = (int)((sqrtf(8.0f * (float)v + 1.0f) - 1.0f) * 0.5f);
+    while ((mt + 1) * (mt + 2) / 2 <= v) ++mt;
+    while (mt * (mt + 1) / 2 > v) --mt;
+    r.tile = mt * t.grid_n + (v - mt * (mt + 1) / 2);   // same encoding as a full grid
+  }
   if (t.mkr) {
     const int2 kr = t.mkr[(u / t.grid_n) % t.grid_m];
     r.kb = kr.x;
