@@ -456,6 +456,19 @@ ibmi_status mixed_run(ibmi_plan_s* P, const double* A, int64_t lda, double* H, i
     *flops += fr;
     return refine_read(R, st, acc);
   };
+  // Before a radius test: digit groups q <= 7 (36 of 52 pair products) give
+  // Q = I - X A to about 2^-56 of |X| |A| sqrt(p), ample for the radius and for
+  // a first Newton-Schulz step; a value at or below tol is certified in full.
+  auto reduced = [&](double* acc) -> ibmi_status {
+    IBMI_TRY(graph_or_run(M, &M->g_export_resid_ns0, st, [&]() -> ibmi_status {
+      IBMI_TRY(mixed_export_launch(P, H, ldh, st));
+      return refine_residual_launch(R, H, ldh, st, kNs0Groups);
+    }));
+    *flops += fr * kNs0Pairs / 52.0;
+    IBMI_TRY(refine_read(R, st, acc));
+    if (*acc <= d.tol) IBMI_TRY(accurate(acc));
+    return IBMI_OK;
+  };
   // Sweeps, then the Newton-Schulz tail; a tail entered early that fails
   // returns here.
   for (;;) {
@@ -492,7 +505,7 @@ ibmi_status mixed_run(ibmi_plan_s* P, const double* A, int64_t lda, double* H, i
       if (d.ns_theta > 0.0 && p >= kEarlyMinOrder && rho * sqrtp <= 16.0 * d.ns_theta &&
           rho <= next_radius_test && cad.sweeps_to(rho, d.ns_theta / sqrtp) > slow_sweeps) {
         double acc, rad;
-        IBMI_TRY(accurate(&acc));
+        IBMI_TRY(reduced(&acc));
         res->resid_f = acc;
         if (acc <= d.tol) return IBMI_OK;
         IBMI_TRY(graph_or_run(M, &M->g_radius, st, [&]() { return refine_q_radius_launch(R, kRadiusIters, st); }));
@@ -532,7 +545,7 @@ ibmi_status mixed_run(ibmi_plan_s* P, const double* A, int64_t lda, double* H, i
           // ||I - A H||_F bounds the spectral radius of I - X A that
           // eq. newton needs from above, often by far; measure the radius.
           double acc, rad;
-          IBMI_TRY(accurate(&acc));
+          IBMI_TRY(reduced(&acc));
           res->resid_f = acc;
           if (acc <= d.tol) return IBMI_OK;
           IBMI_TRY(graph_or_run(M, &M->g_radius, st, [&]() { return refine_q_radius_launch(R, kRadiusIters, st); }));
@@ -565,13 +578,7 @@ ibmi_status mixed_run(ibmi_plan_s* P, const double* A, int64_t lda, double* H, i
         // Newton-Schulz corrects the error of one step in the next, and the
         // residual that certifies tol is always the full one.  Digit groups
         // q <= 7 (36 of 52 pair products) leave about 2^-56 of |X| |A| sqrt(p).
-        IBMI_TRY(graph_or_run(M, &M->g_export_resid_ns0, st, [&]() -> ibmi_status {
-          IBMI_TRY(mixed_export_launch(P, H, ldh, st));
-          return refine_residual_launch(R, H, ldh, st, kNs0Groups);
-        }));
-        *flops += fr * kNs0Pairs / 52.0;
-        IBMI_TRY(refine_read(R, st, &rho));
-        if (rho <= d.tol) IBMI_TRY(accurate(&rho));   // certify with the full residual
+        IBMI_TRY(reduced(&rho));
       } else if (prev * prev > 1e3 * d.tol) {
         // rho is about prev^2 here, far above tol: groups q <= 8 (44 pairs) are
         // enough for a step that another step will follow
