@@ -36,23 +36,32 @@ struct F64Operands {
   bool lower_tiles = false;
 };
 
+// Threads of a T x T tile: a 4 x 4 register block per thread for T = 64 and
+// 4 x 2 for T = 32, so that a 32 x 32 tile runs four warps, one per SM
+// partition (each partition's FP64 pipe takes about one FMA every other
+// clock; two warps would leave half of the SM's DFMA rate idle when a small
+// launch has one CTA per SM).
+template <int T>
+constexpr int f64_threads() { return (T / 4) * (T / (T == 64 ? 4 : 2)); }
+
 template <bool A_KMAJOR, bool B_NMAJOR, class Epi, int T = F64_BM>
-__global__ void __launch_bounds__((T / 4) * (T / 4))
+__global__ void __launch_bounds__(f64_threads<T>())
 k_gemm_f64(F64Operands op, Epi epi) {
-  // T x T output tile, (T/4)^2 threads with a 4 x 4 register block each.
-  constexpr int NT = (T / 4) * (T / 4), Q = T / 4;
+  // T x T output tile; thread (ty, tx) owns rows ty + QX x and columns tx + QY y.
+  constexpr int RX = 4, RY = T == 64 ? 4 : 2, QX = T / RX, QY = T / RY, NT = QX * QY;
+  static_assert(NT == f64_threads<T>() && T * F64_BK % NT == 0, "tile / thread layout");
   __shared__ double As[F64_BK][T + 1];
   __shared__ double Bs[F64_BK][T + 1];
-  const int tx = threadIdx.x % Q, ty = threadIdx.x / Q;
+  const int tx = threadIdx.x % QY, ty = threadIdx.x / QY;
   const int64_t i0 = (int64_t)blockIdx.y * T, j0 = (int64_t)blockIdx.x * T;
   if (op.lower_tiles && j0 >= i0 + T) return;
   op.A += blockIdx.z * op.zA;
   op.B += blockIdx.z * op.zB;
-  double acc[4][4];
+  double acc[RX][RY];
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+  for (int a = 0; a < RX; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+    for (int b = 0; b < RY; ++b) acc[a][b] = 0.0;
 
   const int64_t lstart = op.tri_k ? (i0 > j0 ? i0 : j0) / F64_BK * F64_BK : 0;
   for (int64_t l0 = lstart; l0 < op.K; l0 += F64_BK) {
@@ -82,22 +91,24 @@ k_gemm_f64(F64Operands op, Epi epi) {
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < F64_BK; ++k) {
-      double a[4], b[4];
+      double a[RX], b[RY];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) { a[q] = As[k][ty + Q * q]; b[q] = Bs[k][tx + Q * q]; }
+      for (int q = 0; q < RX; ++q) a[q] = As[k][ty + QX * q];
 #pragma unroll
-      for (int x = 0; x < 4; ++x)
+      for (int q = 0; q < RY; ++q) b[q] = Bs[k][tx + QY * q];
 #pragma unroll
-        for (int y = 0; y < 4; ++y) acc[x][y] = fma(a[x], b[y], acc[x][y]);
+      for (int x = 0; x < RX; ++x)
+#pragma unroll
+        for (int y = 0; y < RY; ++y) acc[x][y] = fma(a[x], b[y], acc[x][y]);
     }
     __syncthreads();
   }
   epi.begin();
 #pragma unroll
-  for (int x = 0; x < 4; ++x)
+  for (int x = 0; x < RX; ++x)
 #pragma unroll
-    for (int y = 0; y < 4; ++y) {
-      int64_t i = i0 + ty + Q * x, j = j0 + tx + Q * y;
+    for (int y = 0; y < RY; ++y) {
+      int64_t i = i0 + ty + QX * x, j = j0 + tx + QY * y;
       if (i < op.M && j < op.N) epi(i, j, acc[x][y]);
     }
   epi.end();
@@ -199,11 +210,12 @@ inline cudaError_t launch_gemm_f64(const F64Operands& op, const Epi& epi, cudaSt
     // on one SM; 32 x 32 tiles quarter that critical path
     if (tiles64 < F64_SMALL_LAUNCH || op.tri_k) {
       dim3 grid((unsigned)((op.N + 31) / 32), (unsigned)((op.M + 31) / 32), (unsigned)op.batch);
-      k_gemm_f64<A_KMAJOR, B_NMAJOR, Epi, 32><<<grid, 64, 0, st>>>(op, epi);
+      k_gemm_f64<A_KMAJOR, B_NMAJOR, Epi, 32><<<grid, f64_threads<32>(), 0, st>>>(op, epi);
       return cudaGetLastError();
     }
   }
   dim3 grid((unsigned)((op.N + F64_BN - 1) / F64_BN), (unsigned)((op.M + F64_BM - 1) / F64_BM), (unsigned)op.batch);
+  static_assert(f64_threads<F64_BM>() == F64_THREADS, "EpiResidual reduces over F64_THREADS");
   k_gemm_f64<A_KMAJOR, B_NMAJOR, Epi><<<grid, F64_THREADS, 0, st>>>(op, epi);
   return cudaGetLastError();
 }

@@ -175,8 +175,10 @@ ibmi_status invariants_all(ibmi_plan_s* P, const double* A, int64_t lda, bool fu
       F64Operands op = bat(F64Operands{panel, mmax, id, id, Li, jb, id, id, rest, jb, jb}, zL, zLi);
       IBMI_CUDA_TRY((launch_gemm_f64<true, false>(op, EpiStore{panel, mmax, 1.0, 0.0, zL}, st)));
     }
-    {  // trailing -= panel panel^T
+    {  // trailing -= panel panel^T, on the tiles that touch the lower triangle
+       // (the factorisation and the solves read nothing above the diagonal)
       F64Operands op = bat(F64Operands{panel, mmax, id, id, panel, mmax, id, id, rest, rest, jb}, zL, zL);
+      op.lower_tiles = true;
       IBMI_CUDA_TRY((launch_gemm_f64<true, false>(op, EpiStore{panel + jb, mmax, -1.0, 1.0, zL}, st)));
     }
   }
