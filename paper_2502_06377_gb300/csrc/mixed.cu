@@ -5,6 +5,7 @@
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
+#include <map>
 #include <mutex>
 
 #include "mixed.cuh"
@@ -47,8 +48,8 @@ bool make_map_bf16(CUtensorMap* map, const void* base, int64_t rows, int64_t col
 
 constexpr int MX_BN = 128;   // N tile of the sweep products
 constexpr int kRadiusIters = 40;            // power-iteration steps of the radius estimate
-constexpr int kNs0Groups = 7;               // digit groups of the first Newton-Schulz residual
-constexpr double kNs0Pairs = 36.0;          // its pair products (all pairs of groups 0..7)
+constexpr int kNsFirstGroups = 5;           // digit groups of a residual before the tail is calibrated
+constexpr double kNsGrowth = 16.0;          // pessimistic rho_{k+1} / rho_k^2 of a Newton-Schulz step
 constexpr double kEarlyHandOver = 0.6;      // radius below which slow sweeps hand over early
 constexpr int64_t kEarlyMinOrder = 2048;    // smallest order for that test
 constexpr int64_t kTcInverseMinOrder = 1024;   // block order from which Y^T Y runs on the tensor cores
@@ -79,18 +80,70 @@ struct MixedState {
   bool graphs = false;
   const double* gA = nullptr;
   const double* gH = nullptr;
-  PhaseGraph g_setup, g_sweep[2], g_cheap, g_reslice, g_export_resid, g_export_resid_ns0, g_resid, g_resid_q8, g_update,
-      g_radius;
+  PhaseGraph g_setup, g_sweep[2], g_cheap, g_reslice, g_export_resid, g_update, g_radius;
+  std::map<int, PhaseGraph> g_tail;      // tail residuals by digit groups (see ns_graph_key)
 };
 
 static void drop_graphs(MixedState* M) {
   for (PhaseGraph* g : {&M->g_setup, &M->g_sweep[0], &M->g_sweep[1], &M->g_cheap, &M->g_reslice,
-                        &M->g_export_resid, &M->g_export_resid_ns0, &M->g_resid, &M->g_resid_q8, &M->g_update,
-                        &M->g_radius}) {
+                        &M->g_export_resid, &M->g_update, &M->g_radius}) {
     if (g->exec) cudaGraphExecDestroy(g->exec);
     *g = PhaseGraph{};
   }
+  for (auto& kv : M->g_tail)
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+  M->g_tail.clear();
 }
+
+// ---------------------------------------------- Newton-Schulz tail plan ----
+//
+// With Q = I - X A exact, a step (eq. newton) leaves E' = E^2 (E = I - A X).
+// A residual that keeps digit groups q <= qc carries the truncation error D
+// of the groups left out, about 2^-7 of the norm g of group qc's part (each
+// group's part is about 2^-7 of the one before; g is measured with the
+// residual).  The step X + X (Q + D)^T, made symmetric, leaves
+// E' = E^2 - (D^T + A D X) / 2: for an unstructured D the second term is
+// about ||A||_F ||X||_F / p times D (also measured; 60 to 8000 on the
+// benchmark's matrices, and this is what the measured floors follow).  The
+// error only has to stay below what the steps still to come square away.
+
+// pair products of digit groups 0..q
+static int ns_pairs(int q) {
+  int n = 0;
+  for (int g = 0; g <= q; ++g)
+    for (int s = 0; s <= g; ++s)
+      if (s < OZ_SX && g - s < OZ_SA) ++n;
+  return n;
+}
+// error (in rho) a step takes from a residual of groups <= q, from g measured
+// at group qc and amp = ||A||_F ||X||_F / p, with a factor 2 of margin
+static double ns_floor(int q, double g, int qc, double amp) {
+  return 2.0 * g * ldexp(1.0, -7 * (q + 1 - qc)) * (1.0 + 0.5 * amp);
+}
+// steps from rho to rho <= tol / 4 if each one squares it (the optimistic count)
+static int ns_steps(double rho, double tol) {
+  int n = 0;
+  for (double r = rho; r > 0.25 * tol && n < 12; r *= r) ++n;
+  return n < 1 ? 1 : n;
+}
+// largest rho from which k steps reach tol / 4 when each multiplies rho^2 by kNsGrowth
+static double ns_bound(int k, double tol) {
+  double b = 0.25 * tol;
+  for (int i = 0; i < k; ++i) b = sqrt(b / kNsGrowth);
+  return b;
+}
+// truncation error allowed in the residual that feeds the step from rho: half
+// of the bound for the steps that follow it
+static double ns_target(double rho, double tol) { return 0.5 * ns_bound(ns_steps(rho, tol) - 1, tol); }
+// fewest groups (>= NS_S - 1, which the update's digits of X need) within `target`
+static int ns_groups_for(double target, double g, int qc, double amp) {
+  for (int q = NS_S - 1; q < OZ_QMAX; ++q)
+    if (ns_floor(q, g, qc, amp) <= target) return q;
+  return OZ_QMAX;
+}
+// graph keys of the tail's residuals: (export of H first, groups) and extensions (from, to)
+static int ns_graph_key(bool export_h, int q) { return (export_h ? 100 : 0) + q; }
+static int ns_extend_key(int qfrom, int qto) { return 200 + 10 * qfrom + qto; }
 
 // Runs `body` (kernel launches only, no host synchronisation) directly, or in
 // graph mode captures it once into *g and replays the graph.  While per-class
@@ -440,6 +493,7 @@ ibmi_status mixed_run(ibmi_plan_s* P, const double* A, int64_t lda, double* H, i
   double next_radius_test = INFINITY;   // slow convergence: rho below which the radius is measured again
   double handover_below = INFINITY;     // after a failed tail: rho below which the next hand-over may come
   double handover_rho = 0.0;            // rho of the stop test that handed over
+  double last_cheap = INFINITY;         // rho of the last stop test of the sweeps
   // sweeps whose cost matches about two tail steps (time ratio of a step to a
   // sweep ~ 8.4 fr / fs, from the measured rates of the two kinds of product)
   const double slow_sweeps = 2.0 * 8.4 * fr / std::max(fs, 1.0);
@@ -456,17 +510,37 @@ ibmi_status mixed_run(ibmi_plan_s* P, const double* A, int64_t lda, double* H, i
     *flops += fr;
     return refine_read(R, st, acc);
   };
-  // Before a radius test: digit groups q <= 7 (36 of 52 pair products) give
-  // Q = I - X A to about 2^-56 of |X| |A| sqrt(p), ample for the radius and for
-  // a first Newton-Schulz step; a value at or below tol is certified in full.
-  auto reduced = [&](double* acc) -> ibmi_status {
-    IBMI_TRY(graph_or_run(M, &M->g_export_resid_ns0, st, [&]() -> ibmi_status {
-      IBMI_TRY(mixed_export_launch(P, H, ldh, st));
-      return refine_residual_launch(R, H, ldh, st, kNs0Groups);
+  // A residual of the tail with digit groups <= q (exporting H first when
+  // the sweeps just left it): its rho, the norm of group q's part and
+  // ||A||_F ||X||_F / p.
+  auto tail_residual = [&](bool export_h, int q, double* rho, double* g, double* amp) -> ibmi_status {
+    IBMI_TRY(graph_or_run(M, &M->g_tail[ns_graph_key(export_h, q)], st, [&]() -> ibmi_status {
+      if (export_h) IBMI_TRY(mixed_export_launch(P, H, ldh, st));
+      return refine_residual_launch(R, H, ldh, st, q);
     }));
-    *flops += fr * kNs0Pairs / 52.0;
-    IBMI_TRY(refine_read(R, st, acc));
-    if (*acc <= d.tol) IBMI_TRY(accurate(acc));
+    *flops += fr * ns_pairs(q) / ns_pairs(OZ_QMAX);
+    return refine_read_groups(R, st, rho, g, amp);
+  };
+  // The same residual extended from groups <= qfrom to <= qto (only the new
+  // groups' pair products run).
+  auto tail_extend = [&](int qfrom, int qto, double* rho, double* g, double* amp) -> ibmi_status {
+    IBMI_TRY(graph_or_run(M, &M->g_tail[ns_extend_key(qfrom, qto)], st,
+                          [&]() { return refine_residual_extend_launch(R, H, ldh, st, qfrom, qto); }));
+    *flops += fr * (ns_pairs(qto) - ns_pairs(qfrom)) / ns_pairs(OZ_QMAX);
+    return refine_read_groups(R, st, rho, g, amp);
+  };
+  // Before a radius test: kNsFirstGroups groups give Q ample for the radius
+  // and, if the tail starts, for its first step (checked there); a value at
+  // or below tol is certified with all groups.
+  double pending_g = NAN, pending_amp = NAN;
+  int pending_q = 0;
+  auto reduced = [&](double* acc) -> ibmi_status {
+    pending_q = kNsFirstGroups;
+    IBMI_TRY(tail_residual(true, pending_q, acc, &pending_g, &pending_amp));
+    if (*acc <= d.tol) {
+      IBMI_TRY(tail_extend(pending_q, OZ_QMAX, acc, &pending_g, &pending_amp));
+      pending_q = OZ_QMAX;
+    }
     return IBMI_OK;
   };
   // Sweeps, then the Newton-Schulz tail; a tail entered early that fails
@@ -488,6 +562,7 @@ ibmi_status mixed_run(ibmi_plan_s* P, const double* A, int64_t lda, double* H, i
       IBMI_TRY(refine_read(R, st, &rho));
       *flops += fr;
       res->resid_f = rho;
+      last_cheap = rho;
       if (!isfinite(rho)) return IBMI_ERR_NONFINITE;
       if (d.ns_theta > 0.0 && rho * sqrtp <= d.ns_theta && rho <= handover_below) {
         early = true;   // a failing tail returns to the sweeps
@@ -568,32 +643,35 @@ ibmi_status mixed_run(ibmi_plan_s* P, const double* A, int64_t lda, double* H, i
       }
       cad.after(r, rho, target);
     }
-    double prev = INFINITY;
+    double prev = INFINITY, prev_floor = 0.0;
+    double gcal = NAN, acal = NAN;   // calibration: norm of the last group of the last residual,
+    int qcal = -1;                   // that group and ||A||_F ||X||_F / p
     for (int s = 0;; ++s) {
-      double rho;
+      double rho, g, amp;
+      int qc;
       if (s == 0 && !isnan(pending)) {
         rho = pending;
-      } else if (s == 0) {
-        // The first step's residual only has to be small against rho^2 / kappa:
-        // Newton-Schulz corrects the error of one step in the next, and the
-        // residual that certifies tol is always the full one.  Digit groups
-        // q <= 7 (36 of 52 pair products) leave about 2^-56 of |X| |A| sqrt(p).
-        IBMI_TRY(reduced(&rho));
-      } else if (prev * prev > 1e3 * d.tol) {
-        // rho is about prev^2 here, far above tol: groups q <= 8 (44 pairs) are
-        // enough for a step that another step will follow
-        IBMI_TRY(graph_or_run(M, &M->g_resid_q8, st, [&]() { return refine_residual_launch(R, H, ldh, st, 8); }));
-        *flops += fr * 44.0 / 52.0;
-        IBMI_TRY(refine_read(R, st, &rho));
-        if (rho <= d.tol) {   // certify with the full residual
-          IBMI_TRY(graph_or_run(M, &M->g_resid, st, [&]() { return refine_residual_launch(R, H, ldh, st); }));
-          *flops += fr;
-          IBMI_TRY(refine_read(R, st, &rho));
-        }
+        g = pending_g;
+        amp = pending_amp;
+        qc = pending_q;
       } else {
-        IBMI_TRY(graph_or_run(M, &M->g_resid, st, [&]() { return refine_residual_launch(R, H, ldh, st); }));
-        *flops += fr;
-        IBMI_TRY(refine_read(R, st, &rho));
+        // all groups where this residual is expected to certify tol; else
+        // enough for the step it feeds, judged from the rho it should show
+        const double rho_hat = s == 0 ? last_cheap : std::max(prev * prev, prev_floor);
+        qc = rho_hat <= d.tol ? OZ_QMAX
+             : qcal < 0       ? kNsFirstGroups
+                              : ns_groups_for(ns_target(rho_hat, d.tol), gcal, qcal, acal);
+        IBMI_TRY(tail_residual(s == 0, qc, &rho, &g, &amp));
+      }
+      // a value at or below tol is certified with all groups; a step needs
+      // the truncation error within its target (both extend the same residual)
+      for (;;) {
+        int qn = qc;
+        if (rho <= d.tol || !isfinite(rho)) qn = isfinite(rho) ? OZ_QMAX : qc;
+        else qn = std::max(qc, ns_groups_for(ns_target(rho, d.tol), g, qc, amp));
+        if (qn == qc) break;
+        IBMI_TRY(tail_extend(qc, qn, &rho, &g, &amp));
+        qc = qn;
       }
       res->resid_f = rho;
       if (!isfinite(rho)) return IBMI_ERR_NONFINITE;
@@ -605,6 +683,10 @@ ibmi_status mixed_run(ibmi_plan_s* P, const double* A, int64_t lda, double* H, i
         }
         return IBMI_NOT_CONVERGED;
       }
+      gcal = g;
+      acal = amp;
+      qcal = qc;
+      prev_floor = ns_floor(qc, g, qc, amp);
       prev = rho;
       IBMI_TRY(graph_or_run(M, &M->g_update, st, [&]() { return refine_ns_update(R, H, ldh, st); }));
       *flops += fr;

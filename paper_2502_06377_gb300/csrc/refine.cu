@@ -23,8 +23,10 @@ struct SlicePtrs {
   __nv_bfloat16* s[OZ_S];
 };
 
+// rowsq (optional): sum over the row of (x 2^-e)^2 in float, so that the
+// row's squared norm is rowsq 2^(2e) (integer and float operations only).
 __global__ void k_oz_slices(const double* X, int64_t ldx, int64_t ncols, int64_t c0, int64_t ldp, SlicePtrs out,
-                            int nslices, int* expo) {
+                            int nslices, int* expo, float* rowsq) {
   const int64_t i = blockIdx.x;
   const double* row = X + i * ldx;
   // row maximum of |x| on the bit patterns (integer order = order of |x|)
@@ -50,6 +52,7 @@ __global__ void k_oz_slices(const double* X, int64_t ldx, int64_t ncols, int64_t
   if (threadIdx.x == 0) expo[i] = nonfinite ? OZ_NONFINITE_EXP : e;
   // F = rint(x 2^{55-e}) and Flo = the remainder carried 14 bits further,
   // from the bit pattern of x with integer operations only (no FP64 ALU).
+  float sq = 0.f;
   for (int64_t c = threadIdx.x; c < ldp; c += blockDim.x) {
     long long F = 0, Flo = 0;
     if (c >= c0 && c < c0 + ncols) {
@@ -59,6 +62,10 @@ __global__ void k_oz_slices(const double* X, int64_t ldx, int64_t ncols, int64_t
       if (ex != 0 && !nonfinite) {   // zeros and subnormals are far below 2^(e-69)
         const unsigned long long m = (bits & 0xfffffffffffffull) | 0x10000000000000ull;   // 53-bit significand
         const int sh = ex - 1075 + 55 - e;   // x 2^{55-e} = m 2^sh, sh <= 2 because |x| < 2^e
+        if (rowsq) {   // |x| 2^-e ~ (m >> 29) 2^(ex - 1046 - e), 24 bits
+          const float xs = ldexpf((float)(m >> 29), ex - 1046 - e);
+          sq += xs * xs;
+        }
         long long qq = 0, lo14 = 0;
         if (sh >= 0) {
           qq = (long long)(m << sh);
@@ -105,6 +112,17 @@ __global__ void k_oz_slices(const double* X, int64_t ldx, int64_t ncols, int64_t
         }
         out.s[s][i * ldp + c] = __int2bfloat16_rn((int)d);
       }
+    }
+  }
+  if (rowsq) {   // the same for every thread of the block
+    __shared__ float sred[32];
+    for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+    if ((threadIdx.x & 31) == 0) sred[threadIdx.x >> 5] = sq;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float t = 0.f;
+      for (int w = 0; w < (int)(blockDim.x / 32); ++w) t += sred[w];
+      rowsq[i] = t;
     }
   }
 }
@@ -228,13 +246,20 @@ __device__ __forceinline__ double oz_value(const int* T, int64_t plane, int64_t 
 }
 
 // C = 2^{e_i + f_j - 12} sum_q T_q 2^{-7q};  Q = I - C (FP64, ld p);
-// sum Q^2 per CTA.
+// sum Q^2 per CTA, and (second half of `partials`) the sum of squares of the
+// last group's part 2^{e_i + f_j - 12 - 7 qmax} T_qmax, whose norm scales the
+// truncation error of the groups left out.
 __global__ void k_oz_combine(const int* T, int64_t p, int64_t ldp, const int* ex, const int* ea, int qmax,
                              double* Q, double* partials) {
   const int64_t i = blockIdx.y, j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  float sq = 0.f;
+  float sq = 0.f, gq = 0.f;
   if (j < p) {
-    const double c = oz_value(T, p * ldp, i * ldp + j, qmax, ex[i] + ea[j] - 12);
+    const int e = ex[i] + ea[j] - 12;
+    const double c = oz_value(T, p * ldp, i * ldp + j, qmax, e);
+    // float is ample for a norm estimate: parts below ~1e-19 underflow to 0
+    // (far below any tolerance) and an overflow reads as an infinite norm
+    const float g = ldexpf((float)T[(int64_t)qmax * p * ldp + i * ldp + j], e - 7 * qmax);
+    gq = g * g;
     // off the diagonal Q = -c is a sign flip; the squares for rho need only
     // float precision (FP64 arithmetic is scarce on this GPU)
     const double q = i == j ? 1.0 - c : ozr_bits_to_double(ozr_double_to_bits(c) ^ 0x8000000000000000ull);
@@ -242,28 +267,73 @@ __global__ void k_oz_combine(const int* T, int64_t p, int64_t ldp, const int* ex
     sq = qf * qf;
     Q[i * p + j] = q;
   }
-  __shared__ double red[8];
-  for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (double)sq;
+  __shared__ double red[8], redg[8];
+  for (int o = 16; o > 0; o >>= 1) {
+    sq += __shfl_xor_sync(0xffffffffu, sq, o);
+    gq += __shfl_xor_sync(0xffffffffu, gq, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[threadIdx.x >> 5] = (double)sq;
+    redg[threadIdx.x >> 5] = (double)gq;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int w = 0; w < (int)(blockDim.x / 32); ++w) t += red[w];
-    partials[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = t;
+    double t = 0.0, tg = 0.0;
+    for (int w = 0; w < (int)(blockDim.x / 32); ++w) {
+      t += red[w];
+      tg += redg[w];
+    }
+    const int64_t b = (int64_t)blockIdx.y * gridDim.x + blockIdx.x, nb = (int64_t)gridDim.x * gridDim.y;
+    partials[b] = t;
+    partials[nb + b] = tg;
   }
 }
 
-__global__ void k_sum_partials(const double* partials, int64_t n, int64_t p, double* out) {
+// out[k] = sqrt(sum of partials[k n .. (k + 1) n)) / sqrt(p) for k < nout;
+// with row data of X and A (sqx: sum of (x 2^-ex)^2 per row), also
+// out[2] = ||X||_F ||A||_F / p.
+__global__ void k_sum_partials(const double* partials, int64_t n, int64_t p, double* out, int nout = 1,
+                               const float* sqx = nullptr, const int* ex = nullptr, const float* sqa = nullptr,
+                               const int* ea = nullptr) {
   __shared__ double red[32];
-  double s = 0.0;
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += partials[i];
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int w = 0; w < (int)(blockDim.x / 32); ++w) t += red[w];
-    out[0] = sqrt(t) / sqrt((double)p);
+  if (sqx) {
+    double sx = 0.0, sa = 0.0;
+    for (int64_t i = threadIdx.x; i < p; i += blockDim.x) {
+      sx += ldexp((double)sqx[i], 2 * ex[i]);
+      sa += ldexp((double)sqa[i], 2 * ea[i]);
+    }
+    __shared__ double red2[32];
+    for (int o = 16; o > 0; o >>= 1) {
+      sx += __shfl_xor_sync(0xffffffffu, sx, o);
+      sa += __shfl_xor_sync(0xffffffffu, sa, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      red[threadIdx.x >> 5] = sx;
+      red2[threadIdx.x >> 5] = sa;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double tx = 0.0, ta = 0.0;
+      for (int w = 0; w < (int)(blockDim.x / 32); ++w) {
+        tx += red[w];
+        ta += red2[w];
+      }
+      out[2] = sqrt(tx) * sqrt(ta) / (double)p;
+    }
+    __syncthreads();
+  }
+  for (int k = 0; k < nout; ++k) {
+    double s = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += partials[k * n + i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < (int)(blockDim.x / 32); ++w) t += red[w];
+      out[k] = sqrt(t) / sqrt((double)p);
+    }
+    __syncthreads();
   }
 }
 
@@ -374,10 +444,10 @@ ibmi_status refine_create(RefineState* R, int64_t p, int* err) {
   const int64_t ldp = R->ldp;
   const size_t plane16 = sizeof(__nv_bfloat16) * p * ldp;
   const int64_t tiles = ((p + 127) / 128) * ((p + RF_BN - 1) / RF_BN);
-  R->n_partials = std::max<int64_t>(tiles * 4, p * ((p + 255) / 256)) + 8;
+  R->n_partials = std::max<int64_t>(tiles * 4, 2 * p * ((p + 255) / 256)) + 8;
   size_t bytes = plane16 * (OZ_SA + OZ_SX + NS_S + 2) + sizeof(int) * (size_t)(OZ_QMAX + 1) * p * ldp +
                  sizeof(double) * p * p + sizeof(double) * R->n_partials + 3 * sizeof(int) * p +
-                 sizeof(double) * (2 * p + 8) + 64 * 256;
+                 sizeof(double) * (2 * p + 8) + 2 * sizeof(float) * p + 64 * 256;
   if (cudaMalloc(&R->pool, bytes) != cudaSuccess) {
     cudaGetLastError();
     return IBMI_ERR_OOM;
@@ -396,6 +466,8 @@ ibmi_status refine_create(RefineState* R, int64_t p, int* err) {
   R->expX = (int*)take(sizeof(int) * p);
   R->expQ = (int*)take(sizeof(int) * p);
   R->pv = (double*)take(sizeof(double) * (2 * p + 8));
+  R->sqA = (float*)take(sizeof(float) * p);
+  R->sqX = (float*)take(sizeof(float) * p);
   bool ok = true;
   R->bn = oz_bn_for(p);
   for (int s = 0; s < OZ_SA; ++s) ok &= tc::make_map_bf16(&R->mAo[s], R->Ao[s], p, p, ldp, R->bn);
@@ -415,20 +487,21 @@ void refine_destroy(RefineState* R) {
 }
 
 static ibmi_status slice_digits(RefineState* R, const double* X, int64_t ldx, __nv_bfloat16* const* dst, int nslices,
-                                int* expo, cudaStream_t st, int64_t rows = -1, int64_t ncols = -1, int64_t c0 = 0) {
+                                int* expo, cudaStream_t st, int64_t rows = -1, int64_t ncols = -1, int64_t c0 = 0,
+                                float* rowsq = nullptr) {
   SlicePtrs sp;
   for (int s = 0; s < OZ_S; ++s) sp.s[s] = s < nslices ? dst[s] : nullptr;
   if (rows < 0) rows = R->p;
   if (ncols < 0) ncols = R->p;
   note_launch();
-  k_oz_slices<<<(unsigned)rows, 256, 0, st>>>(X, ldx, ncols, c0, R->ldp, sp, nslices, expo);
+  k_oz_slices<<<(unsigned)rows, 256, 0, st>>>(X, ldx, ncols, c0, R->ldp, sp, nslices, expo, rowsq);
   IBMI_CUDA_TRY(cudaGetLastError());
   return IBMI_OK;
 }
 
 ibmi_status refine_set_matrix(RefineState* R, const double* A, int64_t lda, cudaStream_t st) {
   ProfScope ps(IBMI_K_OTHER, st, 0.0);
-  IBMI_TRY(slice_digits(R, A, lda, R->Ao, OZ_SA, R->expA, st));
+  IBMI_TRY(slice_digits(R, A, lda, R->Ao, OZ_SA, R->expA, st, -1, -1, 0, R->sqA));
   note_launch();
   k_fsplit2<<<grid2(R->ldp, R->p), 256, 0, st>>>(A, lda, R->p, R->ldp, R->Af[0], R->Af[1]);
   IBMI_CUDA_TRY(cudaGetLastError());
@@ -492,18 +565,18 @@ static ibmi_status digit_gemm(RefineState* R, const DigitGemm& g, cudaStream_t s
   return IBMI_OK;
 }
 
-// All pairs (s, u) with s + u <= qmax of a p x p x p sliced product in one
-// persistent launch (k_oz_pairs), in group order so that the first pair of
-// each group stores and the others add.
+// All pairs (s, u) with qmin <= s + u <= qmax of a p x p x p sliced product in
+// one persistent launch (k_oz_pairs), in group order so that the first pair of
+// each group stores and the others add (groups below qmin are left as they are).
 static ibmi_status pair_products(RefineState* R, const CUtensorMap* ma, int nsa, const CUtensorMap* mb, int nsb,
-                                 int qmax, int kclass, cudaStream_t st) {
+                                 int qmax, int kclass, cudaStream_t st, int qmin = 0) {
   const int64_t p = R->p, ldp = R->ldp;
   tc::OzPairMaps maps;
   for (int s = 0; s < nsa; ++s) maps.a[s] = ma[s];
   for (int u = 0; u < nsb; ++u) maps.b[u] = mb[u];
   tc::OzPairArgs g{};
   int n = 0;
-  for (int q = 0; q <= qmax; ++q) {
+  for (int q = qmin; q <= qmax; ++q) {
     bool first = true;
     for (int s = 0; s <= q; ++s) {
       const int u = q - s;
@@ -663,6 +736,22 @@ ibmi_status refine_form_w_all(RefineState* R, const std::vector<const double*>& 
 
 ibmi_status refine_read(RefineState* R, cudaStream_t st, double* rho) { return read_scalar(R, st, rho); }
 
+ibmi_status refine_read_groups(RefineState* R, cudaStream_t st, double* rho, double* last_group, double* amp) {
+  double v[3];
+  int herr = 0;
+  IBMI_CUDA_TRY(cudaMemcpyAsync(v, R->dout, sizeof(v), cudaMemcpyDeviceToHost, st));
+  IBMI_CUDA_TRY(cudaMemcpyAsync(&herr, R->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  IBMI_CUDA_TRY(cudaStreamSynchronize(st));
+  if (herr != 0) {
+    set_last_error("tcgen05 kernel: bounded wait expired");
+    return IBMI_ERR_TIMEOUT;
+  }
+  *rho = v[0];
+  *last_group = v[1];
+  *amp = v[2];
+  return IBMI_OK;
+}
+
 ibmi_status refine_q_radius_launch(RefineState* R, int iters, cudaStream_t st) {
   const int64_t p = R->p;
   double* v = R->pv;
@@ -746,27 +835,45 @@ ibmi_status refine_residual(RefineState* R, const double* X, int64_t ldx, cudaSt
   return read_scalar(R, st, rho);
 }
 
+// Q = I - X A from the group sums q <= qmax, ||Q||_F / sqrt(p) and the norm of
+// group qmax's part into dout[0..1].
+static ibmi_status combine_residual(RefineState* R, int qmax, cudaStream_t st) {
+  const int64_t p = R->p, ldp = R->ldp;
+  ProfScope ps(IBMI_K_OTHER, st, 0.0);
+  const dim3 gc = grid2(p, p);
+  const int64_t nb = (int64_t)gc.x * gc.y;
+  if (2 * nb > R->n_partials) return IBMI_ERR_INVALID_ARG;
+  note_launch();
+  k_oz_combine<<<gc, 256, 0, st>>>(R->T, p, ldp, R->expX, R->expA, qmax, R->Xn, R->partials);
+  IBMI_CUDA_TRY(cudaGetLastError());
+  note_launch();
+  k_sum_partials<<<1, 1024, 0, st>>>(R->partials, nb, p, R->dout, 2, R->sqX, R->expX, R->sqA, R->expA);
+  IBMI_CUDA_TRY(cudaGetLastError());
+  return IBMI_OK;
+}
+
 ibmi_status refine_residual_launch(RefineState* R, const double* X, int64_t ldx, cudaStream_t st, int qmax) {
   const int64_t p = R->p, ldp = R->ldp;
   if (qmax < NS_S - 1 || qmax > OZ_QMAX) return IBMI_ERR_INVALID_ARG;
   const int nsx = std::min(OZ_SX, qmax + 1);   // digits of X that groups <= qmax use
   {
     ProfScope ps(IBMI_K_OTHER, st, 0.0);
-    IBMI_TRY(slice_digits(R, X, ldx, R->Xo, nsx, R->expX, st));
+    IBMI_TRY(slice_digits(R, X, ldx, R->Xo, nsx, R->expX, st, -1, -1, 0, R->sqX));
   }
   IBMI_TRY(pair_products(R, R->mXo, nsx, R->mAo, OZ_SA, qmax, IBMI_K_RESIDUAL, st));
-  {
+  return combine_residual(R, qmax, st);
+}
+
+ibmi_status refine_residual_extend_launch(RefineState* R, const double* X, int64_t ldx, cudaStream_t st, int qfrom,
+                                          int qto) {
+  if (qfrom < NS_S - 1 || qto <= qfrom || qto > OZ_QMAX) return IBMI_ERR_INVALID_ARG;
+  const int nsx_from = std::min(OZ_SX, qfrom + 1), nsx = std::min(OZ_SX, qto + 1);
+  if (nsx > nsx_from) {   // the digits are prefix-stable: the first nsx_from come out the same
     ProfScope ps(IBMI_K_OTHER, st, 0.0);
-    const dim3 gc = grid2(p, p);
-    const int64_t nb = (int64_t)gc.x * gc.y;
-    note_launch();
-    k_oz_combine<<<gc, 256, 0, st>>>(R->T, p, ldp, R->expX, R->expA, qmax, R->Xn, R->partials);
-    IBMI_CUDA_TRY(cudaGetLastError());
-    note_launch();
-    k_sum_partials<<<1, 1024, 0, st>>>(R->partials, nb, p, R->dout);
-    IBMI_CUDA_TRY(cudaGetLastError());
+    IBMI_TRY(slice_digits(R, X, ldx, R->Xo, nsx, R->expX, st));
   }
-  return IBMI_OK;
+  IBMI_TRY(pair_products(R, R->mXo, nsx, R->mAo, OZ_SA, qto, IBMI_K_RESIDUAL, st, qfrom + 1));
+  return combine_residual(R, qto, st);
 }
 
 ibmi_status refine_ns_update(RefineState* R, double* X, int64_t ldx, cudaStream_t st) {

@@ -43,6 +43,8 @@ struct RefineState {
   int64_t n_partials = 0;
   double* dout = nullptr;         // device scalars
   double* pv = nullptr;           // power-iteration vectors (2 p) and estimate
+  float* sqA = nullptr;           // per row of A and of the last residual's X: sum of (x 2^-e)^2
+  float* sqX = nullptr;
   int* err = nullptr;
   CUtensorMap mAo[OZ_SA], mXo[OZ_S], mQo[NS_S], mAf[2];
   CUtensorMap mXo_b[NS_S];        // the first X digit planes with BN-row boxes (as a right operand)
@@ -113,6 +115,15 @@ ibmi_status refine_form_w_all(RefineState* R, const std::vector<const double*>& 
 // update still finds its five digits of X).
 ibmi_status refine_residual_launch(RefineState* R, const double* X, int64_t ldx, cudaStream_t st,
                                    int qmax = OZ_QMAX);
+// Extends the last residual (of the same X, groups <= qfrom) to groups
+// <= qto: only the pair products of groups qfrom + 1 .. qto are added (the
+// digits of X are prefix-stable, so a wider slicing repeats the first ones).
+ibmi_status refine_residual_extend_launch(RefineState* R, const double* X, int64_t ldx, cudaStream_t st, int qfrom,
+                                          int qto);
+// rho of the last digit-sliced residual, the norm (/ sqrt(p)) of its last
+// digit group's part (the groups left out fall below it by about 2^-7 each)
+// and ||X||_F ||A||_F / p.
+ibmi_status refine_read_groups(RefineState* R, cudaStream_t st, double* rho, double* last_group, double* amp);
 // ||I - H A||_F / sqrt(p) from BF16x3 products, for H given by its BF16 hi/lo
 // slice maps (about 5 significant digits; the stop test of the sweeps and the
 // hand-over to Newton-Schulz); value read by refine_read.
