@@ -49,6 +49,8 @@ bool make_map_bf16(CUtensorMap* map, const void* base, int64_t rows, int64_t col
 constexpr int MX_BN = 128;   // N tile of the sweep products
 constexpr int kRadiusIters = 40;            // power-iteration steps of the radius estimate
 constexpr int kNsFirstGroups = 5;           // digit groups of a residual before the tail is calibrated
+constexpr int kNsFixedFirst = 7;            // below kEarlyMinOrder: groups of the first tail residual ...
+constexpr int kNsFixedNext = 8;             // ... and of the next ones while rho^2 > 1e3 tol
 constexpr double kNsGrowth = 16.0;          // pessimistic rho_{k+1} / rho_k^2 of a Newton-Schulz step
 constexpr double kEarlyHandOver = 0.6;      // radius below which slow sweeps hand over early
 constexpr int64_t kEarlyMinOrder = 2048;    // smallest order for that test
@@ -510,13 +512,18 @@ ibmi_status mixed_run(ibmi_plan_s* P, const double* A, int64_t lda, double* H, i
     *flops += fr;
     return refine_read(R, st, acc);
   };
+  // From order kEarlyMinOrder the tail plans its residuals' digit groups on
+  // the measured error model; below it launch latency, not the pair
+  // products, sets a residual's cost, and a fixed schedule (no extension
+  // round trips, few distinct graphs) does better.
+  const bool planned = p >= kEarlyMinOrder;
   // A residual of the tail with digit groups <= q (exporting H first when
   // the sweeps just left it): its rho, the norm of group q's part and
   // ||A||_F ||X||_F / p.
   auto tail_residual = [&](bool export_h, int q, double* rho, double* g, double* amp) -> ibmi_status {
     IBMI_TRY(graph_or_run(M, &M->g_tail[ns_graph_key(export_h, q)], st, [&]() -> ibmi_status {
       if (export_h) IBMI_TRY(mixed_export_launch(P, H, ldh, st));
-      return refine_residual_launch(R, H, ldh, st, q);
+      return refine_residual_launch(R, H, ldh, st, q, planned);
     }));
     *flops += fr * ns_pairs(q) / ns_pairs(OZ_QMAX);
     return refine_read_groups(R, st, rho, g, amp);
@@ -525,17 +532,18 @@ ibmi_status mixed_run(ibmi_plan_s* P, const double* A, int64_t lda, double* H, i
   // groups' pair products run).
   auto tail_extend = [&](int qfrom, int qto, double* rho, double* g, double* amp) -> ibmi_status {
     IBMI_TRY(graph_or_run(M, &M->g_tail[ns_extend_key(qfrom, qto)], st,
-                          [&]() { return refine_residual_extend_launch(R, H, ldh, st, qfrom, qto); }));
+                          [&]() { return refine_residual_extend_launch(R, H, ldh, st, qfrom, qto, planned); }));
     *flops += fr * (ns_pairs(qto) - ns_pairs(qfrom)) / ns_pairs(OZ_QMAX);
     return refine_read_groups(R, st, rho, g, amp);
   };
   // Before a radius test: kNsFirstGroups groups give Q ample for the radius
   // and, if the tail starts, for its first step (checked there); a value at
   // or below tol is certified with all groups.
+  const int q_first = planned ? kNsFirstGroups : kNsFixedFirst;
   double pending_g = NAN, pending_amp = NAN;
   int pending_q = 0;
   auto reduced = [&](double* acc) -> ibmi_status {
-    pending_q = kNsFirstGroups;
+    pending_q = q_first;
     IBMI_TRY(tail_residual(true, pending_q, acc, &pending_g, &pending_amp));
     if (*acc <= d.tol) {
       IBMI_TRY(tail_extend(pending_q, OZ_QMAX, acc, &pending_g, &pending_amp));
@@ -658,9 +666,9 @@ ibmi_status mixed_run(ibmi_plan_s* P, const double* A, int64_t lda, double* H, i
         // all groups where this residual is expected to certify tol; else
         // enough for the step it feeds, judged from the rho it should show
         const double rho_hat = s == 0 ? last_cheap : std::max(prev * prev, prev_floor);
-        qc = rho_hat <= d.tol ? OZ_QMAX
-             : qcal < 0       ? kNsFirstGroups
-                              : ns_groups_for(ns_target(rho_hat, d.tol), gcal, qcal, acal);
+        if (rho_hat <= d.tol) qc = OZ_QMAX;
+        else if (!planned) qc = s == 0 ? kNsFixedFirst : (prev * prev > 1e3 * d.tol ? kNsFixedNext : OZ_QMAX);
+        else qc = qcal < 0 ? kNsFirstGroups : ns_groups_for(ns_target(rho_hat, d.tol), gcal, qcal, acal);
         IBMI_TRY(tail_residual(s == 0, qc, &rho, &g, &amp));
       }
       // a value at or below tol is certified with all groups; a step needs
@@ -668,7 +676,7 @@ ibmi_status mixed_run(ibmi_plan_s* P, const double* A, int64_t lda, double* H, i
       for (;;) {
         int qn = qc;
         if (rho <= d.tol || !isfinite(rho)) qn = isfinite(rho) ? OZ_QMAX : qc;
-        else qn = std::max(qc, ns_groups_for(ns_target(rho, d.tol), g, qc, amp));
+        else if (planned) qn = std::max(qc, ns_groups_for(ns_target(rho, d.tol), g, qc, amp));
         if (qn == qc) break;
         IBMI_TRY(tail_extend(qc, qn, &rho, &g, &amp));
         qc = qn;
@@ -686,7 +694,7 @@ ibmi_status mixed_run(ibmi_plan_s* P, const double* A, int64_t lda, double* H, i
       gcal = g;
       acal = amp;
       qcal = qc;
-      prev_floor = ns_floor(qc, g, qc, amp);
+      prev_floor = planned ? ns_floor(qc, g, qc, amp) : 0.0;
       prev = rho;
       IBMI_TRY(graph_or_run(M, &M->g_update, st, [&]() { return refine_ns_update(R, H, ldh, st); }));
       *flops += fr;

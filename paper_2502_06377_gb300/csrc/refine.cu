@@ -835,9 +835,10 @@ ibmi_status refine_residual(RefineState* R, const double* X, int64_t ldx, cudaSt
   return read_scalar(R, st, rho);
 }
 
-// Q = I - X A from the group sums q <= qmax, ||Q||_F / sqrt(p) and the norm of
-// group qmax's part into dout[0..1].
-static ibmi_status combine_residual(RefineState* R, int qmax, cudaStream_t st) {
+// Q = I - X A from the group sums q <= qmax and ||Q||_F / sqrt(p) into
+// dout[0]; with `stats`, the norm of group qmax's part and ||X||_F ||A||_F / p
+// into dout[1..2] (the row sums of the last slicing of X).
+static ibmi_status combine_residual(RefineState* R, int qmax, bool stats, cudaStream_t st) {
   const int64_t p = R->p, ldp = R->ldp;
   ProfScope ps(IBMI_K_OTHER, st, 0.0);
   const dim3 gc = grid2(p, p);
@@ -847,25 +848,29 @@ static ibmi_status combine_residual(RefineState* R, int qmax, cudaStream_t st) {
   k_oz_combine<<<gc, 256, 0, st>>>(R->T, p, ldp, R->expX, R->expA, qmax, R->Xn, R->partials);
   IBMI_CUDA_TRY(cudaGetLastError());
   note_launch();
-  k_sum_partials<<<1, 1024, 0, st>>>(R->partials, nb, p, R->dout, 2, R->sqX, R->expX, R->sqA, R->expA);
+  if (stats)
+    k_sum_partials<<<1, 1024, 0, st>>>(R->partials, nb, p, R->dout, 2, R->sqX, R->expX, R->sqA, R->expA);
+  else
+    k_sum_partials<<<1, 1024, 0, st>>>(R->partials, nb, p, R->dout);
   IBMI_CUDA_TRY(cudaGetLastError());
   return IBMI_OK;
 }
 
-ibmi_status refine_residual_launch(RefineState* R, const double* X, int64_t ldx, cudaStream_t st, int qmax) {
+ibmi_status refine_residual_launch(RefineState* R, const double* X, int64_t ldx, cudaStream_t st, int qmax,
+                                   bool stats) {
   const int64_t p = R->p, ldp = R->ldp;
   if (qmax < NS_S - 1 || qmax > OZ_QMAX) return IBMI_ERR_INVALID_ARG;
   const int nsx = std::min(OZ_SX, qmax + 1);   // digits of X that groups <= qmax use
   {
     ProfScope ps(IBMI_K_OTHER, st, 0.0);
-    IBMI_TRY(slice_digits(R, X, ldx, R->Xo, nsx, R->expX, st, -1, -1, 0, R->sqX));
+    IBMI_TRY(slice_digits(R, X, ldx, R->Xo, nsx, R->expX, st, -1, -1, 0, stats ? R->sqX : nullptr));
   }
   IBMI_TRY(pair_products(R, R->mXo, nsx, R->mAo, OZ_SA, qmax, IBMI_K_RESIDUAL, st));
-  return combine_residual(R, qmax, st);
+  return combine_residual(R, qmax, stats, st);
 }
 
 ibmi_status refine_residual_extend_launch(RefineState* R, const double* X, int64_t ldx, cudaStream_t st, int qfrom,
-                                          int qto) {
+                                          int qto, bool stats) {
   if (qfrom < NS_S - 1 || qto <= qfrom || qto > OZ_QMAX) return IBMI_ERR_INVALID_ARG;
   const int nsx_from = std::min(OZ_SX, qfrom + 1), nsx = std::min(OZ_SX, qto + 1);
   if (nsx > nsx_from) {   // the digits are prefix-stable: the first nsx_from come out the same
@@ -873,7 +878,7 @@ ibmi_status refine_residual_extend_launch(RefineState* R, const double* X, int64
     IBMI_TRY(slice_digits(R, X, ldx, R->Xo, nsx, R->expX, st));
   }
   IBMI_TRY(pair_products(R, R->mXo, nsx, R->mAo, OZ_SA, qto, IBMI_K_RESIDUAL, st, qfrom + 1));
-  return combine_residual(R, qto, st);
+  return combine_residual(R, qto, stats, st);
 }
 
 ibmi_status refine_ns_update(RefineState* R, double* X, int64_t ldx, cudaStream_t st) {

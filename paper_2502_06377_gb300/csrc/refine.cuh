@@ -113,16 +113,19 @@ ibmi_status refine_form_w_all(RefineState* R, const std::vector<const double*>& 
 // absolute error of about 2^(e_X + e_A - 7 (qmax + 1)) sqrt(p), for a
 // Newton-Schulz step that does not need FP64 accuracy (qmax >= 4, so that the
 // update still finds its five digits of X).
+// stats: also the statistics refine_read_groups returns (else those two
+// values are undefined).
 ibmi_status refine_residual_launch(RefineState* R, const double* X, int64_t ldx, cudaStream_t st,
-                                   int qmax = OZ_QMAX);
+                                   int qmax = OZ_QMAX, bool stats = false);
 // Extends the last residual (of the same X, groups <= qfrom) to groups
 // <= qto: only the pair products of groups qfrom + 1 .. qto are added (the
 // digits of X are prefix-stable, so a wider slicing repeats the first ones).
+// stats needs the last full slicing of X to have been made with stats.
 ibmi_status refine_residual_extend_launch(RefineState* R, const double* X, int64_t ldx, cudaStream_t st, int qfrom,
-                                          int qto);
+                                          int qto, bool stats = false);
 // rho of the last digit-sliced residual, the norm (/ sqrt(p)) of its last
 // digit group's part (the groups left out fall below it by about 2^-7 each)
-// and ||X||_F ||A||_F / p.
+// and ||X||_F ||A||_F / p (the last two from a residual launched with stats).
 ibmi_status refine_read_groups(RefineState* R, cudaStream_t st, double* rho, double* last_group, double* amp);
 // ||I - H A||_F / sqrt(p) from BF16x3 products, for H given by its BF16 hi/lo
 // slice maps (about 5 significant digits; the stop test of the sweeps and the
