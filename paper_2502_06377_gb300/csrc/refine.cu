@@ -289,51 +289,71 @@ __global__ void k_oz_combine(const int* T, int64_t p, int64_t ldp, const int* ex
   }
 }
 
-// out[k] = sqrt(sum of partials[k n .. (k + 1) n)) / sqrt(p) for k < nout;
-// with row data of X and A (sqx: sum of (x 2^-ex)^2 per row), also
-// out[2] = ||X||_F ||A||_F / p.
+// out[0] = sqrt(sum of partials[0 .. n)) / sqrt(p) (FP64 sum); with nout = 2
+// also out[1] from partials[n .. 2n), and with row data of X and A (sqx: sum
+// of (x 2^-ex)^2 per row) out[2] = ||X||_F ||A||_F / p.  The last two are
+// estimates for planning and are summed in float (FP64 adds are scarce on
+// this GPU and this kernel runs on one SM); the norms are scaled by the
+// largest row exponent first.
+__device__ __forceinline__ float block_sum_f(float v, float* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  float t = 0.f;
+  for (int w = 0; w < (int)(blockDim.x / 32); ++w) t += sh[w];
+  return t;
+}
+__device__ __forceinline__ int block_max_i(int v, int* sh) {
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  int t = sh[0];
+  for (int w = 1; w < (int)(blockDim.x / 32); ++w) t = max(t, sh[w]);
+  return t;
+}
+
 __global__ void k_sum_partials(const double* partials, int64_t n, int64_t p, double* out, int nout = 1,
                                const float* sqx = nullptr, const int* ex = nullptr, const float* sqa = nullptr,
                                const int* ea = nullptr) {
   __shared__ double red[32];
-  if (sqx) {
-    double sx = 0.0, sa = 0.0;
-    for (int64_t i = threadIdx.x; i < p; i += blockDim.x) {
-      sx += ldexp((double)sqx[i], 2 * ex[i]);
-      sa += ldexp((double)sqa[i], 2 * ea[i]);
-    }
-    __shared__ double red2[32];
-    for (int o = 16; o > 0; o >>= 1) {
-      sx += __shfl_xor_sync(0xffffffffu, sx, o);
-      sa += __shfl_xor_sync(0xffffffffu, sa, o);
-    }
-    if ((threadIdx.x & 31) == 0) {
-      red[threadIdx.x >> 5] = sx;
-      red2[threadIdx.x >> 5] = sa;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double tx = 0.0, ta = 0.0;
-      for (int w = 0; w < (int)(blockDim.x / 32); ++w) {
-        tx += red[w];
-        ta += red2[w];
-      }
-      out[2] = sqrt(tx) * sqrt(ta) / (double)p;
-    }
-    __syncthreads();
-  }
-  for (int k = 0; k < nout; ++k) {
+  __shared__ float redf[32];
+  __shared__ int redi[32];
+  {
     double s = 0.0;
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += partials[k * n + i];
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += partials[i];
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
     __syncthreads();
     if (threadIdx.x == 0) {
       double t = 0.0;
       for (int w = 0; w < (int)(blockDim.x / 32); ++w) t += red[w];
-      out[k] = sqrt(t) / sqrt((double)p);
+      out[0] = sqrt(t) / sqrt((double)p);
     }
-    __syncthreads();
+  }
+  if (nout > 1) {
+    float s = 0.f;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += (float)partials[n + i];
+    const float t = block_sum_f(s, redf);
+    if (threadIdx.x == 0) out[1] = sqrt((double)t) / sqrt((double)p);
+  }
+  if (sqx) {
+    int mx = -(1 << 30), ma = -(1 << 30);
+    for (int64_t i = threadIdx.x; i < p; i += blockDim.x) {
+      mx = max(mx, ex[i]);
+      ma = max(ma, ea[i]);
+    }
+    mx = block_max_i(mx, redi);
+    ma = block_max_i(ma, redi);
+    float sx = 0.f, sa = 0.f;
+    for (int64_t i = threadIdx.x; i < p; i += blockDim.x) {
+      sx += ldexpf(sqx[i], 2 * (ex[i] - mx));
+      sa += ldexpf(sqa[i], 2 * (ea[i] - ma));
+    }
+    sx = block_sum_f(sx, redf);
+    sa = block_sum_f(sa, redf);
+    if (threadIdx.x == 0) out[2] = ldexp(sqrt((double)sx) * sqrt((double)sa), mx + ma) / (double)p;
   }
 }
 
