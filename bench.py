@@ -406,14 +406,15 @@ def main():
                  "residual": "a6 residual (FP64 DFMA)", "newton_schulz": "a7 Newton-Schulz (FP64 DFMA)",
                  "invariants": "a2 Cholesky + triangular solves (FP64 DFMA)"}.get(dom, dom)
     total_kernel_ms = sum(v[1] for v in prof.values())
-    traffic = None
+    traffic, traffic_src = None, None
     tpath = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tpath):
         ent = json.load(open(tpath)).get(f"{args.precision}/{dom}")
         if ent:
-            traffic = ent.get("bytes_per_launch")
+            traffic, traffic_src = ent.get("bytes_per_launch"), ent.get("source")
     roofline = {"bound": bound, "kernel": kdesc, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": (achieved / peak) if achieved else None, "traffic": traffic, "peak_source": psrc,
+                "frac": (achieved / peak) if achieved else None, "traffic": traffic, "traffic_source": traffic_src,
+                "peak_source": psrc,
                 "launches": n_d, "share_of_kernel_time": ms_d / total_kernel_ms if total_kernel_ms else None,
                 "timing": f"per-class CUDA events on the launching stream over {prof_steps} further steps of the "
                           "same workload (instrumented pass; the headline time is uninstrumented)",
