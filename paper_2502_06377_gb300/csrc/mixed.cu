@@ -536,9 +536,9 @@ ibmi_status mixed_run(ibmi_plan_s* P, const double* A, int64_t lda, double* H, i
     *flops += fr * (ns_pairs(qto) - ns_pairs(qfrom)) / ns_pairs(OZ_QMAX);
     return refine_read_groups(R, st, rho, g, amp);
   };
-  // Before a radius test: kNsFirstGroups groups give Q ample for the radius
-  // and, if the tail starts, for its first step (checked there); a value at
-  // or below tol is certified with all groups.
+  // Before a radius test: the first tail residual's groups (q_first) give Q
+  // ample for the radius and, if the tail starts, for its first step
+  // (checked there); a value at or below tol is certified with all groups.
   const int q_first = planned ? kNsFirstGroups : kNsFixedFirst;
   double pending_g = NAN, pending_amp = NAN;
   int pending_q = 0;
