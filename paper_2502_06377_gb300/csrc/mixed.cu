@@ -52,6 +52,7 @@ constexpr int kNsFirstGroups = 5;           // digit groups of a residual before
 constexpr int kNsFixedFirst = 7;            // below kEarlyMinOrder: groups of the first tail residual ...
 constexpr int kNsFixedNext = 8;             // ... and of the next ones while rho^2 > 1e3 tol
 constexpr double kNsGrowth = 16.0;          // pessimistic rho_{k+1} / rho_k^2 of a Newton-Schulz step
+constexpr double kNsUpdateFloor = 512.0;    // update error model constant (measured 75-260; see ns_update_floor)
 constexpr double kEarlyHandOver = 0.6;      // radius below which slow sweeps hand over early
 constexpr int64_t kEarlyMinOrder = 2048;    // smallest order for that test
 constexpr int64_t kTcInverseMinOrder = 1024;   // block order from which Y^T Y runs on the tensor cores
@@ -82,13 +83,13 @@ struct MixedState {
   bool graphs = false;
   const double* gA = nullptr;
   const double* gH = nullptr;
-  PhaseGraph g_setup, g_sweep[2], g_cheap, g_reslice, g_export_resid, g_update, g_radius;
+  PhaseGraph g_setup, g_sweep[2], g_cheap, g_reslice, g_export_resid, g_update[2], g_radius;
   std::map<int, PhaseGraph> g_tail;      // tail residuals by digit groups (see ns_graph_key)
 };
 
 static void drop_graphs(MixedState* M) {
   for (PhaseGraph* g : {&M->g_setup, &M->g_sweep[0], &M->g_sweep[1], &M->g_cheap, &M->g_reslice,
-                        &M->g_export_resid, &M->g_update, &M->g_radius}) {
+                        &M->g_export_resid, &M->g_update[0], &M->g_update[1], &M->g_radius}) {
     if (g->exec) cudaGraphExecDestroy(g->exec);
     *g = PhaseGraph{};
   }
@@ -142,6 +143,14 @@ static int ns_groups_for(double target, double g, int qc, double amp) {
   for (int q = NS_S - 1; q < OZ_QMAX; ++q)
     if (ns_floor(q, g, qc, amp) <= target) return q;
   return OZ_QMAX;
+}
+// error (in rho) of an update from a residual rho that keeps digit groups
+// <= qu of the product X Q^T: its truncation D_U enters E' as A D_U, which
+// for the row-scaled digits measured about c a rho 2^(-7 (qu + 1)) with
+// c = 75..260 on the benchmark's large matrices (probe of 3 and 4 groups on
+// five of them); kNsUpdateFloor doubles the largest.
+static double ns_update_floor(int qu, double rho, double amp) {
+  return kNsUpdateFloor * amp * rho * ldexp(1.0, -7 * (qu + 1));
 }
 // graph keys of the tail's residuals: (export of H first, groups) and extensions (from, to)
 static int ns_graph_key(bool export_h, int q) { return (export_h ? 100 : 0) + q; }
@@ -694,10 +703,14 @@ ibmi_status mixed_run(ibmi_plan_s* P, const double* A, int64_t lda, double* H, i
       gcal = g;
       acal = amp;
       qcal = qc;
-      prev_floor = planned ? ns_floor(qc, g, qc, amp) : 0.0;
+      // the update keeps 10 of its 15 pair products where their error fits
+      // the same target as the residual's (planned tail only)
+      const int qu = planned && ns_update_floor(NS_S - 2, rho, amp) <= ns_target(rho, d.tol) ? NS_S - 2 : NS_S - 1;
+      prev_floor = planned ? ns_floor(qc, g, qc, amp) + ns_update_floor(qu, rho, amp) : 0.0;
       prev = rho;
-      IBMI_TRY(graph_or_run(M, &M->g_update, st, [&]() { return refine_ns_update(R, H, ldh, st); }));
-      *flops += fr;
+      IBMI_TRY(graph_or_run(M, &M->g_update[qu == NS_S - 1 ? 0 : 1], st,
+                            [&]() { return refine_ns_update(R, H, ldh, st, qu); }));
+      *flops += fr * (qu == NS_S - 1 ? 1.0 : 10.0 / 15.0);
       res->ns_steps = s + 1;
     }
     if (!resume) return IBMI_NOT_CONVERGED;   // not reached: the tail returns

@@ -901,16 +901,17 @@ ibmi_status refine_residual_extend_launch(RefineState* R, const double* X, int64
   return combine_residual(R, qto, stats, st);
 }
 
-ibmi_status refine_ns_update(RefineState* R, double* X, int64_t ldx, cudaStream_t st) {
+ibmi_status refine_ns_update(RefineState* R, double* X, int64_t ldx, cudaStream_t st, int qmax) {
   const int64_t p = R->p, ldp = R->ldp;
+  if (qmax < 0 || qmax > NS_S - 1) return IBMI_ERR_INVALID_ARG;
   {
     ProfScope ps(IBMI_K_OTHER, st, 0.0);
     IBMI_TRY(slice_digits(R, R->Xn, p, R->Qo, NS_S, R->expQ, st));
   }
-  IBMI_TRY(pair_products(R, R->mXo, NS_S, R->mQo, NS_S, NS_S - 1, IBMI_K_NS, st));
+  IBMI_TRY(pair_products(R, R->mXo, NS_S, R->mQo, NS_S, qmax, IBMI_K_NS, st));
   ProfScope ps(IBMI_K_OTHER, st, 0.0);
   note_launch();
-  k_oz_update<<<grid2(p, p), 256, 0, st>>>(R->T, p, ldp, R->expX, R->expQ, NS_S - 1, X, ldx, R->Xn);
+  k_oz_update<<<grid2(p, p), 256, 0, st>>>(R->T, p, ldp, R->expX, R->expQ, qmax, X, ldx, R->Xn);
   IBMI_CUDA_TRY(cudaGetLastError());
   note_launch();
   k_sym_into<<<dim3((unsigned)((p + 31) / 32), (unsigned)((p + 31) / 32)), dim3(32, 8), 0, st>>>(R->Xn, p, X, ldx);
