@@ -9,6 +9,7 @@
 #include <mutex>
 
 #include "mixed.cuh"
+#include "tail_plan.h"
 #include "refine.cuh"
 #include "tc_gemm.cuh"
 
@@ -51,8 +52,6 @@ constexpr int kRadiusIters = 40;            // power-iteration steps of the radi
 constexpr int kNsFirstGroups = 5;           // digit groups of a residual before the tail is calibrated
 constexpr int kNsFixedFirst = 7;            // below kEarlyMinOrder: groups of the first tail residual ...
 constexpr int kNsFixedNext = 8;             // ... and of the next ones while rho^2 > 1e3 tol
-constexpr double kNsGrowth = 16.0;          // pessimistic rho_{k+1} / rho_k^2 of a Newton-Schulz step
-constexpr double kNsUpdateFloor = 512.0;    // update error model constant (measured 75-260; see ns_update_floor)
 constexpr double kEarlyHandOver = 0.6;      // radius below which slow sweeps hand over early
 constexpr int64_t kEarlyMinOrder = 2048;    // smallest order for that test
 constexpr int64_t kTcInverseMinOrder = 1024;   // block order from which Y^T Y runs on the tensor cores
@@ -98,60 +97,7 @@ static void drop_graphs(MixedState* M) {
   M->g_tail.clear();
 }
 
-// ---------------------------------------------- Newton-Schulz tail plan ----
-//
-// With Q = I - X A exact, a step (eq. newton) leaves E' = E^2 (E = I - A X).
-// A residual that keeps digit groups q <= qc carries the truncation error D
-// of the groups left out, about 2^-7 of the norm g of group qc's part (each
-// group's part is about 2^-7 of the one before; g is measured with the
-// residual).  The step X + X (Q + D)^T, made symmetric, leaves
-// E' = E^2 - (D^T + A D X) / 2: for an unstructured D the second term is
-// about ||A||_F ||X||_F / p times D (also measured; 60 to 8000 on the
-// benchmark's matrices, and this is what the measured floors follow).  The
-// error only has to stay below what the steps still to come square away.
-
-// pair products of digit groups 0..q
-static int ns_pairs(int q) {
-  int n = 0;
-  for (int g = 0; g <= q; ++g)
-    for (int s = 0; s <= g; ++s)
-      if (s < OZ_SX && g - s < OZ_SA) ++n;
-  return n;
-}
-// error (in rho) a step takes from a residual of groups <= q, from g measured
-// at group qc and amp = ||A||_F ||X||_F / p, with a factor 2 of margin
-static double ns_floor(int q, double g, int qc, double amp) {
-  return 2.0 * g * ldexp(1.0, -7 * (q + 1 - qc)) * (1.0 + 0.5 * amp);
-}
-// steps from rho to rho <= tol / 4 if each one squares it (the optimistic count)
-static int ns_steps(double rho, double tol) {
-  int n = 0;
-  for (double r = rho; r > 0.25 * tol && n < 12; r *= r) ++n;
-  return n < 1 ? 1 : n;
-}
-// largest rho from which k steps reach tol / 4 when each multiplies rho^2 by kNsGrowth
-static double ns_bound(int k, double tol) {
-  double b = 0.25 * tol;
-  for (int i = 0; i < k; ++i) b = sqrt(b / kNsGrowth);
-  return b;
-}
-// truncation error allowed in the residual that feeds the step from rho: half
-// of the bound for the steps that follow it
-static double ns_target(double rho, double tol) { return 0.5 * ns_bound(ns_steps(rho, tol) - 1, tol); }
-// fewest groups (>= NS_S - 1, which the update's digits of X need) within `target`
-static int ns_groups_for(double target, double g, int qc, double amp) {
-  for (int q = NS_S - 1; q < OZ_QMAX; ++q)
-    if (ns_floor(q, g, qc, amp) <= target) return q;
-  return OZ_QMAX;
-}
-// error (in rho) of an update from a residual rho that keeps digit groups
-// <= qu of the product X Q^T: its truncation D_U enters E' as A D_U, which
-// for the row-scaled digits measured about c a rho 2^(-7 (qu + 1)) with
-// c = 75..260 on the benchmark's large matrices (probe of 3 and 4 groups on
-// five of them); kNsUpdateFloor doubles the largest.
-static double ns_update_floor(int qu, double rho, double amp) {
-  return kNsUpdateFloor * amp * rho * ldexp(1.0, -7 * (qu + 1));
-}
+// Newton-Schulz tail plan: tail_plan.h (host logic, tested on the CPU).
 // graph keys of the tail's residuals: (export of H first, groups) and extensions (from, to)
 static int ns_graph_key(bool export_h, int q) { return (export_h ? 100 : 0) + q; }
 static int ns_extend_key(int qfrom, int qto) { return 200 + 10 * qfrom + qto; }
@@ -534,7 +480,7 @@ ibmi_status mixed_run(ibmi_plan_s* P, const double* A, int64_t lda, double* H, i
       if (export_h) IBMI_TRY(mixed_export_launch(P, H, ldh, st));
       return refine_residual_launch(R, H, ldh, st, q, planned);
     }));
-    *flops += fr * ns_pairs(q) / ns_pairs(OZ_QMAX);
+    *flops += fr * tail::pairs(q, OZ_SX, OZ_SA) / tail::pairs(OZ_QMAX, OZ_SX, OZ_SA);
     return refine_read_groups(R, st, rho, g, amp);
   };
   // The same residual extended from groups <= qfrom to <= qto (only the new
@@ -542,7 +488,8 @@ ibmi_status mixed_run(ibmi_plan_s* P, const double* A, int64_t lda, double* H, i
   auto tail_extend = [&](int qfrom, int qto, double* rho, double* g, double* amp) -> ibmi_status {
     IBMI_TRY(graph_or_run(M, &M->g_tail[ns_extend_key(qfrom, qto)], st,
                           [&]() { return refine_residual_extend_launch(R, H, ldh, st, qfrom, qto, planned); }));
-    *flops += fr * (ns_pairs(qto) - ns_pairs(qfrom)) / ns_pairs(OZ_QMAX);
+    *flops += fr * (tail::pairs(qto, OZ_SX, OZ_SA) - tail::pairs(qfrom, OZ_SX, OZ_SA)) /
+              tail::pairs(OZ_QMAX, OZ_SX, OZ_SA);
     return refine_read_groups(R, st, rho, g, amp);
   };
   // Before a radius test: the first tail residual's groups (q_first) give Q
@@ -677,7 +624,9 @@ ibmi_status mixed_run(ibmi_plan_s* P, const double* A, int64_t lda, double* H, i
         const double rho_hat = s == 0 ? last_cheap : std::max(prev * prev, prev_floor);
         if (rho_hat <= d.tol) qc = OZ_QMAX;
         else if (!planned) qc = s == 0 ? kNsFixedFirst : (prev * prev > 1e3 * d.tol ? kNsFixedNext : OZ_QMAX);
-        else qc = qcal < 0 ? kNsFirstGroups : ns_groups_for(ns_target(rho_hat, d.tol), gcal, qcal, acal);
+        else
+          qc = qcal < 0 ? kNsFirstGroups
+                        : tail::residual_groups(tail::target(rho_hat, d.tol), gcal, qcal, acal, NS_S - 1, OZ_QMAX);
         IBMI_TRY(tail_residual(s == 0, qc, &rho, &g, &amp));
       }
       // a value at or below tol is certified with all groups; a step needs
@@ -685,7 +634,8 @@ ibmi_status mixed_run(ibmi_plan_s* P, const double* A, int64_t lda, double* H, i
       for (;;) {
         int qn = qc;
         if (rho <= d.tol || !isfinite(rho)) qn = isfinite(rho) ? OZ_QMAX : qc;
-        else if (planned) qn = std::max(qc, ns_groups_for(ns_target(rho, d.tol), g, qc, amp));
+        else if (planned)
+          qn = std::max(qc, tail::residual_groups(tail::target(rho, d.tol), g, qc, amp, NS_S - 1, OZ_QMAX));
         if (qn == qc) break;
         IBMI_TRY(tail_extend(qc, qn, &rho, &g, &amp));
         qc = qn;
@@ -705,12 +655,12 @@ ibmi_status mixed_run(ibmi_plan_s* P, const double* A, int64_t lda, double* H, i
       qcal = qc;
       // the update keeps 10 of its 15 pair products where their error fits
       // the same target as the residual's (planned tail only)
-      const int qu = planned && ns_update_floor(NS_S - 2, rho, amp) <= ns_target(rho, d.tol) ? NS_S - 2 : NS_S - 1;
-      prev_floor = planned ? ns_floor(qc, g, qc, amp) + ns_update_floor(qu, rho, amp) : 0.0;
+      const int qu = planned ? tail::update_groups(rho, amp, d.tol, NS_S - 1) : NS_S - 1;
+      prev_floor = planned ? tail::residual_floor(qc, g, qc, amp) + tail::update_floor(qu, rho, amp) : 0.0;
       prev = rho;
       IBMI_TRY(graph_or_run(M, &M->g_update[qu == NS_S - 1 ? 0 : 1], st,
                             [&]() { return refine_ns_update(R, H, ldh, st, qu); }));
-      *flops += fr * (qu == NS_S - 1 ? 1.0 : 10.0 / 15.0);
+      *flops += fr * tail::pairs(qu, NS_S, NS_S) / tail::pairs(NS_S - 1, NS_S, NS_S);
       res->ns_steps = s + 1;
     }
     if (!resume) return IBMI_NOT_CONVERGED;   // not reached: the tail returns
