@@ -110,7 +110,9 @@ typedef struct ibmi_result {
   double resid_f;          /* last ||I - A H||_F / sqrt(p) evaluated (FP64)                 */
   double paper_est;        /* last eq. error estimate (NaN unless evaluated)                */
   double seconds;          /* wall time of the call on the stream                          */
-  double flops;            /* algorithmic flops: plan + sweeps + residuals + Newton-Schulz */
+  double flops;            /* algorithmic flops: plan + sweeps + residuals + Newton-Schulz;
+                              a digit-sliced residual or update that keeps part of its
+                              pair products counts that share of its 2 p^3 (mixed)          */
 } ibmi_result;
 
 typedef struct ibmi_plan_s* ibmi_plan_t;
