@@ -205,6 +205,46 @@ def test_symmetry_exact():
     assert np.array_equal(res.h, res.h.T)
 
 
+@pytest.mark.parametrize("p,rho,K,h", [(64, 0.5, 4, 2), (96, 0.8, 3, 1), (120, 0.9, 5, 4), (64, 0.8, 8, 2),
+                                       (50, 0.95, 2, 1)])
+def test_kms_overlapping_sets_exact_in_one_sweep(p, rho, K, h):
+    """AR(1)/KMS, several overlapping sets swept left to right (Algorithm 1).
+    For a set I = [lo, hi) the coupling to the columns left of it is rank one,
+    A[i, j] = rho^(i-lo) rho^(lo-j), and rho^(i-lo) is the first column of A_I,
+    so A_I^{-1} maps it to the first unit vector; on the right it is the last
+    column.  Hence W = A_I^{-1} A_{I,I^c} is zero except in its first and
+    last rows, and eq. IBMI leaves every row of H[I, :] but the last one
+    depending on T only through its left part, which the tridiagonal inverse
+    (whose A_{I'}^{-1} block of the previous set differs from A^{-1} only in
+    that set's last row and column) makes exact.  With overlap the next set
+    rewrites that last row, and the last set has no right complement: one
+    sweep gives A^{-1} from any symmetric starting H."""
+    a = wl.kms(p, rho)
+    sig = kms_inverse(p, rho)
+    sets = O.partition(p, K, h)
+    g = np.random.default_rng(p).standard_normal((p, p))
+    for h0 in (3.0 * np.eye(p), g + g.T):
+        res = O.ibmi(a, sets, tol=0.0, max_sweeps=1, h0=h0)
+        assert res.sweeps == 1
+        np.testing.assert_allclose(res.h, sig, rtol=0, atol=5e-15 * np.max(np.abs(sig)) * p)
+
+
+@pytest.mark.parametrize("K", [3, 4, 6])
+def test_kms_nonoverlapping_sets_contract_by_rho4(K):
+    """The same matrix without overlap: each boundary between consecutive sets
+    keeps an error that the next sweep multiplies by rho^4, the rate of the
+    two-block trajectory above (rho^(4r-2)); once the boundaries' errors have
+    settled the ratio of consecutive sweeps' errors is rho^4."""
+    p, rho = 60, 0.8
+    a = wl.kms(p, rho)
+    sig = kms_inverse(p, rho)
+    sets = O.partition(p, K, 0)
+    errs = [np.max(np.abs(O.ibmi(a, sets, tol=0.0, max_sweeps=r, h0=2.0 * np.eye(p)).h - sig))
+            for r in range(4, 8)]
+    for e0, e1 in zip(errs, errs[1:]):
+        assert e1 / e0 == pytest.approx(rho ** 4, rel=1e-6)
+
+
 def test_multiblock_overlap_converges_to_inverse():
     """Remark of Section 3: the multi-block overlapping sweep converges in
     practice; checked against LAPACK's inverse."""
