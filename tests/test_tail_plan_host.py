@@ -137,3 +137,107 @@ def test_plan_extends_the_first_residual_of_a_harder_matrix(plan):
     assert plan(f"UG {rho0!r} {amp!r} {tol!r} 4") == [4]
     rho2 = 1.7829e-04   # third residual: still 15 pairs
     assert plan(f"UG {rho2!r} {amp!r} {tol!r} 4") == [4]
+
+
+# ------------------------------------------------------------------------
+# The error model against an exact emulation of the digit-sliced products
+# (CPU, p = 128): row-scaled 7-bit digits of X and A as integers, the group
+# sums as exact int64 products, one symmetrised Newton-Schulz step in FP64.
+
+def _digits(X, nd):
+    """F = rint(x 2^(55-e)) with |x| < 2^e per row; digit s (rounded, 7 bits
+    apart) weighs 2^(e - 6 - 7 s)."""
+    import numpy as np
+    p = X.shape[0]
+    mx = np.max(np.abs(X), axis=1)
+    e = np.array([math.frexp(float(v))[1] if v > 0 else 0 for v in mx], dtype=np.int64)
+    D = np.zeros((nd, p, p), dtype=np.int64)
+    for i in range(p):
+        for j in range(p):
+            f = int(round(math.ldexp(float(X[i, j]), 55 - int(e[i]))))
+            for s in range(nd):
+                sh = 49 - 7 * s
+                d = (f + (1 << (sh - 1))) >> sh
+                f -= d << sh
+                D[s, i, j] = d
+    return D, e
+
+
+def _product(DX, ex, DB, eb, q):
+    """sum over pairs s + u <= q of digit products of X B^T, and group q's part."""
+    import numpy as np
+    p = DX.shape[1]
+    C = np.zeros((p, p))
+    last = None
+    for g in range(q + 1):
+        Tg = np.zeros((p, p), dtype=np.int64)
+        for s in range(g + 1):
+            if s < DX.shape[0] and g - s < DB.shape[0]:
+                Tg += DX[s] @ DB[g - s].T
+        last = Tg.astype(float) * 2.0 ** (-7 * g)
+        C += last
+    scale = np.ldexp(1.0, (ex[:, None] + eb[None, :] - 12).astype(np.int64))
+    return C * scale, last * scale
+
+
+def _cases():
+    import numpy as np
+    import workloads as wl
+    yield "se", wl.squared_exp(wl.uniform_points(np.random.default_rng(7), 128, 3), 0.3, nugget=1e-3)
+    yield "matern", wl.matern32(wl.uniform_points(np.random.default_rng(8), 128, 2), 0.1, nugget=1e-2)
+    yield "kms", wl.kms(128, 0.9)
+
+
+def _iterate(A, eps):
+    import numpy as np
+    p = A.shape[0]
+    P = np.random.default_rng(1).standard_normal((p, p))
+    P = 0.5 * (P + P.T)
+    X = np.linalg.inv(A) @ (np.eye(p) - eps * P / np.linalg.norm(P, 2))
+    return 0.5 * (X + X.T)
+
+
+def test_residual_floor_model_against_emulation(plan):
+    """The floor a truncated residual leaves after one symmetrised step is
+    what residual_floor predicts (which carries a factor 2 of margin): the
+    model stays within [1, 3] times the emulated floor for the groups the plan
+    uses (q >= 3), with amp from 30 to 1500."""
+    import numpy as np
+    for name, A in _cases():
+        p = A.shape[0]
+        X = _iterate(A, 1e-3)
+        amp = np.linalg.norm(A) * np.linalg.norm(X) / p
+        DX, ex = _digits(X, 7)
+        DA, ea = _digits(A, 7)
+
+        def step(Q):
+            Xn = X + X @ Q.T
+            return np.eye(p) - A @ (0.5 * (Xn + Xn.T))
+        E_exact = step(np.eye(p) - X @ A)
+        for q in (3, 4, 5):
+            C, last = _product(DX, ex, DA, ea, q)
+            g = np.linalg.norm(last) / math.sqrt(p)
+            floor = np.linalg.norm(step(np.eye(p) - C) - E_exact) / math.sqrt(p)
+            model = plan(f"RF {q} {float(g)!r} {q} {float(amp)!r}")[0]
+            assert floor <= model <= 3.0 * floor, (name, q, floor, model)
+
+
+def test_update_floor_model_is_conservative_at_small_order(plan):
+    """The update's constant was measured at orders 2048-4096 (c = 75..260,
+    kUpdateFloor 512); the row-scaled digits' error grows with the order, and
+    at p = 128 the emulated floor sits below the model."""
+    import numpy as np
+    for name, A in _cases():
+        p = A.shape[0]
+        for eps in (1e-2, 1e-4):
+            X = _iterate(A, eps)
+            amp = np.linalg.norm(A) * np.linalg.norm(X) / p
+            Q = np.eye(p) - X @ A
+            rho = np.linalg.norm(Q) / math.sqrt(p)
+            DX, ex = _digits(X, 5)
+            DQ, eq = _digits(Q, 5)
+            E_exact = np.eye(p) - A @ (X + X @ Q.T)
+            for qu in (3, 4):
+                U, _ = _product(DX, ex, DQ, eq, qu)
+                floor = np.linalg.norm(np.eye(p) - A @ (X + 0.5 * (U + U.T)) - E_exact) / math.sqrt(p)
+                assert floor <= plan(f"UF {qu} {float(rho)!r} {float(amp)!r}")[0], (name, eps, qu)
