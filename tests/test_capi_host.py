@@ -64,12 +64,9 @@ def test_invalid_plans_rejected(lib, kw):
     ([5, 40], [50, 100]),        # does not start at 0
     ([0, 40], [50, 90]),         # does not end at p
     ([0, 0], [50, 100]),         # not ascending
-    ([0], [100]) ,               # K=1 is fine -> expect success path not taken here
 ])
 def test_invalid_explicit_sets(lib, lo, hi):
     import paper_2502_06377_gb300 as ibmi
-    if len(lo) == 1:
-        pytest.skip("single full set is valid (direct inverse)")
     with pytest.raises(ibmi.IbmiError) as e:
         ibmi.ibmi_plan(100, lo=lo, hi=hi)
     assert e.value.status == ibmi.IBMI_ERR_INVALID_ARG
