@@ -466,7 +466,14 @@ ibmi_status ibmi_refine(const double* A, int64_t lda, double* X, int64_t ldx, in
   lda = p;
   if (precision == IBMI_MIXED) {
     int* err = nullptr;
-    IBMI_CUDA_TRY(cudaMalloc(&err, sizeof(int)));
+    if (cudaMalloc(&err, sizeof(int)) != cudaSuccess) {
+      cudaGetLastError();
+      return (ibmi_status)(res->status = IBMI_ERR_OOM);
+    }
+    struct FreeWord {
+      int* q;
+      ~FreeWord() { cudaFree(q); }   // after refine_destroy below (reverse order of scope)
+    } keep_err{err};
     IBMI_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
     RefineState R;
     s = refine_create(&R, p, err);
@@ -488,15 +495,26 @@ ibmi_status ibmi_refine(const double* A, int64_t lda, double* X, int64_t ldx, in
     }
     cudaStreamSynchronize(st);
     refine_destroy(&R);
-    cudaFree(err);
   } else {
     ibmi_plan_s P;
     P.d.p = p;
     P.n_partials = gemm_f64_ctas(p, p);
     const size_t b = sizeof(double) * (size_t)p * p;
-    IBMI_CUDA_TRY(cudaMalloc(&P.nsR, b));
-    IBMI_CUDA_TRY(cudaMalloc(&P.nsX, b));
-    IBMI_CUDA_TRY(cudaMalloc(&P.partials, sizeof(double) * (P.n_partials + 4)));
+    struct FreeBuffers {   // the three buffers below, also on an early return
+      ibmi_plan_s* P;
+      ~FreeBuffers() {
+        cudaFree(P->nsR);
+        cudaFree(P->nsX);
+        cudaFree(P->partials);
+        P->nsR = P->nsX = nullptr;
+        P->partials = nullptr;
+      }
+    } keep_bufs{&P};
+    if (cudaMalloc(&P.nsR, b) != cudaSuccess || cudaMalloc(&P.nsX, b) != cudaSuccess ||
+        cudaMalloc(&P.partials, sizeof(double) * (P.n_partials + 4)) != cudaSuccess) {
+      cudaGetLastError();
+      return (ibmi_status)(res->status = IBMI_ERR_OOM);
+    }
     P.dscalar = P.partials + P.n_partials;
     double prev = INFINITY;
     for (int it = 0;; ++it) {
@@ -515,11 +533,6 @@ ibmi_status ibmi_refine(const double* A, int64_t lda, double* X, int64_t ldx, in
       res->ns_steps = it + 1;
     }
     cudaStreamSynchronize(st);
-    cudaFree(P.nsR);
-    cudaFree(P.nsX);
-    cudaFree(P.partials);
-    P.nsR = P.nsX = nullptr;
-    P.partials = nullptr;
   }
   res->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   res->status = s;
