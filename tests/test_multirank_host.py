@@ -62,3 +62,19 @@ def test_split_is_deterministic_and_single_rank_identity():
     assert shard.shard_by_cost(sizes, 3, 1) == shard.shard_by_cost(sizes, 3, 1)
     with pytest.raises(ValueError):
         shard.shard_by_cost(sizes, 2, 2)
+
+
+@pytest.mark.parametrize("world", [2, 3, 4, 5, 8])
+def test_split_partitions_and_respects_the_greedy_bound(world):
+    """Every index on exactly one rank, and with many items of a few sizes the
+    greedy split's largest load is within 2% of the lower bound
+    max(total / world, largest item) on the optimum."""
+    import numpy as np
+    rng = np.random.default_rng(world)
+    sizes = [int(v) for v in 64 * rng.integers(1, 17, size=300)]
+    parts = [shard.shard_by_cost(sizes, world, r) for r in range(world)]
+    flat = sorted(i for part in parts for i in part)
+    assert flat == list(range(len(sizes)))
+    loads = [sum(shard.cost(sizes[i]) for i in part) for part in parts]
+    opt_lb = max(sum(loads) / world, max(shard.cost(s) for s in sizes))
+    assert max(loads) <= 1.02 * opt_lb
