@@ -24,17 +24,11 @@
 #include <unordered_map>
 #include <vector>
 
+#include "batch_plan.h"
 #include "mixed.cuh"
 #include "plan.cuh"
 
 namespace ibmi {
-
-// Padded order of a bucket: multiples of 64 up to 1024, of 128 up to 4096,
-// of 256 beyond.
-static int64_t bucket_of(int64_t p) {
-  const int64_t g = p <= 1024 ? 64 : (p <= 4096 ? 128 : 256);
-  return (p + g - 1) / g * g;
-}
 
 // Copies A (p x p, lda) into the top-left of Ab (pb x pb) and fills the rest
 // with the identity; H is copied back by the caller from the top-left block.
@@ -52,21 +46,6 @@ __global__ void k_unpad(const double* Hb, int64_t pb, int64_t p, double* H, int6
   H[i * ldh + j] = Hb[i * pb + j];
 }
 
-struct Shape {
-  int64_t p;
-  int32_t K;
-  int64_t h;
-  bool operator<(const Shape& o) const { return std::tie(p, K, h) < std::tie(o.p, o.K, o.h); }
-};
-
-// Default partition of a bucket when not tuned: ~256-row cores, 2..4 sets,
-// overlap 2h = 20% of the core.
-static Shape default_shape(int64_t pb) {
-  int32_t K = (int32_t)std::min<int64_t>(4, std::max<int64_t>(2, (pb + 255) / 256));
-  int64_t h = std::max<int64_t>(8, (int64_t)llround(0.1 * (double)pb / K));
-  return Shape{pb, K, h};
-}
-
 static ibmi_plan_desc desc_for(const Shape& s, const ibmi_batch_opts& o) {
   ibmi_plan_desc d;
   ibmi_plan_desc_init(&d);
@@ -77,10 +56,8 @@ static ibmi_plan_desc desc_for(const Shape& s, const ibmi_batch_opts& o) {
   d.tol = o.tol;
   d.max_sweeps = o.max_sweeps;
   d.check_every = 1;
-  // hand-over: for small orders a sweep costs about as much as a tail step
-  // (both launch-latency bound), so the tail starts earlier; an unfinished
-  // tail returns to the sweeps
-  d.ns_theta = o.precision != IBMI_MIXED ? 0.0 : (o.ns_theta > 0.0 ? o.ns_theta : (s.p <= 1024 ? 3.0 : 0.9));
+  // an unfinished tail returns to the sweeps
+  d.ns_theta = handover_theta(s.p, o.precision == IBMI_MIXED, o.ns_theta);
   d.ns_max = o.ns_max;
   return d;
 }
@@ -185,9 +162,8 @@ struct Worker {
 static std::mutex g_tune_mu;
 static std::map<std::pair<int64_t, int>, Shape> g_tuned;
 
-// Times candidate partitions of bucket pb on one matrix and keeps the fastest
-// that converges.  Candidates: K in {2, 3, 4}, 2h in {10%, 20%, 30%} of the
-// core width.
+// Times the candidate partitions of bucket pb (tune_candidates) on one matrix
+// and keeps the fastest that converges.
 static Shape tune_bucket(Worker& w, int64_t pb, const ibmi_batch_opts& o, const double* A, int64_t lda, int64_t p,
                          double* H, int64_t ldh) {
   {
@@ -197,23 +173,17 @@ static Shape tune_bucket(Worker& w, int64_t pb, const ibmi_batch_opts& o, const 
   }
   Shape best = default_shape(pb);
   double best_t = INFINITY;
-  for (int32_t K = 2; K <= 4; ++K) {
-    for (double f : {0.1, 0.2, 0.3}) {
-      const int64_t m = pb / K;
-      const int64_t h = std::max<int64_t>(4, (int64_t)llround(0.5 * f * (double)m));
-      if (K * m < pb / 2 || 2 * h >= m) continue;
-      Shape s{pb, K, h};
-      ibmi_result r;
-      double t = INFINITY;
-      for (int rep = 0; rep < 2; ++rep) {   // first run includes plan creation
-        auto t0 = std::chrono::steady_clock::now();
-        ibmi_status st = w.run(s, o, 0, A, lda, p, H, ldh, &r);
-        double dt = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-        if (st != IBMI_OK) { t = INFINITY; break; }
-        t = dt;
-      }
-      if (t < best_t) { best_t = t; best = s; }
+  for (const Shape& s : tune_candidates(pb)) {
+    ibmi_result r;
+    double t = INFINITY;
+    for (int rep = 0; rep < 2; ++rep) {   // first run includes plan creation
+      auto t0 = std::chrono::steady_clock::now();
+      ibmi_status st = w.run(s, o, 0, A, lda, p, H, ldh, &r);
+      double dt = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+      if (st != IBMI_OK) { t = INFINITY; break; }
+      t = dt;
     }
+    if (t < best_t) { best_t = t; best = s; }
   }
   w.release_plans();
   std::lock_guard<std::mutex> g(g_tune_mu);
@@ -227,15 +197,6 @@ static Shape tune_bucket(Worker& w, int64_t pb, const ibmi_batch_opts& o, const 
 static std::mutex g_pool_mu;
 static std::map<int, std::vector<std::unique_ptr<Worker>>> g_pool;
 static constexpr size_t kWorkerPlanCap = (size_t)6 << 30;   // plan bytes a pooled worker may keep
-
-// The partition used when the tuned one does not converge for a matrix:
-// cores of about 256 rows (2 to 8 sets), overlap 2h = 30% of the core.
-// Smaller blocks keep the mixed-precision floor of the sweeps low.
-static Shape robust_shape(int64_t pb) {
-  const int32_t K = (int32_t)std::min<int64_t>(8, std::max<int64_t>(2, pb / 256));
-  const int64_t m = pb / K;
-  return Shape{pb, K, std::max<int64_t>(4, (int64_t)llround(0.15 * (double)m))};
-}
 
 static Shape shape_for(int64_t p, const ibmi_batch_opts& o) {
   const int64_t pb = bucket_of(p);
