@@ -21,10 +21,10 @@
  *   - Matrices are dense, row-major, FP64, with a leading dimension ld >= p
  *     (in elements).  Since A and H are symmetric, row- and column-major agree.
  *   - A is read-only, and only its lower triangle (i >= j) is read: the
- *     strict upper triangle may hold anything (ibmi_residual_noalloc, which
- *     allocates nothing, is the exception and reads A in full).  H is owned by
- *     the caller and written in full.
- *   - Device pointers must be CUDA device memory of the current device;
+ *     strict upper triangle may hold anything.  H is owned by the caller and
+ *     written in full.
+ *   - Device pointers must be CUDA device memory of the current device (or
+ *     managed memory); a pointer into another GPU's memory is rejected;
  *     "_host" variants take host memory and copy inside the call.
  *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
  *     Calls are synchronous with respect to the host: when an entry point
@@ -263,16 +263,21 @@ int64_t ibmi_launch_count(void);
  * process with hard admission limits) or a latency-critical loop in which an
  * allocation, and the device synchronisation it can imply, is not allowed.
  * Same arguments, result and meaning as ibmi_residual (FP64 DFMA,
- * rho_F = ||I - A H||_F / sqrt(p) written to *out), same kernels.
+ * rho_F = ||I - A H||_F / sqrt(p) written to *out), same kernels; like every
+ * other entry point it reads only the lower triangle of A (the product reads
+ * element (i, j) of A from (max(i, j), min(i, j)), so no symmetric copy is
+ * needed).
  * Scratch: a fixed array of 16,386 doubles (about 128 KB) inside the library,
  * held on every GPU that loads the library until the process exits; it limits
  * the order to p <= 8192 -- larger p returns IBMI_ERR_INVALID_ARG with a
  * message in ibmi_last_error().  The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress); make that first call before
- * any stream capture.  Every call reuses the same array (each call writes all
- * the partial sums it reads, so nothing has to start at zero): calls that can
- * overlap on the GPU -- on different streams or from different host threads --
- * race on it and must be serialised by the caller.  Synchronises `stream`. */
+ * array's device address (cudaGetSymbolAddress).  Every call copies the
+ * result to the host and synchronises `stream`, so it must not be called
+ * while that stream is being captured into a CUDA graph.  Every call reuses
+ * the same array (each call writes all the partial sums it reads, so nothing
+ * has to start at zero): calls that can overlap on the GPU -- on different
+ * streams or from different host threads -- race on it and must be serialised
+ * by the caller. */
 ibmi_status ibmi_residual_noalloc(const double* A, int64_t lda, const double* H, int64_t ldh, int64_t p,
                                   void* stream, double* out);
 
@@ -293,13 +298,25 @@ ibmi_status ibmi_refine(const double* A, int64_t lda, double* X, int64_t ldx, in
 
 /* rho_F = ||I - A H||_F / sqrt(p) for symmetric device A, H, computed on the
  * tcgen05 tensor cores with the error-free sliced products of the Newton-Schulz
- * tail (every row cut into eight signed 7-bit digits; 36 exact digit-pair
- * products accumulated in integers and combined once in FP64), so the value
- * agrees with an FP64 evaluation to FP64 rounding.  Allocates its workspace
- * (about 26 p^2 bytes) for the duration of the call.  A and H must be
- * symmetric: the kernel evaluates ||I - H A||_F. */
+ * tail: every row of H is cut into ten signed 7-bit digits (69 bits) and every
+ * row of A into eight (55 bits), relative to the row maximum; the 52 exact
+ * digit-pair products of digit groups 0..9 are accumulated in integers and
+ * combined once in FP64, so the value agrees with an FP64 evaluation to FP64
+ * rounding.  Allocates its workspace (about 100 p^2 bytes) for the duration
+ * of the call.  H must be symmetric (the kernel evaluates ||I - H A||_F); A
+ * is read from its lower triangle. */
 ibmi_status ibmi_residual_tc(const double* A, int64_t lda, const double* H, int64_t ldh, int64_t p,
                              void* stream, double* out);
+
+/* Self-test of the bounded device-side waits (no counterpart in the paper):
+ * runs one small tcgen05 launch whose loads are never issued, so the MMA
+ * thread's wait on its first stage expires after about 2 s; the kernel then
+ * records the timeout, waits for its own issued work, frees its tensor memory
+ * and exits, and the call reads the error word.  Returns IBMI_ERR_TIMEOUT when
+ * all of that worked (the intended outcome), IBMI_OK if the wait did not
+ * expire, or IBMI_ERR_CUDA.  The CUDA context stays usable afterwards.
+ * Allocates 16 KB for the call; synchronises `stream`. */
+ibmi_status ibmi_selftest_wait_timeout(void* stream);
 
 /* Human-readable name of a status, and the text of the last CUDA error seen by
  * this thread (empty if none). */

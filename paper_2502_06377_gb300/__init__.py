@@ -132,6 +132,12 @@ def ibmi_residual_noalloc(A, H, stream=None) -> float:
     return out.value
 
 
+def ibmi_selftest_wait_timeout(stream=None) -> int:
+    """Runs the bounded-wait self-test launch; returns its status
+    (IBMI_ERR_TIMEOUT is the intended outcome)."""
+    return _lib.load().ibmi_selftest_wait_timeout(_stream_ptr(stream))
+
+
 def ibmi_residual_tc(A, H, stream=None) -> float:
     """FP64-accurate ||I - A H||_F / sqrt(p) on tensor cores (sliced error-free products)."""
     out = C.c_double()

@@ -67,6 +67,7 @@ _SIGS = {
     "ibmi_residual": (C.c_int, [_P, C.c_int64, _P, C.c_int64, C.c_int64, _P, _D]),
     "ibmi_residual_tc": (C.c_int, [_P, C.c_int64, _P, C.c_int64, C.c_int64, _P, _D]),
     "ibmi_residual_noalloc": (C.c_int, [_P, C.c_int64, _P, C.c_int64, C.c_int64, _P, _D]),
+    "ibmi_selftest_wait_timeout": (C.c_int, [_P]),
     "ibmi_refine": (C.c_int, [_P, C.c_int64, _P, C.c_int64, C.c_int64, C.c_int32, C.c_double, C.c_int32, _P,
                               C.POINTER(ibmi_result)]),
     "ibmi_prof_enable": (None, [C.c_int]),

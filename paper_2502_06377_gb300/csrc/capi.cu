@@ -45,13 +45,20 @@ static ibmi_status validate_sets(int64_t p, const std::vector<int64_t>& lo, cons
   return IBMI_OK;
 }
 
-static bool is_device_ptr(const void* ptr) {
+bool is_device_ptr(const void* ptr) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (a.type == cudaMemoryTypeManaged) return true;
+  if (a.type != cudaMemoryTypeDevice) return false;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.device == dev;   // another GPU's memory would be a peer access or a fault
 }
 
 static double flops_sweep(const ibmi_plan_s* P) {
@@ -169,16 +176,20 @@ static ibmi_status invert_impl(ibmi_plan_s* P, const double* A, int64_t lda, dou
     status = IBMI_NOT_CONVERGED;
     double prev = res->resid_f;
     for (int s = 0; s < d.ns_max; ++s) {
-      IBMI_TRY(ns_step_f64(P, A, lda, H, ldh, st));
+      IBMI_TRY(ns_step_f64(P, A, lda, H, ldh, st, P->nsR));   // nsR keeps the iterate before the step
       flops += 2.0 * fr;
       double rho;
       IBMI_TRY(residual_host(P, A, lda, H, ldh, st, &rho));
       flops += fr;
       res->ns_steps = s + 1;
+      if (!(rho < prev)) {
+        // a step that does not reduce the residual (or overflows) ends the
+        // tail, and H goes back to the better iterate before it
+        IBMI_TRY(copy_square(H, ldh, P->nsR, p, p, st));
+        break;
+      }
       res->resid_f = rho;
-      if (!isfinite(rho)) { status = IBMI_ERR_NONFINITE; break; }
       if (rho <= d.tol) { status = IBMI_OK; break; }
-      if (!(rho < prev)) break;   // a step that does not reduce the residual ends the tail
       prev = rho;
     }
   }
@@ -478,22 +489,33 @@ ibmi_status ibmi_refine(const double* A, int64_t lda, double* X, int64_t ldx, in
     RefineState R;
     s = refine_create(&R, p, err);
     if (s == IBMI_OK) s = refine_set_matrix(&R, A, lda, st);
+    double* Xprev = nullptr;   // X before the last update
+    if (s == IBMI_OK && ns_max > 0 && cudaMalloc(&Xprev, sizeof(double) * p * p) != cudaSuccess) {
+      cudaGetLastError();
+      s = IBMI_ERR_OOM;
+    }
     double prev = INFINITY;
     for (int it = 0; s == IBMI_OK; ++it) {
       double rho;
       s = refine_residual(&R, X, ldx, st, &rho);
       if (s != IBMI_OK) break;
       res->flops += fr;
+      if (it > 0 && !(rho < prev)) {   // the last update did not help: undo it
+        s = copy_square(X, ldx, Xprev, p, p, st);
+        if (s == IBMI_OK) s = IBMI_NOT_CONVERGED;
+        break;
+      }
       res->resid_f = rho;
       if (!isfinite(rho)) { s = IBMI_ERR_NONFINITE; break; }
       if (rho <= tol) { s = IBMI_OK; break; }
-      if (it >= ns_max || !(rho < prev)) { s = IBMI_NOT_CONVERGED; break; }
+      if (it >= ns_max) { s = IBMI_NOT_CONVERGED; break; }
       prev = rho;
-      s = refine_ns_update(&R, X, ldx, st);
+      s = refine_ns_update(&R, X, ldx, st, NS_S - 1, Xprev);
       res->flops += fr;
       res->ns_steps = it + 1;
     }
     cudaStreamSynchronize(st);
+    cudaFree(Xprev);
     refine_destroy(&R);
   } else {
     ibmi_plan_s P;
@@ -522,12 +544,17 @@ ibmi_status ibmi_refine(const double* A, int64_t lda, double* X, int64_t ldx, in
       s = residual_host(&P, A, lda, X, ldx, st, &rho);
       if (s != IBMI_OK) break;
       res->flops += fr;
+      if (it > 0 && !(rho < prev)) {   // the last step did not help: undo it (nsR holds X before it)
+        s = copy_square(X, ldx, P.nsR, p, p, st);
+        if (s == IBMI_OK) s = IBMI_NOT_CONVERGED;
+        break;
+      }
       res->resid_f = rho;
       if (!isfinite(rho)) { s = IBMI_ERR_NONFINITE; break; }
       if (rho <= tol) { s = IBMI_OK; break; }
-      if (it >= ns_max || !(rho < prev)) { s = IBMI_NOT_CONVERGED; break; }
+      if (it >= ns_max) { s = IBMI_NOT_CONVERGED; break; }
       prev = rho;
-      s = ns_step_f64(&P, A, lda, X, ldx, st);
+      s = ns_step_f64(&P, A, lda, X, ldx, st, P.nsR);
       if (s != IBMI_OK) break;
       res->flops += 2.0 * fr;
       res->ns_steps = it + 1;

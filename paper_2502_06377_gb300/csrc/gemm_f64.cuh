@@ -34,6 +34,9 @@ struct F64Operands {
   // Symmetric result: tiles entirely above the diagonal are skipped (the
   // consumer reads element (i, j) with j > i from (j, i)).
   bool lower_tiles = false;
+  // Symmetric A known by its lower triangle only (A_KMAJOR): element (r, c)
+  // is read from (max(r, c), min(r, c)).
+  bool a_lower = false;
 };
 
 // Threads of a T x T tile: a 4 x 4 register block per thread for T = 64 and
@@ -73,8 +76,19 @@ k_gemm_f64(F64Operands op, Epi epi) {
       if (A_KMAJOR) { r = e / F64_BK; c = e % F64_BK; } else { r = e % T; c = e / T; }
       int64_t i = i0 + r, l = l0 + c;
       double v = 0.0;
-      if (i < op.M && l < op.K)
-        v = A_KMAJOR ? op.A[op.mA(i) * op.lda + op.kA(l)] : op.A[op.kA(l) * op.lda + op.mA(i)];
+      if (i < op.M && l < op.K) {
+        if (A_KMAJOR) {
+          int64_t ra = op.mA(i), ca = op.kA(l);
+          if (op.a_lower && ca > ra) {
+            const int64_t t = ra;
+            ra = ca;
+            ca = t;
+          }
+          v = op.A[ra * op.lda + ca];
+        } else {
+          v = op.A[op.kA(l) * op.lda + op.mA(i)];
+        }
+      }
       As[c][r] = v;
     }
 #pragma unroll

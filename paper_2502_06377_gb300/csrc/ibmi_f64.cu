@@ -302,11 +302,12 @@ __global__ void k_finish_residual(const double* partials, int64_t n, int64_t p, 
 }
 
 ibmi_status residual_f64_dev(const double* A, int64_t lda, const double* H, int64_t ldh, int64_t p,
-                             double* partials, int64_t n_partials, double* dout, cudaStream_t st) {
+                             double* partials, int64_t n_partials, double* dout, cudaStream_t st, bool a_lower) {
   const GapMap id{0, 0};
   if (gemm_f64_ctas(p, p) > n_partials) return IBMI_ERR_INVALID_ARG;
   ProfScope ps(IBMI_K_RESIDUAL, st, 2.0 * (double)p * p * p);
   F64Operands op{A, lda, id, id, H, ldh, id, id, p, p, p};
+  op.a_lower = a_lower;
   IBMI_CUDA_TRY((launch_gemm_f64<true, true>(op, EpiResidual{partials, 0.0}, st)));
   note_launch();
   k_finish_residual<<<1, 1024, 0, st>>>(partials, gemm_f64_ctas(p, p), p, dout);
@@ -324,7 +325,7 @@ __global__ void k_symmetrize_full(const double* Xn, int64_t p, double* X, int64_
 }
 
 ibmi_status ns_step_f64(ibmi_plan_s* P, const double* A, int64_t lda, double* X, int64_t ldx,
-                        cudaStream_t st) {
+                        cudaStream_t st, double* backup) {
   const int64_t p = P->d.p;
   const GapMap id{0, 0};
   ProfScope ps(IBMI_K_NS, st, 4.0 * (double)p * p * p);
@@ -336,6 +337,9 @@ ibmi_status ns_step_f64(ibmi_plan_s* P, const double* A, int64_t lda, double* X,
     F64Operands op{X, ldx, id, id, P->nsR, p, id, id, p, p, p};
     IBMI_CUDA_TRY((launch_gemm_f64<true, true>(op, EpiAddTo{X, ldx, P->nsX, p}, st)));
   }
+  if (backup)   // X before the step (R is no longer read: the copy is ordered after the product)
+    IBMI_CUDA_TRY(cudaMemcpy2DAsync(backup, sizeof(double) * p, X, sizeof(double) * ldx, sizeof(double) * p, p,
+                                    cudaMemcpyDeviceToDevice, st));
   note_launch();
   k_symmetrize_full<<<nblk(p * p), 256, 0, st>>>(P->nsX, p, X, ldx);
   IBMI_CUDA_TRY(cudaGetLastError());

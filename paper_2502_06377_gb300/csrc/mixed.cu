@@ -76,6 +76,7 @@ struct MixedState {
   CUtensorMap mapH[3];
   std::vector<CUtensorMap> mapW[3];
   void* pool = nullptr;
+  double* Xprev = nullptr;               // p x p: the tail's iterate before its last update
   RefineState ref;                       // FP64-accurate residual + Newton-Schulz
   // CUDA graphs of the pipeline's phases (graph mode): captured on first use
   // for the A and H the plan was run with, replayed afterwards.
@@ -293,7 +294,7 @@ ibmi_status mixed_create(ibmi_plan_s* P) {
   if (sms <= 0) sms = 148;
   M->splits_max = (int)std::max<int64_t>(1, std::min<int64_t>(std::max<int64_t>(1, sms / tiles2), kt / 4 > 0 ? kt / 4 : 1));
   size_t bytes = sizeof(float) * p * ldp + 3 * sizeof(__nv_bfloat16) * p * ldp + 512 +
-                 sizeof(float) * (size_t)M->splits_max * P->mmax * P->mmax + 256;
+                 sizeof(float) * (size_t)M->splits_max * P->mmax * P->mmax + 256 + sizeof(double) * p * p + 256;
   for (int k = 0; k < K; ++k) bytes += 3 * sizeof(__nv_bfloat16) * (P->hi[k] - P->lo[k]) * ldp + 768;
   if (cudaMalloc(&M->pool, bytes) != cudaSuccess) {
     cudaGetLastError();
@@ -305,6 +306,7 @@ ibmi_status mixed_create(ibmi_plan_s* P) {
   for (int s = 0; s < 3; ++s) M->Hs[s] = (__nv_bfloat16*)take(sizeof(__nv_bfloat16) * p * ldp);
   M->Spart = (float*)take(sizeof(float) * (size_t)M->splits_max * P->mmax * P->mmax);
   M->err = (int*)take(256);
+  M->Xprev = (double*)take(sizeof(double) * p * p);
   for (int k = 0; k < K; ++k) {
     const int64_t m = P->hi[k] - P->lo[k];
     for (int s = 0; s < 3; ++s) M->Ws[s].push_back((__nv_bfloat16*)take(sizeof(__nv_bfloat16) * m * ldp));
@@ -640,14 +642,20 @@ ibmi_status mixed_run(ibmi_plan_s* P, const double* A, int64_t lda, double* H, i
         IBMI_TRY(tail_extend(qc, qn, &rho, &g, &amp));
         qc = qn;
       }
-      res->resid_f = rho;
-      if (!isfinite(rho)) return IBMI_ERR_NONFINITE;
-      if (rho <= d.tol) return IBMI_OK;
-      if (s >= d.ns_max || !(rho < prev)) {
-        if (early && r < d.max_sweeps) {   // back to the sweeps
+      // the last update did not reduce the residual (or overflowed)
+      const bool worse = s > 0 && !(rho < prev);
+      if (!worse) {
+        res->resid_f = rho;
+        if (!isfinite(rho)) return IBMI_ERR_NONFINITE;
+        if (rho <= d.tol) return IBMI_OK;
+      }
+      if (s >= d.ns_max || worse) {
+        if (early && r < d.max_sweeps) {   // back to the sweeps (they re-export H)
           resume = true;
           break;
         }
+        // H goes back to the better iterate before the failed update
+        if (worse) IBMI_TRY(copy_square(H, ldh, M->Xprev, p, p, st));
         return IBMI_NOT_CONVERGED;
       }
       gcal = g;
@@ -659,7 +667,7 @@ ibmi_status mixed_run(ibmi_plan_s* P, const double* A, int64_t lda, double* H, i
       prev_floor = planned ? tail::residual_floor(qc, g, qc, amp) + tail::update_floor(qu, rho, amp) : 0.0;
       prev = rho;
       IBMI_TRY(graph_or_run(M, &M->g_update[qu == NS_S - 1 ? 0 : 1], st,
-                            [&]() { return refine_ns_update(R, H, ldh, st, qu); }));
+                            [&]() { return refine_ns_update(R, H, ldh, st, qu, M->Xprev); }));
       *flops += fr * tail::pairs(qu, NS_S, NS_S) / tail::pairs(NS_S - 1, NS_S, NS_S);
       res->ns_steps = s + 1;
     }
@@ -671,4 +679,39 @@ ibmi_status mixed_run(ibmi_plan_s* P, const double* A, int64_t lda, double* H, i
   }
 }
 
+// Epilogue of the wait self-test: never reached (no accumulator completes).
+struct EpiNone : tc::EpiBase {
+  __device__ __forceinline__ void operator()(int64_t, int64_t, int, const float (&)[16]) {}
+};
+
 }  // namespace ibmi
+
+extern "C" ibmi_status ibmi_selftest_wait_timeout(void* stream) {
+  using namespace ibmi;
+  cudaStream_t st = (cudaStream_t)stream;
+  // one 128 x 64 BF16 tile for the tensor maps (never loaded) and the error word
+  constexpr size_t kTile = 128 * 64 * sizeof(__nv_bfloat16);
+  void* buf = nullptr;
+  IBMI_CUDA_TRY(cudaMalloc(&buf, kTile + 256));
+  struct FreeOnExit {
+    void* q;
+    ~FreeOnExit() { cudaFree(q); }
+  } keep{buf};
+  int* err = (int*)((uint8_t*)buf + kTile);
+  IBMI_CUDA_TRY(cudaMemsetAsync(buf, 0, kTile + 256, st));
+  tc::Maps maps;
+  for (int s = 0; s < 2; ++s)
+    if (!tc::make_map_bf16(&maps.a[s], buf, 128, 64, 64, 128) || !tc::make_map_bf16(&maps.b[s], buf, 128, 64, 64, 128))
+      return IBMI_ERR_CUDA;
+  tc::Tiles t{128, 0, 0, 1, 0, 1, 1, 1, 1, err};
+  t.starve = 1;
+  IBMI_CUDA_TRY((tc::launch<2, 128>(maps, t, 1, 1, EpiNone{}, st)));
+  int herr = 0;
+  IBMI_CUDA_TRY(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  IBMI_CUDA_TRY(cudaStreamSynchronize(st));
+  if (herr == tc::ERR_TIMEOUT) {
+    set_last_error("self-test: bounded wait expired as intended");
+    return IBMI_ERR_TIMEOUT;
+  }
+  return herr == 0 ? IBMI_OK : IBMI_ERR_CUDA;
+}

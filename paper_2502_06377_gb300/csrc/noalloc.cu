@@ -49,19 +49,13 @@ extern "C" ibmi_status ibmi_residual_noalloc(const double* A, int64_t lda, const
     set_last_error("ibmi_residual_noalloc: order exceeds the fixed scratch (p <= 8192)");
     return IBMI_ERR_INVALID_ARG;
   }
-  cudaPointerAttributes pa, ph;
-  if (cudaPointerGetAttributes(&pa, A) != cudaSuccess || cudaPointerGetAttributes(&ph, H) != cudaSuccess) {
-    cudaGetLastError();
-    return IBMI_ERR_INVALID_ARG;
-  }
-  if ((pa.type != cudaMemoryTypeDevice && pa.type != cudaMemoryTypeManaged) ||
-      (ph.type != cudaMemoryTypeDevice && ph.type != cudaMemoryTypeManaged))
-    return IBMI_ERR_INVALID_ARG;
+  if (!is_device_ptr(A) || !is_device_ptr(H)) return IBMI_ERR_INVALID_ARG;
   double* scratch = nullptr;
   IBMI_TRY(noalloc_scratch(&scratch));
   cudaStream_t st = (cudaStream_t)stream;
   const int64_t n = gemm_f64_ctas(p, p);   // <= NOALLOC_PARTIALS; each call writes every partial it reads
-  IBMI_TRY(residual_f64_dev(A, lda, H, ldh, p, scratch, n, scratch + NOALLOC_PARTIALS, st));
+  // A is read from its lower triangle, like every other entry point
+  IBMI_TRY(residual_f64_dev(A, lda, H, ldh, p, scratch, n, scratch + NOALLOC_PARTIALS, st, true));
   double v = 0.0;
   IBMI_CUDA_TRY(cudaMemcpyAsync(&v, scratch + NOALLOC_PARTIALS, sizeof(double), cudaMemcpyDeviceToHost, st));
   IBMI_CUDA_TRY(cudaStreamSynchronize(st));

@@ -44,7 +44,8 @@ __global__ void __launch_bounds__(THREADS, Cfg<1, BN>::CTAS_PER_SM) k_oz_pairs(c
   uint64_t* empty = full + C::STAGES;
   uint64_t* accf = empty + C::STAGES;
   uint64_t* acce = accf + 2;
-  uint32_t* tmem_slot = (uint32_t*)(acce + 2);
+  uint64_t* drain = acce + 2;   // MMA completion on an error exit
+  uint32_t* tmem_slot = (uint32_t*)(drain + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nchunks = (g.kt_total + g.chunk - 1) / g.chunk;
 
@@ -57,6 +58,7 @@ __global__ void __launch_bounds__(THREADS, Cfg<1, BN>::CTAS_PER_SM) k_oz_pairs(c
       mbar_init(&accf[b], 1);
       mbar_init(&acce[b], 4);
     }
+    mbar_init(drain, 1);
     fence_barrier_init();
   }
   if (warp == 1) tmem_alloc(tmem_slot, C::TMEM_COLS);
@@ -125,6 +127,7 @@ __global__ void __launch_bounds__(THREADS, Cfg<1, BN>::CTAS_PER_SM) k_oz_pairs(c
             }
             mma_commit(&accf[buf]);
           }
+      if (!ok || *(volatile int*)g.err != 0) mma_drain_on_error(drain);
     }
   } else {  // epilogue warps 2..5
     const int qw = warp & 3;

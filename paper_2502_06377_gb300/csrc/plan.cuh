@@ -64,13 +64,27 @@ ibmi_status invariants_all(ibmi_plan_s* P, const double* A, int64_t lda, bool fu
 ibmi_status sweep_step_f64(ibmi_plan_s* P, int k, double* H, int64_t ldh, cudaStream_t st);
 
 // a6: rho_F = ||I - A H||_F / sqrt(p), FP64, value left in *dout (device).
+// a_lower: A is read from its lower triangle only.
 ibmi_status residual_f64_dev(const double* A, int64_t lda, const double* H, int64_t ldh, int64_t p,
-                             double* partials, int64_t n_partials, double* dout, cudaStream_t st);
+                             double* partials, int64_t n_partials, double* dout, cudaStream_t st,
+                             bool a_lower = false);
 
-// a7: one Newton-Schulz step X <- sym(X + X (I - A X)) in FP64; leaves
-// ||I - A X_old||_F^2 in *dout.
+// Device memory of the current device (plain or managed): the pointer checks
+// of the entry points.
+bool is_device_ptr(const void* ptr);
+
+// a7: one Newton-Schulz step X <- sym(X + X (I - A X)) in FP64 (scratch
+// P->nsR, P->nsX).  backup (p x p, row pitch p; may be P->nsR): receives X
+// before the step, so that a step that does not help can be undone.
 ibmi_status ns_step_f64(ibmi_plan_s* P, const double* A, int64_t lda, double* X, int64_t ldx,
-                        cudaStream_t st);
+                        cudaStream_t st, double* backup = nullptr);
+
+// Copies a p x p FP64 matrix between device buffers (row pitches in elements).
+inline ibmi_status copy_square(double* dst, int64_t ldd, const double* src, int64_t lds, int64_t p, cudaStream_t st) {
+  IBMI_CUDA_TRY(cudaMemcpy2DAsync(dst, sizeof(double) * ldd, src, sizeof(double) * lds, sizeof(double) * p, p,
+                                  cudaMemcpyDeviceToDevice, st));
+  return IBMI_OK;
+}
 
 ibmi_status set_identity(double* H, int64_t ldh, int64_t p, cudaStream_t st);
 

@@ -901,7 +901,7 @@ ibmi_status refine_residual_extend_launch(RefineState* R, const double* X, int64
   return combine_residual(R, qto, stats, st);
 }
 
-ibmi_status refine_ns_update(RefineState* R, double* X, int64_t ldx, cudaStream_t st, int qmax) {
+ibmi_status refine_ns_update(RefineState* R, double* X, int64_t ldx, cudaStream_t st, int qmax, double* backup) {
   const int64_t p = R->p, ldp = R->ldp;
   if (qmax < 0 || qmax > NS_S - 1) return IBMI_ERR_INVALID_ARG;
   {
@@ -913,6 +913,9 @@ ibmi_status refine_ns_update(RefineState* R, double* X, int64_t ldx, cudaStream_
   note_launch();
   k_oz_update<<<grid2(p, p), 256, 0, st>>>(R->T, p, ldp, R->expX, R->expQ, qmax, X, ldx, R->Xn);
   IBMI_CUDA_TRY(cudaGetLastError());
+  if (backup)
+    IBMI_CUDA_TRY(cudaMemcpy2DAsync(backup, sizeof(double) * p, X, sizeof(double) * ldx, sizeof(double) * p, p,
+                                    cudaMemcpyDeviceToDevice, st));
   note_launch();
   k_sym_into<<<dim3((unsigned)((p + 31) / 32), (unsigned)((p + 31) / 32)), dim3(32, 8), 0, st>>>(R->Xn, p, X, ldx);
   IBMI_CUDA_TRY(cudaGetLastError());

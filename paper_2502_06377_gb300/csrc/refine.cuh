@@ -75,8 +75,10 @@ ibmi_status refine_residual(RefineState* R, const double* X, int64_t ldx, cudaSt
 // product X Q^T uses the five leading digits of X and of Q, digit groups
 // <= qmax of their exact pair products (qmax = 4: all 15 pairs, 2^-34
 // relative truncation; 3: 10 pairs), so its error stays proportional to Q.
-// Must follow refine_residual on the same X.
-ibmi_status refine_ns_update(RefineState* R, double* X, int64_t ldx, cudaStream_t st, int qmax = NS_S - 1);
+// Must follow refine_residual on the same X.  backup (p x p, row pitch p),
+// if given, receives X before the update.
+ibmi_status refine_ns_update(RefineState* R, double* X, int64_t ldx, cudaStream_t st, int qmax = NS_S - 1,
+                             double* backup = nullptr);
 
 // W = A_I^{-1} A_{I,:} (m x p, zero columns on I) from exact digit products
 // (five digits of A_I^{-1}, four of A), written as three BF16 slices with

@@ -72,6 +72,9 @@ struct Tiles {
   // the units are the tiles on or below the diagonal, for a symmetric result
   // whose consumer reads element (i, j) with j > i from (j, i).
   int lower = 0;
+  // Self-test of the bounded waits only: the producer issues no loads, so the
+  // MMA thread's first wait expires and the kernel takes its error exit.
+  int starve = 0;
 };
 
 __device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
@@ -204,6 +207,17 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
                : "memory");
 }
 
+// Error exit of the MMA thread: commit every tcgen05.mma it has issued to the
+// spare barrier `drain` (count 1, phase 0) and wait, bounded by 1 s, for its
+// arrival, so that no MMA still writes the accumulators when TMEM is freed.
+// (With nothing issued the commit arrives at once.)
+__device__ __forceinline__ void mma_drain_on_error(uint64_t* drain) {
+  mma_commit(drain);
+  const uint64_t t0 = globaltimer();
+  while (!mbar_try_wait(drain, 0) && globaltimer() - t0 < 1000000000ull) {
+  }
+}
+
 __device__ __forceinline__ void tc_fence_before() {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
@@ -284,7 +298,8 @@ __global__ void __launch_bounds__(THREADS, Cfg<S, BN>::CTAS_PER_SM) k_tc_gemm(co
   uint64_t* empty = full + C::STAGES;
   uint64_t* accf = empty + C::STAGES;   // [2] accumulator ready
   uint64_t* acce = accf + 2;            // [2] accumulator drained
-  uint32_t* tmem_slot = (uint32_t*)(acce + 2);
+  uint64_t* drain = acce + 2;           // MMA completion on an error exit
+  uint32_t* tmem_slot = (uint32_t*)(drain + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int units = unit_count(t);
@@ -300,6 +315,7 @@ __global__ void __launch_bounds__(THREADS, Cfg<S, BN>::CTAS_PER_SM) k_tc_gemm(co
       mbar_init(&accf[b], 1);
       mbar_init(&acce[b], 4);   // one arrival per epilogue warp
     }
+    mbar_init(drain, 1);
     fence_barrier_init();
   }
   if (warp == 1) tmem_alloc(tmem_slot, C::TMEM_COLS);
@@ -309,7 +325,7 @@ __global__ void __launch_bounds__(THREADS, Cfg<S, BN>::CTAS_PER_SM) k_tc_gemm(co
   const uint32_t tmem = *tmem_slot;
 
   if (warp == 0) {
-    if (lane == 0) {  // TMA producer
+    if (lane == 0 && !t.starve) {  // TMA producer
       int kc = 0;     // k blocks issued so far (ring position)
       bool ok = true;
       for (int u = blockIdx.x; ok && u < units; u += gridDim.x) {
@@ -381,6 +397,7 @@ __global__ void __launch_bounds__(THREADS, Cfg<S, BN>::CTAS_PER_SM) k_tc_gemm(co
         }
         mma_commit(&accf[buf]);
       }
+      if (!ok || *(volatile int*)t.err != 0) mma_drain_on_error(drain);
     }
   } else {  // epilogue warps 2..5
     const int q = warp & 3;

@@ -305,3 +305,109 @@ def test_table2_exp_1d_one_iteration():
         assert res.status == "converged" and res.sweeps == row["iterations"]
         err = np.linalg.norm(res.h - np.linalg.inv(a), 2)
         assert err <= 10 * row["error_2norm"]
+
+
+# ------------------------------------------------------------ flop counts ----
+
+class _CountingArray(np.ndarray):
+    """ndarray whose matrix products add their multiply-add count
+    (rows x inner x columns) to a shared tally and return plain arrays."""
+    tally = [0]
+
+    @staticmethod
+    def _count(a, b):
+        a, b = np.asarray(a), np.asarray(b)
+        inner = a.shape[-1]
+        rows = a.shape[0] if a.ndim == 2 else 1
+        cols = b.shape[1] if b.ndim == 2 else 1
+        _CountingArray.tally[0] += rows * inner * cols
+        return a @ b
+
+    def __matmul__(self, other):
+        return self._count(self, other)
+
+    def __rmatmul__(self, other):
+        return self._count(other, self)
+
+
+def _textbook_chol_inverse_fmas(m):
+    """Multiply-adds of the column Cholesky (one length-j dot per entry of
+    column j on and below the diagonal) and of the two triangular solves with
+    m right-hand sides (a length-i dot per row i and right-hand side), counted
+    by walking the loops."""
+    n = 0
+    for j in range(m):
+        for _ in range(j, m):
+            n += j
+    for i in range(m):
+        n += 2 * i * m
+    return n
+
+
+def test_flop_counts_match_counted_operations():
+    """plan_flops / sweep_flops (Section 4 cost model, FMA = 2 flops) against
+    the multiply-adds the oracle's own products perform (counted on the
+    operands) plus loop counts of the textbook factorisation and solves."""
+    p, K, h = 224, 3, 6
+    a = wl.matern32(wl.uniform_points(np.random.default_rng(3), p, 2), 0.2, 1.0, 1e-2)
+    sets = O.partition(p, K, h)
+    ac = a.view(_CountingArray)
+    for lo, hi in sets:
+        m = hi - lo
+        _CountingArray.tally[0] = 0
+        inv = O.block_invariants(ac, lo, hi)            # counts the W product
+        counted = 2 * (_CountingArray.tally[0] + _textbook_chol_inverse_fmas(m))
+        want = O.plan_flops(p, [(lo, hi)])
+        assert abs(want - counted) <= 2.0 / m * counted, (m, want, counted)
+        _CountingArray.tally[0] = 0
+        h_it = np.eye(p).view(_CountingArray)
+        inv.w = inv.w.view(_CountingArray)
+        O.block_update(h_it, inv)                        # W T and X W^T
+        assert O.sweep_flops(p, [(lo, hi)]) == 2 * _CountingArray.tally[0]
+    assert O.sweep_flops(p, sets) == sum(O.sweep_flops(p, [s]) for s in sets)
+
+
+# ------------------------------------------------------ stop-test cadence ----
+
+def test_check_every_tests_less_often_on_the_same_iterates():
+    """Algorithm 1 with the stop test every 3rd sweep: the iterates are those
+    of the per-sweep test (the test does not touch H), the tests fall on
+    sweeps 3, 6, ... and the last one, and convergence is seen at the first
+    tested sweep at or after the per-sweep run's stopping sweep."""
+    a = wl.matern32(wl.uniform_points(np.random.default_rng(8), 160, 2), 0.1, 1.0, 1e-2)
+    sets = O.partition(160, 4, 4)
+    every = O.ibmi(a, sets, tol=0.0, max_sweeps=7)
+    third = O.ibmi(a, sets, tol=0.0, max_sweeps=7, check_every=3)
+    assert np.array_equal(every.h, third.h)
+    assert [r for r, _, _ in third.history] == [3, 6, 7]
+    rf = {r: v for r, v, _ in every.history}
+    for r, v, _ in third.history:
+        assert v == rf[r]
+    ref = O.ibmi(a, sets, tol=1e-6, max_sweeps=200)
+    assert ref.status == "converged" and ref.sweeps % 3 != 0
+    got = O.ibmi(a, sets, tol=1e-6, max_sweeps=200, check_every=3)
+    r_star = 3 * math.ceil(ref.sweeps / 3)
+    assert got.status == "converged" and got.sweeps == r_star
+    assert np.array_equal(got.h, O.ibmi(a, sets, tol=0.0, max_sweeps=r_star).h)
+
+
+# ----------------------------------------------- Newton-Schulz divergence ----
+
+def test_newton_schulz_divergence_keeps_the_previous_iterate():
+    """eq. newton converges only when the spectral radius of I - A X is below
+    1.  KMS with the initial guess 100 I leaves, after one two-block sweep, an
+    error of q rho^2 [[1, -rho], [-rho, rho^2]] with q ~ 520 (the KMS
+    trajectory above), far outside that region: the step grows the residual,
+    so the tail stops and returns the iterate of the hand-over with its
+    residual."""
+    p, rho = 16, 0.9
+    a = wl.kms(p, rho)
+    sets = O.partition(p, 2, 0)
+    h0 = 100.0 * np.eye(p)
+    one = O.ibmi(a, sets, tol=0.0, max_sweeps=1, h0=h0)
+    assert max(abs(np.linalg.eigvals(np.eye(p) - a @ one.h))) > 1.0
+    res = O.ibmi(a, sets, tol=1e-12, max_sweeps=50, ns_theta=1e9, h0=h0)
+    assert res.status == "ns_diverged" and res.sweeps == 1 and res.ns_steps == 1
+    assert np.array_equal(res.h, one.h)
+    assert res.resid_f == one.resid_f
+    assert res.history[-1][2] > res.resid_f      # the rejected step's residual

@@ -50,6 +50,23 @@ def test_noalloc_residual_matches_allocating_entry(lib):
     assert results[0] != results[1]
 
 
+def test_noalloc_residual_matches_the_oracle_and_reads_the_lower_triangle(lib):
+    """Against the FP64 oracle's ||I - A H||_F / sqrt(p), with NaN in the
+    strict upper triangle of A (only the lower triangle may be read), two
+    calls in a row."""
+    from oracle import ibmi_oracle as O
+    for p, seed in ((333, 3), (1000, 4)):
+        rng = np.random.default_rng(seed)
+        A = wl.matern32(wl.uniform_points(rng, p, 2), 0.1, 1.0, 1e-2)
+        H = np.linalg.inv(A) + 1e-8 * rng.standard_normal((p, p))
+        want = O.residual_f(A, H)
+        An = A.copy()
+        An[np.triu_indices(p, 1)] = np.nan
+        dA, dH = torch.from_numpy(An).cuda(), torch.from_numpy(H).cuda()
+        got = _resid(lib, "ibmi_residual_noalloc", dA, dH)
+        assert got == pytest.approx(want, rel=1e-9)
+
+
 def test_noalloc_rejects_orders_beyond_its_scratch(lib):
     A = torch.empty((1, 1), dtype=torch.float64, device="cuda")
     out = C.c_double()
