@@ -72,8 +72,16 @@ typedef enum ibmi_stop_rule {
 
 typedef enum ibmi_init {
   IBMI_INIT_IDENTITY = 0,   /* H[I_1^c, I_1^c] = identity (Section 2.4)              */
-  IBMI_INIT_USER = 1        /* the caller's H holds the initial guess in H[I_1^c, I_1^c];
+  IBMI_INIT_USER = 1,       /* the caller's H holds the initial guess in H[I_1^c, I_1^c];
                                it should be SPD (Theorem of Section 3)               */
+  IBMI_INIT_SCHUR = 2       /* H[I_1^c, I_1^c] = A_{I_1^c}^{-1}, the inverse of A's block on
+                               the complement [hi_1, p) of the first set (one of the
+                               initial guesses of Section 5.6, Table 6), formed on the
+                               device: FP64 Cholesky of the block and its inverse (the
+                               mixed path forms Y^T Y, Y = L^{-1}, with exact sliced
+                               tensor-core products from order 1024).  The plan holds
+                               about 2 (p - m_1)^2 doubles for it.  A non-SPD block
+                               returns IBMI_ERR_NOT_SPD with bad_block = K.             */
 } ibmi_init;
 
 /* Plan description.  Fill with ibmi_plan_desc_init() then override fields. */
@@ -139,6 +147,28 @@ ibmi_status ibmi_plan_sets(ibmi_plan_t plan, int32_t* K, int64_t* lo, int64_t* h
  * IBMI_ERR_NONFINITE, IBMI_ERR_INVALID_ARG or IBMI_ERR_CUDA.  `out` may be NULL. */
 ibmi_status ibmi_invert(ibmi_plan_t plan, const double* A, int64_t lda, double* H,
                         int64_t ldh, void* stream, ibmi_result* out);
+
+/* Partial inverse (Section 6, Discussion: approximating only block-diagonal
+ * parts of the inverse): the diagonal blocks H[I_1, I_1] and H[I_2, I_2] of
+ * the IBMI iterate for a plan with exactly two sets (any overlap), without
+ * forming the rest of H.  With two sets the step for I_1 reads
+ * T = H[I_1^c, I_1^c], which lies inside H[I_2, I_2], and the step for I_2
+ * reads H[I_2^c, I_2^c] inside H[I_1, I_1] (eq. IBMI), so the two blocks
+ * evolve on their own with the same products as the full sweep; after the
+ * last sweep D holds exactly the diagonal blocks of the full iterate.
+ * D: device, m_1^2 + m_2^2 doubles: H[I_1, I_1] (m_1 x m_1, row-major), then
+ * H[I_2, I_2] (m_2 x m_2); written in full.  With IBMI_INIT_USER the second
+ * block of D carries the initial guess of H[I_2, I_2], of which only the
+ * part on I_1^c = [hi_1, p) is read.  Stop quantity (out->resid_f): the last
+ * set's rows of the residual, ||(H A - I)[I_2, :]||_F / sqrt(p), evaluated
+ * like the stop test of ibmi_invert (check_every and the cadence); it is zero
+ * exactly when H[I_2^c, I_2^c] is the inverse Schur complement.  The plan
+ * must be IBMI_FP64 with IBMI_STOP_RESID_F (else IBMI_ERR_INVALID_ARG).
+ * Work per sweep as ibmi_invert's; device memory m_1^2 + m_2^2 (the caller's
+ * D) plus m_max p + m_2 p doubles of scratch the plan allocates on first use,
+ * instead of the p^2 of H.  Returns like ibmi_invert. */
+ibmi_status ibmi_invert_block_diag(ibmi_plan_t plan, const double* A, int64_t lda, double* D, void* stream,
+                                   ibmi_result* out);
 
 /* Same on host buffers: copies A (and H for IBMI_INIT_USER) to the device,
  * runs ibmi_invert, copies H back.  Uses device scratch owned by the plan. */
@@ -253,6 +283,12 @@ void ibmi_prof_enable(int on);
 /* launches: launches of that class; ms: summed event time; flops: algorithmic
  * flops of those launches.  Returns IBMI_ERR_INVALID_ARG for a bad class. */
 ibmi_status ibmi_prof_get(int32_t kernel_class, int64_t* launches, double* ms, double* flops);
+/* Algorithmic flops of the launches of that class recorded so far: the flops
+ * of the products the method asks for (2 m n^2 for X = -W T, 2 p^3 for a
+ * residual, ...), whatever the sliced arithmetic issued to do them; a digit-
+ * sliced residual or update that keeps part of its pair products counts that
+ * share.  Equal to the flops of ibmi_prof_get for the FP64 classes. */
+ibmi_status ibmi_prof_get_alg(int32_t kernel_class, double* alg_flops);
 /* Total kernel launches made by this library since the last ibmi_prof_enable(1)
  * (counted whether or not profiling is on). */
 int64_t ibmi_launch_count(void);

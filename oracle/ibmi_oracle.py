@@ -36,7 +36,8 @@ import numpy as np
 __all__ = [
     "NotSPD", "partition", "complement", "cholesky", "forward_subst", "backward_subst",
     "spd_inverse", "block_invariants", "block_update", "residual_f", "paper_error",
-    "newton_schulz_step", "ibmi", "IbmiResult", "sweep_flops", "plan_flops",
+    "newton_schulz_step", "ibmi", "IbmiResult", "sweep_flops", "plan_flops", "schur_initial_guess",
+    "ibmi_block_diagonal", "BlockDiagResult",
 ]
 
 
@@ -155,6 +156,19 @@ def block_update(h: np.ndarray, inv: BlockInv) -> None:
     h[np.ix_(I, I)] = 0.5 * (S + S.T)
 
 
+def schur_initial_guess(a: np.ndarray, sets) -> np.ndarray:
+    """Initial iterate whose block on the complement of the first set is
+    A_{I_1^c}^{-1}, one of the initial guesses of Section 5.6 (Table 6); the
+    rest is the identity (only H[I_1^c, I_1^c] is read before it is
+    rewritten, Section 2.4)."""
+    p = a.shape[0]
+    h = np.eye(p)
+    ic = complement(p, *sets[0])
+    if len(ic):
+        h[np.ix_(ic, ic)] = spd_inverse(a[np.ix_(ic, ic)])
+    return h
+
+
 # --------------------------------------------------------------- errors ----
 
 def residual_f(a: np.ndarray, h: np.ndarray) -> float:
@@ -266,6 +280,72 @@ def ibmi(a: np.ndarray, sets, tol: float, max_sweeps: int = 500, h0: np.ndarray 
             res.status = "converged"
             return res
     res.status = "not_converged"
+    return res
+
+
+# ---------------------------------------------- partial (block-diagonal) ----
+
+@dataclass
+class BlockDiagResult:
+    d1: np.ndarray              # H[I_1, I_1]
+    d2: np.ndarray              # H[I_2, I_2]
+    status: str                 # "converged" | "not_converged" | "nonfinite"
+    sweeps: int = 0
+    resid_rows: float = float("nan")   # ||(H A - I)[I_2, :]||_F / sqrt(p), last evaluated
+
+
+def ibmi_block_diagonal(a: np.ndarray, sets, tol: float, max_sweeps: int = 500, t0=None,
+                        check_every: int = 1) -> BlockDiagResult:
+    """The diagonal blocks of the IBMI iterate alone, for two sets (the partial
+    inverse the Discussion of Section 6 proposes).  The step for I_1 reads
+    T = H[I_1^c, I_1^c], which lies inside H[I_2, I_2]; the step for I_2 reads
+    H[I_2^c, I_2^c], inside H[I_1, I_1] as just rewritten (eq. IBMI), so the
+    two blocks evolve on their own.  t0: initial H[I_2, I_2] (only its part on
+    I_1^c is read), identity if None.  The stop quantity is the last set's
+    rows of the residual, from H[I_2, :] = [X_2 | D_2]; afterwards the overlap
+    rows and columns of D_1 take what the last step for I_2 wrote there, as in
+    the full iterate."""
+    (l1, h1), (l2, h2) = sets
+    a = np.asarray(a, dtype=np.float64)
+    p = a.shape[0]
+    if len(sets) != 2 or l1 != 0 or h2 != p or l2 > h1:
+        raise ValueError("two sets covering [0, p)")
+    inv1, inv2 = block_invariants(a, l1, h1), block_invariants(a, l2, h2)
+    ov = h1 - l2
+    d1 = np.eye(h1 - l1)
+    d2 = np.eye(h2 - l2) if t0 is None else np.array(t0, dtype=np.float64, copy=True)
+    res = BlockDiagResult(d1, d2, "not_converged")
+    x2 = None
+    r = 0
+    while True:
+        r += 1
+        t1 = d2[ov:, ov:]                        # H[I_1^c, I_1^c]
+        x1 = -(inv1.w @ t1)
+        s1 = inv1.ainv - x1 @ inv1.w.T
+        d1 = 0.5 * (s1 + s1.T)
+        t2 = d1[:l2, :l2]                        # H[I_2^c, I_2^c]
+        x2 = -(inv2.w @ t2)
+        s2 = inv2.ainv - x2 @ inv2.w.T
+        d2 = 0.5 * (s2 + s2.T)
+        res.sweeps = r
+        if r % check_every != 0 and r < max_sweeps:
+            continue
+        rows = np.hstack([x2, d2])               # H[I_2, :] (columns I_2^c = [0, l2) first)
+        R = rows @ a - np.eye(p)[l2:h2]
+        res.resid_rows = float(np.sqrt(np.sum(R * R)) / math.sqrt(p))
+        if not math.isfinite(res.resid_rows):
+            res.status = "nonfinite"
+            break
+        if res.resid_rows <= tol:
+            res.status = "converged"
+            break
+        if r >= max_sweeps:
+            break
+    d1 = d1.copy()
+    d1[l2:h1, :l2] = x2[:ov]
+    d1[:l2, l2:h1] = x2[:ov].T
+    d1[l2:h1, l2:h1] = d2[:ov, :ov]
+    res.d1, res.d2 = d1, d2
     return res
 
 

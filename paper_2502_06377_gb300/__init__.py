@@ -12,7 +12,7 @@ import ctypes as C
 import numpy as np
 
 from . import _lib
-from ._lib import (IBMI_FP64, IBMI_MIXED, IBMI_INIT_IDENTITY, IBMI_INIT_USER,  # noqa: F401
+from ._lib import (IBMI_FP64, IBMI_MIXED, IBMI_INIT_IDENTITY, IBMI_INIT_USER, IBMI_INIT_SCHUR,  # noqa: F401
                    IBMI_STOP_RESID_F, IBMI_STOP_PAPER_EST, IBMI_OK, IBMI_NOT_CONVERGED,
                    IBMI_ERR_NOT_SPD, IBMI_ERR_INVALID_ARG, IBMI_ERR_NONFINITE, IBMI_ERR_OOM,
                    IBMI_ERR_TIMEOUT, IBMI_ERR_CUDA, ibmi_plan_desc, ibmi_result)
@@ -95,6 +95,18 @@ def ibmi_invert(plan: Plan, A, H, stream=None):
     res = ibmi_result()
     s = _lib.load().ibmi_invert(plan.handle, C.c_void_p(A.data_ptr()), A.stride(0),
                                 C.c_void_p(H.data_ptr()), H.stride(0), _stream_ptr(stream), C.byref(res))
+    return s, res.as_dict()
+
+
+def ibmi_invert_block_diag(plan: Plan, A, D, stream=None):
+    """Diagonal blocks of the iterate for a two-set plan: D is a float64 CUDA
+    tensor of m_1^2 + m_2^2 elements (H[I_1, I_1] then H[I_2, I_2], row-major).
+    Returns (status, result dict)."""
+    assert str(A.dtype) == "torch.float64" and A.is_cuda and A.stride(1) == 1
+    assert str(D.dtype) == "torch.float64" and D.is_cuda and D.is_contiguous()
+    res = ibmi_result()
+    s = _lib.load().ibmi_invert_block_diag(plan.handle, C.c_void_p(A.data_ptr()), A.stride(0),
+                                           C.c_void_p(D.data_ptr()), _stream_ptr(stream), C.byref(res))
     return s, res.as_dict()
 
 

@@ -1,6 +1,6 @@
 """Command-line runner for single library calls on cuda:0.
 
-  python -m paper_2502_06377_gb300 invert   --p 4096 --K 8 --h 32 --precision mixed
+  python -m paper_2502_06377_gb300 invert   --p 4096 --K 8 --h 32 --precision mixed --theta 0.9
   python -m paper_2502_06377_gb300 residual --p 4096 --method tc
 
 Inputs are the seeded Matern-3/2 covariance of the benchmark (points in the
@@ -31,6 +31,8 @@ def main():
                     help="matern: the Matern-3/2 workload; random_spd: Q diag(lambda) Q^T, lambda "
                          "log-uniform in [1, 1e4] (seed 3)")
     ap.add_argument("--max-sweeps", type=int, default=500)
+    ap.add_argument("--theta", type=float, default=0.5,
+                    help="Newton-Schulz hand-over on ||I - A H||_F (mixed precision)")
     a = ap.parse_args()
 
     import numpy as np
@@ -47,7 +49,7 @@ def main():
     prec = ibmi.IBMI_MIXED if a.precision == "mixed" else ibmi.IBMI_FP64
     if a.cmd == "invert":
         plan = ibmi.ibmi_plan(a.p, K=a.K, h=a.h, precision=prec, tol=a.tol, max_sweeps=a.max_sweeps,
-                              ns_theta=0.5 if prec == ibmi.IBMI_MIXED else 0.0)
+                              ns_theta=a.theta if prec == ibmi.IBMI_MIXED else 0.0)
         ibmi._lib.load().ibmi_prof_enable(1)
         out = None
         for _ in range(a.repeat):

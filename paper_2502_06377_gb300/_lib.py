@@ -31,6 +31,7 @@ IBMI_STOP_RESID_F = 0
 IBMI_STOP_PAPER_EST = 1
 IBMI_INIT_IDENTITY = 0
 IBMI_INIT_USER = 1
+IBMI_INIT_SCHUR = 2
 
 
 class ibmi_plan_desc(C.Structure):
@@ -64,6 +65,7 @@ _SIGS = {
     "ibmi_plan_sets": (C.c_int, [_P, C.POINTER(C.c_int32), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "ibmi_invert": (C.c_int, [_P, _P, C.c_int64, _P, C.c_int64, _P, C.POINTER(ibmi_result)]),
     "ibmi_invert_host": (C.c_int, [_P, _P, C.c_int64, _P, C.c_int64, _P, C.POINTER(ibmi_result)]),
+    "ibmi_invert_block_diag": (C.c_int, [_P, _P, C.c_int64, _P, _P, C.POINTER(ibmi_result)]),
     "ibmi_residual": (C.c_int, [_P, C.c_int64, _P, C.c_int64, C.c_int64, _P, _D]),
     "ibmi_residual_tc": (C.c_int, [_P, C.c_int64, _P, C.c_int64, C.c_int64, _P, _D]),
     "ibmi_residual_noalloc": (C.c_int, [_P, C.c_int64, _P, C.c_int64, C.c_int64, _P, _D]),
@@ -72,6 +74,7 @@ _SIGS = {
                               C.POINTER(ibmi_result)]),
     "ibmi_prof_enable": (None, [C.c_int]),
     "ibmi_prof_get": (C.c_int, [C.c_int32, C.POINTER(C.c_int64), _D, _D]),
+    "ibmi_prof_get_alg": (C.c_int, [C.c_int32, _D]),
     "ibmi_launch_count": (C.c_int64, []),
     "ibmi_status_string": (C.c_char_p, [C.c_int]),
     "ibmi_last_error": (C.c_char_p, []),

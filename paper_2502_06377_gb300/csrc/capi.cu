@@ -130,6 +130,11 @@ static ibmi_status invert_impl(ibmi_plan_s* P, const double* A, int64_t lda, dou
     return IBMI_ERR_NOT_SPD;
   }
   if (d.init == IBMI_INIT_IDENTITY) IBMI_TRY(set_identity(H, ldh, p, st));
+  if (d.init == IBMI_INIT_SCHUR) {
+    IBMI_TRY(schur_guess_launch(P, A, lda, H, ldh, st, nullptr));
+    IBMI_TRY(schur_guess_status(P, st, res));
+    flops += schur_guess_flops(P);
+  }
   // Algorithm 1: sweeps with the stop test every check_every sweeps
   ibmi_status status = IBMI_NOT_CONVERGED;
   bool to_ns = false;
@@ -230,7 +235,8 @@ ibmi_status ibmi_plan(const ibmi_plan_desc* desc, ibmi_plan_t* out) {
     set_last_error("the paper's estimate is offered as stop rule on the FP64 path only");
     return IBMI_ERR_INVALID_ARG;
   }
-  if (d.init != IBMI_INIT_IDENTITY && d.init != IBMI_INIT_USER) return IBMI_ERR_INVALID_ARG;
+  if (d.init != IBMI_INIT_IDENTITY && d.init != IBMI_INIT_USER && d.init != IBMI_INIT_SCHUR)
+    return IBMI_ERR_INVALID_ARG;
   if (d.max_sweeps < 1 || d.check_every < 1 || d.ns_max < 0 || !(d.tol >= 0.0) || !(d.ns_theta >= 0.0))
     return IBMI_ERR_INVALID_ARG;
   ibmi_plan_s* P = new ibmi_plan_s();
@@ -317,6 +323,10 @@ ibmi_status ibmi_plan(const ibmi_plan_desc* desc, ibmi_plan_t* out) {
     ibmi_status s = mixed_create(P);
     if (s != IBMI_OK) { ibmi_plan_destroy(P); return s; }
   }
+  if (d.init == IBMI_INIT_SCHUR) {
+    ibmi_status s = schur_guess_create(P);
+    if (s != IBMI_OK) { ibmi_plan_destroy(P); return s; }
+  }
   *out = P;
   return IBMI_OK;
 }
@@ -324,6 +334,9 @@ ibmi_status ibmi_plan(const ibmi_plan_desc* desc, ibmi_plan_t* out) {
 ibmi_status ibmi_plan_destroy(ibmi_plan_t P) {
   if (!P) return IBMI_ERR_INVALID_ARG;
   if (P->mixed) mixed_destroy(P);
+  schur_guess_destroy(P);
+  cudaFree(P->bdX);
+  cudaFree(P->bdRows);
   cudaFree(P->pool);
   cudaFree(P->bat_pool);
   cudaFree(P->dstatus);
@@ -596,6 +609,7 @@ struct ProfClass {
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
   int64_t launches = 0;
   double flops = 0.0;
+  double alg = 0.0;
   double ms = 0.0;
 };
 std::atomic<bool> g_prof_on{false};
@@ -630,7 +644,7 @@ void prof_begin(int k, cudaStream_t st) {
   cudaEventRecord(g_open_event, st);
 }
 
-void prof_end(int k, cudaStream_t st, double flops) {
+void prof_end(int k, cudaStream_t st, double flops, double alg) {
   if (!g_prof_on.load(std::memory_order_relaxed) || k != g_open_class || !g_open_event) return;
   std::lock_guard<std::mutex> g(g_prof_mu);
   cudaEvent_t e = take_event();
@@ -638,6 +652,7 @@ void prof_end(int k, cudaStream_t st, double flops) {
   g_prof[k].ev.emplace_back(g_open_event, e);
   g_prof[k].launches += 1;
   g_prof[k].flops += flops;
+  g_prof[k].alg += alg;
   g_open_event = nullptr;
   g_open_class = -1;
 }
@@ -675,6 +690,14 @@ ibmi_status ibmi_prof_get(int32_t k, int64_t* launches, double* ms, double* flop
   if (launches) *launches = c.launches;
   if (ms) *ms = c.ms;
   if (flops) *flops = c.flops;
+  return IBMI_OK;
+}
+
+ibmi_status ibmi_prof_get_alg(int32_t k, double* alg_flops) {
+  using namespace ibmi;
+  if (k < 0 || k >= IBMI_K_COUNT || !alg_flops) return IBMI_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> g(g_prof_mu);
+  *alg_flops = g_prof[k].alg;
   return IBMI_OK;
 }
 

@@ -31,13 +31,16 @@ void set_last_error(const std::string& s);
 bool prof_on();
 void note_launch(int n = 1);
 void prof_begin(int kclass, cudaStream_t st);
-void prof_end(int kclass, cudaStream_t st, double flops);
+void prof_end(int kclass, cudaStream_t st, double flops, double alg_flops);
 
-// Scoped helper: times everything launched on `st` inside the scope as class k.
+// Scoped helper: times everything launched on `st` inside the scope as class
+// k.  flops: operations issued to the executing unit (a sliced product counts
+// every slice product); alg: the flops of the product the method itself asks
+// for (its share, for a launch that forms part of one); negative = flops.
 struct ProfScope {
-  int k; cudaStream_t st; double flops;
-  ProfScope(int k_, cudaStream_t s, double f) : k(k_), st(s), flops(f) { prof_begin(k, st); }
-  ~ProfScope() { prof_end(k, st, flops); }
+  int k; cudaStream_t st; double flops, alg;
+  ProfScope(int k_, cudaStream_t s, double f, double a = -1.0) : k(k_), st(s), flops(f), alg(a) { prof_begin(k, st); }
+  ~ProfScope() { prof_end(k, st, flops, alg < 0.0 ? flops : alg); }
 };
 
 // Logical index l in [0, n) of I^c -> physical row/column of A or H, for the

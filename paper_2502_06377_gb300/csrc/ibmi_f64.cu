@@ -315,6 +315,51 @@ ibmi_status residual_f64_dev(const double* A, int64_t lda, const double* H, int6
   return IBMI_OK;
 }
 
+// Residual rows: out[0] = ||(H A)[rows] - I[rows]||_F / sqrt(p) for the m
+// rows H[row0 .. row0 + m) of an iterate, given as an m x p strip.
+struct EpiResidualRows {
+  double* partials; int64_t row0;
+  double s;
+  __device__ void begin() { s = 0.0; }
+  __device__ __forceinline__ void operator()(int64_t i, int64_t j, double acc) {
+    const double r = (i + row0 == j ? 1.0 : 0.0) - acc;
+    s = fma(r, r, s);
+  }
+  __device__ void end() {
+    __shared__ double red[F64_THREADS / 32];
+    double v = s;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < F64_THREADS / 32; ++w) t += red[w];
+      partials[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = t;
+    }
+  }
+};
+
+ibmi_status residual_rows_f64_dev(const double* Hrows, int64_t ldh, int64_t m, int64_t row0, const double* A,
+                                  int64_t lda, int64_t p, double* partials, int64_t n_partials, double* dout,
+                                  cudaStream_t st) {
+  const GapMap id{0, 0};
+  if (gemm_f64_ctas(m, p) > n_partials) return IBMI_ERR_INVALID_ARG;
+  ProfScope ps(IBMI_K_RESIDUAL, st, 2.0 * (double)m * p * p);
+  F64Operands op{Hrows, ldh, id, id, A, lda, id, id, m, p, p};
+  IBMI_CUDA_TRY((launch_gemm_f64<true, true>(op, EpiResidualRows{partials, row0, 0.0}, st)));
+  note_launch();
+  k_finish_residual<<<1, 1024, 0, st>>>(partials, gemm_f64_ctas(m, p), p, dout);
+  IBMI_CUDA_TRY(cudaGetLastError());
+  return IBMI_OK;
+}
+
+ibmi_status symmetrize_into(const double* S, int64_t m, double* H, int64_t ldh, int64_t lo, cudaStream_t st) {
+  note_launch();
+  k_symmetrize_into<<<nblk(m * m), 256, 0, st>>>(S, m, H, ldh, lo);
+  IBMI_CUDA_TRY(cudaGetLastError());
+  return IBMI_OK;
+}
+
 // ------------------------------------------------------- Newton-Schulz ----
 
 __global__ void k_symmetrize_full(const double* Xn, int64_t p, double* X, int64_t ldx) {

@@ -358,7 +358,7 @@ ibmi_status mixed_sweep_step(ibmi_plan_s* P, int k, cudaStream_t st) {
     }
     tc::Tiles t{m, 0, 0, nr.r0_end, nr.r1_begin, kr.r0_end, kr.r1_begin, kr.r1_end, 1, M->err};
     EpiTcSweepX epi{{}, M->Hf, M->Hs[0], M->Hs[1], S == 3 ? M->Hs[2] : nullptr, M->ldp, lo, hi, p, m};
-    ProfScope ps(IBMI_K_SWEEP_X, st, mult * 2.0 * m * n * n);
+    ProfScope ps(IBMI_K_SWEEP_X, st, mult * 2.0 * m * n * n, 2.0 * m * n * n);
     if (S == 2) IBMI_CUDA_TRY((tc::launch<2, MX_BN>(maps, t, nr.count(), (int)((m + 127) / 128), epi, st)));
     else IBMI_CUDA_TRY((tc::launch<3, MX_BN>(maps, t, nr.count(), (int)((m + 127) / 128), epi, st)));
   }
@@ -375,7 +375,8 @@ ibmi_status mixed_sweep_step(ibmi_plan_s* P, int k, cudaStream_t st) {
     tc::Tiles t{m, lo, 0, ntn, ntn, kr.r0_end, kr.r1_begin, kr.r1_end, splits, M->err};
     t.lower = 1;   // P is symmetric up to rounding: tiles on and below the diagonal only
     EpiTcPartial epi{{}, M->Spart, m};
-    ProfScope ps(IBMI_K_SWEEP_S, st, mult * 2.0 * n * (double)(ntn * (ntn + 1) / 2) * MX_BN * MX_BN);
+    ProfScope ps(IBMI_K_SWEEP_S, st, mult * 2.0 * n * (double)(ntn * (ntn + 1) / 2) * MX_BN * MX_BN,
+                 2.0 * m * m * n);
     if (S == 2) IBMI_CUDA_TRY((tc::launch<2, MX_BN>(maps, t, ntn, (int)((m + 127) / 128), epi, st)));
     else IBMI_CUDA_TRY((tc::launch<3, MX_BN>(maps, t, ntn, (int)((m + 127) / 128), epi, st)));
     note_launch();
@@ -427,6 +428,7 @@ ibmi_status mixed_run(ibmi_plan_s* P, const double* A, int64_t lda, double* H, i
         IBMI_TRY(refine_block_inverse(R, P->bat_R + (int64_t)k * P->mmax * P->mmax, P->mmax, P->hi[k] - P->lo[k],
                                       P->ainv[k], st));
     if (d.init == IBMI_INIT_IDENTITY) IBMI_TRY(set_identity(H, ldh, p, st));
+    if (d.init == IBMI_INIT_SCHUR) IBMI_TRY(schur_guess_launch(P, A, lda, H, ldh, st, R));
     IBMI_TRY(refine_set_matrix(R, A, lda, st));
     if (R->w_rows > 0) {
       std::vector<const double*> ainv(P->ainv.begin(), P->ainv.end());
@@ -438,7 +440,8 @@ ibmi_status mixed_run(ibmi_plan_s* P, const double* A, int64_t lda, double* H, i
     }
     return mixed_prepare(P, H, ldh, st);
   }));
-  *flops += fplan;
+  *flops += fplan + (d.init == IBMI_INIT_SCHUR ? schur_guess_flops(P) : 0.0);
+  IBMI_TRY(schur_guess_status(P, st, res));
   DevStatus hs;
   IBMI_CUDA_TRY(cudaMemcpyAsync(&hs, P->dstatus, sizeof(hs), cudaMemcpyDeviceToHost, st));
   IBMI_CUDA_TRY(cudaStreamSynchronize(st));

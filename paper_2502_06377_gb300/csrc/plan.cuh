@@ -43,6 +43,13 @@ struct ibmi_plan_s {
   double* dH = nullptr;
   // mixed-precision state (allocated at plan time when precision == MIXED)
   void* mixed = nullptr;
+  // IBMI_INIT_SCHUR: one-set plan over the complement [hi_1, p) of the first
+  // set, whose block inverse is the initial guess (guess.cu)
+  ibmi_plan_s* guess = nullptr;
+  // ibmi_invert_block_diag scratch (allocated on first use): X of one set
+  // (mmax x p) and the last set's rows of H (m_K x p)
+  double* bdX = nullptr;
+  double* bdRows = nullptr;
 };
 
 namespace ibmi {
@@ -69,6 +76,15 @@ ibmi_status residual_f64_dev(const double* A, int64_t lda, const double* H, int6
                              double* partials, int64_t n_partials, double* dout, cudaStream_t st,
                              bool a_lower = false);
 
+// ||(H A)[rows] - I[rows]||_F / sqrt(p) for the m rows [row0, row0 + m) of an
+// iterate given as an m x p strip (row pitch ldh); value left in *dout.
+ibmi_status residual_rows_f64_dev(const double* Hrows, int64_t ldh, int64_t m, int64_t row0, const double* A,
+                                  int64_t lda, int64_t p, double* partials, int64_t n_partials, double* dout,
+                                  cudaStream_t st);
+
+// H[lo + i, lo + j] = (S[i, j] + S[j, i]) / 2 for an m x m S (row pitch m).
+ibmi_status symmetrize_into(const double* S, int64_t m, double* H, int64_t ldh, int64_t lo, cudaStream_t st);
+
 // Device memory of the current device (plain or managed): the pointer checks
 // of the entry points.
 bool is_device_ptr(const void* ptr);
@@ -87,6 +103,22 @@ inline ibmi_status copy_square(double* dst, int64_t ldd, const double* src, int6
 }
 
 ibmi_status set_identity(double* H, int64_t ldh, int64_t p, cudaStream_t st);
+
+// IBMI_INIT_SCHUR (guess.cu): workspace of the complement block of the first
+// set; H = identity with H[I_1^c, I_1^c] = A_{I_1^c}^{-1} (R: the mixed path's
+// refinement state, whose sliced Y^T Y serves blocks of order >= 1024; NULL:
+// FP64); its algorithmic flops; NOT_SPD of that block (bad_block = K) after
+// a stream sync.
+struct RefineState;
+ibmi_status schur_guess_create(ibmi_plan_s* P);
+void schur_guess_destroy(ibmi_plan_s* P);
+ibmi_status schur_guess_launch(ibmi_plan_s* P, const double* A, int64_t lda, double* H, int64_t ldh,
+                               cudaStream_t st, RefineState* R);
+// The guess block alone: A_{I_1^c}^{-1} into T0 ((p - hi_1) x (p - hi_1), row pitch ldt).
+ibmi_status schur_guess_block(ibmi_plan_s* P, const double* A, int64_t lda, double* T0, int64_t ldt,
+                              cudaStream_t st, RefineState* R);
+double schur_guess_flops(const ibmi_plan_s* P);
+ibmi_status schur_guess_status(ibmi_plan_s* P, cudaStream_t st, ibmi_result* res);
 
 // S (ld lds) = the symmetric matrix whose lower triangle is A's; the strict
 // upper triangle of A is never read.

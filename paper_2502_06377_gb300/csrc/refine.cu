@@ -551,9 +551,10 @@ struct DigitGemm {
   int kt0, kt1;
   int qmax;
   int kclass;
+  double alg_first = 0.0;   // algorithmic flops of the product (recorded with its first launch)
 };
 
-static ibmi_status digit_gemm(RefineState* R, const DigitGemm& g, cudaStream_t st) {
+static ibmi_status digit_gemm(RefineState* R, DigitGemm g, cudaStream_t st) {
   const int64_t p = R->p, ldp = R->ldp;
   const int chunk_tiles = OZ_KCHUNK / tc::BK;
   const int BNr = R->bn;
@@ -573,7 +574,8 @@ static ibmi_status digit_gemm(RefineState* R, const DigitGemm& g, cudaStream_t s
         t.pdl = 1;   // digit planes are written only by the slicing kernels
         int* Tq = R->T + (int64_t)q * p * ldp;
         EpiOzAcc epi{{}, Tq, ldp, g.M, g.N, first ? 1 : 0};
-        ProfScope ps(g.kclass, st, 2.0 * (double)g.M * g.N * (double)(k1 - k0) * tc::BK);
+        ProfScope ps(g.kclass, st, 2.0 * (double)g.M * g.N * (double)(k1 - k0) * tc::BK, g.alg_first);
+        g.alg_first = 0.0;   // the product's algorithmic flops go with its first launch
         IBMI_TRY(with_bn(R, [&](auto bn) -> ibmi_status {
           IBMI_CUDA_TRY((tc::launch<1, decltype(bn)::value>(maps, t, grid_n, grid_m, epi, st)));
           return IBMI_OK;
@@ -620,7 +622,17 @@ static ibmi_status pair_products(RefineState* R, const CUtensorMap* ma, int nsa,
   g.M = p;
   g.N = p;
   g.err = R->err;
-  ProfScope ps(kclass, st, 2.0 * n * (double)p * p * (double)g.kt_total * tc::BK);
+  // the method's share: these pairs out of all pairs of the full product
+  // (52 for the residual, 15 for the Newton-Schulz update), of 2 p^3
+  auto count_pairs = [](int na, int nb, int qm) {
+    int c = 0;
+    for (int q = 0; q <= qm; ++q)
+      for (int a = 0; a <= q; ++a) c += (a < na && q - a < nb) ? 1 : 0;
+    return c;
+  };
+  const int full = kclass == IBMI_K_NS ? count_pairs(NS_S, NS_S, NS_S - 1) : count_pairs(OZ_SX, OZ_SA, OZ_QMAX);
+  ProfScope ps(kclass, st, 2.0 * n * (double)p * p * (double)g.kt_total * tc::BK,
+               2.0 * (double)p * p * p * n / full);
   return with_bn(R, [&](auto bn) -> ibmi_status {
     IBMI_CUDA_TRY(tc::launch_oz_pairs<decltype(bn)::value>(maps, g, st));
     return IBMI_OK;
@@ -657,7 +669,8 @@ ibmi_status refine_form_w(RefineState* R, const double* Ainv, int64_t m, int64_t
     IBMI_TRY(slice_digits(R, Ainv, m, R->Xo, NW_A, R->expX, st, m, m, lo));
   }
   IBMI_TRY(digit_gemm(R, DigitGemm{R->mXo, NW_A, R->mAo, NW_B, m, p, (int)(lo / tc::BK),
-                                   (int)((hi + tc::BK - 1) / tc::BK), QW, IBMI_K_INVARIANTS_TC}, st));
+                                   (int)((hi + tc::BK - 1) / tc::BK), QW, IBMI_K_INVARIANTS_TC,
+                                   2.0 * (double)m * m * (double)(p - m)}, st));
   ProfScope ps(IBMI_K_OTHER, st, 0.0);
   note_launch();
   k_oz_wcombine<<<grid2(ldp, m), 256, 0, st>>>(R->T, p * ldp, m, p, ldp, R->expX, R->expA, QW, lo, hi, W0, W1, W2);
@@ -722,6 +735,11 @@ ibmi_status refine_form_w_all(RefineState* R, const std::vector<const double*>& 
     flops += 2.0 * (double)((hi[k] - lo[k] + 127) / 128 * 128) * p *
              (double)(((hi[k] + tc::BK - 1) / tc::BK - lo[k] / tc::BK) * tc::BK);
   const int grid_n = (int)((p + R->bn - 1) / R->bn), grid_m = (int)(rows / 128);
+  double alg_w = 0.0;   // 2 m^2 (p - m) per set: W = A_I^{-1} A_{I, I^c}
+  for (int k = 0; k < K; ++k) {
+    const double m = (double)(hi[k] - lo[k]);
+    alg_w += 2.0 * m * m * ((double)p - m);
+  }
   for (int q = 0; q <= QW; ++q) {
     bool first = true;
     for (int s = 0; s <= q; ++s) {
@@ -734,7 +752,8 @@ ibmi_status refine_form_w_all(RefineState* R, const std::vector<const double*>& 
       t.mkr = R->w_kr;
       t.pdl = 1;
       EpiOzAcc epi{{}, R->T + (int64_t)q * rows * ldp, ldp, rows, p, first ? 1 : 0};
-      ProfScope ps(IBMI_K_INVARIANTS_TC, st, flops);
+      ProfScope ps(IBMI_K_INVARIANTS_TC, st, flops, alg_w);
+      alg_w = 0.0;   // W's algorithmic flops go with the first pair launch
       IBMI_TRY(with_bn(R, [&](auto bn) -> ibmi_status {
         IBMI_CUDA_TRY((tc::launch<1, decltype(bn)::value>(maps, t, grid_n, grid_m, epi, st)));
         return IBMI_OK;
@@ -831,7 +850,8 @@ ibmi_status refine_block_inverse(RefineState* R, const double* Y, int64_t ldy, i
   g.N = m;
   g.err = R->err;
   {
-    ProfScope ps(IBMI_K_INVARIANTS_TC, st, 2.0 * n * (double)m * m * (double)g.kt_total * tc::BK);
+    ProfScope ps(IBMI_K_INVARIANTS_TC, st, 2.0 * n * (double)m * m * (double)g.kt_total * tc::BK,
+                 (double)m * m * m / 3.0);   // Y^T Y with triangular Y, lower half
     IBMI_TRY(with_bn(R, [&](auto bn) -> ibmi_status {
       IBMI_CUDA_TRY(tc::launch_oz_pairs<decltype(bn)::value>(maps, g, st));
       return IBMI_OK;
@@ -933,7 +953,7 @@ ibmi_status refine_cheap_residual_launch(RefineState* R, const CUtensorMap* mapH
   const int grid_n = (int)((p + RF_BN - 1) / RF_BN), grid_m = (int)((p + 127) / 128);
   int grid = 0;
   {
-    ProfScope ps(IBMI_K_RESIDUAL, st, 3.0 * 2.0 * (double)p * p * p);
+    ProfScope ps(IBMI_K_RESIDUAL, st, 3.0 * 2.0 * (double)p * p * p, 2.0 * (double)p * p * p);
     tc::Tiles t{p, 0, 0, grid_n, 0, 0, 0, nkt, 1, R->err};
     EpiResidSq epi{R->partials, p, 0.0};
     IBMI_CUDA_TRY((tc::launch<2, RF_BN>(maps, t, grid_n, grid_m, epi, st, &grid)));

@@ -411,3 +411,66 @@ def test_newton_schulz_divergence_keeps_the_previous_iterate():
     assert np.array_equal(res.h, one.h)
     assert res.resid_f == one.resid_f
     assert res.history[-1][2] > res.resid_f      # the rejected step's residual
+
+
+# ------------------------------------------------ initial guess (Table 6) ----
+
+def test_schur_initial_guess_kms_closed_form():
+    """For KMS the complement block of the first set is again a KMS matrix,
+    whose inverse is the tridiagonal closed form."""
+    p, rho = 48, 0.7
+    a = wl.kms(p, rho)
+    sets = O.partition(p, 3, 2)
+    h0 = O.schur_initial_guess(a, sets)
+    hi1 = sets[0][1]
+    np.testing.assert_allclose(h0[hi1:, hi1:], kms_inverse(p - hi1, rho), rtol=0, atol=1e-12)
+    np.testing.assert_array_equal(h0[:hi1], np.eye(p)[:hi1])
+    np.testing.assert_array_equal(h0[:, :hi1], np.eye(p)[:, :hi1])
+
+
+def test_schur_initial_guess_two_blocks_is_the_second_block_inverse():
+    """Two non-overlapping sets: I_1^c = I_2, so T_0 = A_2^{-1} (LAPACK)."""
+    a = rand_spd(40, 21)
+    sets = O.partition(40, 2, 0)
+    h0 = O.schur_initial_guess(a, sets)
+    np.testing.assert_allclose(h0[20:, 20:], np.linalg.inv(a[20:, 20:]), rtol=0, atol=1e-10)
+
+
+# ------------------------------------- partial (block-diagonal) inverse ----
+
+@pytest.mark.parametrize("p,h", [(40, 0), (48, 5), (60, 12)])
+@pytest.mark.parametrize("r", [1, 2, 5])
+def test_block_diagonal_equals_the_full_iterates_blocks(p, h, r):
+    """The two-set recurrence on the diagonal blocks alone reproduces, sweep
+    by sweep, the diagonal blocks of the full Algorithm 1 iterate, and its
+    stop quantity is the norm of the full residual's rows I_2."""
+    a = rand_spd(p, 30 + p)
+    sets = O.partition(p, 2, h)
+    (l1, h1), (l2, h2) = sets
+    full = O.ibmi(a, sets, tol=0.0, max_sweeps=r)
+    part = O.ibmi_block_diagonal(a, sets, tol=0.0, max_sweeps=r)
+    assert part.sweeps == r
+    np.testing.assert_allclose(part.d1, full.h[:h1, :h1], rtol=0, atol=1e-13)
+    np.testing.assert_allclose(part.d2, full.h[l2:, l2:], rtol=0, atol=1e-13)
+    R = full.h[l2:] @ a - np.eye(p)[l2:]
+    assert part.resid_rows == pytest.approx(np.linalg.norm(R) / math.sqrt(p), rel=1e-10)
+
+
+def test_block_diagonal_kms_closed_form_and_convergence():
+    """KMS, two non-overlapping sets, identity guess: converged blocks are
+    those of the tridiagonal closed-form inverse; a random SPD matrix with
+    overlapping sets converges to LAPACK's blocks."""
+    p = 64
+    a = wl.kms(p, 0.6)
+    res = O.ibmi_block_diagonal(a, O.partition(p, 2, 0), tol=1e-13)
+    inv = kms_inverse(p, 0.6)
+    assert res.status == "converged"
+    np.testing.assert_allclose(res.d1, inv[:32, :32], rtol=0, atol=1e-12)
+    np.testing.assert_allclose(res.d2, inv[32:, 32:], rtol=0, atol=1e-12)
+    b = rand_spd(50, 77, cond=20.0)
+    sets = O.partition(50, 2, 6)
+    res = O.ibmi_block_diagonal(b, sets, tol=1e-13, max_sweeps=400)
+    invb = np.linalg.inv(b)
+    assert res.status == "converged"
+    np.testing.assert_allclose(res.d1, invb[:31, :31], rtol=0, atol=1e-10)
+    np.testing.assert_allclose(res.d2, invb[19:, 19:], rtol=0, atol=1e-10)
