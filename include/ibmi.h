@@ -182,6 +182,70 @@ ibmi_status ibmi_residual(const double* A, int64_t lda, const double* H, int64_t
                           int64_t p, void* stream, double* out);
 
 /* ------------------------------------------------------------------------
+ * Partition and ordering search for one matrix.
+ *
+ * Section 5.4 (Tables 3-4) finds the overlap of the sets decisive for the
+ * convergence of Algorithm 1 and the number of sets less so; Section 5.7 finds
+ * the ordering of the rows decisive as well (a red-black ordering of a matrix
+ * that contiguous sets over its natural ordering invert in a few sweeps
+ * mostly fails to converge), and the discussion closing Section 5 recommends
+ * orderings that keep the weight of the matrix near its diagonal.
+ * ------------------------------------------------------------------------ */
+typedef enum ibmi_order {
+  IBMI_ORDER_IDENTITY = 0,  /* the given order                                            */
+  IBMI_ORDER_XSORT = 1,     /* by the first coordinate (stable)                           */
+  IBMI_ORDER_HILBERT = 2,   /* along a Hilbert curve through the bounding box of the
+                               points (any dimension; 62 / dim bits per axis, at most 20)  */
+  IBMI_ORDER_KD = 3,        /* leaves of a k-d tree: median split across the coordinate of
+                               widest spread, recursively, left half first                 */
+  IBMI_ORDER_REDBLACK = 4   /* even positions of the given order, then odd positions (the
+                               red-black ordering Section 5.7 compares against)           */
+} ibmi_order;
+
+/* Ordering of n points (host, n x dim row-major doubles, 1 <= dim <= 16):
+ * perm[i] (host, n entries) = the index of the point placed at position i, so
+ * that the covariance matrix in the new order is A'[i][j] = A[perm[i]][perm[j]].
+ * Host code only.  IBMI_ERR_INVALID_ARG for a bad order, size or a non-finite
+ * coordinate. */
+ibmi_status ibmi_order_points(const double* points, int64_t n, int32_t dim, int32_t order, int64_t* perm);
+
+/* Symmetric permutation on the device: B[i][j] = A[perm[i]][perm[j]]
+ * (inverse = 0) or B[perm[i]][perm[j]] = A[i][j] (inverse = 1), for the
+ * symmetric A of order p whose lower triangle is read (element (r, c) from
+ * (max, min)).  perm: host array of p distinct indices (copied).  A and B
+ * must not be the same buffer.  Allocates p indices (stream-ordered) for the
+ * call; synchronises `stream`. */
+ibmi_status ibmi_permute(const double* A, int64_t lda, int64_t p, const int64_t* perm, int32_t inverse, double* B,
+                         int64_t ldb, void* stream);
+
+typedef struct ibmi_tune_candidate {
+  int32_t order;           /* -1: the given order; else the index of the caller's permutation */
+  int32_t K;               /* sets                                                            */
+  int64_t h;               /* overlap half-width of the default layout                         */
+  int32_t status;          /* ibmi_status of the inversion with this choice                    */
+  int32_t sweeps;
+  int32_t ns_steps;
+  double seconds;          /* device time of the whole inversion (CUDA events), INFINITY if none */
+  double resid_f;
+} ibmi_tune_candidate;
+
+/* Measured search over orderings and partitions of one device matrix A
+ * (p x p, lda): for the given order and each of the n_perms host permutations
+ * (each p distinct indices, as from ibmi_order_points), and each K in
+ * {2, 3, 4, 6, 8} whose cores p / K have at least 64 rows with an overlap 2h
+ * of 10, 20 and 30% of the core, the whole inversion runs once with the
+ * options of `base` (precision, tol, max_sweeps, ns_theta, ...; its p, K, h
+ * and sets are replaced; IBMI_INIT_USER becomes the identity) on the permuted
+ * matrix, timed on the device.  *best: the fastest that converged (IBMI_OK);
+ * all (optional, max_all entries) and *n_all: every candidate in the order
+ * tried.  Returns IBMI_OK, or IBMI_NOT_CONVERGED when no candidate converged;
+ * IBMI_ERR_CUDA / IBMI_ERR_TIMEOUT abort the search.  Allocates 2 p^2
+ * doubles plus each candidate's plan while it runs.  Synchronous. */
+ibmi_status ibmi_tune(const double* A, int64_t lda, int64_t p, const int64_t* const* perms, int32_t n_perms,
+                      const ibmi_plan_desc* base, void* stream, ibmi_tune_candidate* best,
+                      ibmi_tune_candidate* all, int32_t max_all, int32_t* n_all);
+
+/* ------------------------------------------------------------------------
  * Many matrices: batched inversion and the continuous-batching server.
  *
  * Both run the single-matrix pipeline (Algorithm 1 with the options below) on

@@ -168,6 +168,52 @@ def ibmi_refine(A, X, precision=IBMI_MIXED, tol=1e-10, ns_max=8, stream=None):
     return s, res.as_dict()
 
 
+# ------------------------------------------------- orderings and tuning --
+
+from ._lib import (IBMI_ORDER_IDENTITY, IBMI_ORDER_XSORT, IBMI_ORDER_HILBERT, IBMI_ORDER_KD,  # noqa: E402,F401
+                   IBMI_ORDER_REDBLACK, ibmi_tune_candidate)
+
+
+def ibmi_order_points(points: np.ndarray, order: int) -> np.ndarray:
+    """Permutation (int64, n) placing the points (n x dim) in the given order."""
+    pts = np.ascontiguousarray(points, dtype=np.float64)
+    if pts.ndim == 1:
+        pts = pts[:, None]
+    perm = np.empty(pts.shape[0], dtype=np.int64)
+    s = _lib.load().ibmi_order_points(pts.ctypes.data_as(C.POINTER(C.c_double)), pts.shape[0], pts.shape[1],
+                                      order, perm.ctypes.data_as(C.POINTER(C.c_int64)))
+    if s != IBMI_OK:
+        raise IbmiError(s, "ibmi_order_points")
+    return perm
+
+
+def ibmi_permute(A, perm, B, inverse: bool = False, stream=None) -> None:
+    """B = A[perm][:, perm] (or its inverse) on the device."""
+    q = np.ascontiguousarray(perm, dtype=np.int64)
+    s = _lib.load().ibmi_permute(C.c_void_p(A.data_ptr()), A.stride(0), A.shape[0],
+                                 q.ctypes.data_as(C.POINTER(C.c_int64)), 1 if inverse else 0,
+                                 C.c_void_p(B.data_ptr()), B.stride(0), _stream_ptr(stream))
+    if s != IBMI_OK:
+        raise IbmiError(s, "ibmi_permute")
+
+
+def ibmi_tune(A, perms=(), stream=None, **base):
+    """Measured search over orderings (the given one and `perms`) and
+    partitions; `base` sets the plan options (precision, tol, ...).  Returns
+    (status, best candidate dict, list of all candidate dicts)."""
+    p = A.shape[0]
+    qs = [np.ascontiguousarray(q, dtype=np.int64) for q in perms]
+    arr = (C.POINTER(C.c_int64) * max(1, len(qs)))(*[q.ctypes.data_as(C.POINTER(C.c_int64)) for q in qs])
+    d = ibmi_plan_desc_init(p=p, **base)
+    best = ibmi_tune_candidate()
+    cap = 256
+    allc = (ibmi_tune_candidate * cap)()
+    n = C.c_int32()
+    s = _lib.load().ibmi_tune(C.c_void_p(A.data_ptr()), A.stride(0), p, arr, len(qs), C.byref(d),
+                              _stream_ptr(stream), C.byref(best), allc, cap, C.byref(n))
+    return s, best.as_dict(), [allc[i].as_dict() for i in range(min(n.value, cap))]
+
+
 # ----------------------------------------------------------------- batches --
 
 from ._lib import ibmi_batch_opts  # noqa: E402

@@ -104,6 +104,30 @@ def exported_symbols():
     return list(_SIGS)
 
 
+IBMI_ORDER_IDENTITY, IBMI_ORDER_XSORT, IBMI_ORDER_HILBERT, IBMI_ORDER_KD, IBMI_ORDER_REDBLACK = 0, 1, 2, 3, 4
+
+
+class ibmi_tune_candidate(C.Structure):
+    _fields_ = [
+        ("order", C.c_int32), ("K", C.c_int32), ("h", C.c_int64), ("status", C.c_int32),
+        ("sweeps", C.c_int32), ("ns_steps", C.c_int32), ("seconds", C.c_double), ("resid_f", C.c_double),
+    ]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_SIGS.update({
+    "ibmi_order_points": (C.c_int, [C.POINTER(C.c_double), C.c_int64, C.c_int32, C.c_int32,
+                                    C.POINTER(C.c_int64)]),
+    "ibmi_permute": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.POINTER(C.c_int64), C.c_int32, C.c_void_p,
+                               C.c_int64, C.c_void_p]),
+    "ibmi_tune": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.POINTER(C.POINTER(C.c_int64)), C.c_int32,
+                            C.POINTER(ibmi_plan_desc), C.c_void_p, C.POINTER(ibmi_tune_candidate),
+                            C.POINTER(ibmi_tune_candidate), C.c_int32, C.POINTER(C.c_int32)]),
+})
+
+
 class ibmi_batch_opts(C.Structure):
     _fields_ = [
         ("precision", C.c_int32), ("tol", C.c_double), ("max_sweeps", C.c_int32),
