@@ -272,6 +272,17 @@ typedef struct ibmi_batch_opts {
   int32_t graphs;      /* 1 (default): mixed plans replay captured CUDA graphs
                           (one capture per plan and phase); 0: direct launches.
                           Both give bit-identical results.                     */
+  int32_t device_batch; /* 1 (default, mixed precision): matrices of order <= 2048
+                          of one size bucket and partition run as groups in
+                          lockstep on the device -- every launch covers one step
+                          of all matrices of the group that take it, with one
+                          host synchronisation per round of the group; a matrix
+                          the lockstep rules leave unfinished (a stall needing
+                          the spectral-radius test, a failed tail, the sweep
+                          cap) is run again on the single-matrix pipeline.
+                          Each result is bitwise the same whatever the group
+                          around it.  0: every matrix on the single-matrix
+                          pipeline of a worker.                                */
 } ibmi_batch_opts;
 void ibmi_batch_opts_init(ibmi_batch_opts* opts);
 
@@ -290,6 +301,22 @@ size_t ibmi_plan_bytes(const ibmi_plan_desc* desc);
 ibmi_status ibmi_invert_batched(int32_t n, const int64_t* p, const double* const* A, const int64_t* lda,
                                 double* const* H, const int64_t* ldh, const ibmi_batch_opts* opts,
                                 ibmi_result* out);
+
+/* Counters of the last ibmi_invert_batched call of this process: matrices
+ * run as device groups, groups, rounds (the longest group's and the sum over
+ * groups), matrices handed on to the single-matrix pipeline after their group
+ * (fallbacks), and the wall seconds of the group phase and of the
+ * single-matrix phase.  Observability only. */
+typedef struct ibmi_batch_stats {
+  int64_t device_matrices;
+  int64_t groups;
+  int64_t rounds_max;
+  int64_t rounds_total;
+  int64_t fallbacks;
+  double seconds_groups;
+  double seconds_single;
+} ibmi_batch_stats;
+ibmi_status ibmi_batch_last_stats(ibmi_batch_stats* out);
 
 /* Frees the pooled batch workers (streams, plans, graphs) of every device. */
 ibmi_status ibmi_batch_release(void);

@@ -250,6 +250,15 @@ def ibmi_invert_batched(As, Hs, **opts):
     return s, [out[i].as_dict() for i in range(n)]
 
 
+def ibmi_batch_last_stats() -> dict:
+    """Counters of the last batched call (device groups, rounds, fallbacks, phase seconds)."""
+    st = _lib.ibmi_batch_stats()
+    s = _lib.load().ibmi_batch_last_stats(C.byref(st))
+    if s != IBMI_OK:
+        raise IbmiError(s, "ibmi_batch_last_stats")
+    return st.as_dict()
+
+
 def ibmi_batch_release() -> None:
     """Frees the pooled batch workers (streams, plans, captured graphs)."""
     s = _lib.load().ibmi_batch_release()

@@ -132,11 +132,23 @@ class ibmi_batch_opts(C.Structure):
     _fields_ = [
         ("precision", C.c_int32), ("tol", C.c_double), ("max_sweeps", C.c_int32),
         ("ns_theta", C.c_double), ("ns_max", C.c_int32), ("workers", C.c_int32), ("autotune", C.c_int32),
-        ("graphs", C.c_int32),
+        ("graphs", C.c_int32), ("device_batch", C.c_int32),
     ]
 
 
+class ibmi_batch_stats(C.Structure):
+    _fields_ = [
+        ("device_matrices", C.c_int64), ("groups", C.c_int64), ("rounds_max", C.c_int64),
+        ("rounds_total", C.c_int64), ("fallbacks", C.c_int64), ("seconds_groups", C.c_double),
+        ("seconds_single", C.c_double),
+    ]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 _SIGS.update({
+    "ibmi_batch_last_stats": (C.c_int, [C.POINTER(ibmi_batch_stats)]),
     "ibmi_batch_opts_init": (None, [C.POINTER(ibmi_batch_opts)]),
     "ibmi_plan_bytes": (C.c_size_t, [C.POINTER(ibmi_plan_desc)]),
     "ibmi_invert_batched": (C.c_int, [C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_void_p),

@@ -24,6 +24,7 @@
 #include <unordered_map>
 #include <vector>
 
+#include "batch_dev.cuh"
 #include "batch_plan.h"
 #include "mixed.cuh"
 #include "plan.cuh"
@@ -76,6 +77,9 @@ struct Worker {
   std::map<std::pair<Shape, int>, Cached> plans;   // by (partition, precision)
   size_t plan_bytes = 0;
   uint64_t clock = 0;
+  // device-batched groups this worker ran, by (partition, group size): their
+  // buffers are kept for the next batched call of the same composition
+  std::map<std::pair<Shape, int>, std::unique_ptr<DevGroup>> groups;
 
   ibmi_status init(int dev) {
     device = dev;
@@ -102,6 +106,7 @@ struct Worker {
   void destroy() {
     cudaSetDevice(device);
     release_plans();
+    groups.clear();
     if (stream) cudaStreamDestroy(stream);
   }
   ibmi_status plan(const Shape& s, const ibmi_batch_opts& o, size_t max_plan_bytes, ibmi_plan_t* out) {
@@ -197,6 +202,11 @@ static Shape tune_bucket(Worker& w, int64_t pb, const ibmi_batch_opts& o, const 
 static std::mutex g_pool_mu;
 static std::map<int, std::vector<std::unique_ptr<Worker>>> g_pool;
 static constexpr size_t kWorkerPlanCap = (size_t)6 << 30;   // plan bytes a pooled worker may keep
+static constexpr int64_t kDevMaxOrder = 2048;                // largest bucket run as device groups
+static std::mutex g_stats_mu;
+static ibmi_batch_stats g_stats{};                           // of the last batched call
+static constexpr size_t kDevGroupMax = 64;                   // matrices per device group
+static constexpr size_t kDevGroupBytes = (size_t)4 << 30;    // device bytes per group
 
 static Shape shape_for(int64_t p, const ibmi_batch_opts& o) {
   const int64_t pb = bucket_of(p);
@@ -368,6 +378,7 @@ void ibmi_batch_opts_init(ibmi_batch_opts* o) {
   o->workers = 8;
   o->autotune = 1;
   o->graphs = 1;
+  o->device_batch = 1;
 }
 
 size_t ibmi_plan_bytes(const ibmi_plan_desc* d) {
@@ -437,24 +448,129 @@ ibmi_status ibmi_invert_batched(int32_t n, const int64_t* p, const double* const
       });
     for (auto& t : th) t.join();
   }
-  std::atomic<int> next{0};
   std::vector<ibmi_status> st(n, IBMI_OK);
+  ibmi_batch_stats stats{};
+  auto t_groups = std::chrono::steady_clock::now();
+  // device-side groups: matrices of one bucket and partition, in lockstep
+  std::vector<int32_t> rest;               // matrices for the single-matrix pipeline
+  std::vector<ibmi_result> first_try(n);   // a fallback's device attempt (its counts are added)
+  std::vector<char> tried(n, 0);
+  if (o.precision == IBMI_MIXED && o.device_batch) {
+    std::map<Shape, std::vector<int32_t>> by_shape;
+    for (int32_t i : order) {
+      if (bucket_of(p[i]) > kDevMaxOrder) rest.push_back(i);
+      else by_shape[shape_for(p[i], o)].push_back(i);
+    }
+    struct Task {
+      Shape s;
+      std::vector<int32_t> idx;
+    };
+    std::vector<Task> tasks;
+    for (auto& kv : by_shape) {
+      const size_t per = DevGroup::bytes_per_matrix(kv.first.p, kv.first.K, kv.first.h);
+      const size_t cap = std::max<size_t>(1, std::min<size_t>(kDevGroupMax, kDevGroupBytes / per));
+      const size_t nb = (kv.second.size() + cap - 1) / cap;   // balanced chunks
+      for (size_t c = 0; c < nb; ++c) {
+        Task t{kv.first, {}};
+        for (size_t j = c; j < kv.second.size(); j += nb) t.idx.push_back(kv.second[j]);
+        tasks.push_back(std::move(t));
+      }
+    }
+    // most work first; task t always runs on worker t % W, so a repeated call
+    // with the same batch finds its groups' buffers where it left them
+    std::stable_sort(tasks.begin(), tasks.end(), [](const Task& a, const Task& b) {
+      return (double)a.idx.size() * a.s.p * a.s.p * a.s.p > (double)b.idx.size() * b.s.p * b.s.p * b.s.p;
+    });
+    std::mutex mu;
+    std::vector<std::thread> tg;
+    for (int wi = 0; wi < W; ++wi)
+      tg.emplace_back([&, wi] {
+        cudaSetDevice(dev);
+        Worker& w = *pool[wi];
+        for (size_t t = wi; t < tasks.size(); t += W) {
+          const Task& task = tasks[t];
+          const int ng = (int)task.idx.size();
+          auto& slot = w.groups[{task.s, ng}];
+          ibmi_status s = IBMI_OK;
+          if (!slot) {
+            slot.reset(new DevGroup());
+            s = slot->create(task.s.p, task.s.K, task.s.h, ng);
+            if (s != IBMI_OK) slot.reset();
+          }
+          std::vector<BatchMat> mats(ng);
+          std::vector<ibmi_result> r(ng);
+          std::vector<int> fb(ng, 1);
+          for (int b = 0; b < ng; ++b) {
+            const int32_t i = task.idx[b];
+            mats[b] = BatchMat{A[i], lda[i], H[i], ldh[i], p[i]};
+          }
+          if (s == IBMI_OK) s = slot->run(mats.data(), o, handover_theta(task.s.p, true, o.ns_theta), w.stream,
+                                          r.data(), fb.data());
+          std::lock_guard<std::mutex> g(mu);
+          if (s == IBMI_OK) {
+            stats.groups += 1;
+            stats.device_matrices += ng;
+            stats.rounds_max = std::max<int64_t>(stats.rounds_max, slot->rounds());
+            stats.rounds_total += slot->rounds();
+          }
+          for (int b = 0; b < ng; ++b) {
+            const int32_t i = task.idx[b];
+            if (s == IBMI_OK && fb[b]) stats.fallbacks += 1;
+            if (s == IBMI_OK && !fb[b]) {
+              out[i] = r[b];
+              st[i] = (ibmi_status)r[b].status;
+            } else {
+              if (s == IBMI_OK) {
+                first_try[i] = r[b];
+                tried[i] = 1;
+              }
+              rest.push_back(i);
+            }
+          }
+        }
+      });
+    for (auto& t : tg) t.join();
+    std::stable_sort(rest.begin(), rest.end(), [&](int32_t a, int32_t b) { return p[a] > p[b]; });
+  } else {
+    rest = order;
+  }
+  auto t_single = std::chrono::steady_clock::now();
+  stats.seconds_groups = std::chrono::duration<double>(t_single - t_groups).count();
+  std::atomic<int> next{0};
   std::vector<std::thread> th;
+  const int nrest = (int)rest.size();
   for (int wi = 0; wi < W; ++wi)
     th.emplace_back([&, wi] {
       cudaSetDevice(dev);
       Worker& w = *pool[wi];
-      for (int j; (j = next.fetch_add(1)) < n;) {
-        const int32_t i = order[j];
+      for (int j; (j = next.fetch_add(1)) < nrest;) {
+        const int32_t i = rest[j];
         st[i] = run_tuned(w, o, kWorkerPlanCap, A[i], lda[i], p[i], H[i], ldh[i], &out[i]);
         out[i].status = st[i];
+        if (tried[i]) {   // the device attempt's work counts too
+          out[i].sweeps += first_try[i].sweeps;
+          out[i].ns_steps += first_try[i].ns_steps;
+          out[i].flops += first_try[i].flops;
+        }
       }
     });
   for (auto& t : th) t.join();
+  stats.seconds_single = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_single).count();
+  {
+    std::lock_guard<std::mutex> g(g_stats_mu);
+    g_stats = stats;
+  }
   ibmi_status worst = IBMI_OK;
   for (int32_t i = 0; i < n; ++i)
     if (st[i] != IBMI_OK && (worst == IBMI_OK || worst == IBMI_NOT_CONVERGED)) worst = st[i];
   return worst;
+}
+
+ibmi_status ibmi_batch_last_stats(ibmi_batch_stats* out) {
+  if (!out) return IBMI_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> g(g_stats_mu);
+  *out = g_stats;
+  return IBMI_OK;
 }
 
 ibmi_status ibmi_batch_release(void) {

@@ -37,6 +37,10 @@ struct F64Operands {
   // Symmetric A known by its lower triangle only (A_KMAJOR): element (r, c)
   // is read from (max(r, c), min(r, c)).
   bool a_lower = false;
+  // If > 0: the batch size the tile choice below is made for (a batch of
+  // several matrices' blocks then tiles each block as a batch of tile_batch
+  // would, so a matrix's arithmetic does not depend on the others).
+  int tile_batch = 0;
 };
 
 // Threads of a T x T tile: a 4 x 4 register block per thread for T = 64 and
@@ -217,7 +221,8 @@ constexpr int64_t F64_SMALL_LAUNCH = 300;
 template <bool A_KMAJOR, bool B_NMAJOR, class Epi>
 inline cudaError_t launch_gemm_f64(const F64Operands& op, const Epi& epi, cudaStream_t st) {
   if (op.M <= 0 || op.N <= 0) return cudaSuccess;
-  const int64_t tiles64 = ((op.N + F64_BN - 1) / F64_BN) * ((op.M + F64_BM - 1) / F64_BM) * op.batch;
+  const int64_t tiles64 =
+      ((op.N + F64_BN - 1) / F64_BN) * ((op.M + F64_BM - 1) / F64_BM) * (op.tile_batch > 0 ? op.tile_batch : op.batch);
   note_launch();
   if constexpr (std::is_same<Epi, EpiStore>::value) {
     // triangular K: a 64 x 64 tile at the start of the diagonal sums all of K

@@ -27,7 +27,9 @@ namespace ibmi {
 // global pivot lo_z + row0 + j) and is replaced by 1 so the factorisation
 // finishes.
 __global__ void __launch_bounds__(1024) k_potrf_tile(double* T, int64_t ld, int64_t zT, int jb, double* linv,
-                                                     int64_t zL, DevStatus* st, const int64_t* dlo, int64_t row0) {
+                                                     int64_t zL, DevStatus* st, const int64_t* dlo, int64_t row0,
+                                                     int status_per_block) {
+  if (status_per_block) st += blockIdx.z;   // one status word per block (batched groups)
   __shared__ double L[CHOL_NB][CHOL_NB + 1];
   __shared__ double X[CHOL_NB][CHOL_NB + 1];
   __shared__ double rd[CHOL_NB];   // rsqrt of the pivots
@@ -78,9 +80,12 @@ __global__ void __launch_bounds__(1024) k_potrf_tile(double* T, int64_t ld, int6
 }
 
 // Lw[z] = [[A[I_z, I_z], 0], [0, I]]  (mmax x mmax)
+// doffA (optional): element offset of block z's matrix within A (blocks of
+// several matrices stacked in one batch).
 __global__ void k_bat_copy_block(const double* A, int64_t lda, const int64_t* dlo, const int64_t* dm, int64_t mmax,
-                                 double* Lw) {
+                                 double* Lw, const int64_t* doffA) {
   const int z = blockIdx.z;
+  if (doffA) A += doffA[z];
   int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= mmax * mmax) return;
   int64_t i = idx / mmax, j = idx - i * mmax;
@@ -92,8 +97,9 @@ __global__ void k_bat_copy_block(const double* A, int64_t lda, const int64_t* dl
 // with the identity on the columns of I_z (so the solution is A_I^{-1} on the
 // columns of I and A_I^{-1} A_{I,I^c} elsewhere); otherwise R[z] = identity.
 __global__ void k_bat_rhs(const double* A, int64_t lda, const int64_t* dlo, const int64_t* dm, int64_t mmax,
-                          int64_t ncols, int full_w, double* R) {
+                          int64_t ncols, int full_w, double* R, const int64_t* doffA) {
   const int z = blockIdx.z;
+  if (doffA) A += doffA[z];
   int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= mmax * ncols) return;
   int64_t i = idx / ncols, c = idx - i * ncols;
@@ -155,10 +161,11 @@ ibmi_status invariants_all(ibmi_plan_s* P, const double* A, int64_t lda, bool fu
     op.zA = za;
     op.zB = zb;
     op.batch = K;
+    op.tile_batch = P->tile_batch;
     return op;
   };
   note_launch();
-  k_bat_copy_block<<<dim3(nblk(mmax * mmax), 1, K), 256, 0, st>>>(A, lda, P->dlo, P->dm, mmax, Lw);
+  k_bat_copy_block<<<dim3(nblk(mmax * mmax), 1, K), 256, 0, st>>>(A, lda, P->dlo, P->dm, mmax, Lw, P->doffA);
   IBMI_CUDA_TRY(cudaGetLastError());
   // blocked right-looking Cholesky, nb = 32
   for (int64_t j0 = 0; j0 < mmax; j0 += CHOL_NB) {
@@ -166,7 +173,7 @@ ibmi_status invariants_all(ibmi_plan_s* P, const double* A, int64_t lda, bool fu
     double* Li = P->bat_linv + j0 * CHOL_NB;
     note_launch();
     k_potrf_tile<<<dim3(1, 1, K), dim3(32, 32), 0, st>>>(Lw + j0 * mmax + j0, mmax, zL, jb, Li, zLi, P->dstatus,
-                                                          P->dlo, j0);
+                                                          P->dlo, j0, P->doffA ? 1 : 0);
     IBMI_CUDA_TRY(cudaGetLastError());
     const int64_t rest = mmax - j0 - jb;
     if (rest <= 0) break;
@@ -184,7 +191,8 @@ ibmi_status invariants_all(ibmi_plan_s* P, const double* A, int64_t lda, bool fu
   }
   // R <- L^{-T} L^{-1} R (full_w); A_I^{-1} = L^{-T} L^{-1} otherwise
   note_launch();
-  k_bat_rhs<<<dim3(nblk(mmax * ncols), 1, K), 256, 0, st>>>(A, lda, P->dlo, P->dm, mmax, ncols, full_w ? 1 : 0, R);
+  k_bat_rhs<<<dim3(nblk(mmax * ncols), 1, K), 256, 0, st>>>(A, lda, P->dlo, P->dm, mmax, ncols, full_w ? 1 : 0, R,
+                                                           P->doffA);
   IBMI_CUDA_TRY(cudaGetLastError());
   // Both triangular solves work in place: the diagonal-block product reads
   // rows j0..j0+jb of one column tile and writes the same tile (one CTA owns

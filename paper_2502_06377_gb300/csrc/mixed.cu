@@ -9,6 +9,7 @@
 #include <mutex>
 
 #include "mixed.cuh"
+#include "oz_rows.cuh"
 #include "tail_plan.h"
 #include "refine.cuh"
 #include "tc_gemm.cuh"
@@ -40,6 +41,21 @@ bool make_map_bf16(CUtensorMap* map, const void* base, int64_t rows, int64_t col
   cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+bool make_map_bf16_3d(CUtensorMap* map, const void* base, int64_t nb, int64_t rows, int64_t cols, int64_t ld,
+                      int box_rows) {
+  auto enc = get_encode();
+  if (!enc) return false;
+  if (((uintptr_t)base & 15) != 0 || ((ld * 2) & 15) != 0 || nb < 1) return false;
+  cuuint64_t dims[3] = {(cuuint64_t)cols, (cuuint64_t)rows, (cuuint64_t)nb};
+  cuuint64_t strides[2] = {(cuuint64_t)(ld * 2), (cuuint64_t)(rows * ld * 2)};
+  cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)box_rows, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, estr,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
@@ -155,14 +171,6 @@ static MixedState* MS(ibmi_plan_s* P) { return (MixedState*)P->mixed; }
 
 // ------------------------------------------------------------- kernels ----
 
-// x (FP32) ~ s0 + s1 + s2 with BF16 slices taken in turn from the remainder;
-// the first two are the classic hi/lo pair.
-__device__ __forceinline__ void split3(float x, __nv_bfloat16& a, __nv_bfloat16& b, __nv_bfloat16& c) {
-  a = __float2bfloat16_rn(x);
-  const float r = x - __bfloat162float(a);
-  b = __float2bfloat16_rn(r);
-  c = __float2bfloat16_rn(r - __bfloat162float(b));
-}
 
 // FP64 H (ldh) -> FP32 master + BF16 hi/lo (ldp)
 // Elementwise kernels run on 2-D grids: row = blockIdx.y, column =

@@ -31,6 +31,12 @@ struct OzPairArgs {
   int* T;                                  // group planes: T + q * plane, row pitch ldt
   int64_t plane, ldt, M, N;
   int* err;
+  // Batch (nb > 0): 3-D maps with the problem as third coordinate; tiles of
+  // problem bsel[i] (or i) follow those of the one before; group planes of
+  // problem b at T + b * tstride.
+  int nb;
+  const int* bsel;
+  int64_t tstride;
 };
 
 template <int BN>
@@ -48,6 +54,7 @@ __global__ void __launch_bounds__(THREADS, Cfg<1, BN>::CTAS_PER_SM) k_oz_pairs(c
   uint32_t* tmem_slot = (uint32_t*)(drain + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nchunks = (g.kt_total + g.chunk - 1) / g.chunk;
+  const int total = g.tiles * (g.nb > 0 ? g.nb : 1);   // tiles of all problems
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < C::STAGES; ++s) {
@@ -73,8 +80,10 @@ __global__ void __launch_bounds__(THREADS, Cfg<1, BN>::CTAS_PER_SM) k_oz_pairs(c
       bool ok = true;
       for (int pi = 0; ok && pi < g.n; ++pi)
         for (int ci = 0; ok && ci < nchunks; ++ci)
-          for (int tt = blockIdx.x; ok && tt < g.tiles; tt += gridDim.x) {
-            const int mt = tt / g.grid_n, ntl = tt - mt * g.grid_n;
+          for (int tt = blockIdx.x; ok && tt < total; tt += gridDim.x) {
+            const int bi = tt / g.tiles, tl = tt - bi * g.tiles;
+            const int bb = g.bsel ? g.bsel[bi] : bi;
+            const int mt = tl / g.grid_n, ntl = tl - mt * g.grid_n;
             const int kb = ci * g.chunk, nk = min(g.chunk, g.kt_total - kb);
             const CUtensorMap* ma = &maps.a[g.s[pi]];
             const CUtensorMap* mb = &maps.b[g.u[pi]];
@@ -85,8 +94,13 @@ __global__ void __launch_bounds__(THREADS, Cfg<1, BN>::CTAS_PER_SM) k_oz_pairs(c
               const int kx = (kb + it) * BK;
               uint8_t* sa = tiles + st * C::STAGE_BYTES;
               mbar_expect_tx(&full[st], C::STAGE_BYTES);
-              tma_load_2d(sa, ma, &full[st], kx, mt * BM);
-              tma_load_2d(sa + C::A_BYTES, mb, &full[st], kx, ntl * BN);
+              if (g.nb > 0) {
+                tma_load_3d(sa, ma, &full[st], kx, mt * BM, bb);
+                tma_load_3d(sa + C::A_BYTES, mb, &full[st], kx, ntl * BN, bb);
+              } else {
+                tma_load_2d(sa, ma, &full[st], kx, mt * BM);
+                tma_load_2d(sa + C::A_BYTES, mb, &full[st], kx, ntl * BN);
+              }
             }
           }
       if (*(volatile int*)g.err != 0) {   // error exit: wait (bounded) for copies in flight
@@ -106,7 +120,7 @@ __global__ void __launch_bounds__(THREADS, Cfg<1, BN>::CTAS_PER_SM) k_oz_pairs(c
       bool ok = true;
       for (int pi = 0; ok && pi < g.n; ++pi)
         for (int ci = 0; ok && ci < nchunks; ++ci)
-          for (int tt = blockIdx.x; ok && tt < g.tiles; tt += gridDim.x, ++local) {
+          for (int tt = blockIdx.x; ok && tt < total; tt += gridDim.x, ++local) {
             const int nk = min(g.chunk, g.kt_total - ci * g.chunk);
             const int buf = local & 1;
             const uint32_t use = (uint32_t)(local >> 1);
@@ -137,13 +151,15 @@ __global__ void __launch_bounds__(THREADS, Cfg<1, BN>::CTAS_PER_SM) k_oz_pairs(c
     bool ok = true;
     for (int pi = 0; ok && pi < g.n; ++pi)
       for (int ci = 0; ok && ci < nchunks; ++ci)
-        for (int tt = blockIdx.x; ok && tt < g.tiles; tt += gridDim.x, ++local) {
-          const int mt = tt / g.grid_n, ntl = tt - mt * g.grid_n;
+        for (int tt = blockIdx.x; ok && tt < total; tt += gridDim.x, ++local) {
+          const int bi = tt / g.tiles, tl = tt - bi * g.tiles;
+          const int bb = g.bsel ? g.bsel[bi] : bi;
+          const int mt = tl / g.grid_n, ntl = tl - mt * g.grid_n;
           const int buf = local & 1;
           const uint32_t use = (uint32_t)(local >> 1);
           if (!mbar_wait(&accf[buf], use & 1u, g.err)) { ok = false; break; }
           tc_fence_after();
-          int* Tq = g.T + (int64_t)g.q[pi] * g.plane;
+          int* Tq = g.T + (g.nb > 0 ? (int64_t)bb * g.tstride : 0) + (int64_t)g.q[pi] * g.plane;
           const bool first = g.first[pi] && ci == 0;
           const int64_t row0 = (int64_t)mt * BM + qw * 32;
 #pragma unroll 1
@@ -216,7 +232,7 @@ cudaError_t launch_oz_pairs(const OzPairMaps& maps, const OzPairArgs& g, cudaStr
     attr_set.store(true, std::memory_order_release);
   }
   if (g.n <= 0 || g.tiles <= 0 || g.kt_total <= 0) return cudaSuccess;
-  const int grid = std::min(g.tiles, resident_ctas<1, BN>());
+  const int grid = std::min(g.tiles * (g.nb > 0 ? g.nb : 1), resident_ctas<1, BN>());
   note_launch();
   k_oz_pairs<BN><<<grid, THREADS, smem_bytes, st>>>(maps, g);
   return cudaGetLastError();

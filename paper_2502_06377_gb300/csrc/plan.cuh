@@ -25,6 +25,9 @@ struct ibmi_plan_s {
   int64_t* dm = nullptr;         // of A_I^{-1} and W for each set
   int64_t* doff_ainv = nullptr;
   int64_t* doff_w = nullptr;
+  int64_t* doffA = nullptr;      // batched groups: element offset in A of block z's matrix (else NULL);
+                                 // then dstatus holds one status word per block
+  int tile_batch = 0;            // batched groups: sets per matrix (tile choice of the FP64 products)
   void* bat_pool = nullptr;
   // scratch
   double* S = nullptr;           // mmax x mmax, a4 result before symmetrisation

@@ -75,6 +75,12 @@ struct Tiles {
   // Self-test of the bounded waits only: the producer issues no loads, so the
   // MMA thread's first wait expires and the kernel takes its error exit.
   int starve = 0;
+  // Batch of independent problems of the same shape (nb > 0): the maps are
+  // 3-D with the problem index as third coordinate, the units are the units
+  // of one problem for each of nb problems, problem bsel[i] (or i) for the
+  // i-th block of units; the epilogue learns the problem through `bat`.
+  int nb = 0;
+  const int* bsel = nullptr;
 };
 
 __device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
@@ -110,6 +116,19 @@ __device__ __forceinline__ Unit unit_of(const Tiles& t, int u, int nk) {
   r.nk = (int)((int64_t)nk * (r.z + 1) / t.splits) - r.kb;
   return r;
 }
+
+// Unit u of a (possibly batched) launch: its problem b and its unit within the problem.
+__device__ __forceinline__ Unit unit_at(const Tiles& t, int u, int nk, int& b) {
+  b = 0;
+  if (t.nb > 0) {
+    const int per = unit_count(t);
+    const int bi = u / per;
+    b = t.bsel ? t.bsel[bi] : bi;
+    u -= bi * per;
+  }
+  return unit_of(t, u, nk);
+}
+__host__ __device__ inline int total_units(const Tiles& t) { return unit_count(t) * (t.nb > 0 ? t.nb : 1); }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -171,6 +190,13 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
   asm volatile(
       "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
       ::"r"(smem_u32(dst)), "l"(map), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y, int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];"
+      ::"r"(smem_u32(dst)), "l"(map), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z)
       : "memory");
 }
 
@@ -239,8 +265,19 @@ __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
 // Epilogue functors: operator()(row, col0, z, v[16]) per 16-column chunk of a
 // row (called by the thread owning that TMEM lane), then done(quadrant) once.
 struct EpiBase {
+  int bat = 0;   // problem of the current unit (batched launches)
   __device__ __forceinline__ void done(int) {}
 };
+template <class E, class = void>
+struct has_bat : std::false_type {};
+template <class E>
+struct has_bat<E, std::void_t<decltype(&E::bat)>> : std::true_type {};
+// An epilogue with a member unit_end(quadrant, tile) is told when its warp has
+// passed on the last chunk of a unit (per-unit reductions).
+template <class E, class = void>
+struct has_unit_end : std::false_type {};
+template <class E>
+struct has_unit_end<E, std::void_t<decltype(&E::unit_end)>> : std::true_type {};
 
 // An epilogue with a member warp_tile(row0, j0, z, stage, lane) gets each
 // warp's 32 x 16 block through shared memory (stage[r * 17 + c] = row r,
@@ -302,7 +339,7 @@ __global__ void __launch_bounds__(THREADS, Cfg<S, BN>::CTAS_PER_SM) k_tc_gemm(co
   uint32_t* tmem_slot = (uint32_t*)(drain + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int units = unit_count(t);
+  const int units = total_units(t);
   const int nk0 = t.kt0_end;
   const int nk = t.kt0_end + (t.kt1_end - t.kt1_begin);
 
@@ -329,7 +366,8 @@ __global__ void __launch_bounds__(THREADS, Cfg<S, BN>::CTAS_PER_SM) k_tc_gemm(co
       int kc = 0;     // k blocks issued so far (ring position)
       bool ok = true;
       for (int u = blockIdx.x; ok && u < units; u += gridDim.x) {
-        const Unit w = unit_of(t, u, nk);
+        int bb;
+        const Unit w = unit_at(t, u, nk, bb);
         const int ntl = w.tile % t.grid_n, mt = (w.tile / t.grid_n) % t.grid_m;
         const int ntp = ntl < t.nt0 ? ntl : t.nt1_first + (ntl - t.nt0);
         const int64_t n0 = (int64_t)ntp * BN;
@@ -344,12 +382,18 @@ __global__ void __launch_bounds__(THREADS, Cfg<S, BN>::CTAS_PER_SM) k_tc_gemm(co
           uint8_t* sa = tiles + st * C::STAGE_BYTES;
           uint8_t* sb = sa + S * C::A_BYTES;
           mbar_expect_tx(&full[st], C::STAGE_BYTES);
+          const int ya = (int)(t.a_row0 + (int64_t)mt * BM), yb = (int)(t.b_row0 + n0);
+          if (t.nb > 0) {
 #pragma unroll
-          for (int s = 0; s < S; ++s)
-            tma_load_2d(sa + s * C::A_BYTES, &maps.a[s], &full[st], kx, (int)(t.a_row0 + (int64_t)mt * BM));
+            for (int s = 0; s < S; ++s) tma_load_3d(sa + s * C::A_BYTES, &maps.a[s], &full[st], kx, ya, bb);
 #pragma unroll
-          for (int s = 0; s < S; ++s)
-            tma_load_2d(sb + s * C::B_BYTES, &maps.b[s], &full[st], kx, (int)(t.b_row0 + n0));
+            for (int s = 0; s < S; ++s) tma_load_3d(sb + s * C::B_BYTES, &maps.b[s], &full[st], kx, yb, bb);
+          } else {
+#pragma unroll
+            for (int s = 0; s < S; ++s) tma_load_2d(sa + s * C::A_BYTES, &maps.a[s], &full[st], kx, ya);
+#pragma unroll
+            for (int s = 0; s < S; ++s) tma_load_2d(sb + s * C::B_BYTES, &maps.b[s], &full[st], kx, yb);
+          }
         }
       }
       // On an error exit, wait (bounded) for the copies still in flight.
@@ -370,7 +414,8 @@ __global__ void __launch_bounds__(THREADS, Cfg<S, BN>::CTAS_PER_SM) k_tc_gemm(co
       int local = 0;
       bool ok = true;
       for (int u = blockIdx.x; ok && u < units; u += gridDim.x, ++local) {
-        const int my_nk = unit_of(t, u, nk).nk;
+        int bb;
+        const int my_nk = unit_at(t, u, nk, bb).nk;
         const int buf = local & 1;
         const uint32_t use = (uint32_t)(local >> 1);
         if (!mbar_wait(&acce[buf], (use & 1u) ^ 1u, t.err)) break;   // accumulator drained
@@ -410,7 +455,9 @@ __global__ void __launch_bounds__(THREADS, Cfg<S, BN>::CTAS_PER_SM) k_tc_gemm(co
     float* stage = (float*)(smem + C::STAGES * C::STAGE_BYTES + 256) + q * 32 * 17;   // warp_tile epilogues only
     int local = 0;
     for (int u = blockIdx.x; u < units; u += gridDim.x, ++local) {
-      const Unit w = unit_of(t, u, nk);
+      int bb;
+      const Unit w = unit_at(t, u, nk, bb);
+      if constexpr (has_bat<Epi>::value) e.bat = bb;
       const int ntl = w.tile % t.grid_n, mt = (w.tile / t.grid_n) % t.grid_m, z = w.z;
       const int ntp = ntl < t.nt0 ? ntl : t.nt1_first + (ntl - t.nt0);
       const int64_t n0 = (int64_t)ntp * BN;
@@ -438,6 +485,7 @@ __global__ void __launch_bounds__(THREADS, Cfg<S, BN>::CTAS_PER_SM) k_tc_gemm(co
           e((int64_t)mt * BM + row, n0 + c, z, v);
         }
       }
+      if constexpr (has_unit_end<Epi>::value) e.unit_end(q, w.tile);
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&acce[buf]);
@@ -456,6 +504,11 @@ __global__ void __launch_bounds__(THREADS, Cfg<S, BN>::CTAS_PER_SM) k_tc_gemm(co
 // Encodes a 2-D BF16 tensor map: `rows` rows of `cols` elements, row pitch
 // `ld` elements (ld * 2 must be a multiple of 16), box = 64 x box_rows.
 bool make_map_bf16(CUtensorMap* map, const void* base, int64_t rows, int64_t cols, int64_t ld, int box_rows);
+// The same over nb problems stored one after another (rows x ld elements
+// each): a 3-D map whose third coordinate is the problem; rows past `rows`
+// of a problem read as zero.
+bool make_map_bf16_3d(CUtensorMap* map, const void* base, int64_t nb, int64_t rows, int64_t cols, int64_t ld,
+                      int box_rows);
 
 // Range bookkeeping shared by the launchers: K and N tiles that overlap the
 // complement [0, lo) U [hi, p) of a set.
@@ -505,7 +558,7 @@ cudaError_t launch(const Maps& maps, const Tiles& t0, int grid_n, int grid_m, co
   Tiles t = t0;
   t.grid_n = grid_n;
   t.grid_m = grid_m;
-  const int64_t total = unit_count(t);
+  const int64_t total = total_units(t);
   const int grid = (int)std::min<int64_t>(total, (int64_t)resident_ctas<S, BN>());
   if (grid_used) *grid_used = grid;
   note_launch();

@@ -1,5 +1,9 @@
 """Batched inversion and the continuous-batching server vs the FP64 oracle.
 
+The batched entry runs matrices of order <= 2048 as device groups in
+lockstep by default (device_batch = 1); the single-matrix pipeline serves the
+rest, the fallbacks and every matrix with device_batch = 0.
+
 Matrices whose condition number puts the FP64 floor of ||I - A H||_F/sqrt(p)
 (about eps_64 * kappa) above the 1e-10 tolerance cannot reach it in any FP64
 arithmetic -- the oracle's Newton-Schulz tail stalls there too.  For those the
@@ -181,3 +185,57 @@ def test_serve_cancel_and_budget_reject(ibmi, batch):
         time.sleep(0.002)
     srv.close()
     assert not pending
+
+
+def test_device_groups_match_the_single_matrix_pipeline(ibmi, batch):
+    """The lockstep device groups (default) and the per-matrix pipeline
+    (device_batch=0) both converge on every matrix, to the same inverse."""
+    mats, refs = batch
+    _, r1, H1 = _run_batched(ibmi, mats, workers=8)
+    _, r0, H0 = _run_batched(ibmi, mats, workers=8, device_batch=0)
+    for A, a, b, x, y, ref in zip(mats, H1, H0, r1, r0, refs):
+        if ref.status != "converged":
+            continue
+        assert x["status"] == ibmi.IBMI_OK and y["status"] == ibmi.IBMI_OK, (A.shape, x, y)
+        sc = np.abs(b).max()
+        assert np.abs(a - b).max() <= 1e-8 * sc, A.shape
+
+
+@pytest.fixture(scope="module")
+def large_batch():
+    """The upper buckets of the 512-matrix workload (orders 576..1024)."""
+    rng = np.random.default_rng(41)
+    mats = []
+    for p in (576, 640, 768, 896, 960, 1024, 1024, 768):
+        ell = float(np.exp(rng.uniform(np.log(0.05), np.log(0.5))))
+        mats.append(wl.squared_exp(wl.uniform_points(rng, p, 3), ell, 1.0, 1e-3))
+    refs = []
+    for A in mats:
+        p = A.shape[0]
+        refs.append(O.ibmi(A, O.partition(p, 4, max(4, round(0.1 * (p // 4)))), tol=1e-10, max_sweeps=300,
+                           ns_theta=0.5))
+    return mats, refs
+
+
+def test_batched_upper_buckets_vs_oracle(ibmi, large_batch):
+    mats, refs = large_batch
+    s, res, Hs = _run_batched(ibmi, mats, workers=4)
+    for A, H, r, ref in zip(mats, Hs, res, refs):
+        _check(A, H, r, ref)
+        print(A.shape[0], r["sweeps"], r["ns_steps"], f"{r['resid_f']:.2e}", "oracle", ref.sweeps, ref.ns_steps)
+
+
+def test_unfinished_matrices_fall_back_and_rerun(ibmi, batch):
+    """Without Newton-Schulz steps the sweeps' accuracy floor keeps rho_F
+    above 1e-10: every path gives up (the device group, the tuned
+    single-matrix run, and the robust rerun where its partition differs) and
+    the result is NOT_CONVERGED with the sweeps of all attempts."""
+    mats, _ = batch
+    sub = [mats[i] for i in (1, 4)]
+    s, res, Hs = _run_batched(ibmi, sub, workers=2, ns_max=0, max_sweeps=12)
+    assert s == ibmi.IBMI_NOT_CONVERGED
+    st = ibmi.ibmi_batch_last_stats()
+    assert st["device_matrices"] == 2 and st["fallbacks"] == 2, st
+    for r, A, H in zip(res, sub, Hs):
+        assert r["status"] == ibmi.IBMI_NOT_CONVERGED and r["sweeps"] >= 2 * 12, r
+        assert np.all(np.isfinite(H)) and O.residual_f(A, H) < 1.0
