@@ -413,6 +413,7 @@ def measure_c4(ibmi, lib, local, args, steps=3):
     dt = (time.perf_counter() - t0) / steps
     clk = clocks.stop()
     launches = (lib.ibmi_launch_count() - l0) / steps
+    bstats = ibmi.ibmi_batch_last_stats()
     ok = sum(r["status"] == 0 for r in res)
     rf = sorted(r["resid_f"] for r in res)
     flops = sum(r["flops"] for r in res)
@@ -451,7 +452,7 @@ def measure_c4(ibmi, lib, local, args, steps=3):
             "value": len(mats) / dt, "unit": "inverses/s", "ms_per_batch": dt * 1000.0, "steps": steps,
             "warmup": 2, "converged": ok, "not_converged": len(res) - ok, "resid_f_median": rf[len(rf) // 2],
             "resid_f_max": rf[-1], "achieved_tflops_algorithmic": flops / dt / 1e12,
-            "gpu_launches_per_batch": launches, "sample64": out,
+            "gpu_launches_per_batch": launches, "batch_stats": bstats, "sample64": out,
             "mixed_over_fp64_on_sample": out["mixed"]["value"] / out["fp64"]["value"],
             "cpu_oracle_sample": {"value": 8.0 / cpu_s, "unit": "inverses/s", "matrices": 8,
                                   "cores": host_cores(), "kind": "oracle"},

@@ -78,8 +78,40 @@ struct Worker {
   size_t plan_bytes = 0;
   uint64_t clock = 0;
   // device-batched groups this worker ran, by (partition, group size): their
-  // buffers are kept for the next batched call of the same composition
-  std::map<std::pair<Shape, int>, std::unique_ptr<DevGroup>> groups;
+  // buffers are kept for the next call of the same composition
+  struct CachedGroup {
+    std::unique_ptr<DevGroup> g;
+    uint64_t last_use = 0;
+  };
+  std::map<std::pair<Shape, int>, CachedGroup> groups;
+  size_t group_bytes = 0;
+  // The cached group for (s, n), created if missing; with a nonzero cap, least
+  // recently used groups and plans go first until it fits (nullptr if it
+  // cannot be created).
+  DevGroup* group(const Shape& s, int n, size_t cap) {
+    auto it = groups.find({s, n});
+    if (it != groups.end()) {
+      it->second.last_use = ++clock;
+      return it->second.g.get();
+    }
+    const size_t need = DevGroup::bytes_per_matrix(s.p, s.K, s.h) * (size_t)n;
+    if (cap) {
+      while (!groups.empty() && group_bytes + plan_bytes + need > cap) {
+        auto lru = groups.begin();
+        for (auto jt = groups.begin(); jt != groups.end(); ++jt)
+          if (jt->second.last_use < lru->second.last_use) lru = jt;
+        group_bytes -= lru->second.g->bytes();
+        groups.erase(lru);
+      }
+      evict_for(group_bytes + need, cap);
+    }
+    std::unique_ptr<DevGroup> g(new DevGroup());
+    if (g->create(s.p, s.K, s.h, n) != IBMI_OK) return nullptr;
+    group_bytes += g->bytes();
+    DevGroup* r = g.get();
+    groups[{s, n}] = CachedGroup{std::move(g), ++clock};
+    return r;
+  }
 
   ibmi_status init(int dev) {
     device = dev;
@@ -107,6 +139,7 @@ struct Worker {
     cudaSetDevice(device);
     release_plans();
     groups.clear();
+    group_bytes = 0;
     if (stream) cudaStreamDestroy(stream);
   }
   ibmi_status plan(const Shape& s, const ibmi_batch_opts& o, size_t max_plan_bytes, ibmi_plan_t* out) {
@@ -282,83 +315,173 @@ static size_t request_bytes(int64_t p) {
   return sizeof(double) * (size_t)(2 * p * p + 2 * pb * pb);
 }
 
+static constexpr int kServeGroupMax = 8;   // requests one device group of the server takes
+
+static bool same_shape(const Shape& a, const Shape& b) { return !(a < b) && !(b < a); }
+
+// One server worker: admits the oldest queued request that fits the budget,
+// together with the queued requests of the same size bucket, partition and
+// tolerance that fit too (at most kServeGroupMax, orders up to kDevMaxOrder,
+// mixed precision), and inverts them as one device group; a request the
+// group leaves unfinished, and every other request, runs on the
+// single-matrix pipeline of this worker.  Requests that arrive meanwhile are
+// taken by the next free worker.
 static void server_loop(ibmi_server_impl* S, int wi) {
   Worker& w = S->workers[wi];
   cudaSetDevice(S->device);
-  double* dA = nullptr;
-  double* dH = nullptr;
-  int64_t dcap = 0;
+  std::vector<double*> dA, dH;   // staging per request slot
+  std::vector<int64_t> dcap;
+  const size_t cache_cap = (S->budget - S->req_budget) / S->workers.size();
+  auto fits = [&](const std::shared_ptr<Request>& q) {
+    return q->state == 0 && (S->in_use + q->bytes <= S->req_budget || S->in_use == 0);
+  };
   while (true) {
-    std::shared_ptr<Request> r;
+    std::vector<std::shared_ptr<Request>> batch;
+    Shape sh{};
+    bool grouped = false;
     {
       std::unique_lock<std::mutex> lk(S->mu);
       S->cv.wait(lk, [&] {
         if (S->stop) return true;
-        // admission: the oldest queued request whose bytes fit in the budget
-        for (uint64_t id : S->queue) {
-          auto& q = S->reqs[id];
-          if (q->state == 0 && (S->in_use + q->bytes <= S->req_budget || S->in_use == 0)) return true;
-        }
+        for (uint64_t id : S->queue)
+          if (fits(S->reqs[id])) return true;
         return false;
       });
       if (S->stop) break;
+      std::shared_ptr<Request> r;
       for (auto it = S->queue.begin(); it != S->queue.end(); ++it) {
         auto& q = S->reqs[*it];
-        if (q->state == 0 && (S->in_use + q->bytes <= S->req_budget || S->in_use == 0)) {
+        if (fits(q)) {
           r = q;
           S->queue.erase(it);
           break;
         }
       }
       if (!r) continue;
-      r->state = 1;
-      r->t_admit = std::chrono::steady_clock::now();
-      S->in_use += r->bytes;
-    }
-    const int64_t p = r->p;
-    ibmi_status st = IBMI_OK;
-    if (p * p > dcap) {
-      cudaFree(dA);
-      cudaFree(dH);
-      dA = dH = nullptr;
-      dcap = 0;
-      if (cudaMalloc(&dA, sizeof(double) * p * p) != cudaSuccess ||
-          cudaMalloc(&dH, sizeof(double) * p * p) != cudaSuccess) {
-        cudaGetLastError();
-        st = IBMI_ERR_OOM;
-      } else {
-        dcap = p * p;
+      auto admit = [&](const std::shared_ptr<Request>& q) {
+        q->state = 1;
+        q->t_admit = std::chrono::steady_clock::now();
+        S->in_use += q->bytes;
+        batch.push_back(q);
+      };
+      admit(r);
+      grouped = S->opts.precision == IBMI_MIXED && S->opts.device_batch && bucket_of(r->p) <= kDevMaxOrder;
+      if (grouped) {
+        sh = shape_for(r->p, S->opts);
+        for (auto it = S->queue.begin(); it != S->queue.end() && (int)batch.size() < kServeGroupMax;) {
+          auto& q = S->reqs[*it];
+          if (q->state == 0 && q->tol == r->tol && bucket_of(q->p) == sh.p && same_shape(shape_for(q->p, S->opts), sh) &&
+              S->in_use + q->bytes <= S->req_budget) {
+            admit(q);
+            it = S->queue.erase(it);
+          } else {
+            ++it;
+          }
+        }
       }
     }
-    ibmi_batch_opts o = S->opts;
-    o.tol = r->tol;
-    if (st == IBMI_OK && cudaMemcpyAsync(dA, r->A.data(), sizeof(double) * p * p, cudaMemcpyHostToDevice,
-                                         w.stream) != cudaSuccess)
-      st = IBMI_ERR_CUDA;
-    if (st == IBMI_OK)
-      st = run_tuned(w, o, (S->budget - S->req_budget) / S->workers.size(), dA, p, p, dH, p, &r->res);
-    if (st == IBMI_OK || st == IBMI_NOT_CONVERGED) {
-      r->H.resize((size_t)p * p);
-      if (cudaMemcpyAsync(r->H.data(), dH, sizeof(double) * p * p, cudaMemcpyDeviceToHost, w.stream) != cudaSuccess ||
-          cudaStreamSynchronize(w.stream) != cudaSuccess)
-        st = IBMI_ERR_CUDA;
+    const int nb = (int)batch.size();
+    std::vector<ibmi_status> st(nb, IBMI_OK);
+    if ((int)dA.size() < nb) {
+      dA.resize(nb, nullptr);
+      dH.resize(nb, nullptr);
+      dcap.resize(nb, 0);
     }
-    r->res.status = st;
+    for (int b = 0; b < nb; ++b) {
+      const int64_t p = batch[b]->p;
+      if (p * p > dcap[b]) {
+        cudaFree(dA[b]);
+        cudaFree(dH[b]);
+        dA[b] = dH[b] = nullptr;
+        dcap[b] = 0;
+        if (cudaMalloc(&dA[b], sizeof(double) * p * p) != cudaSuccess ||
+            cudaMalloc(&dH[b], sizeof(double) * p * p) != cudaSuccess) {
+          cudaGetLastError();
+          st[b] = IBMI_ERR_OOM;
+          continue;
+        }
+        dcap[b] = p * p;
+      }
+      if (cudaMemcpyAsync(dA[b], batch[b]->A.data(), sizeof(double) * p * p, cudaMemcpyHostToDevice, w.stream) !=
+          cudaSuccess)
+        st[b] = IBMI_ERR_CUDA;
+    }
+    ibmi_batch_opts o = S->opts;
+    o.tol = batch[0]->tol;
+    std::vector<int> single(nb, 1);   // requests for the single-matrix pipeline
+    std::vector<ibmi_result> first(nb);
+    std::vector<char> tried(nb, 0);
+    if (grouped) {
+      std::vector<int> ok;
+      for (int b = 0; b < nb; ++b)
+        if (st[b] == IBMI_OK) ok.push_back(b);
+      int cap = 1;
+      while (cap < (int)ok.size()) cap *= 2;
+      DevGroup* g = ok.empty() ? nullptr : w.group(sh, cap, cache_cap);
+      if (g) {
+        std::vector<BatchMat> mats;
+        for (int b : ok) mats.push_back(BatchMat{dA[b], batch[b]->p, dH[b], batch[b]->p, batch[b]->p});
+        std::vector<ibmi_result> r(ok.size());
+        std::vector<int> fb(ok.size(), 1);
+        const ibmi_status gs =
+            g->run(mats.data(), (int)ok.size(), o, handover_theta(sh.p, true, o.ns_theta), w.stream, r.data(), fb.data());
+        if (gs == IBMI_OK) {
+          for (size_t j = 0; j < ok.size(); ++j) {
+            const int b = ok[j];
+            if (!fb[j]) {
+              batch[b]->res = r[j];
+              st[b] = (ibmi_status)r[j].status;
+              single[b] = 0;
+            } else {
+              first[b] = r[j];
+              tried[b] = 1;
+            }
+          }
+        }
+      }
+    }
+    for (int b = 0; b < nb; ++b) {
+      if (!single[b] || st[b] != IBMI_OK) continue;
+      const int64_t p = batch[b]->p;
+      st[b] = run_tuned(w, o, cache_cap, dA[b], p, p, dH[b], p, &batch[b]->res);
+      if (tried[b]) {
+        batch[b]->res.sweeps += first[b].sweeps;
+        batch[b]->res.ns_steps += first[b].ns_steps;
+        batch[b]->res.flops += first[b].flops;
+      }
+    }
+    for (int b = 0; b < nb; ++b) {
+      Request& r = *batch[b];
+      const int64_t p = r.p;
+      if (st[b] == IBMI_OK || st[b] == IBMI_NOT_CONVERGED) {
+        r.H.resize((size_t)p * p);
+        if (cudaMemcpyAsync(r.H.data(), dH[b], sizeof(double) * p * p, cudaMemcpyDeviceToHost, w.stream) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(w.stream) != cudaSuccess)
+          st[b] = IBMI_ERR_CUDA;
+      }
+      r.res.status = st[b];
+    }
     {
       std::lock_guard<std::mutex> lk(S->mu);
-      r->t_done = std::chrono::steady_clock::now();
-      S->in_use -= r->bytes;
-      if (r->state != 3) r->state = 2;
-      std::vector<double>().swap(r->A);
-      S->latencies.push_back(std::chrono::duration<double>(r->t_done - r->t_submit).count());
-      if (S->completed == 0) S->t_first_done = r->t_done;
-      S->t_last_done = r->t_done;
-      ++S->completed;
+      for (auto& rp : batch) {
+        Request& r = *rp;
+        r.t_done = std::chrono::steady_clock::now();
+        S->in_use -= r.bytes;
+        if (r.state != 3) r.state = 2;
+        std::vector<double>().swap(r.A);
+        S->latencies.push_back(std::chrono::duration<double>(r.t_done - r.t_submit).count());
+        if (S->completed == 0) S->t_first_done = r.t_done;
+        S->t_last_done = r.t_done;
+        ++S->completed;
+      }
     }
     S->cv.notify_all();
   }
-  cudaFree(dA);
-  cudaFree(dH);
+  for (size_t b = 0; b < dA.size(); ++b) {
+    cudaFree(dA[b]);
+    cudaFree(dH[b]);
+  }
 }
 
 }  // namespace ibmi
@@ -490,13 +613,8 @@ ibmi_status ibmi_invert_batched(int32_t n, const int64_t* p, const double* const
         for (size_t t = wi; t < tasks.size(); t += W) {
           const Task& task = tasks[t];
           const int ng = (int)task.idx.size();
-          auto& slot = w.groups[{task.s, ng}];
-          ibmi_status s = IBMI_OK;
-          if (!slot) {
-            slot.reset(new DevGroup());
-            s = slot->create(task.s.p, task.s.K, task.s.h, ng);
-            if (s != IBMI_OK) slot.reset();
-          }
+          DevGroup* slot = w.group(task.s, ng, 0);
+          ibmi_status s = slot ? IBMI_OK : IBMI_ERR_OOM;
           std::vector<BatchMat> mats(ng);
           std::vector<ibmi_result> r(ng);
           std::vector<int> fb(ng, 1);
@@ -504,7 +622,7 @@ ibmi_status ibmi_invert_batched(int32_t n, const int64_t* p, const double* const
             const int32_t i = task.idx[b];
             mats[b] = BatchMat{A[i], lda[i], H[i], ldh[i], p[i]};
           }
-          if (s == IBMI_OK) s = slot->run(mats.data(), o, handover_theta(task.s.p, true, o.ns_theta), w.stream,
+          if (s == IBMI_OK) s = slot->run(mats.data(), ng, o, handover_theta(task.s.p, true, o.ns_theta), w.stream,
                                           r.data(), fb.data());
           std::lock_guard<std::mutex> g(mu);
           if (s == IBMI_OK) {

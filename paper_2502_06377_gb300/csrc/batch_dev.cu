@@ -413,6 +413,12 @@ struct Alloc {
 DevGroup::DevGroup() : d(new Impl()) {}
 DevGroup::~DevGroup() { delete d; }
 int DevGroup::rounds() const { return d->rounds; }
+int DevGroup::capacity() const { return d->n; }
+size_t DevGroup::bytes() const {
+  const Impl& g = *d;
+  const size_t Z = (size_t)g.n * g.K;
+  return g.pool_bytes + sizeof(double) * (Z * (2 * g.mmax * g.mmax + g.mmax * CHOL_NB) + (size_t)g.n * g.ainv_total);
+}
 
 size_t DevGroup::bytes_per_matrix(int64_t pb, int K, int64_t h) {
   const int64_t ldp = (pb + 63) / 64 * 64;
@@ -590,10 +596,11 @@ struct MState {
 
 }  // namespace
 
-ibmi_status DevGroup::run(const BatchMat* mats, const ibmi_batch_opts& o, double theta, cudaStream_t st,
+ibmi_status DevGroup::run(const BatchMat* mats, int nrun, const ibmi_batch_opts& o, double theta, cudaStream_t st,
                           ibmi_result* res, int* fallback) {
   Impl& g = *d;
-  const int n = g.n, K = g.K;
+  if (nrun < 1 || nrun > g.n) return IBMI_ERR_INVALID_ARG;
+  const int n = nrun, cap = g.n, K = g.K;   // matrices of this run, of the group's buffers
   const int64_t pb = g.pb, ldp = g.ldp, pl = pb * g.ldp;
   IBMI_CUDA_TRY(cudaMemcpyAsync(g.din, mats, sizeof(BatchMat) * n, cudaMemcpyHostToDevice, st));
   IBMI_CUDA_TRY(cudaMemsetAsync(g.err, 0, sizeof(int), st));
@@ -620,7 +627,19 @@ ibmi_status DevGroup::run(const BatchMat* mats, const ibmi_batch_opts& o, double
   note_launch();
   k_b_embed<<<g2, 256, 0, st>>>(g.din, pb, g.A64);
   IBMI_CUDA_TRY(cudaGetLastError());
-  IBMI_TRY(invariants_all(&g.F, g.A64, pb, false, st));
+  {  // the FP64 factorisations of this run's n K blocks
+    const size_t zall = g.F.lo.size();
+    g.F.lo.resize((size_t)n * K);
+    g.F.hi.resize((size_t)n * K);
+    const ibmi_status fs_ = invariants_all(&g.F, g.A64, pb, false, st);
+    g.F.lo.resize(zall);
+    g.F.hi.resize(zall);
+    for (size_t z = 0; z < zall; ++z) {
+      g.F.lo[z] = g.lo[z % K];
+      g.F.hi[z] = g.hi[z % K];
+    }
+    IBMI_TRY(fs_);
+  }
   {
     SlicePtrs sp{};
     for (int s = 0; s < OZ_SA; ++s) sp.s[s] = g.Ao[s];
@@ -660,7 +679,7 @@ ibmi_status DevGroup::run(const BatchMat* mats, const ibmi_batch_opts& o, double
         t.mkr = g.w_kr;
         t.nb = n;
         EpiBOzAcc epi;
-        epi.T = g.TW + (int64_t)q * n * g.rows_w * ldp;
+        epi.T = g.TW + (int64_t)q * cap * g.rows_w * ldp;
         epi.ldt = ldp;
         epi.M = g.rows_w;
         epi.N = pb;
@@ -679,7 +698,7 @@ ibmi_status DevGroup::run(const BatchMat* mats, const ibmi_batch_opts& o, double
     for (int k = 0; k < K; ++k) {
       note_launch();
       k_b_wcombine<<<dim3(nblk(ldp), (unsigned)g.m[k], (unsigned)n), 256, 0, st>>>(
-          g.TW, (int64_t)n * g.rows_w * ldp, g.rows_w, g.woff[k], g.m[k], pb, ldp, g.expW, g.expA, g.lo[k], g.hi[k],
+          g.TW, (int64_t)cap * g.rows_w * ldp, g.rows_w, g.woff[k], g.m[k], pb, ldp, g.expW, g.expA, g.lo[k], g.hi[k],
           g.Ws[0][k], g.Ws[1][k], g.Ws[2][k]);
     }
     note_launch();
@@ -704,7 +723,7 @@ ibmi_status DevGroup::run(const BatchMat* mats, const ibmi_batch_opts& o, double
   const double tol = o.tol;
   const int max_sweeps = o.max_sweeps, ns_max = o.ns_max;
   // --- rounds
-  std::vector<int> hsel(16 * n);
+  std::vector<int> hsel(16 * cap);
   std::vector<double> hout(4 * n);
   g.rounds = 0;
   for (int round = 0;; ++round) {
@@ -732,7 +751,7 @@ ibmi_status DevGroup::run(const BatchMat* mats, const ibmi_batch_opts& o, double
     // upload all lists of the round at once
     int nsel = 0;
     auto put = [&](const std::vector<int>& v) -> int* {
-      if (v.empty() || nsel + (int)v.size() > 16 * n) return nullptr;
+      if (v.empty() || nsel + (int)v.size() > 16 * cap) return nullptr;
       int* dptr = g.dsel + nsel;
       std::copy(v.begin(), v.end(), hsel.begin() + nsel);
       nsel += (int)v.size();
@@ -866,7 +885,7 @@ ibmi_status DevGroup::run(const BatchMat* mats, const ibmi_batch_opts& o, double
       a.kt_total = (int)((pb + tc::BK - 1) / tc::BK);
       a.chunk = OZ_KCHUNK / tc::BK;
       a.T = g.T;
-      a.plane = (int64_t)n * pl;
+      a.plane = (int64_t)cap * pl;
       a.ldt = ldp;
       a.M = pb;
       a.N = pb;
@@ -896,7 +915,7 @@ ibmi_status DevGroup::run(const BatchMat* mats, const ibmi_batch_opts& o, double
       ProfScope ps(IBMI_K_OTHER, st, 0.0);
       note_launch(2);
       k_b_update<<<dim3(nblk(pb), (unsigned)pb, (unsigned)nl), 256, 0, st>>>(
-          dLupd, g.T, (int64_t)n * pl, pb, ldp, g.expX, g.expQ, NS_S - 1, g.X64, g.Q, g.Xprev);
+          dLupd, g.T, (int64_t)cap * pl, pb, ldp, g.expX, g.expQ, NS_S - 1, g.X64, g.Q, g.Xprev);
       const unsigned nt = (unsigned)((pb + 31) / 32);
       k_b_symfull<<<dim3(nt, nt, (unsigned)nl), dim3(32, 8), 0, st>>>(dLupd, pb, g.Q, g.X64);
       IBMI_CUDA_TRY(cudaGetLastError());
@@ -905,7 +924,7 @@ ibmi_status DevGroup::run(const BatchMat* mats, const ibmi_batch_opts& o, double
       ProfScope ps(IBMI_K_OTHER, st, 0.0);
       note_launch(2);
       k_b_combine<<<dim3(nblk(pb), (unsigned)pb, (unsigned)nl), 256, 0, st>>>(
-          dl, g.T, (int64_t)n * pl, pb, ldp, g.expX, g.expA, qmax, g.Q, g.partials, g.nparts_c);
+          dl, g.T, (int64_t)cap * pl, pb, ldp, g.expX, g.expA, qmax, g.Q, g.partials, g.nparts_c);
       k_b_sum<<<(unsigned)nl, 256, 0, st>>>(dl, g.partials, g.nparts_c, g.din, g.dout);
       IBMI_CUDA_TRY(cudaGetLastError());
       return IBMI_OK;
