@@ -90,6 +90,7 @@ struct MixedState {
   int splits_max = 0;
   int* err = nullptr;                    // device error word of the tcgen05 kernels
   CUtensorMap mapH[3];
+
   std::vector<CUtensorMap> mapW[3];
   void* pool = nullptr;
   double* Xprev = nullptr;               // p x p: the tail's iterate before its last update
@@ -358,6 +359,10 @@ ibmi_status mixed_sweep_step(ibmi_plan_s* P, int k, cudaStream_t st) {
   const int S = M->level == 0 ? 2 : 3;
   const double mult = S == 2 ? 3.0 : 6.0;   // slice products per product
   {
+    // 128-wide N tiles.  (64-wide ones, which give small sets two tiles per
+    // CTA so that one tile's epilogue runs under the other's MMAs, measured
+    // slower on the 576-row sets of the p = 4096 workload, 31.2 against 23.0
+    // ms per 10 inversions: they double the operand bytes per MMA.)
     const tc::TileRanges nr = tc::complement_tiles(lo, hi, p, MX_BN);
     tc::Maps maps;
     for (int s = 0; s < S; ++s) {
@@ -373,7 +378,9 @@ ibmi_status mixed_sweep_step(ibmi_plan_s* P, int k, cudaStream_t st) {
   // a4: P = X W^T (split over K); A operand = H slices rows [lo, hi), B = W slices.
   {
     const int nk = kr.count();
-    const int splits = std::max(1, std::min(M->splits_max, nk / 2));
+    // K splits to fill the SMs, but units of at least 12 K blocks (shorter
+    // ones are all pipeline fill and partial store)
+    const int splits = std::max(1, std::min(M->splits_max, nk / 12));
     tc::Maps maps;
     for (int s = 0; s < S; ++s) {
       maps.a[s] = M->mapH[s];
