@@ -271,11 +271,12 @@ __global__ void k_b_export(const int* sel, int64_t pb, int64_t ldp, const float*
   X64[(b * pb + i) * pb + j] = (double)Hf[(b * pb + i) * ldp + j];
 }
 
-// Q = I - 2^{e_i + f_j - 12} sum_{q <= qmax} T_q 2^{-7q} of matrix sel[z]
+// Q = I - 2^{e_i + f_j - 12} sum_{q <= qm[z]} T_q 2^{-7q} of matrix sel[z]
 // (FP64, pb x pb) and per-CTA sums of Q^2.
 __global__ void k_b_combine(const int* sel, const int* T, int64_t plane, int64_t pb, int64_t ldp, const int* ex,
-                            const int* ea, int qmax, double* Q, double* partials, int64_t nparts) {
+                            const int* ea, const int* qm, double* Q, double* partials, int64_t nparts) {
   const int64_t b = pick(sel, blockIdx.z), i = blockIdx.y, j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int qmax = qm[blockIdx.z];   // highest digit group of this matrix's residual
   float sq = 0.f;
   if (j < pb) {
     const double c = oz_value(T + b * pb * ldp, plane, i * ldp + j, qmax, ex[b * pb + i] + ea[b * pb + j] - 12);
@@ -590,6 +591,7 @@ struct MState {
   int level = 0, r = 0, stalled = 0, s = 0, qc = 0;
   double best = INFINITY, last_cheap = INFINITY, handover_below = INFINITY, handover_rho = 0.0, prev = INFINITY;
   bool early = false, reslice = false, restore = false;
+  bool waiting = false;   // ready for a tail action, held back to share its launches
   TailAct act = T_NONE;
   int next_q = 0;   // groups of the residual this round's tail action computes
 };
@@ -622,6 +624,7 @@ ibmi_status DevGroup::run(const BatchMat* mats, int nrun, const ibmi_batch_opts&
     fplan += m * m * m / 3.0 + 2.0 * m * m * m + 2.0 * m * m * nn;
   }
   const double fr = 2.0 * (double)pb * pb * pb;
+  const int full_pairs = count_pairs(OZ_SX, OZ_SA, 0, OZ_QMAX);
   const dim3 g2(nblk(pb), (unsigned)pb, (unsigned)n);
   // --- setup: padded inputs, FP64 factorisations, A's digits, W, H = I
   note_launch();
@@ -728,26 +731,35 @@ ibmi_status DevGroup::run(const BatchMat* mats, int nrun, const ibmi_batch_opts&
   g.rounds = 0;
   for (int round = 0;; ++round) {
     g.rounds = round;
+    // Matrices ready to enter the tail (or to certify) wait while more
+    // matrices are still sweeping than are waiting, so that tails run
+    // together and their launches cover many matrices; the slowest
+    // matrix's own path is not lengthened.
+    int nsweep = 0, nwait = 0;
+    for (int b = 0; b < n; ++b) {
+      nsweep += ms[b].phase == SWEEP;
+      nwait += ms[b].phase == TAIL && ms[b].waiting;
+    }
+    if (nwait >= std::max(1, nsweep))
+      for (int b = 0; b < n; ++b) ms[b].waiting = false;
     // selection lists of this round
-    std::vector<int> L[2], Lres, Lsw, Lexp, Lupd, Lrst, R[OZ_QMAX + 1], E[OZ_QMAX + 1];
+    std::vector<int> L[2], Lres, Lsw, Lexp, Lupd, Lrs;
+    std::vector<int> qlo, qhi;   // digit-group range of each residual (positions of Lrs)
     for (int b = 0; b < n; ++b) {
       MState& m = ms[b];
       if (m.phase == SWEEP) {
         L[m.level].push_back(b);
         Lsw.push_back(b);
         if (m.reslice) Lres.push_back(b);
-      } else if (m.phase == TAIL) {
+      } else if (m.phase == TAIL && !m.waiting) {
         if (m.act == T_ENTER || m.act == T_CERTIFY) Lexp.push_back(b);
         if (m.act == T_STEP) Lupd.push_back(b);
-        if (m.act == T_EXTEND) E[m.qc].push_back(b);
-        else R[m.next_q].push_back(b);
+        Lrs.push_back(b);
+        qlo.push_back(m.act == T_EXTEND ? m.qc + 1 : 0);
+        qhi.push_back(m.act == T_EXTEND ? OZ_QMAX : m.next_q);
       }
     }
-    if (Lsw.empty() && Lexp.empty() && Lupd.empty()) {
-      bool any = false;
-      for (int q = 0; q <= OZ_QMAX; ++q) any |= !E[q].empty() || !R[q].empty();
-      if (!any) break;
-    }
+    if (Lsw.empty() && Lrs.empty()) break;   // (waiting matrices are released once nothing sweeps)
     // upload all lists of the round at once
     int nsel = 0;
     auto put = [&](const std::vector<int>& v) -> int* {
@@ -763,12 +775,15 @@ ibmi_status DevGroup::run(const BatchMat* mats, int nrun, const ibmi_batch_opts&
     int* dLsw = put(Lsw);
     int* dLexp = put(Lexp);
     int* dLupd = put(Lupd);
-    int* dR[OZ_QMAX + 1];
-    int* dE[OZ_QMAX + 1];
-    for (int q = 0; q <= OZ_QMAX; ++q) {
-      dR[q] = put(R[q]);
-      dE[q] = put(E[q]);
+    int* dLrs = put(Lrs);
+    int* dqm = put(qhi);
+    std::vector<int> qr2;
+    for (size_t i = 0; i < qlo.size(); ++i) {
+      qr2.push_back(qlo[i]);
+      qr2.push_back(qhi[i]);
     }
+    if (nsel & 1) put(std::vector<int>{0});   // int2 alignment
+    const int2* dqr = (const int2*)put(qr2);
     if (nsel) IBMI_CUDA_TRY(cudaMemcpyAsync(g.dsel, hsel.data(), sizeof(int) * nsel, cudaMemcpyHostToDevice, st));
     // --- sweeps
     if (!Lres.empty()) {
@@ -860,7 +875,7 @@ ibmi_status DevGroup::run(const BatchMat* mats, int nrun, const ibmi_batch_opts&
       IBMI_CUDA_TRY(cudaGetLastError());
     }
     auto pairs = [&](const CUtensorMap* ma, int nsa, const CUtensorMap* mb, int nsb, int qmin, int qmax, int* dl,
-                     int nl, int kclass, double alg) -> ibmi_status {
+                     int nl, int kclass, double alg, const int2* qr) -> ibmi_status {
       tc::OzPairMaps maps;
       for (int s = 0; s < nsa; ++s) maps.a[s] = ma[s];
       for (int u = 0; u < nsb; ++u) maps.b[u] = mb[u];
@@ -893,6 +908,7 @@ ibmi_status DevGroup::run(const BatchMat* mats, int nrun, const ibmi_batch_opts&
       a.nb = nl;
       a.bsel = dl;
       a.tstride = pl;
+      a.qr = qr;
       ProfScope ps(kclass, st, 2.0 * np * (double)nl * pb * pb * (double)a.kt_total * tc::BK, alg);
       return with_bn(g.bn, [&](auto bnc) -> ibmi_status {
         IBMI_CUDA_TRY(tc::launch_oz_pairs<decltype(bnc)::value>(maps, a, st));
@@ -911,7 +927,7 @@ ibmi_status DevGroup::run(const BatchMat* mats, int nrun, const ibmi_batch_opts&
     if (!Lupd.empty()) {  // X <- sym(X + X Q^T) from the last residual's digits of X and Q
       const int nl = (int)Lupd.size();
       IBMI_CUDA_TRY(slice(g.Q, g.Qo, NS_S, g.expQ, dLupd, nl));
-      IBMI_TRY(pairs(g.mXo, NS_S, g.mQo, NS_S, 0, NS_S - 1, dLupd, nl, IBMI_K_NS, nl * fr));
+      IBMI_TRY(pairs(g.mXo, NS_S, g.mQo, NS_S, 0, NS_S - 1, dLupd, nl, IBMI_K_NS, nl * fr, nullptr));
       ProfScope ps(IBMI_K_OTHER, st, 0.0);
       note_launch(2);
       k_b_update<<<dim3(nblk(pb), (unsigned)pb, (unsigned)nl), 256, 0, st>>>(
@@ -920,31 +936,23 @@ ibmi_status DevGroup::run(const BatchMat* mats, int nrun, const ibmi_batch_opts&
       k_b_symfull<<<dim3(nt, nt, (unsigned)nl), dim3(32, 8), 0, st>>>(dLupd, pb, g.Q, g.X64);
       IBMI_CUDA_TRY(cudaGetLastError());
     }
-    auto finish_resid = [&](int qmax, int* dl, int nl) -> ibmi_status {
+    if (!Lrs.empty()) {  // residuals: fresh (groups 0..q) and extended (qc+1..9), one launch
+      const int nl = (int)Lrs.size();
+      IBMI_CUDA_TRY(slice(g.X64, g.Xo, OZ_SX, g.expX, dLrs, nl));   // digits are prefix-stable
+      int q0 = OZ_QMAX, q1 = 0;
+      double alg = 0.0;
+      for (int i = 0; i < nl; ++i) {
+        q0 = std::min(q0, qlo[i]);
+        q1 = std::max(q1, qhi[i]);
+        alg += fr * count_pairs(OZ_SX, OZ_SA, qlo[i], qhi[i]) / full_pairs;
+      }
+      IBMI_TRY(pairs(g.mXo, OZ_SX, g.mAo, OZ_SA, q0, q1, dLrs, nl, IBMI_K_RESIDUAL, alg, dqr));
       ProfScope ps(IBMI_K_OTHER, st, 0.0);
       note_launch(2);
       k_b_combine<<<dim3(nblk(pb), (unsigned)pb, (unsigned)nl), 256, 0, st>>>(
-          dl, g.T, (int64_t)cap * pl, pb, ldp, g.expX, g.expA, qmax, g.Q, g.partials, g.nparts_c);
-      k_b_sum<<<(unsigned)nl, 256, 0, st>>>(dl, g.partials, g.nparts_c, g.din, g.dout);
+          dLrs, g.T, (int64_t)cap * pl, pb, ldp, g.expX, g.expA, dqm, g.Q, g.partials, g.nparts_c);
+      k_b_sum<<<(unsigned)nl, 256, 0, st>>>(dLrs, g.partials, g.nparts_c, g.din, g.dout);
       IBMI_CUDA_TRY(cudaGetLastError());
-      return IBMI_OK;
-    };
-    const int full_pairs = count_pairs(OZ_SX, OZ_SA, 0, OZ_QMAX);
-    for (int q = 0; q <= OZ_QMAX; ++q) {
-      if (!R[q].empty()) {  // fresh residual with digit groups <= q
-        const int nl = (int)R[q].size(), nsx = std::min(OZ_SX, q + 1);
-        IBMI_CUDA_TRY(slice(g.X64, g.Xo, nsx, g.expX, dR[q], nl));
-        IBMI_TRY(pairs(g.mXo, nsx, g.mAo, OZ_SA, 0, q, dR[q], nl, IBMI_K_RESIDUAL,
-                       nl * fr * count_pairs(OZ_SX, OZ_SA, 0, q) / full_pairs));
-        IBMI_TRY(finish_resid(q, dR[q], nl));
-      }
-      if (!E[q].empty()) {  // extension of a residual with groups <= q to all groups
-        const int nl = (int)E[q].size();
-        if (std::min(OZ_SX, q + 1) < OZ_SX) IBMI_CUDA_TRY(slice(g.X64, g.Xo, OZ_SX, g.expX, dE[q], nl));
-        IBMI_TRY(pairs(g.mXo, OZ_SX, g.mAo, OZ_SA, q + 1, OZ_QMAX, dE[q], nl, IBMI_K_RESIDUAL,
-                       nl * fr * count_pairs(OZ_SX, OZ_SA, q + 1, OZ_QMAX) / full_pairs));
-        IBMI_TRY(finish_resid(OZ_QMAX, dE[q], nl));
-      }
     }
     // --- read every value of the round (one synchronisation)
     int herr = 0;
@@ -972,6 +980,7 @@ ibmi_status DevGroup::run(const BatchMat* mats, int nrun, const ibmi_batch_opts&
           m.phase = TAIL; m.act = T_ENTER; m.early = true; m.handover_rho = rho; m.s = 0;
           m.prev = INFINITY;
           m.next_q = rho <= tol ? OZ_QMAX : kFirstGroups;
+          m.waiting = true;
           continue;
         }
         m.stalled = rho > 0.95 * m.best ? m.stalled + 1 : 0;
@@ -983,6 +992,7 @@ ibmi_status DevGroup::run(const BatchMat* mats, int nrun, const ibmi_batch_opts&
             m.phase = TAIL; m.act = T_ENTER; m.early = false; m.handover_rho = rho; m.s = 0;
             m.prev = INFINITY;
             m.next_q = kFirstGroups;
+            m.waiting = true;
             continue;
           } else {
             m.phase = FALLBACK;   // the single-matrix path measures the spectral radius here
@@ -991,9 +1001,10 @@ ibmi_status DevGroup::run(const BatchMat* mats, int nrun, const ibmi_batch_opts&
         }
         if (rho <= tol || m.r >= max_sweeps) {   // BF16x3 cannot certify tol: the FP64-accurate residual
           m.phase = TAIL; m.act = T_CERTIFY; m.next_q = OZ_QMAX;
+          m.waiting = true;
           continue;
         }
-      } else if (m.phase == TAIL) {
+      } else if (m.phase == TAIL && !m.waiting) {
         const TailAct act = m.act;
         if (act == T_CERTIFY) {
           flops[b] += fr;

@@ -37,7 +37,17 @@ struct OzPairArgs {
   int nb;
   const int* bsel;
   int64_t tstride;
+  // Optional per-problem digit-group ranges (indexed like bsel): the tiles of
+  // problem i take only the pairs with qr[i].x <= q <= qr[i].y.
+  const int2* qr;
 };
+
+// Whether the tiles of the problem at position bi take pair pi.
+__device__ __forceinline__ bool oz_pair_on(const OzPairArgs& g, int bi, int pi) {
+  if (!g.qr) return true;
+  const int2 r = g.qr[bi];
+  return g.q[pi] >= r.x && g.q[pi] <= r.y;
+}
 
 template <int BN>
 __global__ void __launch_bounds__(THREADS, Cfg<1, BN>::CTAS_PER_SM) k_oz_pairs(const __grid_constant__ OzPairMaps maps,
@@ -82,6 +92,7 @@ __global__ void __launch_bounds__(THREADS, Cfg<1, BN>::CTAS_PER_SM) k_oz_pairs(c
         for (int ci = 0; ok && ci < nchunks; ++ci)
           for (int tt = blockIdx.x; ok && tt < total; tt += gridDim.x) {
             const int bi = tt / g.tiles, tl = tt - bi * g.tiles;
+            if (!oz_pair_on(g, bi, pi)) continue;
             const int bb = g.bsel ? g.bsel[bi] : bi;
             const int mt = tl / g.grid_n, ntl = tl - mt * g.grid_n;
             const int kb = ci * g.chunk, nk = min(g.chunk, g.kt_total - kb);
@@ -120,7 +131,8 @@ __global__ void __launch_bounds__(THREADS, Cfg<1, BN>::CTAS_PER_SM) k_oz_pairs(c
       bool ok = true;
       for (int pi = 0; ok && pi < g.n; ++pi)
         for (int ci = 0; ok && ci < nchunks; ++ci)
-          for (int tt = blockIdx.x; ok && tt < total; tt += gridDim.x, ++local) {
+          for (int tt = blockIdx.x; ok && tt < total; tt += gridDim.x) {
+            if (!oz_pair_on(g, tt / g.tiles, pi)) continue;
             const int nk = min(g.chunk, g.kt_total - ci * g.chunk);
             const int buf = local & 1;
             const uint32_t use = (uint32_t)(local >> 1);
@@ -140,6 +152,7 @@ __global__ void __launch_bounds__(THREADS, Cfg<1, BN>::CTAS_PER_SM) k_oz_pairs(c
               mma_commit(&empty[st]);
             }
             mma_commit(&accf[buf]);
+            ++local;
           }
       if (!ok || *(volatile int*)g.err != 0) mma_drain_on_error(drain);
     }
@@ -151,8 +164,9 @@ __global__ void __launch_bounds__(THREADS, Cfg<1, BN>::CTAS_PER_SM) k_oz_pairs(c
     bool ok = true;
     for (int pi = 0; ok && pi < g.n; ++pi)
       for (int ci = 0; ok && ci < nchunks; ++ci)
-        for (int tt = blockIdx.x; ok && tt < total; tt += gridDim.x, ++local) {
+        for (int tt = blockIdx.x; ok && tt < total; tt += gridDim.x) {
           const int bi = tt / g.tiles, tl = tt - bi * g.tiles;
+          if (!oz_pair_on(g, bi, pi)) continue;
           const int bb = g.bsel ? g.bsel[bi] : bi;
           const int mt = tl / g.grid_n, ntl = tl - mt * g.grid_n;
           const int buf = local & 1;
@@ -209,6 +223,7 @@ __global__ void __launch_bounds__(THREADS, Cfg<1, BN>::CTAS_PER_SM) k_oz_pairs(c
           tc_fence_before();
           __syncwarp();
           if (lane == 0) mbar_arrive(&acce[buf]);
+          ++local;
         }
   }
   __syncthreads();
