@@ -909,6 +909,7 @@ ibmi_status DevGroup::run(const BatchMat* mats, int nrun, const ibmi_batch_opts&
       a.bsel = dl;
       a.tstride = pl;
       a.qr = qr;
+      tc::oz_make_segments(a);
       ProfScope ps(kclass, st, 2.0 * np * (double)nl * pb * pb * (double)a.kt_total * tc::BK, alg);
       return with_bn(g.bn, [&](auto bnc) -> ibmi_status {
         IBMI_CUDA_TRY(tc::launch_oz_pairs<decltype(bnc)::value>(maps, a, st));

@@ -11,6 +11,8 @@
 // are gone.  Roles as in k_tc_gemm: warp 0 TMA producer, warp 1 MMA issuer,
 // warps 2-5 epilogue through a shared-memory stage (row-coalesced int4).
 #pragma once
+#include <algorithm>
+
 #include "tc_gemm.cuh"
 
 namespace ibmi {
@@ -26,6 +28,10 @@ struct OzPairMaps {
 struct OzPairArgs {
   int n;                                   // pairs
   int8_t s[OZP_MAX_PAIRS], u[OZP_MAX_PAIRS], q[OZP_MAX_PAIRS], first[OZP_MAX_PAIRS];
+  // Segments (oz_make_segments): runs of consecutive pairs of one group that
+  // share one FP32 accumulation and one write of the group plane.
+  int nseg;
+  int8_t seg0[OZP_MAX_PAIRS], segn[OZP_MAX_PAIRS];
   int grid_n, tiles;                       // N tiles; tiles = grid_m * grid_n
   int kt_total, chunk;                     // K tiles; K tiles per exact accumulation
   int* T;                                  // group planes: T + q * plane, row pitch ldt
@@ -41,6 +47,25 @@ struct OzPairArgs {
   // problem i take only the pairs with qr[i].x <= q <= qr[i].y.
   const int2* qr;
 };
+
+// Splits the pair list (in group order) into segments: a pair's product,
+// summed over one K chunk of kc = min(K, 4096) terms, is an integer below
+// kc 2^12 (digits of magnitude <= 64), so L = floor(4096 / kc) pairs of one
+// group summed in FP32 stay below 2^24 and exact; they accumulate in TMEM
+// together and the group plane is written once for them.
+inline void oz_make_segments(OzPairArgs& g) {
+  const int kc = std::min(g.kt_total, g.chunk) * BK;
+  const int L = std::max(1, 4096 / std::max(1, kc));
+  g.nseg = 0;
+  for (int i = 0; i < g.n;) {
+    int j = i + 1;
+    while (j < g.n && j - i < L && g.q[j] == g.q[i]) ++j;
+    g.seg0[g.nseg] = (int8_t)i;
+    g.segn[g.nseg] = (int8_t)(j - i);
+    ++g.nseg;
+    i = j;
+  }
+}
 
 // Whether the tiles of the problem at position bi take pair pi.
 __device__ __forceinline__ bool oz_pair_on(const OzPairArgs& g, int bi, int pi) {
@@ -88,29 +113,32 @@ __global__ void __launch_bounds__(THREADS, Cfg<1, BN>::CTAS_PER_SM) k_oz_pairs(c
     if (lane == 0) {  // TMA producer
       int kc = 0;
       bool ok = true;
-      for (int pi = 0; ok && pi < g.n; ++pi)
+      for (int sg = 0; ok && sg < g.nseg; ++sg)
         for (int ci = 0; ok && ci < nchunks; ++ci)
           for (int tt = blockIdx.x; ok && tt < total; tt += gridDim.x) {
             const int bi = tt / g.tiles, tl = tt - bi * g.tiles;
-            if (!oz_pair_on(g, bi, pi)) continue;
+            const int p0 = g.seg0[sg];
+            if (!oz_pair_on(g, bi, p0)) continue;
             const int bb = g.bsel ? g.bsel[bi] : bi;
             const int mt = tl / g.grid_n, ntl = tl - mt * g.grid_n;
             const int kb = ci * g.chunk, nk = min(g.chunk, g.kt_total - kb);
-            const CUtensorMap* ma = &maps.a[g.s[pi]];
-            const CUtensorMap* mb = &maps.b[g.u[pi]];
-            for (int it = 0; it < nk; ++it, ++kc) {
-              const int st = kc % C::STAGES;
-              const uint32_t ph = (uint32_t)(kc / C::STAGES) & 1u;
-              if (!mbar_wait(&empty[st], ph ^ 1u, g.err)) { ok = false; break; }
-              const int kx = (kb + it) * BK;
-              uint8_t* sa = tiles + st * C::STAGE_BYTES;
-              mbar_expect_tx(&full[st], C::STAGE_BYTES);
-              if (g.nb > 0) {
-                tma_load_3d(sa, ma, &full[st], kx, mt * BM, bb);
-                tma_load_3d(sa + C::A_BYTES, mb, &full[st], kx, ntl * BN, bb);
-              } else {
-                tma_load_2d(sa, ma, &full[st], kx, mt * BM);
-                tma_load_2d(sa + C::A_BYTES, mb, &full[st], kx, ntl * BN);
+            for (int j = 0; ok && j < g.segn[sg]; ++j) {
+              const CUtensorMap* ma = &maps.a[g.s[p0 + j]];
+              const CUtensorMap* mb = &maps.b[g.u[p0 + j]];
+              for (int it = 0; it < nk; ++it, ++kc) {
+                const int st = kc % C::STAGES;
+                const uint32_t ph = (uint32_t)(kc / C::STAGES) & 1u;
+                if (!mbar_wait(&empty[st], ph ^ 1u, g.err)) { ok = false; break; }
+                const int kx = (kb + it) * BK;
+                uint8_t* sa = tiles + st * C::STAGE_BYTES;
+                mbar_expect_tx(&full[st], C::STAGE_BYTES);
+                if (g.nb > 0) {
+                  tma_load_3d(sa, ma, &full[st], kx, mt * BM, bb);
+                  tma_load_3d(sa + C::A_BYTES, mb, &full[st], kx, ntl * BN, bb);
+                } else {
+                  tma_load_2d(sa, ma, &full[st], kx, mt * BM);
+                  tma_load_2d(sa + C::A_BYTES, mb, &full[st], kx, ntl * BN);
+                }
               }
             }
           }
@@ -129,28 +157,30 @@ __global__ void __launch_bounds__(THREADS, Cfg<1, BN>::CTAS_PER_SM) k_oz_pairs(c
       constexpr uint32_t idesc = idesc_bf16(BM, BN);
       int kc = 0, local = 0;
       bool ok = true;
-      for (int pi = 0; ok && pi < g.n; ++pi)
+      for (int sg = 0; ok && sg < g.nseg; ++sg)
         for (int ci = 0; ok && ci < nchunks; ++ci)
           for (int tt = blockIdx.x; ok && tt < total; tt += gridDim.x) {
-            if (!oz_pair_on(g, tt / g.tiles, pi)) continue;
+            if (!oz_pair_on(g, tt / g.tiles, g.seg0[sg])) continue;
             const int nk = min(g.chunk, g.kt_total - ci * g.chunk);
             const int buf = local & 1;
             const uint32_t use = (uint32_t)(local >> 1);
             if (!mbar_wait(&acce[buf], (use & 1u) ^ 1u, g.err)) { ok = false; break; }
             tc_fence_after();
             const uint32_t dacc = tmem + (uint32_t)(buf * BN);
-            for (int it = 0; it < nk; ++it, ++kc) {
-              const int st = kc % C::STAGES;
-              const uint32_t ph = (uint32_t)(kc / C::STAGES) & 1u;
-              if (!mbar_wait(&full[st], ph, g.err)) { ok = false; break; }
-              tc_fence_after();
-              const uint32_t sa = smem_u32(tiles + st * C::STAGE_BYTES);
-              const uint32_t sb = sa + C::A_BYTES;
+            for (int j = 0; ok && j < g.segn[sg]; ++j)
+              for (int it = 0; it < nk; ++it, ++kc) {
+                const int st = kc % C::STAGES;
+                const uint32_t ph = (uint32_t)(kc / C::STAGES) & 1u;
+                if (!mbar_wait(&full[st], ph, g.err)) { ok = false; break; }
+                tc_fence_after();
+                const uint32_t sa = smem_u32(tiles + st * C::STAGE_BYTES);
+                const uint32_t sb = sa + C::A_BYTES;
 #pragma unroll
-              for (int kk = 0; kk < BK / 16; ++kk)
-                mma_bf16(dacc, sdesc_sw128(sa + kk * 32), sdesc_sw128(sb + kk * 32), idesc, (it | kk) != 0 ? 1u : 0u);
-              mma_commit(&empty[st]);
-            }
+                for (int kk = 0; kk < BK / 16; ++kk)
+                  mma_bf16(dacc, sdesc_sw128(sa + kk * 32), sdesc_sw128(sb + kk * 32), idesc,
+                           (j | it | kk) != 0 ? 1u : 0u);
+                mma_commit(&empty[st]);
+              }
             mma_commit(&accf[buf]);
             ++local;
           }
@@ -162,9 +192,10 @@ __global__ void __launch_bounds__(THREADS, Cfg<1, BN>::CTAS_PER_SM) k_oz_pairs(c
     const int c4 = (lane & 3) * 4, r0 = lane >> 2;
     int local = 0;
     bool ok = true;
-    for (int pi = 0; ok && pi < g.n; ++pi)
+    for (int sg = 0; ok && sg < g.nseg; ++sg)
       for (int ci = 0; ok && ci < nchunks; ++ci)
         for (int tt = blockIdx.x; ok && tt < total; tt += gridDim.x) {
+          const int pi = g.seg0[sg];   // the segment's first pair: its group and whether it stores
           const int bi = tt / g.tiles, tl = tt - bi * g.tiles;
           if (!oz_pair_on(g, bi, pi)) continue;
           const int bb = g.bsel ? g.bsel[bi] : bi;
@@ -246,7 +277,7 @@ cudaError_t launch_oz_pairs(const OzPairMaps& maps, const OzPairArgs& g, cudaStr
     if (e != cudaSuccess) return e;
     attr_set.store(true, std::memory_order_release);
   }
-  if (g.n <= 0 || g.tiles <= 0 || g.kt_total <= 0) return cudaSuccess;
+  if (g.n <= 0 || g.tiles <= 0 || g.kt_total <= 0 || g.nseg <= 0) return cudaSuccess;
   const int grid = std::min(g.tiles * (g.nb > 0 ? g.nb : 1), resident_ctas<1, BN>());
   note_launch();
   k_oz_pairs<BN><<<grid, THREADS, smem_bytes, st>>>(maps, g);

@@ -487,6 +487,7 @@ static ibmi_status pair_products(RefineState* R, const CUtensorMap* ma, int nsa,
   g.M = p;
   g.N = p;
   g.err = R->err;
+  tc::oz_make_segments(g);
   // the method's share: these pairs out of all pairs of the full product
   // (52 for the residual, 15 for the Newton-Schulz update), of 2 p^3
   auto count_pairs = [](int na, int nb, int qm) {
@@ -714,6 +715,7 @@ ibmi_status refine_block_inverse(RefineState* R, const double* Y, int64_t ldy, i
   g.M = m;
   g.N = m;
   g.err = R->err;
+  tc::oz_make_segments(g);
   {
     ProfScope ps(IBMI_K_INVARIANTS_TC, st, 2.0 * n * (double)m * m * (double)g.kt_total * tc::BK,
                  (double)m * m * m / 3.0);   // Y^T Y with triangular Y, lower half
