@@ -239,3 +239,44 @@ def test_unfinished_matrices_fall_back_and_rerun(ibmi, batch):
     for r, A, H in zip(res, sub, Hs):
         assert r["status"] == ibmi.IBMI_NOT_CONVERGED and r["sweeps"] >= 2 * 12, r
         assert np.all(np.isfinite(H)) and O.residual_f(A, H) < 1.0
+
+
+def _kms_inverse(p, rho):
+    inv = np.zeros((p, p))
+    c = 1.0 / (1.0 - rho * rho)
+    i = np.arange(p)
+    inv[i, i] = c * (1.0 + rho * rho)
+    inv[0, 0] = inv[p - 1, p - 1] = c
+    inv[i[:-1], i[:-1] + 1] = inv[i[:-1] + 1, i[:-1]] = -rho * c
+    return inv
+
+
+@pytest.mark.parametrize("family,p", [("kms", 2048), ("matern", 3000), ("cs", 4096)])
+def test_serve_families_of_the_trace_at_large_orders(ibmi, family, p):
+    """One request of each family of the served trace at orders 2048-4096,
+    through the server, against the closed forms (KMS tridiagonal inverse,
+    Sherman-Morrison for compound symmetry) or LAPACK (Matern), and the
+    oracle's residual."""
+    if family == "kms":
+        A, inv = wl.kms(p, 0.95), _kms_inverse(p, 0.95)
+    elif family == "cs":
+        a, b = 0.5, 1.0
+        A = wl.compound_symmetry(p, a, b)
+        inv = (np.eye(p) - b / (a + p * b) * np.ones((p, p))) / a
+    else:
+        A = wl.matern32(wl.uniform_points(np.random.default_rng(9), p, 2), 0.1, 1.0, 1e-2)
+        inv = np.linalg.inv(A)
+    srv = ibmi.Server(64 << 30, workers=4)
+    rid = srv.submit(A)
+    t_end = time.time() + 300
+    while time.time() < t_end:
+        st, H, r = srv.poll(rid, p)
+        if st != ibmi.IBMI_NOT_READY:
+            break
+        time.sleep(0.005)
+    srv.close()
+    assert st == ibmi.IBMI_OK, (family, r)
+    rf = O.residual_f(A, H)
+    print(f"{family} p={p}: {r['sweeps']} sweeps + {r['ns_steps']} NS, rho_F {rf:.2e}")
+    assert rf <= 1e-10
+    assert np.abs(H - inv).max() <= 1e-8 * np.abs(inv).max()
