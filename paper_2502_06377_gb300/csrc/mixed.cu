@@ -193,24 +193,12 @@ __global__ void k_export_h(const float* Hf, int64_t ldp, int64_t p, double* H, i
 }
 
 // a4 finish: H[I, I] = A_I^{-1} - P with P = sum of the split-K partials (its
-// lower triangle, mirrored).
+// lower triangle, mirrored: element (max, min) serves both (i, j) and (j, i),
+// so H[I, I] comes out exactly symmetric), by 32 x 32 tiles.
 __global__ void k_mixed_sym(const float* Spart, int splits, int64_t m, const double* Ainv, int64_t lo, int64_t ldp,
                             float* Hf, __nv_bfloat16* s0, __nv_bfloat16* s1, __nv_bfloat16* s2) {
-  const int64_t i = blockIdx.y, j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= m) return;
-  // P is computed on and below the diagonal: element (max, min) serves both
-  // (i, j) and (j, i), so H[I, I] comes out exactly symmetric
-  const int64_t hi_ = i > j ? i : j, lo_ = i > j ? j : i;
-  float a = 0.f;
-  for (int z = 0; z < splits; ++z) a += Spart[(int64_t)z * m * m + hi_ * m + lo_];
-  float x = (float)(Ainv[i * m + j] - (double)a);
-  int64_t o = (lo + i) * ldp + lo + j;
-  Hf[o] = x;
-  __nv_bfloat16 t0, t1, t2;
-  split3(x, t0, t1, t2);
-  s0[o] = t0;
-  s1[o] = t1;
-  if (s2) s2[o] = t2;
+  sym_tile_finish(Spart, splits, m, Ainv, (int64_t)blockIdx.y * 32, (int64_t)blockIdx.x * 32, Hf, s0, s1, s2,
+                  lo * ldp + lo, ldp);
 }
 
 static inline dim3 grid2(int64_t cols, int64_t rows) {
@@ -395,8 +383,9 @@ ibmi_status mixed_sweep_step(ibmi_plan_s* P, int k, cudaStream_t st) {
     if (S == 2) IBMI_CUDA_TRY((tc::launch<2, MX_BN>(maps, t, ntn, (int)((m + 127) / 128), epi, st)));
     else IBMI_CUDA_TRY((tc::launch<3, MX_BN>(maps, t, ntn, (int)((m + 127) / 128), epi, st)));
     note_launch();
-    k_mixed_sym<<<grid2(m, m), 256, 0, st>>>(M->Spart, splits, m, P->ainv[k], lo, M->ldp, M->Hf, M->Hs[0],
-                                             M->Hs[1], S == 3 ? M->Hs[2] : nullptr);
+    const unsigned nt = (unsigned)((m + 31) / 32);
+    k_mixed_sym<<<dim3(nt, nt), dim3(32, 8), 0, st>>>(M->Spart, splits, m, P->ainv[k], lo, M->ldp, M->Hf, M->Hs[0],
+                                                      M->Hs[1], S == 3 ? M->Hs[2] : nullptr);
     IBMI_CUDA_TRY(cudaGetLastError());
   }
   return IBMI_OK;
