@@ -1,6 +1,6 @@
 """Command-line runner for single library calls on cuda:0.
 
-  python -m paper_2502_06377_gb300 invert   --p 4096 --K 8 --h 32 --precision mixed --theta 0.9
+  python -m paper_2502_06377_gb300 invert   --p 4096 --K 8 --h 32 --precision mixed --theta 0.9 --init identity
   python -m paper_2502_06377_gb300 residual --p 4096 --method tc
   python -m paper_2502_06377_gb300 batch    --only-p 1024 --autotune 0 --repeat 2
 
@@ -36,6 +36,8 @@ def main():
     ap.add_argument("--max-sweeps", type=int, default=500)
     ap.add_argument("--theta", type=float, default=0.5,
                     help="Newton-Schulz hand-over on ||I - A H||_F (mixed precision)")
+    ap.add_argument("--init", choices=["identity", "schur"], default="identity",
+                    help="initial iterate: H = I, or T_0 = A_{I_1^c}^{-1} (invert)")
     ap.add_argument("--only-p", type=int, default=0, help="batch: only the matrices of this order")
     ap.add_argument("--autotune", type=int, default=1, help="batch: tune (K, h) per size bucket")
     ap.add_argument("--device-batch", type=int, default=1, help="batch: run device groups")
@@ -57,7 +59,8 @@ def main():
     prec = ibmi.IBMI_MIXED if a.precision == "mixed" else ibmi.IBMI_FP64
     if a.cmd == "invert":
         plan = ibmi.ibmi_plan(a.p, K=a.K, h=a.h, precision=prec, tol=a.tol, max_sweeps=a.max_sweeps,
-                              ns_theta=a.theta if prec == ibmi.IBMI_MIXED else 0.0)
+                              ns_theta=a.theta if prec == ibmi.IBMI_MIXED else 0.0,
+                              init=ibmi.IBMI_INIT_SCHUR if a.init == "schur" else ibmi.IBMI_INIT_IDENTITY)
         ibmi._lib.load().ibmi_prof_enable(1)
         out = None
         for _ in range(a.repeat):
@@ -68,12 +71,14 @@ def main():
         import ctypes as C
         lib = ibmi._lib.load()
         names = ["sweep_x", "sweep_s", "residual", "newton_schulz", "invariants", "other", "invariants_tc"]
-        prof = {}
+        prof, calls = {}, {}
         for k, nm in enumerate(names):
             n, t, f = C.c_int64(), C.c_double(), C.c_double()
             lib.ibmi_prof_get(k, C.byref(n), C.byref(t), C.byref(f))
             prof[nm] = round(t.value / a.repeat, 3)
+            calls[nm] = n.value / a.repeat
         out["ms_per_class"] = prof
+        out["calls_per_class"] = calls
         print(json.dumps(out))
     else:
         plan = ibmi.ibmi_plan(a.p, K=a.K, h=a.h, precision=ibmi.IBMI_FP64, tol=0.0, max_sweeps=1)

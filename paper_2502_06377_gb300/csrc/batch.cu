@@ -515,7 +515,7 @@ size_t ibmi_plan_bytes(const ibmi_plan_desc* d) {
   if (d->precision == IBMI_MIXED) {
     const double ldp = ceil(p / 64.0) * 64.0;
     b += 4.0 * p * ldp + 4.0 * p * ldp + 4.0 * K * m * ldp + 4.0 * 64.0 * m * m;   // H master + slices, W, split-K
-    b += 2.0 * p * ldp * 25.0 + 4.0 * p * ldp * 10.0 + 8.0 * p * p;           // refinement planes
+    b += 2.0 * p * ldp * 25.0 + 4.0 * p * ldp * 10.0 + 16.0 * p * p;          // refinement planes
   } else {
     b += 8.0 * K * m * p;                                                     // W
     b += (d->ns_theta > 0.0 ? 16.0 * p * p : 0.0);

@@ -209,9 +209,20 @@ struct EpiBPartial : tc::EpiBase {
 __global__ void k_b_sym(const int* sel, const float* Spart, int64_t sbstride, int splits, int64_t m, const double* Ainv,
                         int64_t abstride, int64_t lo, int64_t pb, int64_t ldp, float* Hf, __nv_bfloat16* s0,
                         __nv_bfloat16* s1, __nv_bfloat16* s2) {
-  const int64_t b = pick(sel, blockIdx.z);
-  sym_tile_finish(Spart + b * sbstride, splits, m, Ainv + b * abstride, (int64_t)blockIdx.y * 32,
-                  (int64_t)blockIdx.x * 32, Hf, s0, s1, s2, (b * pb + lo) * ldp + lo, ldp);
+  const int64_t b = pick(sel, blockIdx.z), i = blockIdx.y, j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= m) return;
+  const int64_t hi_ = i > j ? i : j, lo_ = i > j ? j : i;
+  const float* S = Spart + b * sbstride;
+  float a = 0.f;
+  for (int z = 0; z < splits; ++z) a += S[(int64_t)z * m * m + hi_ * m + lo_];
+  const float x = (float)(Ainv[b * abstride + i * m + j] - (double)a);
+  const int64_t o = (b * pb + lo + i) * ldp + lo + j;
+  Hf[o] = x;
+  __nv_bfloat16 t0, t1, t2;
+  split3(x, t0, t1, t2);
+  s0[o] = t0;
+  s1[o] = t1;
+  if (s2) s2[o] = t2;
 }
 
 // BF16x3 stop test of matrix bat: per unit and epilogue warp, the sum of
@@ -827,7 +838,7 @@ ibmi_status DevGroup::run(const BatchMat* mats, int nrun, const ibmi_batch_opts&
           if (S == 2) IBMI_CUDA_TRY((tc::launch<2, kBN>(maps, t, ntn, (int)((m + 127) / 128), epi, st)));
           else IBMI_CUDA_TRY((tc::launch<3, kBN>(maps, t, ntn, (int)((m + 127) / 128), epi, st)));
           note_launch();
-          k_b_sym<<<dim3((unsigned)((m + 31) / 32), (unsigned)((m + 31) / 32), (unsigned)nl), dim3(32, 8), 0, st>>>(
+          k_b_sym<<<dim3(nblk(m), (unsigned)m, (unsigned)nl), 256, 0, st>>>(
               dl, g.Spart, (int64_t)g.splits * g.mmax * g.mmax, splits, m, g.F.pool + g.aoff[k], g.ainv_total, lo, pb,
               ldp, g.Hf, g.Hs[0], g.Hs[1], S == 3 ? g.Hs[2] : nullptr);
           IBMI_CUDA_TRY(cudaGetLastError());

@@ -100,13 +100,14 @@ struct MixedState {
   bool graphs = false;
   const double* gA = nullptr;
   const double* gH = nullptr;
-  PhaseGraph g_setup, g_sweep[2], g_cheap, g_reslice, g_export_resid, g_update[2], g_radius;
+  PhaseGraph g_setup, g_sweep[2], g_cheap, g_reslice, g_export_resid, g_update[4], g_radius;
   std::map<int, PhaseGraph> g_tail;      // tail residuals by digit groups (see ns_graph_key)
 };
 
 static void drop_graphs(MixedState* M) {
   for (PhaseGraph* g : {&M->g_setup, &M->g_sweep[0], &M->g_sweep[1], &M->g_cheap, &M->g_reslice,
-                        &M->g_export_resid, &M->g_update[0], &M->g_update[1], &M->g_radius}) {
+                        &M->g_export_resid, &M->g_update[0], &M->g_update[1], &M->g_update[2],
+                        &M->g_update[3], &M->g_radius}) {
     if (g->exec) cudaGraphExecDestroy(g->exec);
     *g = PhaseGraph{};
   }
@@ -119,6 +120,9 @@ static void drop_graphs(MixedState* M) {
 // graph keys of the tail's residuals: (export of H first, groups) and extensions (from, to)
 static int ns_graph_key(bool export_h, int q) { return (export_h ? 100 : 0) + q; }
 static int ns_extend_key(int qfrom, int qto) { return 200 + 10 * qfrom + qto; }
+// ... and corrections (groups) and their extensions (from, to)
+static int ns_correct_key(int q) { return 400 + q; }
+static int ns_correct_extend_key(int qfrom, int qto) { return 500 + 10 * qfrom + qto; }
 
 // Runs `body` (kernel launches only, no host synchronisation) directly, or in
 // graph mode captures it once into *g and replays the graph.  While per-class
@@ -193,12 +197,26 @@ __global__ void k_export_h(const float* Hf, int64_t ldp, int64_t p, double* H, i
 }
 
 // a4 finish: H[I, I] = A_I^{-1} - P with P = sum of the split-K partials (its
-// lower triangle, mirrored: element (max, min) serves both (i, j) and (j, i),
-// so H[I, I] comes out exactly symmetric), by 32 x 32 tiles.
+// lower triangle, mirrored).  One row per block row: the partials fit in L2
+// (they were just written), so the mirrored half's column reads stay there;
+// measured faster than 32 x 32 tiles through shared memory on 5120-row sets.
 __global__ void k_mixed_sym(const float* Spart, int splits, int64_t m, const double* Ainv, int64_t lo, int64_t ldp,
                             float* Hf, __nv_bfloat16* s0, __nv_bfloat16* s1, __nv_bfloat16* s2) {
-  sym_tile_finish(Spart, splits, m, Ainv, (int64_t)blockIdx.y * 32, (int64_t)blockIdx.x * 32, Hf, s0, s1, s2,
-                  lo * ldp + lo, ldp);
+  const int64_t i = blockIdx.y, j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= m) return;
+  // P is computed on and below the diagonal: element (max, min) serves both
+  // (i, j) and (j, i), so H[I, I] comes out exactly symmetric
+  const int64_t hi_ = i > j ? i : j, lo_ = i > j ? j : i;
+  float a = 0.f;
+  for (int z = 0; z < splits; ++z) a += Spart[(int64_t)z * m * m + hi_ * m + lo_];
+  float x = (float)(Ainv[i * m + j] - (double)a);
+  int64_t o = (lo + i) * ldp + lo + j;
+  Hf[o] = x;
+  __nv_bfloat16 t0, t1, t2;
+  split3(x, t0, t1, t2);
+  s0[o] = t0;
+  s1[o] = t1;
+  if (s2) s2[o] = t2;
 }
 
 static inline dim3 grid2(int64_t cols, int64_t rows) {
@@ -383,9 +401,8 @@ ibmi_status mixed_sweep_step(ibmi_plan_s* P, int k, cudaStream_t st) {
     if (S == 2) IBMI_CUDA_TRY((tc::launch<2, MX_BN>(maps, t, ntn, (int)((m + 127) / 128), epi, st)));
     else IBMI_CUDA_TRY((tc::launch<3, MX_BN>(maps, t, ntn, (int)((m + 127) / 128), epi, st)));
     note_launch();
-    const unsigned nt = (unsigned)((m + 31) / 32);
-    k_mixed_sym<<<dim3(nt, nt), dim3(32, 8), 0, st>>>(M->Spart, splits, m, P->ainv[k], lo, M->ldp, M->Hf, M->Hs[0],
-                                                      M->Hs[1], S == 3 ? M->Hs[2] : nullptr);
+    k_mixed_sym<<<grid2(m, m), 256, 0, st>>>(M->Spart, splits, m, P->ainv[k], lo, M->ldp, M->Hf, M->Hs[0],
+                                             M->Hs[1], S == 3 ? M->Hs[2] : nullptr);
     IBMI_CUDA_TRY(cudaGetLastError());
   }
   return IBMI_OK;
@@ -500,6 +517,25 @@ ibmi_status mixed_run(ibmi_plan_s* P, const double* A, int64_t lda, double* H, i
     *flops += fr * (tail::pairs(qto, OZ_SX, OZ_SA) - tail::pairs(qfrom, OZ_SX, OZ_SA)) /
               tail::pairs(OZ_QMAX, OZ_SX, OZ_SA);
     return refine_read_groups(R, st, rho, g, amp);
+  };
+  // After an update from an exact residual (all groups, or a correction of
+  // one): the residual of the new iterate from the previous one,
+  // Q_X = Q_Xprev - (X - Xprev) A, with groups <= q of the digit products of
+  // the small difference X - Xprev (its rho and the norm of group q's part).
+  auto tail_correct = [&](int q, double* rho, double* g) -> ibmi_status {
+    IBMI_TRY(graph_or_run(M, &M->g_tail[ns_correct_key(q)], st,
+                          [&]() { return refine_residual_correct_launch(R, H, ldh, M->Xprev, st, q); }));
+    *flops += fr * tail::pairs(q, OZ_SX, OZ_SA) / tail::pairs(OZ_QMAX, OZ_SX, OZ_SA);
+    double unused;
+    return refine_read_groups(R, st, rho, g, &unused);
+  };
+  auto tail_correct_extend = [&](int qfrom, int qto, double* rho, double* g) -> ibmi_status {
+    IBMI_TRY(graph_or_run(M, &M->g_tail[ns_correct_extend_key(qfrom, qto)], st,
+                          [&]() { return refine_residual_correct_extend_launch(R, st, qfrom, qto); }));
+    *flops += fr * (tail::pairs(qto, OZ_SX, OZ_SA) - tail::pairs(qfrom, OZ_SX, OZ_SA)) /
+              tail::pairs(OZ_QMAX, OZ_SX, OZ_SA);
+    double unused;
+    return refine_read_groups(R, st, rho, g, &unused);
   };
   // Before a radius test: the first tail residual's groups (q_first) give Q
   // ample for the radius and, if the tail starts, for its first step
@@ -619,14 +655,32 @@ ibmi_status mixed_run(ibmi_plan_s* P, const double* A, int64_t lda, double* H, i
     double prev = INFINITY, prev_floor = 0.0;
     double gcal = NAN, acal = NAN;   // calibration: norm of the last group of the last residual,
     int qcal = -1;                   // that group and ||A||_F ||X||_F / p
+    bool exact = false;              // Q is exact for the iterate before the last update (planned tail)
+    double amp_x = NAN;              // ||A||_F ||X||_F / p of the last direct residual
     for (int s = 0;; ++s) {
-      double rho, g, amp;
+      double rho, g, amp = amp_x;
       int qc;
+      bool corrected = false;
       if (s == 0 && !isnan(pending)) {
         rho = pending;
         g = pending_g;
         amp = pending_amp;
         qc = pending_q;
+      } else if (s > 0 && planned && exact) {
+        // from the exact residual of the previous iterate: groups until the
+        // truncation is negligible against tol, for the value and for a step
+        // it may feed (the correction's parts fall by about 2^-7 a group)
+        qc = tail::kCorrectionGroups;
+        IBMI_TRY(tail_correct(qc, &rho, &g));
+        for (;;) {
+          const int qn = isfinite(rho) ? tail::residual_groups(tail::kExactFraction * d.tol, g, qc, amp, qc, OZ_QMAX)
+                                       : qc;
+          if (qn == qc) break;
+          IBMI_TRY(tail_correct_extend(qc, qn, &rho, &g));
+          qc = qn;
+        }
+        corrected = true;
+        exact = isfinite(rho) && tail::residual_floor(qc, g, qc, amp) <= tail::kExactFraction * d.tol;
       } else {
         // all groups where this residual is expected to certify tol; else
         // enough for the step it feeds, judged from the rho it should show
@@ -640,7 +694,7 @@ ibmi_status mixed_run(ibmi_plan_s* P, const double* A, int64_t lda, double* H, i
       }
       // a value at or below tol is certified with all groups; a step needs
       // the truncation error within its target (both extend the same residual)
-      for (;;) {
+      for (; !corrected;) {
         int qn = qc;
         if (rho <= d.tol || !isfinite(rho)) qn = isfinite(rho) ? OZ_QMAX : qc;
         else if (planned)
@@ -648,6 +702,10 @@ ibmi_status mixed_run(ibmi_plan_s* P, const double* A, int64_t lda, double* H, i
         if (qn == qc) break;
         IBMI_TRY(tail_extend(qc, qn, &rho, &g, &amp));
         qc = qn;
+      }
+      if (!corrected) {
+        exact = planned && qc == OZ_QMAX;
+        amp_x = amp;
       }
       // the last update did not reduce the residual (or overflowed)
       const bool worse = s > 0 && !(rho < prev);
@@ -665,16 +723,18 @@ ibmi_status mixed_run(ibmi_plan_s* P, const double* A, int64_t lda, double* H, i
         if (worse) IBMI_TRY(copy_square(H, ldh, M->Xprev, p, p, st));
         return IBMI_NOT_CONVERGED;
       }
-      gcal = g;
-      acal = amp;
-      qcal = qc;
+      if (!corrected) {   // the calibration of the direct residuals
+        gcal = g;
+        acal = amp;
+        qcal = qc;
+      }
       // the update keeps 10 of its 15 pair products where their error fits
       // the same target as the residual's (planned tail only)
       const int qu = planned ? tail::update_groups(rho, amp, d.tol, NS_S - 1) : NS_S - 1;
       prev_floor = planned ? tail::residual_floor(qc, g, qc, amp) + tail::update_floor(qu, rho, amp) : 0.0;
       prev = rho;
-      IBMI_TRY(graph_or_run(M, &M->g_update[qu == NS_S - 1 ? 0 : 1], st,
-                            [&]() { return refine_ns_update(R, H, ldh, st, qu, M->Xprev); }));
+      IBMI_TRY(graph_or_run(M, &M->g_update[(qu == NS_S - 1 ? 0 : 1) + (corrected ? 2 : 0)], st,
+                            [&]() { return refine_ns_update(R, H, ldh, st, qu, M->Xprev, corrected); }));
       *flops += fr * tail::pairs(qu, NS_S, NS_S) / tail::pairs(NS_S - 1, NS_S, NS_S);
       res->ns_steps = s + 1;
     }

@@ -132,15 +132,15 @@ __device__ __forceinline__ double pow2i(int k) {
   return __longlong_as_double((long long)(k + 1023) << 52);
 }
 
-// 2^e * sum_{q <= qmax} T_q 2^{-7q} for the int32 group sums at `idx` of
-// planes `plane` apart.  The sum is formed exactly in two int64 halves
-// (groups 0..4 and 5..qmax, each below 2^59), so only the final conversion and
-// scaling round.
-__device__ __forceinline__ double oz_value(const int* T, int64_t plane, int64_t idx, int qmax, int e) {
+// 2^e * sum_{qmin <= q <= qmax} T_q 2^{-7q} for the int32 group sums at
+// `idx` of planes `plane` apart.  The sum is formed exactly in two int64
+// halves (groups 0..4 and 5..qmax, each below 2^59), so only the final
+// conversion and scaling round.
+__device__ __forceinline__ double oz_value(const int* T, int64_t plane, int64_t idx, int qmax, int e, int qmin = 0) {
   // all group loads issued together (predicated, no early exit)
   int t[10];
 #pragma unroll
-  for (int q = 0; q < 10; ++q) t[q] = q <= qmax ? T[(int64_t)q * plane + idx] : 0;
+  for (int q = 0; q < 10; ++q) t[q] = (q >= qmin && q <= qmax) ? T[(int64_t)q * plane + idx] : 0;
   long long hi = 0, lo = 0;
 #pragma unroll
   for (int q = 0; q < 10; ++q) {
@@ -163,45 +163,6 @@ __device__ __forceinline__ void split3(float x, __nv_bfloat16& a, __nv_bfloat16&
   const float r = x - __bfloat162float(a);
   b = __float2bfloat16_rn(r);
   c = __float2bfloat16_rn(r - __bfloat162float(b));
-}
-
-// a4 finish of one 32 x 32 tile of H[I, I] (block (32, 8) threads): P is the
-// sum of the split-K partials S[z] (m x m, row-major), computed on and below
-// the diagonal only, so element (i, j) is read at (max, min) -- a tile above
-// the diagonal reads its mirror tile row-wise and transposes it in shared
-// memory; x = A_I^{-1}[i, j] - P[i, j] goes to the FP32 master Hf and the
-// BF16 slices at o(i, j) = o0 + i ldp + j (s2 optional).
-__device__ __forceinline__ void sym_tile_finish(const float* S, int splits, int64_t m, const double* Ainv,
-                                                int64_t I0, int64_t J0, float* Hf, __nv_bfloat16* s0,
-                                                __nv_bfloat16* s1, __nv_bfloat16* s2, int64_t o0, int64_t ldp) {
-  __shared__ float t[32][33];
-  const bool upper = J0 > I0;
-  const int64_t R0 = upper ? J0 : I0, C0 = upper ? I0 : J0;   // source tile, on or below the diagonal
-  const int tx = threadIdx.x;
-  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-    const int64_t i = R0 + r, j = C0 + tx;
-    float a = 0.f;
-    if (i < m && j < m)
-      for (int z = 0; z < splits; ++z) a += S[(int64_t)z * m * m + i * m + j];
-    t[r][tx] = a;
-  }
-  __syncthreads();
-  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-    const int64_t i = I0 + r, j = J0 + tx;
-    if (i >= m || j >= m) continue;
-    float a;
-    if (upper) a = t[tx][r];
-    else if (I0 > J0) a = t[r][tx];
-    else a = r >= tx ? t[r][tx] : t[tx][r];   // diagonal tile
-    const float x = (float)(Ainv[i * m + j] - (double)a);
-    const int64_t o = o0 + i * ldp + j;
-    Hf[o] = x;
-    __nv_bfloat16 h0, h1, h2;
-    split3(x, h0, h1, h2);
-    s0[o] = h0;
-    s1[o] = h1;
-    if (s2) s2[o] = h2;
-  }
 }
 
 }  // namespace ibmi

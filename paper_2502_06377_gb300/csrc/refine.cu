@@ -110,24 +110,26 @@ struct EpiResidSq {
 
 // ------------------------------------------------------------ combine ----
 
-// C = 2^{e_i + f_j - 12} sum_q T_q 2^{-7q};  Q = I - C (FP64, ld p);
-// sum Q^2 per CTA, and (second half of `partials`) the sum of squares of the
-// last group's part 2^{e_i + f_j - 12 - 7 qmax} T_qmax, whose norm scales the
-// truncation error of the groups left out.
-__global__ void k_oz_combine(const int* T, int64_t p, int64_t ldp, const int* ex, const int* ea, int qmax,
-                             double* Q, double* partials) {
+// C = 2^{e_i + f_j - 12} sum_{qmin <= q <= qmax} T_q 2^{-7q};  Q = I - C, or
+// with `sub` Q = Q - C in place (FP64, ld p); sum Q^2 per CTA, and (second
+// half of `partials`) the sum of squares of the last group's part
+// 2^{e_i + f_j - 12 - 7 qmax} T_qmax, whose norm scales the truncation error
+// of the groups left out.
+__global__ void k_oz_combine(const int* T, int64_t p, int64_t ldp, const int* ex, const int* ea, int qmin, int qmax,
+                             int sub, double* Q, double* partials) {
   const int64_t i = blockIdx.y, j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   float sq = 0.f, gq = 0.f;
   if (j < p) {
     const int e = ex[i] + ea[j] - 12;
-    const double c = oz_value(T, p * ldp, i * ldp + j, qmax, e);
+    const double c = oz_value(T, p * ldp, i * ldp + j, qmax, e, qmin);
     // float is ample for a norm estimate: parts below ~1e-19 underflow to 0
     // (far below any tolerance) and an overflow reads as an infinite norm
     const float g = ldexpf((float)T[(int64_t)qmax * p * ldp + i * ldp + j], e - 7 * qmax);
     gq = g * g;
     // off the diagonal Q = -c is a sign flip; the squares for rho need only
     // float precision (FP64 arithmetic is scarce on this GPU)
-    const double q = i == j ? 1.0 - c : ozr_bits_to_double(ozr_double_to_bits(c) ^ 0x8000000000000000ull);
+    const double q = sub ? Q[i * p + j] - c
+                         : (i == j ? 1.0 - c : ozr_bits_to_double(ozr_double_to_bits(c) ^ 0x8000000000000000ull));
     const float qf = ozr_to_float(q);
     sq = qf * qf;
     Q[i * p + j] = q;
@@ -220,6 +222,12 @@ __global__ void k_sum_partials(const double* partials, int64_t n, int64_t p, dou
     sa = block_sum_f(sa, redf);
     if (threadIdx.x == 0) out[2] = ldexp(sqrt((double)sx) * sqrt((double)sa), mx + ma) / (double)p;
   }
+}
+
+// D = X - Xprev (X row pitch ldx; Xprev and D row pitch p).
+__global__ void k_diff(const double* X, int64_t ldx, const double* Xprev, int64_t p, double* D) {
+  const int64_t i = blockIdx.y, j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < p) D[i * p + j] = X[i * ldx + j] - Xprev[i * p + j];
 }
 
 // Newton-Schulz update: Xn = X + 2^{e_i + g_j - 12} sum_{q <= qmax} T_q 2^{-7q}.
@@ -331,7 +339,7 @@ ibmi_status refine_create(RefineState* R, int64_t p, int* err) {
   const int64_t tiles = ((p + 127) / 128) * ((p + RF_BN - 1) / RF_BN);
   R->n_partials = std::max<int64_t>(tiles * 4, 2 * p * ((p + 255) / 256)) + 8;
   size_t bytes = plane16 * (OZ_SA + OZ_SX + NS_S + 2) + sizeof(int) * (size_t)(OZ_QMAX + 1) * p * ldp +
-                 sizeof(double) * p * p + sizeof(double) * R->n_partials + 3 * sizeof(int) * p +
+                 2 * sizeof(double) * p * p + sizeof(double) * R->n_partials + 3 * sizeof(int) * p +
                  sizeof(double) * (2 * p + 8) + 2 * sizeof(float) * p + 64 * 256;
   if (cudaMalloc(&R->pool, bytes) != cudaSuccess) {
     cudaGetLastError();
@@ -345,6 +353,7 @@ ibmi_status refine_create(RefineState* R, int64_t p, int* err) {
   for (int s = 0; s < 2; ++s) R->Af[s] = (__nv_bfloat16*)take(plane16);
   R->T = (int*)take(sizeof(int) * (size_t)(OZ_QMAX + 1) * p * ldp);
   R->Xn = (double*)take(sizeof(double) * p * p);
+  R->Q = (double*)take(sizeof(double) * p * p);
   R->partials = (double*)take(sizeof(double) * R->n_partials);
   R->dout = (double*)take(256);
   R->expA = (int*)take(sizeof(int) * p);
@@ -667,7 +676,7 @@ ibmi_status refine_q_radius_launch(RefineState* R, int iters, cudaStream_t st) {
   k_q_normalize<<<1, 1024, 0, st>>>(y, p, v, est, 1);
   for (int it = 0; it < iters; ++it) {
     note_launch(2);
-    k_q_gemv<<<(unsigned)((p + 7) / 8), 256, 0, st>>>(R->Xn, p, v, y);
+    k_q_gemv<<<(unsigned)((p + 7) / 8), 256, 0, st>>>(R->Q, p, v, y);
     k_q_normalize<<<1, 1024, 0, st>>>(y, p, v, est, 0);
   }
   IBMI_CUDA_TRY(cudaGetLastError());
@@ -742,23 +751,26 @@ ibmi_status refine_residual(RefineState* R, const double* X, int64_t ldx, cudaSt
   return read_scalar(R, st, rho);
 }
 
-// Q = I - X A from the group sums q <= qmax and ||Q||_F / sqrt(p) into
-// dout[0]; with `stats`, the norm of group qmax's part and ||X||_F ||A||_F / p
-// into dout[1..2] (the row sums of the last slicing of X).
-static ibmi_status combine_residual(RefineState* R, int qmax, bool stats, cudaStream_t st) {
+// Q = I - X A from the group sums q <= qmax (or, with `sub`, Q -= the part
+// of groups qmin..qmax of the product in the planes) and ||Q||_F / sqrt(p)
+// into dout[0]; with `nout` = 2 also the norm of group qmax's part into
+// dout[1], with `stats` besides ||X||_F ||A||_F / p into dout[2] (the row
+// sums of the last slicing of X).
+static ibmi_status combine_residual(RefineState* R, int qmin, int qmax, bool sub, int nout, bool stats,
+                                    cudaStream_t st) {
   const int64_t p = R->p, ldp = R->ldp;
   ProfScope ps(IBMI_K_OTHER, st, 0.0);
   const dim3 gc = grid2(p, p);
   const int64_t nb = (int64_t)gc.x * gc.y;
   if (2 * nb > R->n_partials) return IBMI_ERR_INVALID_ARG;
   note_launch();
-  k_oz_combine<<<gc, 256, 0, st>>>(R->T, p, ldp, R->expX, R->expA, qmax, R->Xn, R->partials);
+  k_oz_combine<<<gc, 256, 0, st>>>(R->T, p, ldp, R->expX, R->expA, qmin, qmax, sub ? 1 : 0, R->Q, R->partials);
   IBMI_CUDA_TRY(cudaGetLastError());
   note_launch();
   if (stats)
     k_sum_partials<<<1, 1024, 0, st>>>(R->partials, nb, p, R->dout, 2, R->sqX, R->expX, R->sqA, R->expA);
   else
-    k_sum_partials<<<1, 1024, 0, st>>>(R->partials, nb, p, R->dout);
+    k_sum_partials<<<1, 1024, 0, st>>>(R->partials, nb, p, R->dout, nout);
   IBMI_CUDA_TRY(cudaGetLastError());
   return IBMI_OK;
 }
@@ -773,7 +785,7 @@ ibmi_status refine_residual_launch(RefineState* R, const double* X, int64_t ldx,
     IBMI_TRY(slice_digits(R, X, ldx, R->Xo, nsx, R->expX, st, -1, -1, 0, stats ? R->sqX : nullptr));
   }
   IBMI_TRY(pair_products(R, R->mXo, nsx, R->mAo, OZ_SA, qmax, IBMI_K_RESIDUAL, st));
-  return combine_residual(R, qmax, stats, st);
+  return combine_residual(R, 0, qmax, false, 1, stats, st);
 }
 
 ibmi_status refine_residual_extend_launch(RefineState* R, const double* X, int64_t ldx, cudaStream_t st, int qfrom,
@@ -785,15 +797,43 @@ ibmi_status refine_residual_extend_launch(RefineState* R, const double* X, int64
     IBMI_TRY(slice_digits(R, X, ldx, R->Xo, nsx, R->expX, st));
   }
   IBMI_TRY(pair_products(R, R->mXo, nsx, R->mAo, OZ_SA, qto, IBMI_K_RESIDUAL, st, qfrom + 1));
-  return combine_residual(R, qto, stats, st);
+  return combine_residual(R, 0, qto, false, 1, stats, st);
 }
 
-ibmi_status refine_ns_update(RefineState* R, double* X, int64_t ldx, cudaStream_t st, int qmax, double* backup) {
+ibmi_status refine_residual_correct_launch(RefineState* R, const double* X, int64_t ldx, const double* Xprev,
+                                           cudaStream_t st, int qmax) {
+  const int64_t p = R->p;
+  if (qmax < 0 || qmax > OZ_QMAX) return IBMI_ERR_INVALID_ARG;
+  {
+    ProfScope ps(IBMI_K_OTHER, st, 0.0);
+    note_launch();
+    k_diff<<<grid2(p, p), 256, 0, st>>>(X, ldx, Xprev, p, R->Xn);
+    IBMI_CUDA_TRY(cudaGetLastError());
+    IBMI_TRY(slice_digits(R, R->Xn, p, R->Xo, std::min(OZ_SX, qmax + 1), R->expX, st));
+  }
+  IBMI_TRY(pair_products(R, R->mXo, std::min(OZ_SX, qmax + 1), R->mAo, OZ_SA, qmax, IBMI_K_RESIDUAL, st));
+  return combine_residual(R, 0, qmax, true, 2, false, st);
+}
+
+ibmi_status refine_residual_correct_extend_launch(RefineState* R, cudaStream_t st, int qfrom, int qto) {
+  if (qfrom < 0 || qto <= qfrom || qto > OZ_QMAX) return IBMI_ERR_INVALID_ARG;
+  const int nsx_from = std::min(OZ_SX, qfrom + 1), nsx = std::min(OZ_SX, qto + 1);
+  if (nsx > nsx_from) {   // D is still in the scratch; its first digits come out the same
+    ProfScope ps(IBMI_K_OTHER, st, 0.0);
+    IBMI_TRY(slice_digits(R, R->Xn, R->p, R->Xo, nsx, R->expX, st));
+  }
+  IBMI_TRY(pair_products(R, R->mXo, nsx, R->mAo, OZ_SA, qto, IBMI_K_RESIDUAL, st, qfrom + 1));
+  return combine_residual(R, qfrom + 1, qto, true, 2, false, st);
+}
+
+ibmi_status refine_ns_update(RefineState* R, double* X, int64_t ldx, cudaStream_t st, int qmax, double* backup,
+                             bool reslice_x) {
   const int64_t p = R->p, ldp = R->ldp;
   if (qmax < 0 || qmax > NS_S - 1) return IBMI_ERR_INVALID_ARG;
   {
     ProfScope ps(IBMI_K_OTHER, st, 0.0);
-    IBMI_TRY(slice_digits(R, R->Xn, p, R->Qo, NS_S, R->expQ, st));
+    if (reslice_x) IBMI_TRY(slice_digits(R, X, ldx, R->Xo, NS_S, R->expX, st));
+    IBMI_TRY(slice_digits(R, R->Q, p, R->Qo, NS_S, R->expQ, st));
   }
   IBMI_TRY(pair_products(R, R->mXo, NS_S, R->mQo, NS_S, qmax, IBMI_K_NS, st));
   ProfScope ps(IBMI_K_OTHER, st, 0.0);

@@ -38,7 +38,8 @@ struct RefineState {
   int* T = nullptr;               // (OZ_QMAX+1) x p x ldp int32 group sums
   __nv_bfloat16* Qo[NS_S] = {};   // leading digit slices of Q = I - X A
   __nv_bfloat16* Af[2] = {};      // BF16 hi/lo of A (cheap residual)
-  double* Xn = nullptr;           // p x p FP64: Q after a residual, then X + X Q^T
+  double* Xn = nullptr;           // p x p FP64 scratch: X + X Q^T of an update, X - Xprev of a correction
+  double* Q = nullptr;            // p x p FP64: Q = I - X A of the last residual
   double* partials = nullptr;     // reduction partials
   int64_t n_partials = 0;
   double* dout = nullptr;         // device scalars
@@ -75,10 +76,11 @@ ibmi_status refine_residual(RefineState* R, const double* X, int64_t ldx, cudaSt
 // product X Q^T uses the five leading digits of X and of Q, digit groups
 // <= qmax of their exact pair products (qmax = 4: all 15 pairs, 2^-34
 // relative truncation; 3: 10 pairs), so its error stays proportional to Q.
-// Must follow refine_residual on the same X.  backup (p x p, row pitch p),
-// if given, receives X before the update.
+// Must follow a residual of the same X: a direct one leaves the digits of X
+// the update uses, after a correction (below) reslice_x slices them first.
+// backup (p x p, row pitch p), if given, receives X before the update.
 ibmi_status refine_ns_update(RefineState* R, double* X, int64_t ldx, cudaStream_t st, int qmax = NS_S - 1,
-                             double* backup = nullptr);
+                             double* backup = nullptr, bool reslice_x = false);
 
 // W = A_I^{-1} A_{I,:} (m x p, zero columns on I) from exact digit products
 // (five digits of A_I^{-1}, four of A), written as three BF16 slices with
@@ -126,6 +128,18 @@ ibmi_status refine_residual_launch(RefineState* R, const double* X, int64_t ldx,
 // stats needs the last full slicing of X to have been made with stats.
 ibmi_status refine_residual_extend_launch(RefineState* R, const double* X, int64_t ldx, cudaStream_t st, int qfrom,
                                           int qto, bool stats = false);
+// The residual of X from that of the previous iterate Xprev (p x p, row
+// pitch p), Q_X = Q_Xprev - (X - Xprev) A, by the same exact digit products
+// applied to the difference D = X - Xprev (groups <= qmax, qmax + 1 digits of
+// D): since D is small, few groups give Q_X to the accuracy of a full direct
+// residual.  Q must hold Q_Xprev; rho and the norm of the last group's part
+// of D A go to the values refine_read_groups returns (the third one is left
+// as it was).  The digits of X are not sliced (see refine_ns_update).
+ibmi_status refine_residual_correct_launch(RefineState* R, const double* X, int64_t ldx, const double* Xprev,
+                                           cudaStream_t st, int qmax);
+// Extends the last correction from groups <= qfrom to <= qto (only the new
+// groups' pair products, subtracted from Q).
+ibmi_status refine_residual_correct_extend_launch(RefineState* R, cudaStream_t st, int qfrom, int qto);
 // rho of the last digit-sliced residual, the norm (/ sqrt(p)) of its last
 // digit group's part (the groups left out fall below it by about 2^-7 each)
 // and ||X||_F ||A||_F / p (the last two from a residual launched with stats).

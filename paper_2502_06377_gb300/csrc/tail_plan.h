@@ -19,6 +19,8 @@ namespace ibmi {
 namespace tail {
 
 constexpr double kGrowth = 16.0;         // pessimistic rho_{k+1} / rho_k^2 of a step
+constexpr int kCorrectionGroups = 5;     // digit groups of a first correction Q - (X - Xprev) A (21 pairs)
+constexpr double kExactFraction = 1e-2;  // a correction counts as exact while its floor is below this share of tol
 constexpr double kUpdateFloor = 512.0;   // update error constant (measured 75..260, doubled)
 
 // pair products (s, u), s < sx digits of X and u < sa of the other operand,
