@@ -18,8 +18,8 @@ own clock record:
   c4    512 squared-exponential matrices of order 64..1024 through the
         batched entry point, mixed precision, and mixed vs plain FP64 on a
         64-matrix sample of the batch;
-  c5    Poisson request traces into the continuous-batching server at two
-        offered rates (the 2000 requests/s of the workload and one below
+  c5    Poisson request traces into the continuous-batching server at three
+        offered rates (the 2000 requests/s of the workload and two below
         saturation), p50/p99 latency and drained throughput, and a sample of
         the same requests served in FP64.
 
@@ -75,7 +75,7 @@ def parse():
                          "headline alone; c3 / batch / serve: one of the other workloads alone")
     ap.add_argument("--batch-n", type=int, default=512)
     ap.add_argument("--serve-seconds", type=float, default=0.25)
-    ap.add_argument("--serve-rates", default="2000,60",
+    ap.add_argument("--serve-rates", default="2000,120,60",
                     help="offered request rates (per second) of the served traces")
     return ap.parse_args()
 

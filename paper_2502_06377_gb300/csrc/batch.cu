@@ -282,6 +282,7 @@ struct Request {
   std::vector<double> H;     // host result
   ibmi_result res{};
   int state = 0;             // 0 queued, 1 admitted, 2 done, 3 cancelled
+  int home = 0;              // worker that holds the plans of its size bucket
   size_t bytes = 0;          // device bytes charged while admitted
   std::chrono::steady_clock::time_point t_submit, t_admit, t_done;
 };
@@ -305,6 +306,7 @@ struct ibmi_server_impl {
   int64_t completed = 0;
   std::vector<std::thread> threads;
   std::vector<ibmi::Worker> workers;
+  std::vector<char> busy;            // per worker: running a batch (guarded by mu)
 };
 
 namespace ibmi {
@@ -316,6 +318,13 @@ static size_t request_bytes(int64_t p) {
 }
 
 static constexpr int kServeGroupMax = 8;   // requests one device group of the server takes
+
+// Home worker of a request: the plans and device groups a worker caches are
+// those of the size buckets it ran, so a request goes to the worker of its
+// bucket while that worker is free; a busy home lets any free worker take it.
+static int home_worker(int64_t p, int workers) {
+  return (int)(((uint64_t)bucket_of(p) * 0x9E3779B97F4A7C15ull >> 32) % (uint64_t)workers);
+}
 
 static bool same_shape(const Shape& a, const Shape& b) { return !(a < b) && !(b < a); }
 
@@ -333,7 +342,8 @@ static void server_loop(ibmi_server_impl* S, int wi) {
   std::vector<int64_t> dcap;
   const size_t cache_cap = (S->budget - S->req_budget) / S->workers.size();
   auto fits = [&](const std::shared_ptr<Request>& q) {
-    return q->state == 0 && (S->in_use + q->bytes <= S->req_budget || S->in_use == 0);
+    return q->state == 0 && (q->home == wi || S->busy[q->home]) &&
+           (S->in_use + q->bytes <= S->req_budget || S->in_use == 0);
   };
   while (true) {
     std::vector<std::shared_ptr<Request>> batch;
@@ -365,6 +375,7 @@ static void server_loop(ibmi_server_impl* S, int wi) {
         batch.push_back(q);
       };
       admit(r);
+      S->busy[wi] = 1;
       grouped = S->opts.precision == IBMI_MIXED && S->opts.device_batch && bucket_of(r->p) <= kDevMaxOrder;
       if (grouped) {
         sh = shape_for(r->p, S->opts);
@@ -475,6 +486,7 @@ static void server_loop(ibmi_server_impl* S, int wi) {
         S->t_last_done = r.t_done;
         ++S->completed;
       }
+      S->busy[wi] = 0;
     }
     S->cv.notify_all();
   }
@@ -708,6 +720,7 @@ ibmi_status ibmi_serve_create(size_t hbm_budget, const ibmi_batch_opts* opts, ib
   S->req_budget = hbm_budget / 4;
   cudaGetDevice(&S->device);
   S->workers.resize(S->opts.workers);
+  S->busy.assign(S->opts.workers, 0);
   for (auto& w : S->workers) {
     if (w.init(S->device) != IBMI_OK) {
       for (auto& x : S->workers) x.destroy();
@@ -728,6 +741,7 @@ ibmi_status ibmi_serve_submit(ibmi_server_t h, const double* A_host, int64_t p, 
   r->p = p;
   r->tol = tol;
   r->bytes = request_bytes(p);
+  r->home = home_worker(p, (int)S->workers.size());
   if (r->bytes > S->req_budget) return IBMI_ERR_BUDGET;
   r->A.resize((size_t)p * p);
   for (int64_t i = 0; i < p; ++i) memcpy(&r->A[(size_t)i * p], A_host + i * lda, sizeof(double) * p);
