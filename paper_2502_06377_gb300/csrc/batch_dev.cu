@@ -6,7 +6,8 @@
 // output tiles of all of them through 3-D tensor maps whose third coordinate
 // is the matrix, the elementwise kernels take the matrix from blockIdx.z.
 // Each matrix keeps its own decisions (its sweep count, slice level, hand-over,
-// digit groups of each tail residual), so its arithmetic is exactly what it
+// digit groups of each tail residual, a residual after an exact one taken as
+// its correction Q - (X - Xprev) A), so its arithmetic is exactly what it
 // would be in a group of one; matrices that take different decisions are
 // covered by different launches of the same round.  The host synchronises
 // once per round of the group (one sweep and its stop test for the sweeping
@@ -34,6 +35,16 @@ namespace {
 constexpr int kBN = 128;              // N tile of the sweep products and the BF16x3 stop test
 constexpr int kFirstGroups = 7;       // digit groups of the first tail residual (orders below 2048)
 constexpr int kNextGroups = 8;        // ... and of the next ones while rho^2 > 1e3 tol
+// digit groups of a correction Q - (X - Xprev) A after an exact residual of
+// rho: the fewest (at least 5) whose truncation, about rho 2^(-7 (q + 1)) a c
+// with a = ||A|| ||X|| / p up to 1e4 and c up to ~300 (the row-scaling
+// constant measured for the update's product), is below 1% of tol (for
+// tol = 1e-10: 5 groups, 21 pairs, up to rho = 1e-6; 6 up to 1e-4)
+inline int corr_groups(double rho, double tol) {
+  int q = 5;
+  while (q < OZ_QMAX && rho * std::ldexp(1.0, -7 * (q + 1)) * 3e6 > 1e-2 * tol) ++q;
+  return q;
+}
 constexpr int kWDigitsA = 5, kWDigitsB = 4, kWGroups = 4;   // W = A_I^{-1} A_{I,:}: 34-bit x 27-bit digits
 
 __device__ __forceinline__ int pick(const int* sel, int i) { return sel ? sel[i] : i; }
@@ -271,19 +282,24 @@ __global__ void k_b_export(const int* sel, int64_t pb, int64_t ldp, const float*
   X64[(b * pb + i) * pb + j] = (double)Hf[(b * pb + i) * ldp + j];
 }
 
-// Q = I - 2^{e_i + f_j - 12} sum_{q <= qm[z]} T_q 2^{-7q} of matrix sel[z]
-// (FP64, pb x pb) and per-CTA sums of Q^2.
+// Q = I - C with C = 2^{e_i + f_j - 12} sum_{q <= qm[z]} T_q 2^{-7q} of
+// matrix sel[z] (FP64, pb x pb), or with sub[z] (a correction) Q = Q - C in
+// place; and per-CTA sums of Q^2.
 __global__ void k_b_combine(const int* sel, const int* T, int64_t plane, int64_t pb, int64_t ldp, const int* ex,
-                            const int* ea, const int* qm, double* Q, double* partials, int64_t nparts) {
+                            const int* ea, const int* qm, const int* sub, double* Q, double* partials,
+                            int64_t nparts) {
   const int64_t b = pick(sel, blockIdx.z), i = blockIdx.y, j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int qmax = qm[blockIdx.z];   // highest digit group of this matrix's residual
+  const bool corr = sub[blockIdx.z] != 0;
   float sq = 0.f;
   if (j < pb) {
+    const int64_t o = (b * pb + i) * pb + j;
     const double c = oz_value(T + b * pb * ldp, plane, i * ldp + j, qmax, ex[b * pb + i] + ea[b * pb + j] - 12);
-    const double q = i == j ? 1.0 - c : ozr_bits_to_double(ozr_double_to_bits(c) ^ 0x8000000000000000ull);
+    const double q = corr ? Q[o] - c
+                          : (i == j ? 1.0 - c : ozr_bits_to_double(ozr_double_to_bits(c) ^ 0x8000000000000000ull));
     const float qf = ozr_to_float(q);
     sq = qf * qf;
-    Q[(b * pb + i) * pb + j] = q;
+    Q[o] = q;
   }
   __shared__ double red[8];
   for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
@@ -296,33 +312,50 @@ __global__ void k_b_combine(const int* sel, const int* T, int64_t plane, int64_t
   }
 }
 
-// Newton-Schulz update of matrix sel[z]: Xn = X + 2^{e_i + g_j - 12} sum T_q
-// 2^{-7q} (into Q, whose digits are taken), and Xprev = X.
+// Newton-Schulz update of matrix sel[z] in place: X = X + 2^{e_i + g_j - 12}
+// sum T_q 2^{-7q} (unsymmetrised; Q, whose digits were taken, stays), and
+// Xprev = X before it.
 __global__ void k_b_update(const int* sel, const int* T, int64_t plane, int64_t pb, int64_t ldp, const int* ex,
-                           const int* eq, int qmax, const double* X64, double* Xn, double* Xprev) {
+                           const int* eq, int qmax, double* X64, double* Xprev) {
   const int64_t b = pick(sel, blockIdx.z), i = blockIdx.y, j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= pb) return;
   const int64_t o = (b * pb + i) * pb + j;
   const double x = X64[o];
   Xprev[o] = x;
-  Xn[o] = x + oz_value(T + b * pb * ldp, plane, i * ldp + j, qmax, ex[b * pb + i] + eq[b * pb + j] - 12);
+  X64[o] = x + oz_value(T + b * pb * ldp, plane, i * ldp + j, qmax, ex[b * pb + i] + eq[b * pb + j] - 12);
 }
 
-// X64[b] = (Xn + Xn^T) / 2 by 32 x 32 tiles.
-__global__ void k_b_symfull(const int* sel, int64_t pb, const double* Xn, double* X64) {
+// X64[b] <- (X64 + X64^T) / 2 in place, one block per pair of mirror 32 x 32
+// tiles (I >= J; the block reads both before writing either), and
+// D[b] <- X64_new - D[b] with D holding the iterate before the update: the
+// step's difference, which a correction of the residual slices.
+__global__ void k_b_symfull(const int* sel, int64_t pb, double* X64, double* D) {
+  if (blockIdx.x > blockIdx.y) return;
   __shared__ double a[32][33], c[32][33];
   const int64_t b = pick(sel, blockIdx.z);
-  const double* S = Xn + b * pb * pb;
-  double* D = X64 + b * pb * pb;
+  double* X = X64 + b * pb * pb;
+  double* Dm = D + b * pb * pb;
   const int64_t I0 = (int64_t)(blockIdx.y) * 32, J0 = (int64_t)blockIdx.x * 32;
   const int tx = threadIdx.x;
   for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-    a[r][tx] = (I0 + r < pb && J0 + tx < pb) ? S[(I0 + r) * pb + J0 + tx] : 0.0;
-    c[r][tx] = (J0 + r < pb && I0 + tx < pb) ? S[(J0 + r) * pb + I0 + tx] : 0.0;
+    a[r][tx] = (I0 + r < pb && J0 + tx < pb) ? X[(I0 + r) * pb + J0 + tx] : 0.0;
+    c[r][tx] = (J0 + r < pb && I0 + tx < pb) ? X[(J0 + r) * pb + I0 + tx] : 0.0;
   }
   __syncthreads();
-  for (int r = threadIdx.y; r < 32; r += blockDim.y)
-    if (I0 + r < pb && J0 + tx < pb) D[(I0 + r) * pb + J0 + tx] = 0.5 * (a[r][tx] + c[tx][r]);
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    if (I0 + r < pb && J0 + tx < pb) {
+      const int64_t o = (I0 + r) * pb + J0 + tx;
+      const double v = 0.5 * (a[r][tx] + c[tx][r]);
+      Dm[o] = v - Dm[o];
+      X[o] = v;
+    }
+    if (I0 != J0 && J0 + r < pb && I0 + tx < pb) {
+      const int64_t o = (J0 + r) * pb + I0 + tx;
+      const double v = 0.5 * (c[r][tx] + a[tx][r]);
+      Dm[o] = v - Dm[o];
+      X[o] = v;
+    }
+  }
 }
 
 // N tile of the digit-pair launches, as in the single-matrix path (64-wide
@@ -591,6 +624,9 @@ struct MState {
   int level = 0, r = 0, stalled = 0, s = 0, qc = 0;
   double best = INFINITY, last_cheap = INFINITY, handover_below = INFINITY, handover_rho = 0.0, prev = INFINITY;
   bool early = false, reslice = false, restore = false;
+  bool exact = false;     // the last residual is exact (all groups, or a correction of an exact one)
+  bool corr = false;      // this round's residual is a correction of the last one
+  bool xo_delta = false;  // the X digit planes hold the last correction's difference, not X
   bool waiting = false;   // ready for a tail action, held back to share its launches
   TailAct act = T_NONE;
   int next_q = 0;   // groups of the residual this round's tail action computes
@@ -743,8 +779,8 @@ ibmi_status DevGroup::run(const BatchMat* mats, int nrun, const ibmi_batch_opts&
     if (nwait >= std::max(1, nsweep))
       for (int b = 0; b < n; ++b) ms[b].waiting = false;
     // selection lists of this round
-    std::vector<int> L[2], Lres, Lsw, Lexp, Lupd, Lrs;
-    std::vector<int> qlo, qhi;   // digit-group range of each residual (positions of Lrs)
+    std::vector<int> L[2], Lres, Lsw, Lexp, Lupd, Lrx, Lrs, Ldir, Lcor;
+    std::vector<int> qlo, qhi, csub;   // digit-group range and correction flag of each residual (positions of Lrs)
     for (int b = 0; b < n; ++b) {
       MState& m = ms[b];
       if (m.phase == SWEEP) {
@@ -754,7 +790,11 @@ ibmi_status DevGroup::run(const BatchMat* mats, int nrun, const ibmi_batch_opts&
       } else if (m.phase == TAIL && !m.waiting) {
         if (m.act == T_ENTER || m.act == T_CERTIFY) Lexp.push_back(b);
         if (m.act == T_STEP) Lupd.push_back(b);
+        if (m.act == T_STEP && m.xo_delta) Lrx.push_back(b);
+        const bool corr = m.act == T_STEP && m.corr;
         Lrs.push_back(b);
+        (corr ? Lcor : Ldir).push_back(b);
+        csub.push_back(corr ? 1 : 0);
         qlo.push_back(m.act == T_EXTEND ? m.qc + 1 : 0);
         qhi.push_back(m.act == T_EXTEND ? OZ_QMAX : m.next_q);
       }
@@ -775,8 +815,12 @@ ibmi_status DevGroup::run(const BatchMat* mats, int nrun, const ibmi_batch_opts&
     int* dLsw = put(Lsw);
     int* dLexp = put(Lexp);
     int* dLupd = put(Lupd);
+    int* dLrx = put(Lrx);
     int* dLrs = put(Lrs);
+    int* dLdir = put(Ldir);
+    int* dLcor = put(Lcor);
     int* dqm = put(qhi);
+    int* dcsub = put(csub);
     std::vector<int> qr2;
     for (size_t i = 0; i < qlo.size(); ++i) {
       qr2.push_back(qlo[i]);
@@ -927,19 +971,23 @@ ibmi_status DevGroup::run(const BatchMat* mats, int nrun, const ibmi_batch_opts&
     };
     if (!Lupd.empty()) {  // X <- sym(X + X Q^T) from the last residual's digits of X and Q
       const int nl = (int)Lupd.size();
+      // after a correction the X planes hold its difference: the digits of X first
+      if (!Lrx.empty()) IBMI_CUDA_TRY(slice(g.X64, g.Xo, NS_S, g.expX, dLrx, (int)Lrx.size()));
       IBMI_CUDA_TRY(slice(g.Q, g.Qo, NS_S, g.expQ, dLupd, nl));
       IBMI_TRY(pairs(g.mXo, NS_S, g.mQo, NS_S, 0, NS_S - 1, dLupd, nl, IBMI_K_NS, nl * fr, nullptr));
       ProfScope ps(IBMI_K_OTHER, st, 0.0);
       note_launch(2);
       k_b_update<<<dim3(nblk(pb), (unsigned)pb, (unsigned)nl), 256, 0, st>>>(
-          dLupd, g.T, (int64_t)cap * pl, pb, ldp, g.expX, g.expQ, NS_S - 1, g.X64, g.Q, g.Xprev);
+          dLupd, g.T, (int64_t)cap * pl, pb, ldp, g.expX, g.expQ, NS_S - 1, g.X64, g.Xprev);
       const unsigned nt = (unsigned)((pb + 31) / 32);
-      k_b_symfull<<<dim3(nt, nt, (unsigned)nl), dim3(32, 8), 0, st>>>(dLupd, pb, g.Q, g.X64);
+      k_b_symfull<<<dim3(nt, nt, (unsigned)nl), dim3(32, 8), 0, st>>>(dLupd, pb, g.X64, g.Xprev);
       IBMI_CUDA_TRY(cudaGetLastError());
     }
-    if (!Lrs.empty()) {  // residuals: fresh (groups 0..q) and extended (qc+1..9), one launch
+    if (!Lrs.empty()) {  // residuals: fresh (groups 0..q), extended (qc+1..9) and corrections, one launch
       const int nl = (int)Lrs.size();
-      IBMI_CUDA_TRY(slice(g.X64, g.Xo, OZ_SX, g.expX, dLrs, nl));   // digits are prefix-stable
+      // digits of X (prefix-stable), or of the step's difference X - Xprev for a correction
+      if (!Ldir.empty()) IBMI_CUDA_TRY(slice(g.X64, g.Xo, OZ_SX, g.expX, dLdir, (int)Ldir.size()));
+      if (!Lcor.empty()) IBMI_CUDA_TRY(slice(g.Xprev, g.Xo, OZ_SX, g.expX, dLcor, (int)Lcor.size()));
       int q0 = OZ_QMAX, q1 = 0;
       double alg = 0.0;
       for (int i = 0; i < nl; ++i) {
@@ -951,7 +999,7 @@ ibmi_status DevGroup::run(const BatchMat* mats, int nrun, const ibmi_batch_opts&
       ProfScope ps(IBMI_K_OTHER, st, 0.0);
       note_launch(2);
       k_b_combine<<<dim3(nblk(pb), (unsigned)pb, (unsigned)nl), 256, 0, st>>>(
-          dLrs, g.T, (int64_t)cap * pl, pb, ldp, g.expX, g.expA, dqm, g.Q, g.partials, g.nparts_c);
+          dLrs, g.T, (int64_t)cap * pl, pb, ldp, g.expX, g.expA, dqm, dcsub, g.Q, g.partials, g.nparts_c);
       k_b_sum<<<(unsigned)nl, 256, 0, st>>>(dLrs, g.partials, g.nparts_c, g.din, g.dout);
       IBMI_CUDA_TRY(cudaGetLastError());
     }
@@ -979,7 +1027,7 @@ ibmi_status DevGroup::run(const BatchMat* mats, int nrun, const ibmi_batch_opts&
         if (!isfinite(rho)) { m.phase = FAILED; res[b].status = IBMI_ERR_NONFINITE; continue; }
         if (theta > 0.0 && rho * sqrtp <= theta && rho <= m.handover_below) {
           m.phase = TAIL; m.act = T_ENTER; m.early = true; m.handover_rho = rho; m.s = 0;
-          m.prev = INFINITY;
+          m.prev = INFINITY; m.exact = m.corr = m.xo_delta = false;
           m.next_q = rho <= tol ? OZ_QMAX : kFirstGroups;
           m.waiting = true;
           continue;
@@ -991,7 +1039,7 @@ ibmi_status DevGroup::run(const BatchMat* mats, int nrun, const ibmi_batch_opts&
             m.level = 1; m.stalled = 0; m.best = INFINITY; m.reslice = true;
           } else if (rho * sqrtp <= 8.0 * theta) {
             m.phase = TAIL; m.act = T_ENTER; m.early = false; m.handover_rho = rho; m.s = 0;
-            m.prev = INFINITY;
+            m.prev = INFINITY; m.exact = m.corr = m.xo_delta = false;
             m.next_q = kFirstGroups;
             m.waiting = true;
             continue;
@@ -1002,6 +1050,7 @@ ibmi_status DevGroup::run(const BatchMat* mats, int nrun, const ibmi_batch_opts&
         }
         if (rho <= tol || m.r >= max_sweeps) {   // BF16x3 cannot certify tol: the FP64-accurate residual
           m.phase = TAIL; m.act = T_CERTIFY; m.next_q = OZ_QMAX;
+          m.exact = m.corr = m.xo_delta = false;
           m.waiting = true;
           continue;
         }
@@ -1024,11 +1073,17 @@ ibmi_status DevGroup::run(const BatchMat* mats, int nrun, const ibmi_batch_opts&
         flops[b] += fr * (act == T_EXTEND ? count_pairs(OZ_SX, OZ_SA, m.qc + 1, OZ_QMAX)
                                           : count_pairs(OZ_SX, OZ_SA, 0, qdone)) / full_pairs;
         m.qc = qdone;
+        // a correction of an exact residual is exact (its groups reach below
+        // 1% of tol, corr_groups), and so is a residual of all groups
+        const bool was_corr = act == T_STEP && m.corr;
+        m.exact = was_corr || m.qc == OZ_QMAX;
+        m.xo_delta = was_corr;
+        m.corr = false;
         const bool worse = m.s > 0 && !(rho < m.prev) && act != T_EXTEND;
         if (!worse) {
           res[b].resid_f = rho;
           if (!isfinite(rho)) { m.phase = FAILED; res[b].status = IBMI_ERR_NONFINITE; continue; }
-          if (rho <= tol && m.qc < OZ_QMAX) { m.act = T_EXTEND; continue; }   // certify with all groups
+          if (rho <= tol && !m.exact) { m.act = T_EXTEND; continue; }   // certify with all groups
           if (rho <= tol) { m.phase = DONE; res[b].status = IBMI_OK; continue; }
         }
         if (m.s >= ns_max || worse) {
@@ -1040,11 +1095,14 @@ ibmi_status DevGroup::run(const BatchMat* mats, int nrun, const ibmi_batch_opts&
           m.phase = FALLBACK;
           continue;
         }
-        // one Newton-Schulz step, then the next residual
+        // one Newton-Schulz step, then the next residual: after an exact
+        // one its correction Q - (X - Xprev) A
         m.prev = rho;
         m.act = T_STEP;
         const double rho_hat = rho * rho;
-        m.next_q = rho_hat <= tol ? OZ_QMAX : (rho * rho > 1e3 * tol ? kNextGroups : OZ_QMAX);
+        m.corr = m.exact;
+        m.next_q = m.corr ? corr_groups(rho, tol)
+                          : (rho_hat <= tol ? OZ_QMAX : (rho * rho > 1e3 * tol ? kNextGroups : OZ_QMAX));
       }
     }
   }
