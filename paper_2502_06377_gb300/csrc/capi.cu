@@ -617,8 +617,14 @@ std::mutex g_prof_mu;                    // guards g_prof and the event pool
 ProfClass g_prof[IBMI_K_COUNT];
 std::vector<cudaEvent_t> g_event_pool;
 std::atomic<int64_t> g_launches{0};
-thread_local int g_open_class = -1;      // scopes are per thread (one stream each)
-thread_local cudaEvent_t g_open_event = nullptr;
+// Open scopes, innermost last (per thread: one stream each).  A scope opened
+// inside another pauses it, so every interval of device time goes to one
+// class only.
+struct OpenScope {
+  int k;
+  cudaEvent_t ev;
+};
+thread_local std::vector<OpenScope> g_open;
 
 cudaEvent_t take_event() {
   if (!g_event_pool.empty()) {
@@ -639,22 +645,36 @@ bool prof_on() { return g_prof_on.load(std::memory_order_relaxed); }
 void prof_begin(int k, cudaStream_t st) {
   if (!g_prof_on.load(std::memory_order_relaxed) || k < 0 || k >= IBMI_K_COUNT) return;
   std::lock_guard<std::mutex> g(g_prof_mu);
-  g_open_class = k;
-  g_open_event = take_event();
-  cudaEventRecord(g_open_event, st);
+  if (!g_open.empty() && g_open.back().ev) {   // pause the enclosing scope
+    cudaEvent_t e = take_event();
+    cudaEventRecord(e, st);
+    g_prof[g_open.back().k].ev.emplace_back(g_open.back().ev, e);
+    g_open.back().ev = nullptr;
+  }
+  cudaEvent_t e = take_event();
+  cudaEventRecord(e, st);
+  g_open.push_back(OpenScope{k, e});
 }
 
 void prof_end(int k, cudaStream_t st, double flops, double alg) {
-  if (!g_prof_on.load(std::memory_order_relaxed) || k != g_open_class || !g_open_event) return;
+  if (g_open.empty() || g_open.back().k != k) return;
+  if (!g_prof_on.load(std::memory_order_relaxed)) {   // turned off inside the scope
+    g_open.pop_back();
+    return;
+  }
   std::lock_guard<std::mutex> g(g_prof_mu);
   cudaEvent_t e = take_event();
   cudaEventRecord(e, st);
-  g_prof[k].ev.emplace_back(g_open_event, e);
+  if (g_open.back().ev) g_prof[k].ev.emplace_back(g_open.back().ev, e);
   g_prof[k].launches += 1;
   g_prof[k].flops += flops;
   g_prof[k].alg += alg;
-  g_open_event = nullptr;
-  g_open_class = -1;
+  g_open.pop_back();
+  if (!g_open.empty()) {   // resume the enclosing scope
+    cudaEvent_t r = take_event();
+    cudaEventRecord(r, st);
+    g_open.back().ev = r;
+  }
 }
 }  // namespace ibmi
 

@@ -65,7 +65,7 @@ ibmi_status schur_guess_block(ibmi_plan_s* P, const double* A, int64_t lda, doub
   const int64_t n = G->mmax;
   IBMI_CUDA_TRY(cudaMemsetAsync(G->dstatus, 0, sizeof(DevStatus), st));
   const bool tc = R != nullptr && n >= 1024;
-  IBMI_TRY(invariants_all(G, A, lda, false, st, tc));
+  IBMI_TRY(invariants_all(G, A, lda, false, st, tc, R));
   if (tc) IBMI_TRY(refine_block_inverse(R, G->bat_R, n, n, G->pool, st));
   return copy_square(T0, ldt, G->pool, n, n, st);
 }

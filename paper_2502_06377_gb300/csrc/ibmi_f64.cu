@@ -6,6 +6,7 @@
 
 #include "gemm_f64.cuh"
 #include "plan.cuh"
+#include "refine.cuh"
 
 namespace ibmi {
 
@@ -143,7 +144,7 @@ __global__ void k_bat_extract(const double* R, const int64_t* dlo, const int64_t
 static inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
 ibmi_status invariants_all(ibmi_plan_s* P, const double* A, int64_t lda, bool full_w, cudaStream_t st,
-                           bool leave_y) {
+                           bool leave_y, RefineState* tc) {
   const int64_t p = P->d.p, mmax = P->mmax;
   const int K = (int)P->lo.size();
   const int64_t ncols = full_w ? p : mmax;
@@ -167,27 +168,42 @@ ibmi_status invariants_all(ibmi_plan_s* P, const double* A, int64_t lda, bool fu
   note_launch();
   k_bat_copy_block<<<dim3(nblk(mmax * mmax), 1, K), 256, 0, st>>>(A, lda, P->dlo, P->dm, mmax, Lw, P->doffA);
   IBMI_CUDA_TRY(cudaGetLastError());
-  // blocked right-looking Cholesky, nb = 32
-  for (int64_t j0 = 0; j0 < mmax; j0 += CHOL_NB) {
-    const int jb = (int)std::min<int64_t>(CHOL_NB, mmax - j0);
-    double* Li = P->bat_linv + j0 * CHOL_NB;
-    note_launch();
-    k_potrf_tile<<<dim3(1, 1, K), dim3(32, 32), 0, st>>>(Lw + j0 * mmax + j0, mmax, zL, jb, Li, zLi, P->dstatus,
-                                                          P->dlo, j0, P->doffA ? 1 : 0);
-    IBMI_CUDA_TRY(cudaGetLastError());
-    const int64_t rest = mmax - j0 - jb;
-    if (rest <= 0) break;
-    double* panel = Lw + (j0 + jb) * mmax + j0;
-    {  // panel = panel L_jj^{-T} (in place: one CTA column owns each row)
-      F64Operands op = bat(F64Operands{panel, mmax, id, id, Li, jb, id, id, rest, jb, jb}, zL, zLi);
-      IBMI_CUDA_TRY((launch_gemm_f64<true, false>(op, EpiStore{panel, mmax, 1.0, 0.0, zL}, st)));
+  // blocked right-looking Cholesky, nb = 32, by block columns [J0, J1): the
+  // whole matrix as one block column, or (tc, large blocks) columns of
+  // kTcCholPanel whose own steps run in FP64 while the update of everything
+  // right of them, C -= L21 L21^T with K = J1 - J0, runs on the tensor cores
+  const bool tc_chol = tc != nullptr && mmax >= kTcCholMinOrder;
+  const int64_t ncol = tc_chol ? kTcCholPanel : mmax;
+  for (int64_t J0 = 0; J0 < mmax; J0 += ncol) {
+    const int64_t J1 = std::min(mmax, J0 + ncol);
+    for (int64_t j0 = J0; j0 < J1; j0 += CHOL_NB) {
+      const int jb = (int)std::min<int64_t>(CHOL_NB, J1 - j0);
+      double* Li = P->bat_linv + j0 * CHOL_NB;
+      note_launch();
+      k_potrf_tile<<<dim3(1, 1, K), dim3(32, 32), 0, st>>>(Lw + j0 * mmax + j0, mmax, zL, jb, Li, zLi, P->dstatus,
+                                                            P->dlo, j0, P->doffA ? 1 : 0);
+      IBMI_CUDA_TRY(cudaGetLastError());
+      const int64_t rest = mmax - j0 - jb;
+      if (rest <= 0) break;
+      double* panel = Lw + (j0 + jb) * mmax + j0;
+      {  // panel = panel L_jj^{-T} (in place: one CTA column owns each row)
+        F64Operands op = bat(F64Operands{panel, mmax, id, id, Li, jb, id, id, rest, jb, jb}, zL, zLi);
+        IBMI_CUDA_TRY((launch_gemm_f64<true, false>(op, EpiStore{panel, mmax, 1.0, 0.0, zL}, st)));
+      }
+      // trailing -= panel panel^T on the columns up to J1, on the tiles that
+      // touch the lower triangle (the factorisation and the solves read
+      // nothing above the diagonal)
+      const int64_t ncols = J1 - j0 - jb;
+      if (ncols > 0) {
+        F64Operands op = bat(F64Operands{panel, mmax, id, id, panel, mmax, id, id, rest, ncols, jb}, zL, zL);
+        op.lower_tiles = true;
+        IBMI_CUDA_TRY((launch_gemm_f64<true, false>(op, EpiStore{panel + jb, mmax, -1.0, 1.0, zL}, st)));
+      }
     }
-    {  // trailing -= panel panel^T, on the tiles that touch the lower triangle
-       // (the factorisation and the solves read nothing above the diagonal)
-      F64Operands op = bat(F64Operands{panel, mmax, id, id, panel, mmax, id, id, rest, rest, jb}, zL, zL);
-      op.lower_tiles = true;
-      IBMI_CUDA_TRY((launch_gemm_f64<true, false>(op, EpiStore{panel + jb, mmax, -1.0, 1.0, zL}, st)));
-    }
+    if (J1 < mmax)
+      for (int k = 0; k < K; ++k)
+        IBMI_TRY(refine_syrk_sub(tc, Lw + k * zL + J1 * mmax + J0, mmax, mmax - J1, J1 - J0,
+                                 Lw + k * zL + J1 * mmax + J1, mmax, st));
   }
   // R <- L^{-T} L^{-1} R (full_w); A_I^{-1} = L^{-T} L^{-1} otherwise
   note_launch();

@@ -443,7 +443,7 @@ ibmi_status mixed_run(ibmi_plan_s* P, const double* A, int64_t lda, double* H, i
     // Large blocks: A_I^{-1} = Y^T Y (Y = L^{-1}) as an exact sliced product
     // on the tensor cores instead of the FP64 product, which dominates there
     const bool tc_inverse = P->mmax >= kTcInverseMinOrder;
-    IBMI_TRY(invariants_all(P, A, lda, false, st, tc_inverse));
+    IBMI_TRY(invariants_all(P, A, lda, false, st, tc_inverse, R));
     if (tc_inverse)
       for (int k = 0; k < K; ++k)
         IBMI_TRY(refine_block_inverse(R, P->bat_R + (int64_t)k * P->mmax * P->mmax, P->mmax, P->hi[k] - P->lo[k],

@@ -46,6 +46,8 @@ struct OzPairArgs {
   // Optional per-problem digit-group ranges (indexed like bsel): the tiles of
   // problem i take only the pairs with qr[i].x <= q <= qr[i].y.
   const int2* qr;
+  // Symmetric result (M == N): tiles entirely above the diagonal are skipped.
+  int lower;
 };
 
 // Splits the pair list (in group order) into segments: a pair's product,
@@ -67,8 +69,16 @@ inline void oz_make_segments(OzPairArgs& g) {
   }
 }
 
-// Whether the tiles of the problem at position bi take pair pi.
-__device__ __forceinline__ bool oz_pair_on(const OzPairArgs& g, int bi, int pi) {
+// Whether unit tt (tile tl of the problem at position bi) takes pair pi: the
+// problem's digit-group range, and with `lower` only tiles that reach the
+// diagonal or below it.  The same test in all three roles.
+template <int BN>
+__device__ __forceinline__ bool oz_pair_on(const OzPairArgs& g, int tt, int pi) {
+  const int bi = tt / g.tiles;
+  if (g.lower) {
+    const int tl = tt - bi * g.tiles, mt = tl / g.grid_n, ntl = tl - mt * g.grid_n;
+    if ((int64_t)ntl * BN >= (int64_t)(mt + 1) * BM) return false;
+  }
   if (!g.qr) return true;
   const int2 r = g.qr[bi];
   return g.q[pi] >= r.x && g.q[pi] <= r.y;
@@ -118,7 +128,7 @@ __global__ void __launch_bounds__(THREADS, Cfg<1, BN>::CTAS_PER_SM) k_oz_pairs(c
           for (int tt = blockIdx.x; ok && tt < total; tt += gridDim.x) {
             const int bi = tt / g.tiles, tl = tt - bi * g.tiles;
             const int p0 = g.seg0[sg];
-            if (!oz_pair_on(g, bi, p0)) continue;
+            if (!oz_pair_on<BN>(g, tt, p0)) continue;
             const int bb = g.bsel ? g.bsel[bi] : bi;
             const int mt = tl / g.grid_n, ntl = tl - mt * g.grid_n;
             const int kb = ci * g.chunk, nk = min(g.chunk, g.kt_total - kb);
@@ -160,7 +170,7 @@ __global__ void __launch_bounds__(THREADS, Cfg<1, BN>::CTAS_PER_SM) k_oz_pairs(c
       for (int sg = 0; ok && sg < g.nseg; ++sg)
         for (int ci = 0; ok && ci < nchunks; ++ci)
           for (int tt = blockIdx.x; ok && tt < total; tt += gridDim.x) {
-            if (!oz_pair_on(g, tt / g.tiles, g.seg0[sg])) continue;
+            if (!oz_pair_on<BN>(g, tt, g.seg0[sg])) continue;
             const int nk = min(g.chunk, g.kt_total - ci * g.chunk);
             const int buf = local & 1;
             const uint32_t use = (uint32_t)(local >> 1);
@@ -197,7 +207,7 @@ __global__ void __launch_bounds__(THREADS, Cfg<1, BN>::CTAS_PER_SM) k_oz_pairs(c
         for (int tt = blockIdx.x; ok && tt < total; tt += gridDim.x) {
           const int pi = g.seg0[sg];   // the segment's first pair: its group and whether it stores
           const int bi = tt / g.tiles, tl = tt - bi * g.tiles;
-          if (!oz_pair_on(g, bi, pi)) continue;
+          if (!oz_pair_on<BN>(g, tt, pi)) continue;
           const int bb = g.bsel ? g.bsel[bi] : bi;
           const int mt = tl / g.grid_n, ntl = tl - mt * g.grid_n;
           const int buf = local & 1;

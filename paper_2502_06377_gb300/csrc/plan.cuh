@@ -57,6 +57,7 @@ struct ibmi_plan_s {
 
 namespace ibmi {
 
+struct RefineState;
 constexpr int CHOL_NB = 32;
 
 // Stop-test cadence: cadence.h.
@@ -67,8 +68,13 @@ constexpr int CHOL_NB = 32;
 // the caller after a stream sync).
 // leave_y (with full_w false): stop after the forward solve, leaving Y = L^{-1}
 // of set k in P->bat_R + k * mmax * mmax (row pitch mmax) for the caller.
+// tc (mixed path): blocks of order >= kTcCholMinOrder take the Cholesky's
+// trailing updates beyond each 256-column block column on the tensor cores,
+// FP64-accurate (refine_syrk_sub); the block column itself stays DFMA.
 ibmi_status invariants_all(ibmi_plan_s* P, const double* A, int64_t lda, bool full_w, cudaStream_t st,
-                           bool leave_y = false);
+                           bool leave_y = false, RefineState* tc = nullptr);
+constexpr int64_t kTcCholMinOrder = 2048;   // block order from which tc applies
+constexpr int64_t kTcCholPanel = 256;       // block-column width of that factorisation
 
 // a3 + a4 for set k on an FP64 iterate H.
 ibmi_status sweep_step_f64(ibmi_plan_s* P, int k, double* H, int64_t ldh, cudaStream_t st);

@@ -740,6 +740,77 @@ ibmi_status refine_block_inverse(RefineState* R, const double* Y, int64_t ldy, i
   return IBMI_OK;
 }
 
+// C[i][j] -= 2^{e_i + e_j - 12} sum_{q <= qmax} T_q[i][j] 2^{-7q} on and below
+// the diagonal (C: M x M, row pitch ldc).
+__global__ void k_oz_syrk_sub(const int* T, int64_t plane, int64_t ldt, const int* ex, int qmax, int64_t M,
+                              double* C, int64_t ldc) {
+  const int64_t i = blockIdx.y, j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j > i || j >= M) return;
+  C[i * ldc + j] -= oz_value(T, plane, i * ldt + j, qmax, ex[i] + ex[j] - 12);
+}
+
+ibmi_status refine_syrk_sub(RefineState* R, const double* L, int64_t ldl, int64_t M, int64_t nb, double* C,
+                            int64_t ldc, cudaStream_t st) {
+  constexpr int ND = 8, QG = 8;   // 56-bit digits, groups q <= 8: 43 pair products
+  const int64_t p = R->p, ldp = R->ldp;
+  if (M <= 0) return IBMI_OK;
+  if (nb <= 0 || nb % tc::BK != 0 || nb > OZ_KCHUNK || M > p || M * nb > p * ldp) return IBMI_ERR_INVALID_ARG;
+  {
+    ProfScope ps(IBMI_K_OTHER, st, 0.0);
+    SlicePtrs sp{};
+    for (int d = 0; d < ND; ++d) sp.s[d] = R->Xo[d];   // M rows of nb digits at row pitch nb
+    note_launch();
+    k_oz_slices<<<(unsigned)M, 256, 0, st>>>(L, ldl, nb, 0, nb, sp, ND, R->expX, nullptr);
+    IBMI_CUDA_TRY(cudaGetLastError());
+  }
+  tc::OzPairMaps maps;
+  bool ok = true;
+  for (int d = 0; d < ND; ++d) {
+    ok &= tc::make_map_bf16(&maps.a[d], R->Xo[d], M, nb, nb, 128);
+    ok &= tc::make_map_bf16(&maps.b[d], R->Xo[d], M, nb, nb, R->bn);
+  }
+  if (!ok) return IBMI_ERR_CUDA;
+  tc::OzPairArgs g{};
+  int n = 0;
+  for (int q = 0; q <= QG; ++q) {
+    bool first = true;
+    for (int a = 0; a <= q; ++a) {
+      if (a >= ND || q - a >= ND) continue;
+      g.s[n] = (int8_t)a;
+      g.u[n] = (int8_t)(q - a);
+      g.q[n] = (int8_t)q;
+      g.first[n] = first ? 1 : 0;
+      first = false;
+      ++n;
+    }
+  }
+  g.n = n;
+  g.grid_n = (int)((M + R->bn - 1) / R->bn);
+  g.tiles = g.grid_n * (int)((M + 127) / 128);
+  g.kt_total = (int)(nb / tc::BK);
+  g.chunk = OZ_KCHUNK / tc::BK;
+  g.T = R->T;
+  g.plane = p * ldp;
+  g.ldt = ldp;
+  g.M = M;
+  g.N = M;
+  g.err = R->err;
+  g.lower = 1;
+  tc::oz_make_segments(g);
+  {
+    ProfScope ps(IBMI_K_INVARIANTS_TC, st, (double)n * M * M * (double)nb, (double)M * M * nb);
+    IBMI_TRY(with_bn(R, [&](auto bn) -> ibmi_status {
+      IBMI_CUDA_TRY(tc::launch_oz_pairs<decltype(bn)::value>(maps, g, st));
+      return IBMI_OK;
+    }));
+  }
+  ProfScope ps(IBMI_K_OTHER, st, 0.0);
+  note_launch();
+  k_oz_syrk_sub<<<grid2(M, M), 256, 0, st>>>(R->T, p * ldp, ldp, R->expX, QG, M, C, ldc);
+  IBMI_CUDA_TRY(cudaGetLastError());
+  return IBMI_OK;
+}
+
 ibmi_status refine_q_radius_read(RefineState* R, cudaStream_t st, double* radius) {
   IBMI_CUDA_TRY(cudaMemcpyAsync(radius, R->pv + 2 * R->p, sizeof(double), cudaMemcpyDeviceToHost, st));
   IBMI_CUDA_TRY(cudaStreamSynchronize(st));

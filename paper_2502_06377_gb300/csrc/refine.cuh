@@ -97,6 +97,16 @@ ibmi_status refine_form_w(RefineState* R, const double* Ainv, int64_t m, int64_t
 ibmi_status refine_block_inverse(RefineState* R, const double* Y, int64_t ldy, int64_t m, double* Ainv,
                                  cudaStream_t st);
 
+// The trailing update of a blocked Cholesky step, C -= L L^T on and below the
+// diagonal (C: M x M at row pitch ldc; L: M x nb at row pitch ldl, nb a
+// multiple of 64 and at most 4096; M <= p), FP64-accurate on tensor cores:
+// the rows of L sliced into eight 7-bit digits (56 bits below each row's
+// maximum, FP64's 53 and three more), the 43 exact pair products of digit
+// groups q <= 8 on the tiles that reach the diagonal, recombined exactly and
+// subtracted in FP64.  Borrows the X digit planes and the group planes.
+ibmi_status refine_syrk_sub(RefineState* R, const double* L, int64_t ldl, int64_t M, int64_t nb, double* C,
+                            int64_t ldc, cudaStream_t st);
+
 // Prepares the one-pass formation of W for the sets [lo_k, hi_k): the stacked
 // view fits when 5 slots of sum_k ceil(m_k/128)*128 rows fit in the X digit
 // and T regions and every set spans at most 4096 columns; otherwise W is

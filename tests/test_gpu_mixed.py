@@ -273,6 +273,25 @@ def test_mixed_large_blocks_tensor_core_block_inverse(ibmi):
     assert np.linalg.norm(H - ref.h) / np.linalg.norm(ref.h) < 5e-4
 
 
+def test_mixed_blocks_of_order_2048_factorise_on_tensor_cores(ibmi):
+    """Blocks of order >= 2048 take the Cholesky's trailing updates beyond each
+    256-column block column as exact digit products on the tensor cores
+    (FP64-accurate): fixed-sweep iterates follow the oracle's (FP64
+    factorisation) as closely as the FP64-factorised path does, and the
+    converged inverse certifies 1e-10 against the oracle's residual."""
+    p, K, h = 4200, 2, 0
+    A = wl.random_spd(p, 61, 1.0, 1e3)
+    ref = O.ibmi(A, O.partition(p, K, h), tol=0.0, max_sweeps=2)
+    s, res, H = run(ibmi, A, K=K, h=h, tol=0.0, max_sweeps=2)
+    err = np.linalg.norm(H - ref.h) / np.linalg.norm(ref.h)
+    print(f"p {p}: 2-sweep iterate vs oracle, relative Frobenius {err:.3e}")
+    assert err < 5e-4
+    s, res, H = run(ibmi, A, K=K, h=h, tol=1e-10, ns_theta=0.9, max_sweeps=300)
+    assert s == ibmi.IBMI_OK, res
+    rf = O.residual_f(A, H)
+    assert rf <= 1e-10 and res["resid_f"] == pytest.approx(rf, rel=1e-3, abs=1e-14), (rf, res)
+
+
 def test_bench_configuration_c2_matches_the_oracle(ibmi):
     """The exact configuration the benchmark times (p = 4096 Matern-3/2,
     K = 8, h = 32, theta = 0.9, tol 1e-10), element by element against the
