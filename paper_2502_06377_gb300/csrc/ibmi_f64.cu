@@ -215,23 +215,35 @@ ibmi_status invariants_all(ibmi_plan_s* P, const double* A, int64_t lda, bool fu
   // all jb rows of it, jb <= 32 <= the tile height, and reads its whole K
   // before writing).
   static_assert(CHOL_NB <= 32, "in-place diagonal-block products need jb within one tile row");
-  for (int64_t j0 = 0; j0 < mmax; j0 += CHOL_NB) {
-    const int jb = (int)std::min<int64_t>(CHOL_NB, mmax - j0);
-    const double* Li = P->bat_linv + j0 * CHOL_NB;
-    // With R = I (A_I^{-1} only) the forward solve builds L^{-1}, which is
-    // lower triangular: rows j0.. of R are still zero right of column j0 + jb.
-    const int64_t nc = full_w ? ncols : std::min<int64_t>(ncols, j0 + jb);
-    double* Rj = R + j0 * ncols;
-    {  // R[j0:j0+jb, :nc] = L_jj^{-1} R[j0:j0+jb, :nc]
-      F64Operands op = bat(F64Operands{Li, jb, id, id, Rj, ncols, id, id, jb, nc, jb}, zLi, zR);
-      IBMI_CUDA_TRY((launch_gemm_f64<true, true>(op, EpiStore{Rj, ncols, 1.0, 0.0, zR}, st)));
+  // By block rows [J0, J1) as the factorisation's block columns: with tc
+  // (A_I^{-1} only, large blocks) the update of the rows below a block row,
+  // R[J1:, :J1] -= L[J1:, J0:J1] R[J0:J1, :J1], runs on the tensor cores.
+  const bool tc_fwd = tc_chol && !full_w;
+  const int64_t nrow = tc_fwd ? kTcCholPanel : mmax;
+  for (int64_t J0 = 0; J0 < mmax; J0 += nrow) {
+    const int64_t J1 = std::min(mmax, J0 + nrow);
+    for (int64_t j0 = J0; j0 < J1; j0 += CHOL_NB) {
+      const int jb = (int)std::min<int64_t>(CHOL_NB, J1 - j0);
+      const double* Li = P->bat_linv + j0 * CHOL_NB;
+      // With R = I (A_I^{-1} only) the forward solve builds L^{-1}, which is
+      // lower triangular: rows j0.. of R are still zero right of column j0 + jb.
+      const int64_t nc = full_w ? ncols : std::min<int64_t>(ncols, j0 + jb);
+      double* Rj = R + j0 * ncols;
+      {  // R[j0:j0+jb, :nc] = L_jj^{-1} R[j0:j0+jb, :nc]
+        F64Operands op = bat(F64Operands{Li, jb, id, id, Rj, ncols, id, id, jb, nc, jb}, zLi, zR);
+        IBMI_CUDA_TRY((launch_gemm_f64<true, true>(op, EpiStore{Rj, ncols, 1.0, 0.0, zR}, st)));
+      }
+      const int64_t rest = J1 - j0 - jb;
+      if (rest > 0) {  // R[j0+jb:J1, :nc] -= L[j0+jb:J1, j0:j0+jb] R[j0:j0+jb, :nc]
+        F64Operands op = bat(F64Operands{Lw + (j0 + jb) * mmax + j0, mmax, id, id, Rj, ncols, id, id, rest, nc, jb},
+                             zL, zR);
+        IBMI_CUDA_TRY((launch_gemm_f64<true, true>(op, EpiStore{R + (j0 + jb) * ncols, ncols, -1.0, 1.0, zR}, st)));
+      }
     }
-    const int64_t rest = mmax - j0 - jb;
-    if (rest > 0) {  // R[j0+jb:, :nc] -= L[j0+jb:, j0:j0+jb] R[j0:j0+jb, :nc]
-      F64Operands op = bat(F64Operands{Lw + (j0 + jb) * mmax + j0, mmax, id, id, Rj, ncols, id, id, rest, nc, jb},
-                           zL, zR);
-      IBMI_CUDA_TRY((launch_gemm_f64<true, true>(op, EpiStore{R + (j0 + jb) * ncols, ncols, -1.0, 1.0, zR}, st)));
-    }
+    if (J1 < mmax)
+      for (int k = 0; k < K; ++k)
+        IBMI_TRY(refine_gemm_sub(tc, Lw + k * zL + J1 * mmax + J0, mmax, mmax - J1, J1 - J0, R + k * zR + J0 * ncols,
+                                 ncols, J1, R + k * zR + J1 * ncols, ncols, st));
   }
   double* X = R;   // the solutions
   if (full_w) {

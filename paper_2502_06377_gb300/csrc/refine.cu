@@ -264,6 +264,17 @@ __global__ void k_transpose(const double* Y, int64_t ldy, int64_t m, double* Z) 
     if (J0 + r < m && I0 + threadIdx.x < m) Z[(J0 + r) * m + I0 + threadIdx.x] = t[threadIdx.x][r];
 }
 
+// Z = B^T for a rows x cols block B (row pitch ldb); Z row pitch rows.
+__global__ void k_transpose_rect(const double* B, int64_t ldb, int64_t rows, int64_t cols, double* Z) {
+  __shared__ double t[32][33];
+  const int64_t I0 = (int64_t)blockIdx.y * 32, J0 = (int64_t)blockIdx.x * 32;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y)
+    t[r][threadIdx.x] = (I0 + r < rows && J0 + threadIdx.x < cols) ? B[(I0 + r) * ldb + J0 + threadIdx.x] : 0.0;
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y)
+    if (J0 + r < cols && I0 + threadIdx.x < rows) Z[(J0 + r) * rows + I0 + threadIdx.x] = t[threadIdx.x][r];
+}
+
 // Ainv[i][j] = 2^{e_i + e_j - 12} sum_{q <= qmax} T_q 2^{-7q} (the product Z Z^T).
 __global__ void k_oz_gram(const int* T, int64_t plane, int64_t ldp, int64_t m, const int* ez, int qmax,
                           double* Ainv) {
@@ -807,6 +818,86 @@ ibmi_status refine_syrk_sub(RefineState* R, const double* L, int64_t ldl, int64_
   ProfScope ps(IBMI_K_OTHER, st, 0.0);
   note_launch();
   k_oz_syrk_sub<<<grid2(M, M), 256, 0, st>>>(R->T, p * ldp, ldp, R->expX, QG, M, C, ldc);
+  IBMI_CUDA_TRY(cudaGetLastError());
+  return IBMI_OK;
+}
+
+// C[i][j] -= 2^{ea_i + eb_j - 12} sum_{q <= qmax} T_q[i][j] 2^{-7q} (C: M x N,
+// row pitch ldc).
+__global__ void k_oz_gemm_sub(const int* T, int64_t plane, int64_t ldt, const int* ea, const int* eb, int qmax,
+                              int64_t M, int64_t N, double* C, int64_t ldc) {
+  const int64_t i = blockIdx.y, j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= M || j >= N) return;
+  C[i * ldc + j] -= oz_value(T, plane, i * ldt + j, qmax, ea[i] + eb[j] - 12);
+}
+
+ibmi_status refine_gemm_sub(RefineState* R, const double* A, int64_t lda, int64_t M, int64_t K, const double* B,
+                            int64_t ldb, int64_t N, double* C, int64_t ldc, cudaStream_t st) {
+  constexpr int ND = 8, QG = 8;   // as refine_syrk_sub
+  const int64_t p = R->p, ldp = R->ldp;
+  if (M <= 0 || N <= 0) return IBMI_OK;
+  if (K <= 0 || K % tc::BK != 0 || K > OZ_KCHUNK || M > p || N > p || M * K > p * ldp || N * K > p * ldp)
+    return IBMI_ERR_INVALID_ARG;
+  {
+    ProfScope ps(IBMI_K_OTHER, st, 0.0);
+    note_launch(3);
+    // B^T (N x K, row pitch K) into the FP64 scratch, then the rows of A into
+    // the X digit planes and the rows of B^T into the A digit planes (both at
+    // row pitch K)
+    k_transpose_rect<<<dim3((unsigned)((N + 31) / 32), (unsigned)((K + 31) / 32)), dim3(32, 8), 0, st>>>(B, ldb, K, N,
+                                                                                                     R->Xn);
+    SlicePtrs sa{}, sb{};
+    for (int d = 0; d < ND; ++d) {
+      sa.s[d] = R->Xo[d];
+      sb.s[d] = R->Ao[d];
+    }
+    k_oz_slices<<<(unsigned)M, 256, 0, st>>>(A, lda, K, 0, K, sa, ND, R->expX, nullptr);
+    k_oz_slices<<<(unsigned)N, 256, 0, st>>>(R->Xn, K, K, 0, K, sb, ND, R->expQ, nullptr);
+    IBMI_CUDA_TRY(cudaGetLastError());
+  }
+  tc::OzPairMaps maps;
+  bool ok = true;
+  for (int d = 0; d < ND; ++d) {
+    ok &= tc::make_map_bf16(&maps.a[d], R->Xo[d], M, K, K, 128);
+    ok &= tc::make_map_bf16(&maps.b[d], R->Ao[d], N, K, K, R->bn);
+  }
+  if (!ok) return IBMI_ERR_CUDA;
+  tc::OzPairArgs g{};
+  int n = 0;
+  for (int q = 0; q <= QG; ++q) {
+    bool first = true;
+    for (int a = 0; a <= q; ++a) {
+      if (a >= ND || q - a >= ND) continue;
+      g.s[n] = (int8_t)a;
+      g.u[n] = (int8_t)(q - a);
+      g.q[n] = (int8_t)q;
+      g.first[n] = first ? 1 : 0;
+      first = false;
+      ++n;
+    }
+  }
+  g.n = n;
+  g.grid_n = (int)((N + R->bn - 1) / R->bn);
+  g.tiles = g.grid_n * (int)((M + 127) / 128);
+  g.kt_total = (int)(K / tc::BK);
+  g.chunk = OZ_KCHUNK / tc::BK;
+  g.T = R->T;
+  g.plane = p * ldp;
+  g.ldt = ldp;
+  g.M = M;
+  g.N = N;
+  g.err = R->err;
+  tc::oz_make_segments(g);
+  {
+    ProfScope ps(IBMI_K_INVARIANTS_TC, st, 2.0 * n * (double)M * N * (double)K, 2.0 * (double)M * N * K);
+    IBMI_TRY(with_bn(R, [&](auto bn) -> ibmi_status {
+      IBMI_CUDA_TRY(tc::launch_oz_pairs<decltype(bn)::value>(maps, g, st));
+      return IBMI_OK;
+    }));
+  }
+  ProfScope ps(IBMI_K_OTHER, st, 0.0);
+  note_launch();
+  k_oz_gemm_sub<<<grid2(N, M), 256, 0, st>>>(R->T, p * ldp, ldp, R->expX, R->expQ, QG, M, N, C, ldc);
   IBMI_CUDA_TRY(cudaGetLastError());
   return IBMI_OK;
 }

@@ -107,6 +107,15 @@ ibmi_status refine_block_inverse(RefineState* R, const double* Y, int64_t ldy, i
 ibmi_status refine_syrk_sub(RefineState* R, const double* L, int64_t ldl, int64_t M, int64_t nb, double* C,
                             int64_t ldc, cudaStream_t st);
 
+// C -= A B (C: M x N, A: M x K, B: K x N, row pitches ldc, lda, ldb; K a
+// multiple of 64 and at most 4096; M, N <= p), FP64-accurate on tensor cores
+// as refine_syrk_sub (rows of A and columns of B in eight 7-bit digits, 43
+// exact pair products): the trailing update of a blocked triangular solve.
+// Borrows the X and A digit planes, the FP64 scratch and the group planes:
+// only before refine_set_matrix (the factorisations of the set-up).
+ibmi_status refine_gemm_sub(RefineState* R, const double* A, int64_t lda, int64_t M, int64_t K, const double* B,
+                            int64_t ldb, int64_t N, double* C, int64_t ldc, cudaStream_t st);
+
 // Prepares the one-pass formation of W for the sets [lo_k, hi_k): the stacked
 // view fits when 5 slots of sum_k ceil(m_k/128)*128 rows fit in the X digit
 // and T regions and every set spans at most 4096 columns; otherwise W is
