@@ -273,8 +273,8 @@ def test_mixed_large_blocks_tensor_core_block_inverse(ibmi):
     assert np.linalg.norm(H - ref.h) / np.linalg.norm(ref.h) < 5e-4
 
 
-def test_mixed_blocks_of_order_2048_factorise_on_tensor_cores(ibmi):
-    """Blocks of order >= 2048 take the Cholesky's trailing updates beyond each
+def test_mixed_large_blocks_factorise_on_tensor_cores(ibmi):
+    """Blocks of order >= 1024 take the Cholesky's trailing updates beyond each
     256-column block column as exact digit products on the tensor cores
     (FP64-accurate): fixed-sweep iterates follow the oracle's (FP64
     factorisation) as closely as the FP64-factorised path does, and the
