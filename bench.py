@@ -74,7 +74,7 @@ def parse():
                     help="all: the headline line with the other workloads under 'configs'; c2: the "
                          "headline alone; c3 / batch / serve: one of the other workloads alone")
     ap.add_argument("--batch-n", type=int, default=512)
-    ap.add_argument("--serve-seconds", type=float, default=0.25)
+    ap.add_argument("--serve-seconds", type=float, default=0.5)
     ap.add_argument("--serve-rates", default="2000,120,60",
                     help="offered request rates (per second) of the served traces")
     return ap.parse_args()
