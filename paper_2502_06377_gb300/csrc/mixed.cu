@@ -288,6 +288,56 @@ struct EpiTcPartial : tc::EpiBase {
   }
 };
 
+// a4 with one K split: the finish in the epilogue (no partials, no finishing
+// kernel).  P = X W^T is computed on the tiles on and below the diagonal;
+// each element (i, j), j <= i, gives x = A_I^{-1}[i, j] - P[i, j] (FP32),
+// written to H[I, I] at (i, j) and, from the same x, at (j, i), so H[I, I]
+// is exactly symmetric.  The first pass writes (i, j) along rows (16 columns
+// of two rows per store) and keeps x in the warp's stage; the second writes
+// (j, i) with one lane per row i, 32 consecutive columns of H's row j per
+// store.
+struct EpiTcSymFinish : tc::EpiBase {
+  const double* Ainv; int64_t m, lo, ldp;
+  float* Hf; __nv_bfloat16* s0; __nv_bfloat16* s1; __nv_bfloat16* s2;
+  __device__ __forceinline__ void put(int64_t o, float x) const {
+    Hf[o] = x;
+    __nv_bfloat16 t0, t1, t2;
+    split3(x, t0, t1, t2);
+    s0[o] = t0;
+    s1[o] = t1;
+    if (s2) s2[o] = t2;
+  }
+  __device__ __forceinline__ void warp_tile(int64_t row0, int64_t j0, int, const float* __restrict__ stage_in,
+                                            int lane) const {
+    float* stage = const_cast<float*>(stage_in);   // this warp's own stage: x goes back in place
+    const int c = lane & 15;
+    const int64_t j = j0 + c;
+    double a[16];   // all loads of A_I^{-1} in flight before the first store
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      const int64_t i = row0 + 2 * k + (lane >> 4);
+      a[k] = i < m && j <= i ? Ainv[i * m + j] : 0.0;
+    }
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {   // (i, j): lane = (row, column), 16 columns of two rows per store
+      const int r = 2 * k + (lane >> 4);
+      const int64_t i = row0 + r;
+      if (i < m && j <= i) {
+        const float x = (float)(a[k] - (double)stage[r * 17 + c]);
+        stage[r * 17 + c] = x;
+        put((lo + i) * ldp + lo + j, x);
+      }
+    }
+    __syncwarp();
+    const int64_t i = row0 + lane;   // (j, i): lane = row i, consecutive in H's row j
+#pragma unroll 4
+    for (int cc = 0; cc < 16; ++cc) {
+      const int64_t jj = j0 + cc;
+      if (i < m && jj < i) put((lo + jj) * ldp + lo + i, stage[lane * 17 + cc]);
+    }
+  }
+};
+
 static inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
 // --------------------------------------------------------------- host ----
@@ -395,15 +445,21 @@ ibmi_status mixed_sweep_step(ibmi_plan_s* P, int k, cudaStream_t st) {
     const int ntn = (int)((m + MX_BN - 1) / MX_BN);
     tc::Tiles t{m, lo, 0, ntn, ntn, kr.r0_end, kr.r1_begin, kr.r1_end, splits, M->err};
     t.lower = 1;   // P is symmetric up to rounding: tiles on and below the diagonal only
-    EpiTcPartial epi{{}, M->Spart, m};
     ProfScope ps(IBMI_K_SWEEP_S, st, mult * 2.0 * n * (double)(ntn * (ntn + 1) / 2) * MX_BN * MX_BN,
                  2.0 * m * m * n);
-    if (S == 2) IBMI_CUDA_TRY((tc::launch<2, MX_BN>(maps, t, ntn, (int)((m + 127) / 128), epi, st)));
-    else IBMI_CUDA_TRY((tc::launch<3, MX_BN>(maps, t, ntn, (int)((m + 127) / 128), epi, st)));
-    note_launch();
-    k_mixed_sym<<<grid2(m, m), 256, 0, st>>>(M->Spart, splits, m, P->ainv[k], lo, M->ldp, M->Hf, M->Hs[0],
-                                             M->Hs[1], S == 3 ? M->Hs[2] : nullptr);
-    IBMI_CUDA_TRY(cudaGetLastError());
+    if (splits == 1) {   // the finish in the epilogue (no partials)
+      EpiTcSymFinish epi{{}, P->ainv[k], m, lo, M->ldp, M->Hf, M->Hs[0], M->Hs[1], S == 3 ? M->Hs[2] : nullptr};
+      if (S == 2) IBMI_CUDA_TRY((tc::launch<2, MX_BN>(maps, t, ntn, (int)((m + 127) / 128), epi, st)));
+      else IBMI_CUDA_TRY((tc::launch<3, MX_BN>(maps, t, ntn, (int)((m + 127) / 128), epi, st)));
+    } else {
+      EpiTcPartial epi{{}, M->Spart, m};
+      if (S == 2) IBMI_CUDA_TRY((tc::launch<2, MX_BN>(maps, t, ntn, (int)((m + 127) / 128), epi, st)));
+      else IBMI_CUDA_TRY((tc::launch<3, MX_BN>(maps, t, ntn, (int)((m + 127) / 128), epi, st)));
+      note_launch();
+      k_mixed_sym<<<grid2(m, m), 256, 0, st>>>(M->Spart, splits, m, P->ainv[k], lo, M->ldp, M->Hf, M->Hs[0],
+                                               M->Hs[1], S == 3 ? M->Hs[2] : nullptr);
+      IBMI_CUDA_TRY(cudaGetLastError());
+    }
   }
   return IBMI_OK;
 }
