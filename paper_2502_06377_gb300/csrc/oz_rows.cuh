@@ -136,11 +136,17 @@ __device__ __forceinline__ double pow2i(int k) {
 // `idx` of planes `plane` apart.  The sum is formed exactly in two int64
 // halves (groups 0..4 and 5..qmax, each below 2^59), so only the final
 // conversion and scaling round.
+__device__ __forceinline__ double oz_groups_value(const int (&t)[10], int e);
 __device__ __forceinline__ double oz_value(const int* T, int64_t plane, int64_t idx, int qmax, int e, int qmin = 0) {
   // all group loads issued together (predicated, no early exit)
   int t[10];
 #pragma unroll
   for (int q = 0; q < 10; ++q) t[q] = (q >= qmin && q <= qmax) ? T[(int64_t)q * plane + idx] : 0;
+  return oz_groups_value(t, e);
+}
+
+// 2^e * sum_q t[q] 2^{-7q} (groups left out given as 0), as oz_value.
+__device__ __forceinline__ double oz_groups_value(const int (&t)[10], int e) {
   long long hi = 0, lo = 0;
 #pragma unroll
   for (int q = 0; q < 10; ++q) {

@@ -114,25 +114,42 @@ struct EpiResidSq {
 // with `sub` Q = Q - C in place (FP64, ld p); sum Q^2 per CTA, and (second
 // half of `partials`) the sum of squares of the last group's part
 // 2^{e_i + f_j - 12 - 7 qmax} T_qmax, whose norm scales the truncation error
-// of the groups left out.
-__global__ void k_oz_combine(const int* T, int64_t p, int64_t ldp, const int* ex, const int* ea, int qmin, int qmax,
-                             int sub, double* Q, double* partials) {
-  const int64_t i = blockIdx.y, j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+// of the groups left out.  Four consecutive columns per thread: one int4
+// load per group plane (the planes' row pitch ldp is a multiple of 64, so a
+// load that starts below p stays inside the row).
+__global__ void k_oz_combine(const int* T, int64_t p, int64_t ldp, const int* ex, const int* ea, int qmin,
+                             int qmax, int sub, double* Q, double* partials) {
+  const int64_t i = blockIdx.y, j0 = 4 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
   float sq = 0.f, gq = 0.f;
-  if (j < p) {
-    const int e = ex[i] + ea[j] - 12;
-    const double c = oz_value(T, p * ldp, i * ldp + j, qmax, e, qmin);
-    // float is ample for a norm estimate: parts below ~1e-19 underflow to 0
-    // (far below any tolerance) and an overflow reads as an infinite norm
-    const float g = ldexpf((float)T[(int64_t)qmax * p * ldp + i * ldp + j], e - 7 * qmax);
-    gq = g * g;
-    // off the diagonal Q = -c is a sign flip; the squares for rho need only
-    // float precision (FP64 arithmetic is scarce on this GPU)
-    const double q = sub ? Q[i * p + j] - c
-                         : (i == j ? 1.0 - c : ozr_bits_to_double(ozr_double_to_bits(c) ^ 0x8000000000000000ull));
-    const float qf = ozr_to_float(q);
-    sq = qf * qf;
-    Q[i * p + j] = q;
+  if (j0 < p) {
+    const int64_t plane = p * ldp, idx = i * ldp + j0;
+    int4 t4[10];
+#pragma unroll
+    for (int q = 0; q < 10; ++q)
+      t4[q] = (q >= qmin && q <= qmax) ? *reinterpret_cast<const int4*>(T + q * plane + idx) : make_int4(0, 0, 0, 0);
+    const int exi = ex[i] - 12;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int64_t j = j0 + c;
+      if (j >= p) break;
+      int t[10];
+#pragma unroll
+      for (int q = 0; q < 10; ++q) t[q] = c == 0 ? t4[q].x : (c == 1 ? t4[q].y : (c == 2 ? t4[q].z : t4[q].w));
+      const int e = exi + ea[j];
+      const double v = oz_groups_value(t, e);
+      int tl = 0;   // group qmax: float is ample for a norm estimate (parts below ~1e-19
+                    // underflow to 0, an overflow reads as an infinite norm)
+#pragma unroll
+      for (int q = 0; q < 10; ++q)
+        if (q == qmax) tl = t[q];
+      const float g = ldexpf((float)tl, e - 7 * qmax);
+      gq += g * g;
+      const double qv = sub ? Q[i * p + j] - v
+                            : (i == j ? 1.0 - v : ozr_bits_to_double(ozr_double_to_bits(v) ^ 0x8000000000000000ull));
+      const float qf = ozr_to_float(qv);
+      sq += qf * qf;
+      Q[i * p + j] = qv;
+    }
   }
   __shared__ double red[8], redg[8];
   for (int o = 16; o > 0; o >>= 1) {
@@ -145,13 +162,13 @@ __global__ void k_oz_combine(const int* T, int64_t p, int64_t ldp, const int* ex
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double t = 0.0, tg = 0.0;
+    double tt = 0.0, tg = 0.0;
     for (int w = 0; w < (int)(blockDim.x / 32); ++w) {
-      t += red[w];
+      tt += red[w];
       tg += redg[w];
     }
     const int64_t b = (int64_t)blockIdx.y * gridDim.x + blockIdx.x, nb = (int64_t)gridDim.x * gridDim.y;
-    partials[b] = t;
+    partials[b] = tt;
     partials[nb + b] = tg;
   }
 }
@@ -922,7 +939,7 @@ static ibmi_status combine_residual(RefineState* R, int qmin, int qmax, bool sub
                                     cudaStream_t st) {
   const int64_t p = R->p, ldp = R->ldp;
   ProfScope ps(IBMI_K_OTHER, st, 0.0);
-  const dim3 gc = grid2(p, p);
+  const dim3 gc = grid2((p + 3) / 4, p);
   const int64_t nb = (int64_t)gc.x * gc.y;
   if (2 * nb > R->n_partials) return IBMI_ERR_INVALID_ARG;
   note_launch();
