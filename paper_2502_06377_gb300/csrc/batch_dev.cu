@@ -288,18 +288,34 @@ __global__ void k_b_export(const int* sel, int64_t pb, int64_t ldp, const float*
 __global__ void k_b_combine(const int* sel, const int* T, int64_t plane, int64_t pb, int64_t ldp, const int* ex,
                             const int* ea, const int* qm, const int* sub, double* Q, double* partials,
                             int64_t nparts) {
-  const int64_t b = pick(sel, blockIdx.z), i = blockIdx.y, j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  // four consecutive columns per thread, one int4 load per group plane (row
+  // pitch ldp, a multiple of 64)
+  const int64_t b = pick(sel, blockIdx.z), i = blockIdx.y, j0 = 4 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
   const int qmax = qm[blockIdx.z];   // highest digit group of this matrix's residual
   const bool corr = sub[blockIdx.z] != 0;
   float sq = 0.f;
-  if (j < pb) {
-    const int64_t o = (b * pb + i) * pb + j;
-    const double c = oz_value(T + b * pb * ldp, plane, i * ldp + j, qmax, ex[b * pb + i] + ea[b * pb + j] - 12);
-    const double q = corr ? Q[o] - c
-                          : (i == j ? 1.0 - c : ozr_bits_to_double(ozr_double_to_bits(c) ^ 0x8000000000000000ull));
-    const float qf = ozr_to_float(q);
-    sq = qf * qf;
-    Q[o] = q;
+  if (j0 < pb) {
+    const int* Tb = T + b * pb * ldp + i * ldp + j0;
+    int4 t4[10];
+#pragma unroll
+    for (int q = 0; q < 10; ++q)
+      t4[q] = q <= qmax ? *reinterpret_cast<const int4*>(Tb + q * plane) : make_int4(0, 0, 0, 0);
+    const int exi = ex[b * pb + i] - 12;
+#pragma unroll
+    for (int c4 = 0; c4 < 4; ++c4) {
+      const int64_t j = j0 + c4;
+      if (j >= pb) break;
+      int t[10];
+#pragma unroll
+      for (int q = 0; q < 10; ++q) t[q] = c4 == 0 ? t4[q].x : (c4 == 1 ? t4[q].y : (c4 == 2 ? t4[q].z : t4[q].w));
+      const int64_t o = (b * pb + i) * pb + j;
+      const double c = oz_groups_value(t, exi + ea[b * pb + j]);
+      const double q = corr ? Q[o] - c
+                            : (i == j ? 1.0 - c : ozr_bits_to_double(ozr_double_to_bits(c) ^ 0x8000000000000000ull));
+      const float qf = ozr_to_float(q);
+      sq += qf * qf;
+      Q[o] = q;
+    }
   }
   __shared__ double red[8];
   for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
@@ -317,12 +333,26 @@ __global__ void k_b_combine(const int* sel, const int* T, int64_t plane, int64_t
 // Xprev = X before it.
 __global__ void k_b_update(const int* sel, const int* T, int64_t plane, int64_t pb, int64_t ldp, const int* ex,
                            const int* eq, int qmax, double* X64, double* Xprev) {
-  const int64_t b = pick(sel, blockIdx.z), i = blockIdx.y, j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= pb) return;
-  const int64_t o = (b * pb + i) * pb + j;
-  const double x = X64[o];
-  Xprev[o] = x;
-  X64[o] = x + oz_value(T + b * pb * ldp, plane, i * ldp + j, qmax, ex[b * pb + i] + eq[b * pb + j] - 12);
+  // four consecutive columns per thread (as k_b_combine)
+  const int64_t b = pick(sel, blockIdx.z), i = blockIdx.y, j0 = 4 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+  if (j0 >= pb) return;
+  const int* Tb = T + b * pb * ldp + i * ldp + j0;
+  int4 t4[10];
+#pragma unroll
+  for (int q = 0; q < 10; ++q) t4[q] = q <= qmax ? *reinterpret_cast<const int4*>(Tb + q * plane) : make_int4(0, 0, 0, 0);
+  const int exi = ex[b * pb + i] - 12;
+#pragma unroll
+  for (int c4 = 0; c4 < 4; ++c4) {
+    const int64_t j = j0 + c4;
+    if (j >= pb) break;
+    int t[10];
+#pragma unroll
+    for (int q = 0; q < 10; ++q) t[q] = c4 == 0 ? t4[q].x : (c4 == 1 ? t4[q].y : (c4 == 2 ? t4[q].z : t4[q].w));
+    const int64_t o = (b * pb + i) * pb + j;
+    const double x = X64[o];
+    Xprev[o] = x;
+    X64[o] = x + oz_groups_value(t, exi + eq[b * pb + j]);
+  }
 }
 
 // X64[b] <- (X64 + X64^T) / 2 in place, one block per pair of mirror 32 x 32
@@ -496,7 +526,7 @@ ibmi_status DevGroup::create(int64_t pb, int K, int64_t h, int n) {
   const int64_t tm = (g.mmax + 127) / 128, tiles2 = tm * (tm + 1) / 2;
   const int kt = (int)((pb + tc::BK - 1) / tc::BK);
   g.splits = (int)std::max<int64_t>(1, std::min<int64_t>(std::max<int64_t>(1, 152 / tiles2), kt / 4 > 0 ? kt / 4 : 1));
-  g.nparts_c = pb * nblk(pb);
+  g.nparts_c = pb * nblk((pb + 3) / 4);   // k_b_combine: one partial per CTA of four-column threads
   g.nparts_r = ((pb + 127) / 128) * ((pb + kBN - 1) / kBN) * 4;
   const int64_t nparts = std::max(g.nparts_c, g.nparts_r);
   // FP64 factorisation plan over the n K blocks
@@ -977,7 +1007,7 @@ ibmi_status DevGroup::run(const BatchMat* mats, int nrun, const ibmi_batch_opts&
       IBMI_TRY(pairs(g.mXo, NS_S, g.mQo, NS_S, 0, NS_S - 1, dLupd, nl, IBMI_K_NS, nl * fr, nullptr));
       ProfScope ps(IBMI_K_OTHER, st, 0.0);
       note_launch(2);
-      k_b_update<<<dim3(nblk(pb), (unsigned)pb, (unsigned)nl), 256, 0, st>>>(
+      k_b_update<<<dim3(nblk((pb + 3) / 4), (unsigned)pb, (unsigned)nl), 256, 0, st>>>(
           dLupd, g.T, (int64_t)cap * pl, pb, ldp, g.expX, g.expQ, NS_S - 1, g.X64, g.Xprev);
       const unsigned nt = (unsigned)((pb + 31) / 32);
       k_b_symfull<<<dim3(nt, nt, (unsigned)nl), dim3(32, 8), 0, st>>>(dLupd, pb, g.X64, g.Xprev);
@@ -998,7 +1028,7 @@ ibmi_status DevGroup::run(const BatchMat* mats, int nrun, const ibmi_batch_opts&
       IBMI_TRY(pairs(g.mXo, OZ_SX, g.mAo, OZ_SA, q0, q1, dLrs, nl, IBMI_K_RESIDUAL, alg, dqr));
       ProfScope ps(IBMI_K_OTHER, st, 0.0);
       note_launch(2);
-      k_b_combine<<<dim3(nblk(pb), (unsigned)pb, (unsigned)nl), 256, 0, st>>>(
+      k_b_combine<<<dim3(nblk((pb + 3) / 4), (unsigned)pb, (unsigned)nl), 256, 0, st>>>(
           dLrs, g.T, (int64_t)cap * pl, pb, ldp, g.expX, g.expA, dqm, dcsub, g.Q, g.partials, g.nparts_c);
       k_b_sum<<<(unsigned)nl, 256, 0, st>>>(dLrs, g.partials, g.nparts_c, g.din, g.dout);
       IBMI_CUDA_TRY(cudaGetLastError());

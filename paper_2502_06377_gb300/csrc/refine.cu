@@ -248,11 +248,27 @@ __global__ void k_diff(const double* X, int64_t ldx, const double* Xprev, int64_
 }
 
 // Newton-Schulz update: Xn = X + 2^{e_i + g_j - 12} sum_{q <= qmax} T_q 2^{-7q}.
+// Four consecutive columns per thread, one int4 load per group plane (as
+// k_oz_combine).
 __global__ void k_oz_update(const int* T, int64_t p, int64_t ldp, const int* ex, const int* eq, int qmax,
                             const double* X, int64_t ldx, double* Xn) {
-  const int64_t i = blockIdx.y, j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= p) return;
-  Xn[i * p + j] = X[i * ldx + j] + oz_value(T, p * ldp, i * ldp + j, qmax, ex[i] + eq[j] - 12);
+  const int64_t i = blockIdx.y, j0 = 4 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+  if (j0 >= p) return;
+  const int64_t plane = p * ldp, idx = i * ldp + j0;
+  int4 t4[10];
+#pragma unroll
+  for (int q = 0; q < 10; ++q)
+    t4[q] = q <= qmax ? *reinterpret_cast<const int4*>(T + q * plane + idx) : make_int4(0, 0, 0, 0);
+  const int exi = ex[i] - 12;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const int64_t j = j0 + c;
+    if (j >= p) break;
+    int t[10];
+#pragma unroll
+    for (int q = 0; q < 10; ++q) t[q] = c == 0 ? t4[q].x : (c == 1 ? t4[q].y : (c == 2 ? t4[q].z : t4[q].w));
+    Xn[i * p + j] = X[i * ldx + j] + oz_groups_value(t, exi + eq[j]);
+  }
 }
 
 // X = (Xn + Xn^T) / 2 by 32 x 32 tiles through shared memory (both the tile
@@ -1017,7 +1033,7 @@ ibmi_status refine_ns_update(RefineState* R, double* X, int64_t ldx, cudaStream_
   IBMI_TRY(pair_products(R, R->mXo, NS_S, R->mQo, NS_S, qmax, IBMI_K_NS, st));
   ProfScope ps(IBMI_K_OTHER, st, 0.0);
   note_launch();
-  k_oz_update<<<grid2(p, p), 256, 0, st>>>(R->T, p, ldp, R->expX, R->expQ, qmax, X, ldx, R->Xn);
+  k_oz_update<<<grid2((p + 3) / 4, p), 256, 0, st>>>(R->T, p, ldp, R->expX, R->expQ, qmax, X, ldx, R->Xn);
   IBMI_CUDA_TRY(cudaGetLastError());
   if (backup)
     IBMI_CUDA_TRY(cudaMemcpy2DAsync(backup, sizeof(double) * p, X, sizeof(double) * ldx, sizeof(double) * p, p,
