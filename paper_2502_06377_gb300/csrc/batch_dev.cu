@@ -35,16 +35,6 @@ namespace {
 constexpr int kBN = 128;              // N tile of the sweep products and the BF16x3 stop test
 constexpr int kFirstGroups = 7;       // digit groups of the first tail residual (orders below 2048)
 constexpr int kNextGroups = 8;        // ... and of the next ones while rho^2 > 1e3 tol
-// digit groups of a correction Q - (X - Xprev) A after an exact residual of
-// rho: the fewest (at least 5) whose truncation, about rho 2^(-7 (q + 1)) a c
-// with a = ||A|| ||X|| / p up to 1e4 and c up to ~300 (the row-scaling
-// constant measured for the update's product), is below 1% of tol (for
-// tol = 1e-10: 5 groups, 21 pairs, up to rho = 1e-6; 6 up to 1e-4)
-inline int corr_groups(double rho, double tol) {
-  int q = 5;
-  while (q < OZ_QMAX && rho * std::ldexp(1.0, -7 * (q + 1)) * 3e6 > 1e-2 * tol) ++q;
-  return q;
-}
 constexpr int kWDigitsA = 5, kWDigitsB = 4, kWGroups = 4;   // W = A_I^{-1} A_{I,:}: 34-bit x 27-bit digits
 
 __device__ __forceinline__ int pick(const int* sel, int i) { return sel ? sel[i] : i; }
@@ -1131,7 +1121,7 @@ ibmi_status DevGroup::run(const BatchMat* mats, int nrun, const ibmi_batch_opts&
         m.act = T_STEP;
         const double rho_hat = rho * rho;
         m.corr = m.exact;
-        m.next_q = m.corr ? corr_groups(rho, tol)
+        m.next_q = m.corr ? tail::correction_groups(rho, tol, OZ_QMAX)
                           : (rho_hat <= tol ? OZ_QMAX : (rho * rho > 1e3 * tol ? kNextGroups : OZ_QMAX));
       }
     }

@@ -74,6 +74,19 @@ inline int residual_groups(double t, double g, int qc, double amp, int qlo, int 
   return qhi;
 }
 
+// digit groups of a correction Q - (X - Xprev) A after an exact residual of
+// rho, for a schedule without measured group norms (the batched tail): the
+// fewest, at least kCorrectionGroups and at most qmax, whose truncation,
+// about rho 2^(-7 (q + 1)) a c with a = ||A|| ||X|| / p up to 1e4 and c up
+// to ~300 (the row-scaling constant measured for the update's product), is
+// below kExactFraction of tol (tol = 1e-10: 5 groups, 21 pairs, up to
+// rho = 1e-6; 6 up to 1e-4)
+inline int correction_groups(double rho, double tol, int qmax) {
+  int q = kCorrectionGroups;
+  while (q < qmax && rho * std::ldexp(1.0, -7 * (q + 1)) * 3e6 > kExactFraction * tol) ++q;
+  return q;
+}
+
 // groups of the update from a residual rho: qfull - 1 where its floor fits the
 // step's target, else qfull
 inline int update_groups(double rho, double amp, double tol, int qfull) {

@@ -33,6 +33,8 @@ int main() {
       std::printf("%d\n", residual_groups(t, g, qc, a, lo, hi)); }
     else if (!std::strcmp(c, "UG")) { double r, a, t; int qf; std::scanf("%lf %lf %lf %d", &r, &a, &t, &qf);
       std::printf("%d\n", update_groups(r, a, t, qf)); }
+    else if (!std::strcmp(c, "CG")) { double r, t; int qm; std::scanf("%lf %lf %d", &r, &t, &qm);
+      std::printf("%d\n", correction_groups(r, t, qm)); }
   }
   return 0;
 }
@@ -241,3 +243,20 @@ def test_update_floor_model_is_conservative_at_small_order(plan):
                 U, _ = _product(DX, ex, DQ, eq, qu)
                 floor = np.linalg.norm(np.eye(p) - A @ (X + 0.5 * (U + U.T)) - E_exact) / math.sqrt(p)
                 assert floor <= plan(f"UF {qu} {float(rho)!r} {float(amp)!r}")[0], (name, eps, qu)
+
+
+def test_correction_groups(plan):
+    """The batched tail's correction groups: the fewest (at least 5) with
+    rho 2^(-7(q+1)) 3e6 <= 1e-2 tol, from the definition, and never more
+    than the cap."""
+    def ref(r, t, qm):
+        q = 5
+        while q < qm and r * 2.0 ** (-7 * (q + 1)) * 3e6 > 1e-2 * t:
+            q += 1
+        return q
+    cases = [(1e-9, 1e-10), (1e-6, 1e-10), (1.1e-6, 1e-10), (1e-4, 1e-10), (3e-4, 1e-10), (1e-2, 1e-10),
+             (1e-6, 1e-12), (0.5, 1e-14), (1e-8, 1e-6)]
+    got = plan(*[f"CG {r} {t} 9" for r, t in cases])
+    assert got == [ref(r, t, 9) for r, t in cases]
+    assert got[1] == 5 and got[3] == 6 and got[7] == 9   # 21 pairs up to rho = 1e-6 at tol 1e-10; capped
+    assert plan("CG 1e-2 1e-10 6") == [6]
