@@ -364,6 +364,26 @@ def measure_c3(ibmi, lib, local, steps=2):
     clk = clocks.stop()
     launches = lib.ibmi_launch_count() - l0
     s, r = res[-1]
+    # one more solve with the library's per-class events: the tensor-pipe
+    # rate of the sweep products at these shapes (5120-row sets fill the GPU)
+    import ctypes as C
+    lib.ibmi_prof_enable(1)
+    ibmi.ibmi_invert(plan, dA, dH, stream=stream)
+    torch.cuda.synchronize()
+    peak = measured_peaks()["bf16_sustained"]
+    classes = {}
+    for kc, name in enumerate(CLASSES):
+        n, t, f, a = C.c_int64(), C.c_double(), C.c_double(), C.c_double()
+        lib.ibmi_prof_get(kc, C.byref(n), C.byref(t), C.byref(f))
+        lib.ibmi_prof_get_alg(kc, C.byref(a))
+        if n.value == 0:
+            continue
+        tf = f.value / (t.value / 1000.0) / 1e12 if t.value > 0 else 0.0
+        classes[name] = {"launches": n.value, "ms": round(t.value, 3), "tflops": round(tf, 2),
+                         "tflops_algorithmic": round(a.value / (t.value / 1000.0) / 1e12, 2) if t.value > 0 else 0.0}
+        if name in ("sweep_x", "sweep_s", "residual", "newton_schulz", "invariants_tc"):
+            classes[name]["frac_of_bf16_sustained"] = round(tf / peak, 3)
+    lib.ibmi_prof_enable(0)
     plan.close()
     # the same solve from the identity (the paper's default start), once
     ident = None
@@ -403,7 +423,8 @@ def measure_c3(ibmi, lib, local, steps=2):
             "value": 1000.0 / ms, "unit": "inverses/s", "ms_per_inverse": ms, "steps": steps, "warmup": 1,
             "status": s, "sweeps": r["sweeps"], "ns_steps": r["ns_steps"], "resid_f": r["resid_f"],
             "achieved_tflops_algorithmic": r["flops"] / (ms / 1000.0) / 1e12,
-            "gpu_launches_per_inverse": launches / steps, "identity_start": ident, "fp64_gpu": fp64, "clocks": clk,
+            "gpu_launches_per_inverse": launches / steps, "classes_instrumented": classes,
+            "identity_start": ident, "fp64_gpu": fp64, "clocks": clk,
             "dtype": "bf16 (tcgen05 split/digit-sliced) + f64"}
 
 

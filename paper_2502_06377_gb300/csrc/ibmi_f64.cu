@@ -152,9 +152,9 @@ ibmi_status invariants_all(ibmi_plan_s* P, const double* A, int64_t lda, bool fu
   double* Lw = P->bat_L;
   double* R = P->bat_R;
   double flops = 0.0;
-  for (int k = 0; k < K; ++k) {
-    const double m = (double)(P->hi[k] - P->lo[k]);
-    flops += m * m * m / 3.0 + 2.0 * m * m * (full_w ? (double)p : m);
+  for (int k = 0; k < K; ++k) {   // Cholesky m^3/3; then the two solves for W (2 m^2 p), or L^{-1}
+    const double m = (double)(P->hi[k] - P->lo[k]);   // (m^3/3) and, unless left to the caller, Y^T Y (m^3/3)
+    flops += m * m * m / 3.0 + (full_w ? 2.0 * m * m * (double)p : m * m * m / 3.0 * (leave_y ? 1.0 : 2.0));
   }
   ProfScope ps(IBMI_K_INVARIANTS, st, flops);
   const GapMap id{0, 0};
@@ -201,9 +201,11 @@ ibmi_status invariants_all(ibmi_plan_s* P, const double* A, int64_t lda, bool fu
       }
     }
     if (J1 < mmax)
-      for (int k = 0; k < K; ++k)
+      for (int k = 0; k < K; ++k) {
         IBMI_TRY(refine_syrk_sub(tc, Lw + k * zL + J1 * mmax + J0, mmax, mmax - J1, J1 - J0,
                                  Lw + k * zL + J1 * mmax + J1, mmax, st));
+        ps.flops -= (double)(mmax - J1) * (mmax - J1) * (J1 - J0);   // counted by its own (tensor) class
+      }
   }
   // R <- L^{-T} L^{-1} R (full_w); A_I^{-1} = L^{-T} L^{-1} otherwise
   note_launch();
@@ -241,9 +243,11 @@ ibmi_status invariants_all(ibmi_plan_s* P, const double* A, int64_t lda, bool fu
       }
     }
     if (J1 < mmax)
-      for (int k = 0; k < K; ++k)
+      for (int k = 0; k < K; ++k) {
         IBMI_TRY(refine_gemm_sub(tc, Lw + k * zL + J1 * mmax + J0, mmax, mmax - J1, J1 - J0, R + k * zR + J0 * ncols,
                                  ncols, J1, R + k * zR + J1 * ncols, ncols, st));
+        ps.flops -= 2.0 * (double)(mmax - J1) * J1 * (J1 - J0);   // counted by its own (tensor) class
+      }
   }
   double* X = R;   // the solutions
   if (full_w) {
