@@ -218,6 +218,22 @@ def test_mixed_not_spd_reported_like_oracle(ibmi):
     assert res["bad_block"] == ref.bad_block and res["bad_pivot"] == ref.bad_pivot
 
 
+@pytest.mark.parametrize("pivot", [300, 1900])
+def test_mixed_not_spd_large_blocks_reported_like_oracle(ibmi, pivot):
+    """Blocks of order >= 1024 factorise with tensor-core updates: a negative
+    pivot is still found, in the first block column (300) or after several
+    tensor-core updates (1900 in the second block), at the oracle's block and
+    pivot."""
+    p, K, h = 2400, 2, 16
+    A = wl.random_spd(p, 66, 1.0, 1e2)
+    A[pivot, pivot] = -5.0
+    s, res, _ = run(ibmi, A, K=K, h=h, tol=1e-10, ns_theta=0.9)
+    sets = O.partition(p, K, h)
+    ref = O.ibmi(A, sets, tol=1e-10, max_sweeps=1)
+    assert s == ibmi.IBMI_ERR_NOT_SPD and ref.status == "not_spd"
+    assert res["bad_block"] == ref.bad_block and res["bad_pivot"] == ref.bad_pivot, (res, ref.bad_block, ref.bad_pivot)
+
+
 def test_mixed_nonfinite_reported(ibmi):
     """A NaN outside every diagonal block reaches H through W and the sweeps
     and is reported as IBMI_ERR_NONFINITE (never as a converged result)."""
