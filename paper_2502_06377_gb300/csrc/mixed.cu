@@ -790,7 +790,7 @@ ibmi_status mixed_run(ibmi_plan_s* P, const double* A, int64_t lda, double* H, i
       prev_floor = planned ? tail::residual_floor(qc, g, qc, amp) + tail::update_floor(qu, rho, amp) : 0.0;
       prev = rho;
       IBMI_TRY(graph_or_run(M, &M->g_update[(qu == NS_S - 1 ? 0 : 1) + (corrected ? 2 : 0)], st,
-                            [&]() { return refine_ns_update(R, H, ldh, st, qu, M->Xprev, corrected); }));
+                            [&]() { return refine_ns_update(R, H, ldh, st, qu, M->Xprev, corrected, true); }));
       *flops += fr * tail::pairs(qu, NS_S, NS_S) / tail::pairs(NS_S - 1, NS_S, NS_S);
       res->ns_steps = s + 1;
     }

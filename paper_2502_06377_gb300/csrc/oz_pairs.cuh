@@ -46,9 +46,38 @@ struct OzPairArgs {
   // Optional per-problem digit-group ranges (indexed like bsel): the tiles of
   // problem i take only the pairs with qr[i].x <= q <= qr[i].y.
   const int2* qr;
-  // Symmetric result (M == N): tiles entirely above the diagonal are skipped.
+  // Symmetric result (M == N): only the tiles that reach the diagonal or below
+  // it are units, `tiles` of them (oz_lower_tiles), row by row.
   int lower;
 };
+
+// Tiles of row mt of a lower launch: those whose first column is at most the
+// row tile's last row.
+inline __host__ __device__ int oz_lower_row_tiles(int mt, int grid_n, int bn) {
+  const int n = ((mt + 1) * BM + bn - 1) / bn;
+  return n < grid_n ? n : grid_n;
+}
+inline int oz_lower_tiles(int grid_m, int grid_n, int bn) {
+  int n = 0;
+  for (int mt = 0; mt < grid_m; ++mt) n += oz_lower_row_tiles(mt, grid_n, bn);
+  return n;
+}
+
+// Output tile (mt, ntl) of tile index tl of a problem.
+template <int BN>
+__device__ __forceinline__ void oz_tile(const OzPairArgs& g, int tl, int& mt, int& ntl) {
+  if (!g.lower) {
+    mt = tl / g.grid_n;
+    ntl = tl - mt * g.grid_n;
+    return;
+  }
+  mt = 0;
+  for (int n = oz_lower_row_tiles(0, g.grid_n, BN); tl >= n; n = oz_lower_row_tiles(mt, g.grid_n, BN)) {
+    tl -= n;
+    ++mt;
+  }
+  ntl = tl;
+}
 
 // Splits the pair list (in group order) into segments: a pair's product,
 // summed over one K chunk of kc = min(K, 4096) terms, is an integer below
@@ -69,16 +98,11 @@ inline void oz_make_segments(OzPairArgs& g) {
   }
 }
 
-// Whether unit tt (tile tl of the problem at position bi) takes pair pi: the
-// problem's digit-group range, and with `lower` only tiles that reach the
-// diagonal or below it.  The same test in all three roles.
+// Whether unit tt (a tile of the problem at position bi) takes pair pi: the
+// problem's digit-group range.  The same test in all three roles.
 template <int BN>
 __device__ __forceinline__ bool oz_pair_on(const OzPairArgs& g, int tt, int pi) {
   const int bi = tt / g.tiles;
-  if (g.lower) {
-    const int tl = tt - bi * g.tiles, mt = tl / g.grid_n, ntl = tl - mt * g.grid_n;
-    if ((int64_t)ntl * BN >= (int64_t)(mt + 1) * BM) return false;
-  }
   if (!g.qr) return true;
   const int2 r = g.qr[bi];
   return g.q[pi] >= r.x && g.q[pi] <= r.y;
@@ -130,7 +154,8 @@ __global__ void __launch_bounds__(THREADS, Cfg<1, BN>::CTAS_PER_SM) k_oz_pairs(c
             const int p0 = g.seg0[sg];
             if (!oz_pair_on<BN>(g, tt, p0)) continue;
             const int bb = g.bsel ? g.bsel[bi] : bi;
-            const int mt = tl / g.grid_n, ntl = tl - mt * g.grid_n;
+            int mt, ntl;
+            oz_tile<BN>(g, tl, mt, ntl);
             const int kb = ci * g.chunk, nk = min(g.chunk, g.kt_total - kb);
             for (int j = 0; ok && j < g.segn[sg]; ++j) {
               const CUtensorMap* ma = &maps.a[g.s[p0 + j]];
@@ -209,7 +234,8 @@ __global__ void __launch_bounds__(THREADS, Cfg<1, BN>::CTAS_PER_SM) k_oz_pairs(c
           const int bi = tt / g.tiles, tl = tt - bi * g.tiles;
           if (!oz_pair_on<BN>(g, tt, pi)) continue;
           const int bb = g.bsel ? g.bsel[bi] : bi;
-          const int mt = tl / g.grid_n, ntl = tl - mt * g.grid_n;
+          int mt, ntl;
+          oz_tile<BN>(g, tl, mt, ntl);
           const int buf = local & 1;
           const uint32_t use = (uint32_t)(local >> 1);
           if (!mbar_wait(&accf[buf], use & 1u, g.err)) { ok = false; break; }

@@ -271,6 +271,31 @@ __global__ void k_oz_update(const int* T, int64_t p, int64_t ldp, const int* ex,
   }
 }
 
+// The update of a symmetric X from the lower tiles of the product: X Q^T =
+// X - X A X is symmetric, so X[i][j] + (X Q^T)[i][j] (j <= i) is written at
+// (i, j) and (j, i), in place (one block per tile on or below the diagonal
+// reads its elements before writing the mirror tile, which no block reads).
+__global__ void k_oz_update_lower(const int* T, int64_t p, int64_t ldp, const int* ex, const int* eq, int qmax,
+                                  double* X, int64_t ldx) {
+  if (blockIdx.x > blockIdx.y) return;
+  __shared__ double t[32][33];
+  const int64_t I0 = (int64_t)blockIdx.y * 32, J0 = (int64_t)blockIdx.x * 32;
+  const int tx = threadIdx.x;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int64_t i = I0 + r, j = J0 + tx;
+    if (i < p && j <= i) {
+      const double v = X[i * ldx + j] + oz_value(T, p * ldp, i * ldp + j, qmax, ex[i] + eq[j] - 12);
+      t[r][tx] = v;
+      X[i * ldx + j] = v;
+    }
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int64_t j = J0 + r, i = I0 + tx;   // element (j, i), the mirror of (i, j) with j < i
+    if (i < p && j < i) X[j * ldx + i] = t[tx][r];
+  }
+}
+
 // X = (Xn + Xn^T) / 2 by 32 x 32 tiles through shared memory (both the tile
 // and its mirror read row-wise).
 __global__ void k_sym_into(const double* Xn, int64_t p, double* X, int64_t ldx) {
@@ -509,7 +534,7 @@ static ibmi_status digit_gemm(RefineState* R, DigitGemm g, cudaStream_t st) {
 // one persistent launch (k_oz_pairs), in group order so that the first pair of
 // each group stores and the others add (groups below qmin are left as they are).
 static ibmi_status pair_products(RefineState* R, const CUtensorMap* ma, int nsa, const CUtensorMap* mb, int nsb,
-                                 int qmax, int kclass, cudaStream_t st, int qmin = 0) {
+                                 int qmax, int kclass, cudaStream_t st, int qmin = 0, int lower = 0) {
   const int64_t p = R->p, ldp = R->ldp;
   tc::OzPairMaps maps;
   for (int s = 0; s < nsa; ++s) maps.a[s] = ma[s];
@@ -540,6 +565,8 @@ static ibmi_status pair_products(RefineState* R, const CUtensorMap* ma, int nsa,
   g.M = p;
   g.N = p;
   g.err = R->err;
+  g.lower = lower;
+  if (lower) g.tiles = tc::oz_lower_tiles((int)((p + 127) / 128), g.grid_n, R->bn);
   tc::oz_make_segments(g);
   // the method's share: these pairs out of all pairs of the full product
   // (52 for the residual, 15 for the Newton-Schulz update), of 2 p^3
@@ -550,8 +577,8 @@ static ibmi_status pair_products(RefineState* R, const CUtensorMap* ma, int nsa,
     return c;
   };
   const int full = kclass == IBMI_K_NS ? count_pairs(NS_S, NS_S, NS_S - 1) : count_pairs(OZ_SX, OZ_SA, OZ_QMAX);
-  ProfScope ps(kclass, st, 2.0 * n * (double)p * p * (double)g.kt_total * tc::BK,
-               2.0 * (double)p * p * p * n / full);
+  ProfScope ps(kclass, st, (lower ? 1.0 : 2.0) * n * (double)p * p * (double)g.kt_total * tc::BK,
+               (lower ? 1.0 : 2.0) * (double)p * p * p * n / full);
   return with_bn(R, [&](auto bn) -> ibmi_status {
     IBMI_CUDA_TRY(tc::launch_oz_pairs<decltype(bn)::value>(maps, g, st));
     return IBMI_OK;
@@ -840,6 +867,7 @@ ibmi_status refine_syrk_sub(RefineState* R, const double* L, int64_t ldl, int64_
   g.N = M;
   g.err = R->err;
   g.lower = 1;
+  g.tiles = tc::oz_lower_tiles((int)((M + 127) / 128), g.grid_n, R->bn);
   tc::oz_make_segments(g);
   {
     ProfScope ps(IBMI_K_INVARIANTS_TC, st, (double)n * M * M * (double)nb, (double)M * M * nb);
@@ -1022,7 +1050,7 @@ ibmi_status refine_residual_correct_extend_launch(RefineState* R, cudaStream_t s
 }
 
 ibmi_status refine_ns_update(RefineState* R, double* X, int64_t ldx, cudaStream_t st, int qmax, double* backup,
-                             bool reslice_x) {
+                             bool reslice_x, bool symmetric_x) {
   const int64_t p = R->p, ldp = R->ldp;
   if (qmax < 0 || qmax > NS_S - 1) return IBMI_ERR_INVALID_ARG;
   {
@@ -1030,8 +1058,18 @@ ibmi_status refine_ns_update(RefineState* R, double* X, int64_t ldx, cudaStream_
     if (reslice_x) IBMI_TRY(slice_digits(R, X, ldx, R->Xo, NS_S, R->expX, st));
     IBMI_TRY(slice_digits(R, R->Q, p, R->Qo, NS_S, R->expQ, st));
   }
-  IBMI_TRY(pair_products(R, R->mXo, NS_S, R->mQo, NS_S, qmax, IBMI_K_NS, st));
+  IBMI_TRY(pair_products(R, R->mXo, NS_S, R->mQo, NS_S, qmax, IBMI_K_NS, st, 0, symmetric_x ? 1 : 0));
   ProfScope ps(IBMI_K_OTHER, st, 0.0);
+  if (symmetric_x) {
+    if (backup)
+      IBMI_CUDA_TRY(cudaMemcpy2DAsync(backup, sizeof(double) * p, X, sizeof(double) * ldx, sizeof(double) * p, p,
+                                      cudaMemcpyDeviceToDevice, st));
+    note_launch();
+    const unsigned nt = (unsigned)((p + 31) / 32);
+    k_oz_update_lower<<<dim3(nt, nt), dim3(32, 8), 0, st>>>(R->T, p, ldp, R->expX, R->expQ, qmax, X, ldx);
+    IBMI_CUDA_TRY(cudaGetLastError());
+    return IBMI_OK;
+  }
   note_launch();
   k_oz_update<<<grid2((p + 3) / 4, p), 256, 0, st>>>(R->T, p, ldp, R->expX, R->expQ, qmax, X, ldx, R->Xn);
   IBMI_CUDA_TRY(cudaGetLastError());

@@ -79,8 +79,12 @@ ibmi_status refine_residual(RefineState* R, const double* X, int64_t ldx, cudaSt
 // Must follow a residual of the same X: a direct one leaves the digits of X
 // the update uses, after a correction (below) reslice_x slices them first.
 // backup (p x p, row pitch p), if given, receives X before the update.
+// symmetric_x (X exactly symmetric, as every iterate of the mixed path): X Q^T
+// = X - X A X is symmetric, so only the product's tiles on and below the
+// diagonal are formed (half the pair products) and mirrored; else the whole
+// product is formed and X + X Q^T symmetrised.
 ibmi_status refine_ns_update(RefineState* R, double* X, int64_t ldx, cudaStream_t st, int qmax = NS_S - 1,
-                             double* backup = nullptr, bool reslice_x = false);
+                             double* backup = nullptr, bool reslice_x = false, bool symmetric_x = false);
 
 // W = A_I^{-1} A_{I,:} (m x p, zero columns on I) from exact digit products
 // (five digits of A_I^{-1}, four of A), written as three BF16 slices with
