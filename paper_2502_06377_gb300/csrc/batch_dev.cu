@@ -318,62 +318,40 @@ __global__ void k_b_combine(const int* sel, const int* T, int64_t plane, int64_t
   }
 }
 
-// Newton-Schulz update of matrix sel[z] in place: X = X + 2^{e_i + g_j - 12}
-// sum T_q 2^{-7q} (unsymmetrised; Q, whose digits were taken, stays), and
-// Xprev = X before it.
-__global__ void k_b_update(const int* sel, const int* T, int64_t plane, int64_t pb, int64_t ldp, const int* ex,
-                           const int* eq, int qmax, double* X64, double* Xprev) {
-  // four consecutive columns per thread (as k_b_combine)
-  const int64_t b = pick(sel, blockIdx.z), i = blockIdx.y, j0 = 4 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
-  if (j0 >= pb) return;
-  const int* Tb = T + b * pb * ldp + i * ldp + j0;
-  int4 t4[10];
-#pragma unroll
-  for (int q = 0; q < 10; ++q) t4[q] = q <= qmax ? *reinterpret_cast<const int4*>(Tb + q * plane) : make_int4(0, 0, 0, 0);
-  const int exi = ex[b * pb + i] - 12;
-#pragma unroll
-  for (int c4 = 0; c4 < 4; ++c4) {
-    const int64_t j = j0 + c4;
-    if (j >= pb) break;
-    int t[10];
-#pragma unroll
-    for (int q = 0; q < 10; ++q) t[q] = c4 == 0 ? t4[q].x : (c4 == 1 ? t4[q].y : (c4 == 2 ? t4[q].z : t4[q].w));
-    const int64_t o = (b * pb + i) * pb + j;
-    const double x = X64[o];
-    Xprev[o] = x;
-    X64[o] = x + oz_groups_value(t, exi + eq[b * pb + j]);
-  }
-}
-
-// X64[b] <- (X64 + X64^T) / 2 in place, one block per pair of mirror 32 x 32
-// tiles (I >= J; the block reads both before writing either), and
-// D[b] <- X64_new - D[b] with D holding the iterate before the update: the
-// step's difference, which a correction of the residual slices.
-__global__ void k_b_symfull(const int* sel, int64_t pb, double* X64, double* D) {
+// Newton-Schulz update of the symmetric X of matrix sel[z] from the lower
+// tiles of X Q^T (symmetric: X - X A X), in place: for j <= i,
+// X[i][j] + 2^{e_i + g_j - 12} sum T_q 2^{-7q} goes to (i, j) and (j, i), and
+// D <- the step's difference at both (the correction of the next residual
+// slices it).  One block per tile on or below the diagonal; it reads its
+// elements before writing the mirror tile, which no block reads.
+__global__ void k_b_update_lower(const int* sel, const int* T, int64_t plane, int64_t pb, int64_t ldp, const int* ex,
+                                 const int* eq, int qmax, double* X64, double* D) {
   if (blockIdx.x > blockIdx.y) return;
-  __shared__ double a[32][33], c[32][33];
+  __shared__ double tv[32][33], td[32][33];
   const int64_t b = pick(sel, blockIdx.z);
   double* X = X64 + b * pb * pb;
   double* Dm = D + b * pb * pb;
-  const int64_t I0 = (int64_t)(blockIdx.y) * 32, J0 = (int64_t)blockIdx.x * 32;
+  const int* Tb = T + b * pb * ldp;
+  const int64_t I0 = (int64_t)blockIdx.y * 32, J0 = (int64_t)blockIdx.x * 32;
   const int tx = threadIdx.x;
   for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-    a[r][tx] = (I0 + r < pb && J0 + tx < pb) ? X[(I0 + r) * pb + J0 + tx] : 0.0;
-    c[r][tx] = (J0 + r < pb && I0 + tx < pb) ? X[(J0 + r) * pb + I0 + tx] : 0.0;
+    const int64_t i = I0 + r, j = J0 + tx;
+    if (i < pb && j <= i) {
+      const double xo = X[i * pb + j];
+      const double v = xo + oz_value(Tb, plane, i * ldp + j, qmax, ex[b * pb + i] + eq[b * pb + j] - 12);
+      const double d = v - xo;
+      tv[r][tx] = v;
+      td[r][tx] = d;
+      X[i * pb + j] = v;
+      Dm[i * pb + j] = d;
+    }
   }
   __syncthreads();
   for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-    if (I0 + r < pb && J0 + tx < pb) {
-      const int64_t o = (I0 + r) * pb + J0 + tx;
-      const double v = 0.5 * (a[r][tx] + c[tx][r]);
-      Dm[o] = v - Dm[o];
-      X[o] = v;
-    }
-    if (I0 != J0 && J0 + r < pb && I0 + tx < pb) {
-      const int64_t o = (J0 + r) * pb + I0 + tx;
-      const double v = 0.5 * (c[r][tx] + a[tx][r]);
-      Dm[o] = v - Dm[o];
-      X[o] = v;
+    const int64_t j = J0 + r, i = I0 + tx;   // (j, i), the mirror of (i, j) with j < i
+    if (i < pb && j < i) {
+      X[j * pb + i] = tv[tx][r];
+      Dm[j * pb + i] = td[tx][r];
     }
   }
 }
@@ -939,7 +917,7 @@ ibmi_status DevGroup::run(const BatchMat* mats, int nrun, const ibmi_batch_opts&
       IBMI_CUDA_TRY(cudaGetLastError());
     }
     auto pairs = [&](const CUtensorMap* ma, int nsa, const CUtensorMap* mb, int nsb, int qmin, int qmax, int* dl,
-                     int nl, int kclass, double alg, const int2* qr) -> ibmi_status {
+                     int nl, int kclass, double alg, const int2* qr, int lower = 0) -> ibmi_status {
       tc::OzPairMaps maps;
       for (int s = 0; s < nsa; ++s) maps.a[s] = ma[s];
       for (int u = 0; u < nsb; ++u) maps.b[u] = mb[u];
@@ -973,8 +951,10 @@ ibmi_status DevGroup::run(const BatchMat* mats, int nrun, const ibmi_batch_opts&
       a.bsel = dl;
       a.tstride = pl;
       a.qr = qr;
+      a.lower = lower;
+      if (lower) a.tiles = tc::oz_lower_tiles((int)((pb + 127) / 128), a.grid_n, g.bn);
       tc::oz_make_segments(a);
-      ProfScope ps(kclass, st, 2.0 * np * (double)nl * pb * pb * (double)a.kt_total * tc::BK, alg);
+      ProfScope ps(kclass, st, (lower ? 1.0 : 2.0) * np * (double)nl * pb * pb * (double)a.kt_total * tc::BK, alg);
       return with_bn(g.bn, [&](auto bnc) -> ibmi_status {
         IBMI_CUDA_TRY(tc::launch_oz_pairs<decltype(bnc)::value>(maps, a, st));
         return IBMI_OK;
@@ -994,13 +974,13 @@ ibmi_status DevGroup::run(const BatchMat* mats, int nrun, const ibmi_batch_opts&
       // after a correction the X planes hold its difference: the digits of X first
       if (!Lrx.empty()) IBMI_CUDA_TRY(slice(g.X64, g.Xo, NS_S, g.expX, dLrx, (int)Lrx.size()));
       IBMI_CUDA_TRY(slice(g.Q, g.Qo, NS_S, g.expQ, dLupd, nl));
-      IBMI_TRY(pairs(g.mXo, NS_S, g.mQo, NS_S, 0, NS_S - 1, dLupd, nl, IBMI_K_NS, nl * fr, nullptr));
+      // X Q^T = X - X A X is symmetric (X is): its lower tiles only, mirrored
+      IBMI_TRY(pairs(g.mXo, NS_S, g.mQo, NS_S, 0, NS_S - 1, dLupd, nl, IBMI_K_NS, 0.5 * nl * fr, nullptr, 1));
       ProfScope ps(IBMI_K_OTHER, st, 0.0);
-      note_launch(2);
-      k_b_update<<<dim3(nblk((pb + 3) / 4), (unsigned)pb, (unsigned)nl), 256, 0, st>>>(
-          dLupd, g.T, (int64_t)cap * pl, pb, ldp, g.expX, g.expQ, NS_S - 1, g.X64, g.Xprev);
+      note_launch();
       const unsigned nt = (unsigned)((pb + 31) / 32);
-      k_b_symfull<<<dim3(nt, nt, (unsigned)nl), dim3(32, 8), 0, st>>>(dLupd, pb, g.X64, g.Xprev);
+      k_b_update_lower<<<dim3(nt, nt, (unsigned)nl), dim3(32, 8), 0, st>>>(
+          dLupd, g.T, (int64_t)cap * pl, pb, ldp, g.expX, g.expQ, NS_S - 1, g.X64, g.Xprev);
       IBMI_CUDA_TRY(cudaGetLastError());
     }
     if (!Lrs.empty()) {  // residuals: fresh (groups 0..q), extended (qc+1..9) and corrections, one launch
