@@ -334,11 +334,28 @@ __global__ void k_transpose_rect(const double* B, int64_t ldb, int64_t rows, int
 }
 
 // Ainv[i][j] = 2^{e_i + e_j - 12} sum_{q <= qmax} T_q 2^{-7q} (the product Z Z^T).
+// From the group sums of the tiles on and below the diagonal (the product is
+// symmetric): element (i, j), j <= i, written at (i, j) and (j, i), by 32 x 32
+// tile pairs through shared memory.
 __global__ void k_oz_gram(const int* T, int64_t plane, int64_t ldp, int64_t m, const int* ez, int qmax,
                           double* Ainv) {
-  const int64_t i = blockIdx.y, j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= m) return;
-  Ainv[i * m + j] = oz_value(T, plane, i * ldp + j, qmax, ez[i] + ez[j] - 12);
+  if (blockIdx.x > blockIdx.y) return;
+  __shared__ double t[32][33];
+  const int64_t I0 = (int64_t)blockIdx.y * 32, J0 = (int64_t)blockIdx.x * 32;
+  const int tx = threadIdx.x;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int64_t i = I0 + r, j = J0 + tx;
+    if (i < m && j <= i) {
+      const double v = oz_value(T, plane, i * ldp + j, qmax, ez[i] + ez[j] - 12);
+      t[r][tx] = v;
+      Ainv[i * m + j] = v;
+    }
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int64_t j = J0 + r, i = I0 + tx;   // (j, i), the mirror of (i, j) with j < i
+    if (i < m && j < i) Ainv[j * m + i] = t[tx][r];
+  }
 }
 
 // Power iteration on the dense Q (p x p, row pitch p): y = Q v, one warp per row.
@@ -795,9 +812,11 @@ ibmi_status refine_block_inverse(RefineState* R, const double* Y, int64_t ldy, i
   g.M = m;
   g.N = m;
   g.err = R->err;
+  g.lower = 1;   // Y^T Y is symmetric: the tiles on and below the diagonal
+  g.tiles = tc::oz_lower_tiles((int)((m + 127) / 128), g.grid_n, R->bn);
   tc::oz_make_segments(g);
   {
-    ProfScope ps(IBMI_K_INVARIANTS_TC, st, 2.0 * n * (double)m * m * (double)g.kt_total * tc::BK,
+    ProfScope ps(IBMI_K_INVARIANTS_TC, st, 1.0 * n * (double)m * m * (double)g.kt_total * tc::BK,
                  (double)m * m * m / 3.0);   // Y^T Y with triangular Y, lower half
     IBMI_TRY(with_bn(R, [&](auto bn) -> ibmi_status {
       IBMI_CUDA_TRY(tc::launch_oz_pairs<decltype(bn)::value>(maps, g, st));
@@ -806,7 +825,8 @@ ibmi_status refine_block_inverse(RefineState* R, const double* Y, int64_t ldy, i
   }
   ProfScope ps(IBMI_K_OTHER, st, 0.0);
   note_launch();
-  k_oz_gram<<<grid2(m, m), 256, 0, st>>>(R->T, p * ldp, ldp, m, R->expX, QG, Ainv);
+  const unsigned nt = (unsigned)((m + 31) / 32);
+  k_oz_gram<<<dim3(nt, nt), dim3(32, 8), 0, st>>>(R->T, p * ldp, ldp, m, R->expX, QG, Ainv);
   IBMI_CUDA_TRY(cudaGetLastError());
   return IBMI_OK;
 }
