@@ -200,12 +200,11 @@ ibmi_status invariants_all(ibmi_plan_s* P, const double* A, int64_t lda, bool fu
         IBMI_CUDA_TRY((launch_gemm_f64<true, false>(op, EpiStore{panel + jb, mmax, -1.0, 1.0, zL}, st)));
       }
     }
-    if (J1 < mmax)
-      for (int k = 0; k < K; ++k) {
-        IBMI_TRY(refine_syrk_sub(tc, Lw + k * zL + J1 * mmax + J0, mmax, mmax - J1, J1 - J0,
-                                 Lw + k * zL + J1 * mmax + J1, mmax, st));
-        ps.flops -= (double)(mmax - J1) * (mmax - J1) * (J1 - J0);   // counted by its own (tensor) class
-      }
+    if (J1 < mmax) {   // all K blocks at once
+      IBMI_TRY(refine_syrk_sub(tc, Lw + J1 * mmax + J0, mmax, zL, mmax - J1, J1 - J0, Lw + J1 * mmax + J1, mmax, zL,
+                               K, st));
+      ps.flops -= (double)K * (mmax - J1) * (mmax - J1) * (J1 - J0);   // counted by its own (tensor) class
+    }
   }
   // R <- L^{-T} L^{-1} R (full_w); A_I^{-1} = L^{-T} L^{-1} otherwise
   note_launch();
@@ -242,12 +241,11 @@ ibmi_status invariants_all(ibmi_plan_s* P, const double* A, int64_t lda, bool fu
         IBMI_CUDA_TRY((launch_gemm_f64<true, true>(op, EpiStore{R + (j0 + jb) * ncols, ncols, -1.0, 1.0, zR}, st)));
       }
     }
-    if (J1 < mmax)
-      for (int k = 0; k < K; ++k) {
-        IBMI_TRY(refine_gemm_sub(tc, Lw + k * zL + J1 * mmax + J0, mmax, mmax - J1, J1 - J0, R + k * zR + J0 * ncols,
-                                 ncols, J1, R + k * zR + J1 * ncols, ncols, st));
-        ps.flops -= 2.0 * (double)(mmax - J1) * J1 * (J1 - J0);   // counted by its own (tensor) class
-      }
+    if (J1 < mmax) {   // all K blocks at once
+      IBMI_TRY(refine_gemm_sub(tc, Lw + J1 * mmax + J0, mmax, zL, mmax - J1, J1 - J0, R + J0 * ncols, ncols, zR, J1,
+                               R + J1 * ncols, ncols, zR, K, st));
+      ps.flops -= 2.0 * (double)K * (mmax - J1) * J1 * (J1 - J0);   // counted by its own (tensor) class
+    }
   }
   double* X = R;   // the solutions
   if (full_w) {

@@ -70,7 +70,7 @@ constexpr int kNsFixedFirst = 7;            // below kEarlyMinOrder: groups of t
 constexpr int kNsFixedNext = 8;             // ... and of the next ones while rho^2 > 1e3 tol
 constexpr double kEarlyHandOver = 0.6;      // radius below which slow sweeps hand over early
 constexpr int64_t kEarlyMinOrder = 2048;    // smallest order for that test
-constexpr int64_t kTcInverseMinOrder = 1024;   // block order from which Y^T Y runs on the tensor cores
+constexpr int64_t kTcInverseMinOrder = 512;    // block order from which Y^T Y runs on the tensor cores
 constexpr double kRadiusHandOver = 0.5;     // hand over to Newton-Schulz below this radius
 
 // One captured phase: the executable graph and its kernel-node count (added
@@ -500,10 +500,8 @@ ibmi_status mixed_run(ibmi_plan_s* P, const double* A, int64_t lda, double* H, i
     // on the tensor cores instead of the FP64 product, which dominates there
     const bool tc_inverse = P->mmax >= kTcInverseMinOrder;
     IBMI_TRY(invariants_all(P, A, lda, false, st, tc_inverse, R));
-    if (tc_inverse)
-      for (int k = 0; k < K; ++k)
-        IBMI_TRY(refine_block_inverse(R, P->bat_R + (int64_t)k * P->mmax * P->mmax, P->mmax, P->hi[k] - P->lo[k],
-                                      P->ainv[k], st));
+    if (tc_inverse)   // all sets at once
+      IBMI_TRY(refine_block_inverse_all(R, P->bat_R, P->mmax, K, P->pool, P->doff_ainv, P->dm, st));
     if (d.init == IBMI_INIT_IDENTITY) IBMI_TRY(set_identity(H, ldh, p, st));
     if (d.init == IBMI_INIT_SCHUR) IBMI_TRY(schur_guess_launch(P, A, lda, H, ldh, st, R));
     IBMI_TRY(refine_set_matrix(R, A, lda, st));

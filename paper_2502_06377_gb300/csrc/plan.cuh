@@ -73,7 +73,7 @@ constexpr int CHOL_NB = 32;
 // FP64-accurate (refine_syrk_sub); the block column itself stays DFMA.
 ibmi_status invariants_all(ibmi_plan_s* P, const double* A, int64_t lda, bool full_w, cudaStream_t st,
                            bool leave_y = false, RefineState* tc = nullptr);
-constexpr int64_t kTcCholMinOrder = 1024;   // block order from which tc applies
+constexpr int64_t kTcCholMinOrder = 512;    // block order from which tc applies
 constexpr int64_t kTcCholPanel = 256;       // block-column width of that factorisation
 
 // a3 + a4 for set k on an FP64 iterate H.

@@ -322,17 +322,6 @@ __global__ void k_transpose(const double* Y, int64_t ldy, int64_t m, double* Z) 
     if (J0 + r < m && I0 + threadIdx.x < m) Z[(J0 + r) * m + I0 + threadIdx.x] = t[threadIdx.x][r];
 }
 
-// Z = B^T for a rows x cols block B (row pitch ldb); Z row pitch rows.
-__global__ void k_transpose_rect(const double* B, int64_t ldb, int64_t rows, int64_t cols, double* Z) {
-  __shared__ double t[32][33];
-  const int64_t I0 = (int64_t)blockIdx.y * 32, J0 = (int64_t)blockIdx.x * 32;
-  for (int r = threadIdx.y; r < 32; r += blockDim.y)
-    t[r][threadIdx.x] = (I0 + r < rows && J0 + threadIdx.x < cols) ? B[(I0 + r) * ldb + J0 + threadIdx.x] : 0.0;
-  __syncthreads();
-  for (int r = threadIdx.y; r < 32; r += blockDim.y)
-    if (J0 + r < cols && I0 + threadIdx.x < rows) Z[(J0 + r) * rows + I0 + threadIdx.x] = t[threadIdx.x][r];
-}
-
 // Ainv[i][j] = 2^{e_i + e_j - 12} sum_{q <= qmax} T_q 2^{-7q} (the product Z Z^T).
 // From the group sums of the tiles on and below the diagonal (the product is
 // symmetric): element (i, j), j <= i, written at (i, j) and (j, i), by 32 x 32
@@ -831,116 +820,51 @@ ibmi_status refine_block_inverse(RefineState* R, const double* Y, int64_t ldy, i
   return IBMI_OK;
 }
 
-// C[i][j] -= 2^{e_i + e_j - 12} sum_{q <= qmax} T_q[i][j] 2^{-7q} on and below
-// the diagonal (C: M x M, row pitch ldc).
-__global__ void k_oz_syrk_sub(const int* T, int64_t plane, int64_t ldt, const int* ex, int qmax, int64_t M,
-                              double* C, int64_t ldc) {
-  const int64_t i = blockIdx.y, j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (j > i || j >= M) return;
-  C[i * ldc + j] -= oz_value(T, plane, i * ldt + j, qmax, ex[i] + ex[j] - 12);
+// Rows of nbat stacked M-row operands, row r = b M + i of the output planes
+// (row pitch ldo) from X + b zx + i ldx.
+__global__ void k_oz_slices_bat(const double* X, int64_t ldx, int64_t zx, int64_t M, int64_t ncols, int64_t ldo,
+                                SlicePtrs out, int nslices, int* expo) {
+  const int64_t r = blockIdx.x, b = r / M, i = r - b * M;
+  oz_slice_row(X + b * zx + i * ldx, r, ncols, 0, ldo, out, nslices, expo, nullptr);
 }
 
-ibmi_status refine_syrk_sub(RefineState* R, const double* L, int64_t ldl, int64_t M, int64_t nb, double* C,
-                            int64_t ldc, cudaStream_t st) {
-  constexpr int ND = 8, QG = 8;   // 56-bit digits, groups q <= 8: 43 pair products
+// Z_b = B_b^T for the rows x cols blocks B_b = B + b zb (row pitch ldb); Z_b
+// at Z + b rows cols, row pitch rows.
+__global__ void k_transpose_rect(const double* B, int64_t ldb, int64_t zb, int64_t rows, int64_t cols, double* Z) {
+  __shared__ double t[32][33];
+  const int64_t b = blockIdx.z, I0 = (int64_t)blockIdx.y * 32, J0 = (int64_t)blockIdx.x * 32;
+  const double* Bb = B + b * zb;
+  double* Zb = Z + b * rows * cols;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y)
+    t[r][threadIdx.x] = (I0 + r < rows && J0 + threadIdx.x < cols) ? Bb[(I0 + r) * ldb + J0 + threadIdx.x] : 0.0;
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y)
+    if (J0 + r < cols && I0 + threadIdx.x < rows) Zb[(J0 + r) * rows + I0 + threadIdx.x] = t[threadIdx.x][r];
+}
+
+// C_b[i][j] -= 2^{ea_i + eb_j - 12} sum_{q <= qmax} T_q[i][j] 2^{-7q} for
+// problem b = blockIdx.z (group planes at T + b tstride, exponents at
+// ea + b M, eb + b N), on and below the diagonal only with `lower`.
+__global__ void k_oz_sub_bat(const int* T, int64_t plane, int64_t ldt, int64_t tstride, const int* ea, const int* eb,
+                             int qmax, int64_t M, int64_t N, int lower, double* C, int64_t ldc, int64_t zc) {
+  const int64_t b = blockIdx.z, i = blockIdx.y, j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= M || j >= N || (lower && j > i)) return;
+  C[b * zc + i * ldc + j] -= oz_value(T + b * tstride, plane, i * ldt + j, qmax, ea[b * M + i] + eb[b * N + j] - 12);
+}
+
+// Digit pairs of groups <= QG of ND-digit operands (8 and 8 by default) for
+// nbat problems: A
+// operand rows in the X digit planes (nbat M rows), B operand rows in
+// `bplanes` (nbat N rows), both at row pitch K; sums into the group planes
+// (problem b at row b M).
+static ibmi_status pairs_bat(RefineState* R, __nv_bfloat16* const* bplanes, int64_t M, int64_t N, int64_t K,
+                             int64_t nbat, int lower, double alg, cudaStream_t st, int ND = 8, int QG = 8) {
   const int64_t p = R->p, ldp = R->ldp;
-  if (M <= 0) return IBMI_OK;
-  if (nb <= 0 || nb % tc::BK != 0 || nb > OZ_KCHUNK || M > p || M * nb > p * ldp) return IBMI_ERR_INVALID_ARG;
-  {
-    ProfScope ps(IBMI_K_OTHER, st, 0.0);
-    SlicePtrs sp{};
-    for (int d = 0; d < ND; ++d) sp.s[d] = R->Xo[d];   // M rows of nb digits at row pitch nb
-    note_launch();
-    k_oz_slices<<<(unsigned)M, 256, 0, st>>>(L, ldl, nb, 0, nb, sp, ND, R->expX, nullptr);
-    IBMI_CUDA_TRY(cudaGetLastError());
-  }
   tc::OzPairMaps maps;
   bool ok = true;
   for (int d = 0; d < ND; ++d) {
-    ok &= tc::make_map_bf16(&maps.a[d], R->Xo[d], M, nb, nb, 128);
-    ok &= tc::make_map_bf16(&maps.b[d], R->Xo[d], M, nb, nb, R->bn);
-  }
-  if (!ok) return IBMI_ERR_CUDA;
-  tc::OzPairArgs g{};
-  int n = 0;
-  for (int q = 0; q <= QG; ++q) {
-    bool first = true;
-    for (int a = 0; a <= q; ++a) {
-      if (a >= ND || q - a >= ND) continue;
-      g.s[n] = (int8_t)a;
-      g.u[n] = (int8_t)(q - a);
-      g.q[n] = (int8_t)q;
-      g.first[n] = first ? 1 : 0;
-      first = false;
-      ++n;
-    }
-  }
-  g.n = n;
-  g.grid_n = (int)((M + R->bn - 1) / R->bn);
-  g.tiles = g.grid_n * (int)((M + 127) / 128);
-  g.kt_total = (int)(nb / tc::BK);
-  g.chunk = OZ_KCHUNK / tc::BK;
-  g.T = R->T;
-  g.plane = p * ldp;
-  g.ldt = ldp;
-  g.M = M;
-  g.N = M;
-  g.err = R->err;
-  g.lower = 1;
-  g.tiles = tc::oz_lower_tiles((int)((M + 127) / 128), g.grid_n, R->bn);
-  tc::oz_make_segments(g);
-  {
-    ProfScope ps(IBMI_K_INVARIANTS_TC, st, (double)n * M * M * (double)nb, (double)M * M * nb);
-    IBMI_TRY(with_bn(R, [&](auto bn) -> ibmi_status {
-      IBMI_CUDA_TRY(tc::launch_oz_pairs<decltype(bn)::value>(maps, g, st));
-      return IBMI_OK;
-    }));
-  }
-  ProfScope ps(IBMI_K_OTHER, st, 0.0);
-  note_launch();
-  k_oz_syrk_sub<<<grid2(M, M), 256, 0, st>>>(R->T, p * ldp, ldp, R->expX, QG, M, C, ldc);
-  IBMI_CUDA_TRY(cudaGetLastError());
-  return IBMI_OK;
-}
-
-// C[i][j] -= 2^{ea_i + eb_j - 12} sum_{q <= qmax} T_q[i][j] 2^{-7q} (C: M x N,
-// row pitch ldc).
-__global__ void k_oz_gemm_sub(const int* T, int64_t plane, int64_t ldt, const int* ea, const int* eb, int qmax,
-                              int64_t M, int64_t N, double* C, int64_t ldc) {
-  const int64_t i = blockIdx.y, j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= M || j >= N) return;
-  C[i * ldc + j] -= oz_value(T, plane, i * ldt + j, qmax, ea[i] + eb[j] - 12);
-}
-
-ibmi_status refine_gemm_sub(RefineState* R, const double* A, int64_t lda, int64_t M, int64_t K, const double* B,
-                            int64_t ldb, int64_t N, double* C, int64_t ldc, cudaStream_t st) {
-  constexpr int ND = 8, QG = 8;   // as refine_syrk_sub
-  const int64_t p = R->p, ldp = R->ldp;
-  if (M <= 0 || N <= 0) return IBMI_OK;
-  if (K <= 0 || K % tc::BK != 0 || K > OZ_KCHUNK || M > p || N > p || M * K > p * ldp || N * K > p * ldp)
-    return IBMI_ERR_INVALID_ARG;
-  {
-    ProfScope ps(IBMI_K_OTHER, st, 0.0);
-    note_launch(3);
-    // B^T (N x K, row pitch K) into the FP64 scratch, then the rows of A into
-    // the X digit planes and the rows of B^T into the A digit planes (both at
-    // row pitch K)
-    k_transpose_rect<<<dim3((unsigned)((N + 31) / 32), (unsigned)((K + 31) / 32)), dim3(32, 8), 0, st>>>(B, ldb, K, N,
-                                                                                                     R->Xn);
-    SlicePtrs sa{}, sb{};
-    for (int d = 0; d < ND; ++d) {
-      sa.s[d] = R->Xo[d];
-      sb.s[d] = R->Ao[d];
-    }
-    k_oz_slices<<<(unsigned)M, 256, 0, st>>>(A, lda, K, 0, K, sa, ND, R->expX, nullptr);
-    k_oz_slices<<<(unsigned)N, 256, 0, st>>>(R->Xn, K, K, 0, K, sb, ND, R->expQ, nullptr);
-    IBMI_CUDA_TRY(cudaGetLastError());
-  }
-  tc::OzPairMaps maps;
-  bool ok = true;
-  for (int d = 0; d < ND; ++d) {
-    ok &= tc::make_map_bf16(&maps.a[d], R->Xo[d], M, K, K, 128);
-    ok &= tc::make_map_bf16(&maps.b[d], R->Ao[d], N, K, K, R->bn);
+    ok &= tc::make_map_bf16_3d(&maps.a[d], R->Xo[d], nbat, M, K, K, 128);
+    ok &= tc::make_map_bf16_3d(&maps.b[d], bplanes[d], nbat, N, K, K, R->bn);
   }
   if (!ok) return IBMI_ERR_CUDA;
   tc::OzPairArgs g{};
@@ -959,7 +883,8 @@ ibmi_status refine_gemm_sub(RefineState* R, const double* A, int64_t lda, int64_
   }
   g.n = n;
   g.grid_n = (int)((N + R->bn - 1) / R->bn);
-  g.tiles = g.grid_n * (int)((M + 127) / 128);
+  g.lower = lower;
+  g.tiles = lower ? tc::oz_lower_tiles((int)((M + 127) / 128), g.grid_n, R->bn) : g.grid_n * (int)((M + 127) / 128);
   g.kt_total = (int)(K / tc::BK);
   g.chunk = OZ_KCHUNK / tc::BK;
   g.T = R->T;
@@ -968,18 +893,142 @@ ibmi_status refine_gemm_sub(RefineState* R, const double* A, int64_t lda, int64_
   g.M = M;
   g.N = N;
   g.err = R->err;
+  g.nb = (int)nbat;
+  g.bsel = nullptr;
+  g.tstride = M * ldp;
   tc::oz_make_segments(g);
-  {
-    ProfScope ps(IBMI_K_INVARIANTS_TC, st, 2.0 * n * (double)M * N * (double)K, 2.0 * (double)M * N * K);
-    IBMI_TRY(with_bn(R, [&](auto bn) -> ibmi_status {
-      IBMI_CUDA_TRY(tc::launch_oz_pairs<decltype(bn)::value>(maps, g, st));
-      return IBMI_OK;
-    }));
+  ProfScope ps(IBMI_K_INVARIANTS_TC, st, (lower ? 1.0 : 2.0) * n * (double)nbat * M * N * (double)K, alg);
+  return with_bn(R, [&](auto bn) -> ibmi_status {
+    IBMI_CUDA_TRY(tc::launch_oz_pairs<decltype(bn)::value>(maps, g, st));
+    return IBMI_OK;
+  });
+}
+
+// Ainv_b = 2^{e_i + e_j - 12} sum_{q <= qmax} T_q 2^{-7q} (the product Z Z^T,
+// symmetric) for problem b = blockIdx.z: its leading m_b x m_b part at
+// pool + off[b] (row pitch m_b), from the lower tiles, by 32 x 32 tile pairs.
+__global__ void k_oz_gram_bat(const int* T, int64_t plane, int64_t ldt, int64_t tstride, int64_t mp, const int* ez,
+                              int qmax, double* pool, const int64_t* off, const int64_t* dm) {
+  if (blockIdx.x > blockIdx.y) return;
+  __shared__ double t[32][33];
+  const int64_t b = blockIdx.z, m = dm[b];
+  const int* Tb = T + b * tstride;
+  const int* eb = ez + b * mp;
+  double* Ainv = pool + off[b];
+  const int64_t I0 = (int64_t)blockIdx.y * 32, J0 = (int64_t)blockIdx.x * 32;
+  const int tx = threadIdx.x;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int64_t i = I0 + r, j = J0 + tx;
+    if (i < m && j <= i) {
+      const double v = oz_value(Tb, plane, i * ldt + j, qmax, eb[i] + eb[j] - 12);
+      t[r][tx] = v;
+      Ainv[i * m + j] = v;
+    }
   }
-  ProfScope ps(IBMI_K_OTHER, st, 0.0);
-  note_launch();
-  k_oz_gemm_sub<<<grid2(N, M), 256, 0, st>>>(R->T, p * ldp, ldp, R->expX, R->expQ, QG, M, N, C, ldc);
-  IBMI_CUDA_TRY(cudaGetLastError());
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int64_t j = J0 + r, i = I0 + tx;
+    if (i < m && j < i) Ainv[j * m + i] = t[tx][r];
+  }
+}
+
+ibmi_status refine_block_inverse_all(RefineState* R, const double* Y, int64_t mmax, int64_t nbat, double* pool,
+                                     const int64_t* doff, const int64_t* dm, cudaStream_t st) {
+  constexpr int ND = 5, QG = 4;   // 34-bit digits, groups q <= 4 (15 pairs), as refine_block_inverse
+  const int64_t p = R->p, ldp = R->ldp;
+  if (mmax < 1 || mmax > p || nbat < 1) return IBMI_ERR_INVALID_ARG;
+  const int64_t kp = (mmax + tc::BK - 1) / tc::BK * tc::BK;   // K padded to whole K blocks (zero digits)
+  const int64_t per = std::max<int64_t>(1, std::min<int64_t>({nbat, p / mmax, (p * ldp) / (mmax * kp),
+                                                              (p * p) / (mmax * mmax)}));
+  for (int64_t b0 = 0; b0 < nbat; b0 += per) {
+    const int64_t nn = std::min(per, nbat - b0);
+    {
+      ProfScope ps(IBMI_K_OTHER, st, 0.0);
+      note_launch(2);
+      const unsigned nt = (unsigned)((mmax + 31) / 32);
+      k_transpose_rect<<<dim3(nt, nt, (unsigned)nn), dim3(32, 8), 0, st>>>(Y + b0 * mmax * mmax, mmax, mmax * mmax,
+                                                                            mmax, mmax, R->Xn);
+      SlicePtrs sa{};
+      for (int d = 0; d < ND; ++d) sa.s[d] = R->Xo[d];
+      k_oz_slices_bat<<<(unsigned)(nn * mmax), 256, 0, st>>>(R->Xn, mmax, mmax * mmax, mmax, mmax, kp, sa, ND,
+                                                              R->expX);
+      IBMI_CUDA_TRY(cudaGetLastError());
+    }
+    IBMI_TRY(pairs_bat(R, R->Xo, mmax, mmax, kp, nn, 1, (double)nn * mmax * mmax * mmax / 3.0, st, ND, QG));
+    ProfScope ps(IBMI_K_OTHER, st, 0.0);
+    note_launch();
+    const unsigned nt = (unsigned)((mmax + 31) / 32);
+    k_oz_gram_bat<<<dim3(nt, nt, (unsigned)nn), dim3(32, 8), 0, st>>>(R->T, p * ldp, ldp, mmax * ldp, mmax, R->expX,
+                                                                      QG, pool, doff + b0, dm + b0);
+    IBMI_CUDA_TRY(cudaGetLastError());
+  }
+  return IBMI_OK;
+}
+
+ibmi_status refine_syrk_sub(RefineState* R, const double* L, int64_t ldl, int64_t zl, int64_t M, int64_t nb,
+                            double* C, int64_t ldc, int64_t zc, int64_t nbat, cudaStream_t st) {
+  constexpr int ND = 8, QG = 8;   // 56-bit digits, groups q <= 8: 43 pair products
+  const int64_t p = R->p, ldp = R->ldp;
+  if (M <= 0 || nbat <= 0) return IBMI_OK;
+  if (nb <= 0 || nb % tc::BK != 0 || nb > OZ_KCHUNK || M > p) return IBMI_ERR_INVALID_ARG;
+  // problems per launch: their rows must fit the group planes (p rows) and
+  // the digit planes (p ldp elements)
+  const int64_t per = std::max<int64_t>(1, std::min<int64_t>({nbat, p / M, (p * ldp) / (M * nb)}));
+  for (int64_t b0 = 0; b0 < nbat; b0 += per) {
+    const int64_t nn = std::min(per, nbat - b0);
+    {
+      ProfScope ps(IBMI_K_OTHER, st, 0.0);
+      SlicePtrs sp{};
+      for (int d = 0; d < ND; ++d) sp.s[d] = R->Xo[d];
+      note_launch();
+      k_oz_slices_bat<<<(unsigned)(nn * M), 256, 0, st>>>(L + b0 * zl, ldl, zl, M, nb, nb, sp, ND, R->expX);
+      IBMI_CUDA_TRY(cudaGetLastError());
+    }
+    IBMI_TRY(pairs_bat(R, R->Xo, M, M, nb, nn, 1, (double)nn * M * M * nb, st));
+    ProfScope ps(IBMI_K_OTHER, st, 0.0);
+    note_launch();
+    k_oz_sub_bat<<<dim3((unsigned)((M + 255) / 256), (unsigned)M, (unsigned)nn), 256, 0, st>>>(
+        R->T, p * ldp, ldp, M * ldp, R->expX, R->expX, QG, M, M, 1, C + b0 * zc, ldc, zc);
+    IBMI_CUDA_TRY(cudaGetLastError());
+  }
+  return IBMI_OK;
+}
+
+ibmi_status refine_gemm_sub(RefineState* R, const double* A, int64_t lda, int64_t za, int64_t M, int64_t K,
+                            const double* B, int64_t ldb, int64_t zb, int64_t N, double* C, int64_t ldc, int64_t zc,
+                            int64_t nbat, cudaStream_t st) {
+  constexpr int ND = 8, QG = 8;   // as refine_syrk_sub
+  const int64_t p = R->p, ldp = R->ldp;
+  if (M <= 0 || N <= 0 || nbat <= 0) return IBMI_OK;
+  if (K <= 0 || K % tc::BK != 0 || K > OZ_KCHUNK || M > p || N > p) return IBMI_ERR_INVALID_ARG;
+  const int64_t mn = std::max(M, N);
+  const int64_t per = std::max<int64_t>(1, std::min<int64_t>({nbat, p / mn, (p * ldp) / (mn * K), (p * p) / (N * K)}));
+  for (int64_t b0 = 0; b0 < nbat; b0 += per) {
+    const int64_t nn = std::min(per, nbat - b0);
+    {
+      ProfScope ps(IBMI_K_OTHER, st, 0.0);
+      note_launch(3);
+      // B_b^T (N x K, row pitch K) into the FP64 scratch, then the rows of
+      // A_b into the X digit planes and the rows of B_b^T into the A digit
+      // planes (both at row pitch K)
+      k_transpose_rect<<<dim3((unsigned)((N + 31) / 32), (unsigned)((K + 31) / 32), (unsigned)nn), dim3(32, 8), 0,
+                         st>>>(B + b0 * zb, ldb, zb, K, N, R->Xn);
+      SlicePtrs sa{}, sb{};
+      for (int d = 0; d < ND; ++d) {
+        sa.s[d] = R->Xo[d];
+        sb.s[d] = R->Ao[d];
+      }
+      k_oz_slices_bat<<<(unsigned)(nn * M), 256, 0, st>>>(A + b0 * za, lda, za, M, K, K, sa, ND, R->expX);
+      k_oz_slices_bat<<<(unsigned)(nn * N), 256, 0, st>>>(R->Xn, K, N * K, N, K, K, sb, ND, R->expQ);
+      IBMI_CUDA_TRY(cudaGetLastError());
+    }
+    IBMI_TRY(pairs_bat(R, R->Ao, M, N, K, nn, 0, 2.0 * (double)nn * M * N * K, st));
+    ProfScope ps(IBMI_K_OTHER, st, 0.0);
+    note_launch();
+    k_oz_sub_bat<<<dim3((unsigned)((N + 255) / 256), (unsigned)M, (unsigned)nn), 256, 0, st>>>(
+        R->T, p * ldp, ldp, M * ldp, R->expX, R->expQ, QG, M, N, 0, C + b0 * zc, ldc, zc);
+    IBMI_CUDA_TRY(cudaGetLastError());
+  }
   return IBMI_OK;
 }
 

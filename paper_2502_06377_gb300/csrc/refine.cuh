@@ -101,24 +101,36 @@ ibmi_status refine_form_w(RefineState* R, const double* Ainv, int64_t m, int64_t
 ibmi_status refine_block_inverse(RefineState* R, const double* Y, int64_t ldy, int64_t m, double* Ainv,
                                  cudaStream_t st);
 
-// The trailing update of a blocked Cholesky step, C -= L L^T on and below the
-// diagonal (C: M x M at row pitch ldc; L: M x nb at row pitch ldl, nb a
-// multiple of 64 and at most 4096; M <= p), FP64-accurate on tensor cores:
-// the rows of L sliced into eight 7-bit digits (56 bits below each row's
-// maximum, FP64's 53 and three more), the 43 exact pair products of digit
-// groups q <= 8 on the tiles that reach the diagonal, recombined exactly and
-// subtracted in FP64.  Borrows the X digit planes and the group planes.
-ibmi_status refine_syrk_sub(RefineState* R, const double* L, int64_t ldl, int64_t M, int64_t nb, double* C,
-                            int64_t ldc, cudaStream_t st);
+// The trailing update of a blocked Cholesky step for nbat blocks, C_b -=
+// L_b L_b^T on and below the diagonal (C_b = C + b zc: M x M at row pitch
+// ldc; L_b = L + b zl: M x nb at row pitch ldl, nb a multiple of 64 and at
+// most 4096; M <= p), FP64-accurate on tensor cores: the rows of L_b sliced
+// into eight 7-bit digits (56 bits below each row's maximum, FP64's 53 and
+// three more), the 43 exact pair products of digit groups q <= 8 on the tiles
+// that reach the diagonal, for as many blocks per launch as the planes hold,
+// recombined exactly and subtracted in FP64.  Borrows the X digit planes and
+// the group planes.
+ibmi_status refine_syrk_sub(RefineState* R, const double* L, int64_t ldl, int64_t zl, int64_t M, int64_t nb,
+                            double* C, int64_t ldc, int64_t zc, int64_t nbat, cudaStream_t st);
 
-// C -= A B (C: M x N, A: M x K, B: K x N, row pitches ldc, lda, ldb; K a
-// multiple of 64 and at most 4096; M, N <= p), FP64-accurate on tensor cores
-// as refine_syrk_sub (rows of A and columns of B in eight 7-bit digits, 43
+// C_b -= A_b B_b for nbat problems (C_b = C + b zc: M x N; A_b = A + b za:
+// M x K; B_b = B + b zb: K x N; row pitches ldc, lda, ldb; K a multiple of 64
+// and at most 4096; M, N <= p), FP64-accurate on tensor cores as
+// refine_syrk_sub (rows of A_b and columns of B_b in eight 7-bit digits, 43
 // exact pair products): the trailing update of a blocked triangular solve.
 // Borrows the X and A digit planes, the FP64 scratch and the group planes:
 // only before refine_set_matrix (the factorisations of the set-up).
-ibmi_status refine_gemm_sub(RefineState* R, const double* A, int64_t lda, int64_t M, int64_t K, const double* B,
-                            int64_t ldb, int64_t N, double* C, int64_t ldc, cudaStream_t st);
+ibmi_status refine_gemm_sub(RefineState* R, const double* A, int64_t lda, int64_t za, int64_t M, int64_t K,
+                            const double* B, int64_t ldb, int64_t zb, int64_t N, double* C, int64_t ldc, int64_t zc,
+                            int64_t nbat, cudaStream_t st);
+
+// The same for the nbat blocks of a batched factorisation at once: Y_b =
+// Y + b mmax^2 (mmax x mmax, row pitch mmax, block b padded with an identity
+// beyond its order m_b = dm[b]), A_b^{-1} (m_b x m_b, row pitch m_b) to
+// pool + doff[b] (dm, doff: device arrays).  As many blocks per launch as the
+// planes hold.
+ibmi_status refine_block_inverse_all(RefineState* R, const double* Y, int64_t mmax, int64_t nbat, double* pool,
+                                     const int64_t* doff, const int64_t* dm, cudaStream_t st);
 
 // Prepares the one-pass formation of W for the sets [lo_k, hi_k): the stacked
 // view fits when 5 slots of sum_k ceil(m_k/128)*128 rows fit in the X digit
