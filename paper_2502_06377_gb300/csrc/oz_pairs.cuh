@@ -49,6 +49,11 @@ struct OzPairArgs {
   // Symmetric result (M == N): only the tiles that reach the diagonal or below
   // it are units, `tiles` of them (oz_lower_tiles), row by row.
   int lower;
+  // Optional per-128-row-tile K-tile ranges [x, y) (one problem, no lower):
+  // rows of different products stacked in one launch, each with its own K
+  // range of at most `chunk` K tiles (kt_total = the longest, for the
+  // segments' exactness bound).
+  const int2* mkr;
 };
 
 // Tiles of row mt of a lower launch: those whose first column is at most the
@@ -156,7 +161,12 @@ __global__ void __launch_bounds__(THREADS, Cfg<1, BN>::CTAS_PER_SM) k_oz_pairs(c
             const int bb = g.bsel ? g.bsel[bi] : bi;
             int mt, ntl;
             oz_tile<BN>(g, tl, mt, ntl);
-            const int kb = ci * g.chunk, nk = min(g.chunk, g.kt_total - kb);
+            int kb = ci * g.chunk, nk = min(g.chunk, g.kt_total - kb);
+            if (g.mkr) {
+              const int2 kr = g.mkr[mt];
+              kb = kr.x;
+              nk = kr.y - kr.x;
+            }
             for (int j = 0; ok && j < g.segn[sg]; ++j) {
               const CUtensorMap* ma = &maps.a[g.s[p0 + j]];
               const CUtensorMap* mb = &maps.b[g.u[p0 + j]];
@@ -196,7 +206,12 @@ __global__ void __launch_bounds__(THREADS, Cfg<1, BN>::CTAS_PER_SM) k_oz_pairs(c
         for (int ci = 0; ok && ci < nchunks; ++ci)
           for (int tt = blockIdx.x; ok && tt < total; tt += gridDim.x) {
             if (!oz_pair_on<BN>(g, tt, g.seg0[sg])) continue;
-            const int nk = min(g.chunk, g.kt_total - ci * g.chunk);
+            int nk = min(g.chunk, g.kt_total - ci * g.chunk);
+            if (g.mkr) {
+              int mt, ntl;
+              oz_tile<BN>(g, tt - (tt / g.tiles) * g.tiles, mt, ntl);
+              nk = g.mkr[mt].y - g.mkr[mt].x;
+            }
             const int buf = local & 1;
             const uint32_t use = (uint32_t)(local >> 1);
             if (!mbar_wait(&acce[buf], (use & 1u) ^ 1u, g.err)) { ok = false; break; }

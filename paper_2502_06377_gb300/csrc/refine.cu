@@ -692,26 +692,47 @@ ibmi_status refine_form_w_all(RefineState* R, const std::vector<const double*>& 
     const double m = (double)(hi[k] - lo[k]);
     alg_w += 2.0 * m * m * ((double)p - m);
   }
+  // all pair products in one persistent launch, each row tile over its set's K range
+  tc::OzPairMaps maps;
+  for (int s = 0; s < NW_A; ++s) maps.a[s] = R->mXw[s];
+  for (int u = 0; u < NW_B; ++u) maps.b[u] = R->mAo[u];
+  tc::OzPairArgs g{};
+  int n = 0;
   for (int q = 0; q <= QW; ++q) {
     bool first = true;
     for (int s = 0; s <= q; ++s) {
       const int u = q - s;
       if (s >= NW_A || u >= NW_B) continue;
-      tc::Maps maps;
-      maps.a[0] = R->mXw[s];
-      maps.b[0] = R->mAo[u];
-      tc::Tiles t{rows, 0, 0, grid_n, 0, 1 << 29, 0, 0, 1, R->err};
-      t.mkr = R->w_kr;
-      t.pdl = 1;
-      EpiOzAcc epi{{}, R->T + (int64_t)q * rows * ldp, ldp, rows, p, first ? 1 : 0};
-      ProfScope ps(IBMI_K_INVARIANTS_TC, st, flops, alg_w);
-      alg_w = 0.0;   // W's algorithmic flops go with the first pair launch
-      IBMI_TRY(with_bn(R, [&](auto bn) -> ibmi_status {
-        IBMI_CUDA_TRY((tc::launch<1, decltype(bn)::value>(maps, t, grid_n, grid_m, epi, st)));
-        return IBMI_OK;
-      }));
+      g.s[n] = (int8_t)s;
+      g.u[n] = (int8_t)u;
+      g.q[n] = (int8_t)q;
+      g.first[n] = first ? 1 : 0;
       first = false;
+      ++n;
     }
+  }
+  int kt_max = 1;
+  for (int k = 0; k < K; ++k)
+    kt_max = std::max<int>(kt_max, (int)((hi[k] + tc::BK - 1) / tc::BK - lo[k] / tc::BK));
+  g.n = n;
+  g.grid_n = grid_n;
+  g.tiles = grid_n * grid_m;
+  g.kt_total = kt_max;
+  g.chunk = OZ_KCHUNK / tc::BK;
+  g.T = R->T;
+  g.plane = rows * ldp;
+  g.ldt = ldp;
+  g.M = rows;
+  g.N = p;
+  g.err = R->err;
+  g.mkr = R->w_kr;
+  tc::oz_make_segments(g);
+  {
+    ProfScope ps(IBMI_K_INVARIANTS_TC, st, flops * n, alg_w);
+    IBMI_TRY(with_bn(R, [&](auto bn) -> ibmi_status {
+      IBMI_CUDA_TRY(tc::launch_oz_pairs<decltype(bn)::value>(maps, g, st));
+      return IBMI_OK;
+    }));
   }
   ProfScope ps(IBMI_K_OTHER, st, 0.0);
   for (int k = 0; k < K; ++k) {
