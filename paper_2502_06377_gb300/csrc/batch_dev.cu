@@ -111,25 +111,6 @@ __global__ void k_b_split2(const double* X, int64_t ldx, int64_t ncols, int64_t 
   s1[i * ldp + c] = __float2bfloat16_rn(x - __bfloat162float(h));
 }
 
-// Digit-group sums of W's digit products for matrix bat: T_q (+)= the exact
-// FP32 pair product (an integer below 2^24), 4 columns per lane.
-struct EpiBOzAcc : tc::EpiBase {
-  int* T; int64_t ldt, M, N, bstride; int first;
-  __device__ __forceinline__ void warp_tile(int64_t row0, int64_t j0, int, const float* __restrict__ stage,
-                                            int lane) const {
-    int* Tb = T + (int64_t)bat * bstride;
-    const int c = (lane & 3) * 4, r0 = lane >> 2;
-#pragma unroll
-    for (int k2 = 0; k2 < 4; ++k2) {
-      const int64_t row = row0 + 8 * k2 + r0;
-      if (row >= M) continue;
-      const float* sv = stage + (8 * k2 + r0) * 17 + c;
-      int* t0 = Tb + row * ldt + j0 + c;
-      for (int uu = 0; uu < 4 && j0 + c + uu < N; ++uu) t0[uu] = (first ? 0 : t0[uu]) + __float2int_rn(sv[uu]);
-    }
-  }
-};
-
 // W slices of set k: W = 2^{e_i + f_j - 12} sum_{q <= 4} T_q 2^{-7q} on the
 // columns of I^c, zero on I and on the padding.
 __global__ void k_b_wcombine(const int* TW, int64_t plane, int64_t rows_w, int64_t woff, int64_t m, int64_t pb,
@@ -704,32 +685,51 @@ ibmi_status DevGroup::run(const BatchMat* mats, int nrun, const ibmi_batch_opts&
     for (int k = 0; k < K; ++k) alg += 2.0 * (double)g.m[k] * g.m[k] * (double)(pb - g.m[k]);
     alg *= n;
     const int grid_n = (int)((pb + g.bn - 1) / g.bn), grid_m = (int)(g.rows_w / 128);
+    // all pair products of all matrices in one persistent launch, each row
+    // tile over its set's K range
+    tc::OzPairMaps maps;
+    for (int s = 0; s < kWDigitsA; ++s) maps.a[s] = g.mXW[s];
+    for (int u = 0; u < kWDigitsB; ++u) maps.b[u] = g.mAo[u];
+    tc::OzPairArgs w{};
+    int np = 0;
     for (int q = 0; q <= kWGroups; ++q) {
       bool first = true;
       for (int s = 0; s <= q; ++s) {
         const int u = q - s;
         if (s >= kWDigitsA || u >= kWDigitsB) continue;
-        tc::Maps maps;
-        maps.a[0] = g.mXW[s];
-        maps.b[0] = g.mAo[u];
-        tc::Tiles t{g.rows_w, 0, 0, grid_n, 0, 1 << 29, 0, 0, 1, g.err};
-        t.mkr = g.w_kr;
-        t.nb = n;
-        EpiBOzAcc epi;
-        epi.T = g.TW + (int64_t)q * cap * g.rows_w * ldp;
-        epi.ldt = ldp;
-        epi.M = g.rows_w;
-        epi.N = pb;
-        epi.bstride = g.rows_w * ldp;
-        epi.first = first ? 1 : 0;
-        ProfScope ps(IBMI_K_INVARIANTS_TC, st, 2.0 * n * (double)g.rows_w * pb * (double)pb, alg);
-        alg = 0.0;
-        IBMI_TRY(with_bn(g.bn, [&](auto bnc) -> ibmi_status {
-          IBMI_CUDA_TRY((tc::launch<1, decltype(bnc)::value>(maps, t, grid_n, grid_m, epi, st)));
-          return IBMI_OK;
-        }));
+        w.s[np] = (int8_t)s;
+        w.u[np] = (int8_t)u;
+        w.q[np] = (int8_t)q;
+        w.first[np] = first ? 1 : 0;
         first = false;
+        ++np;
       }
+    }
+    int kt_max = 1;
+    for (int k = 0; k < K; ++k)
+      kt_max = std::max<int>(kt_max, (int)((g.hi[k] + tc::BK - 1) / tc::BK - g.lo[k] / tc::BK));
+    w.n = np;
+    w.grid_n = grid_n;
+    w.tiles = grid_n * grid_m;
+    w.kt_total = kt_max;
+    w.chunk = OZ_KCHUNK / tc::BK;
+    w.T = g.TW;
+    w.plane = (int64_t)cap * g.rows_w * ldp;
+    w.ldt = ldp;
+    w.M = g.rows_w;
+    w.N = pb;
+    w.err = g.err;
+    w.nb = n;
+    w.bsel = nullptr;
+    w.tstride = g.rows_w * ldp;
+    w.mkr = g.w_kr;
+    tc::oz_make_segments(w);
+    {
+      ProfScope ps(IBMI_K_INVARIANTS_TC, st, 2.0 * np * n * (double)g.rows_w * pb * (double)pb, alg);
+      IBMI_TRY(with_bn(g.bn, [&](auto bnc) -> ibmi_status {
+        IBMI_CUDA_TRY(tc::launch_oz_pairs<decltype(bnc)::value>(maps, w, st));
+        return IBMI_OK;
+      }));
     }
     ProfScope ps(IBMI_K_OTHER, st, 0.0);
     for (int k = 0; k < K; ++k) {
