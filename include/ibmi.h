@@ -57,7 +57,10 @@ typedef enum ibmi_status {
 } ibmi_status;
 
 /* Arithmetic of the sweep products (a3/a4).  The Cholesky of the diagonal
- * blocks and the residual are FP64 in both modes. */
+ * blocks and the residual are FP64-accurate in both modes: DFMA in IBMI_FP64;
+ * in IBMI_MIXED the residual, and for blocks of order >= 512 the factorisation
+ * updates beyond each 256-wide block column and A_I^{-1} = Y^T Y, run as
+ * error-free digit-sliced products on the tensor cores. */
 typedef enum ibmi_precision {
   IBMI_FP64 = 0,    /* every product in FP64 (DFMA)                                 */
   IBMI_MIXED = 1    /* sweep products on tcgen05 tensor cores with split-BF16 operands
@@ -360,9 +363,10 @@ typedef enum ibmi_kernel_class {
   IBMI_K_SWEEP_S = 1,     /* a4: S = A_I^{-1} - X W^T                             */
   IBMI_K_RESIDUAL = 2,    /* a6: ||I - A H||_F products                           */
   IBMI_K_NS = 3,          /* a7: Newton-Schulz update products                    */
-  IBMI_K_INVARIANTS = 4,  /* a2: Cholesky, triangular solves (FP64)               */
+  IBMI_K_INVARIANTS = 4,  /* a2: Cholesky, triangular solves (FP64 DFMA part)     */
   IBMI_K_OTHER = 5,       /* slicing, combines, symmetrisation, copies            */
-  IBMI_K_INVARIANTS_TC = 6, /* a2, mixed path: W = A_I^{-1} A_{I,:} on tensor cores */
+  IBMI_K_INVARIANTS_TC = 6, /* a2, mixed path, on tensor cores: W = A_I^{-1} A_{I,:},
+                               Y^T Y and the factorisation updates                  */
   IBMI_K_COUNT = 7
 } ibmi_kernel_class;
 /* The flops recorded per class are the operations issued to the unit that
