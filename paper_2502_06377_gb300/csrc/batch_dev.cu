@@ -169,43 +169,55 @@ struct EpiBSweepX : tc::EpiBase {
   }
 };
 
-// a4 epilogue: split-K partial z of X W^T of matrix bat.
-struct EpiBPartial : tc::EpiBase {
-  float* Spart; int64_t m, bstride;
-  __device__ __forceinline__ void warp_tile(int64_t row0, int64_t j0, int z, const float* __restrict__ stage,
+// a4 of matrix bat (one K split): the finish in the epilogue.  P = X W^T on
+// the tiles on and below the diagonal; each element (i, j), j <= i, gives
+// x = A_I^{-1}[i, j] - P[i, j] (FP32), written to H[I, I] at (i, j) and, from
+// the same x, at (j, i), so the block is exactly symmetric: the first pass
+// writes (i, j) along rows and keeps x in the warp's stage, the second writes
+// (j, i) with one lane per row i.
+struct EpiBSymFinish : tc::EpiBase {
+  const double* Ainv; int64_t abstride, m, lo, pb, ldp;
+  float* Hf; __nv_bfloat16* s0; __nv_bfloat16* s1; __nv_bfloat16* s2;
+  __device__ __forceinline__ void put(int64_t o, float x) const {
+    Hf[o] = x;
+    __nv_bfloat16 t0, t1, t2;
+    split3(x, t0, t1, t2);
+    s0[o] = t0;
+    s1[o] = t1;
+    if (s2) s2[o] = t2;
+  }
+  __device__ __forceinline__ void warp_tile(int64_t row0, int64_t j0, int, const float* __restrict__ stage_in,
                                             int lane) const {
+    float* stage = const_cast<float*>(stage_in);   // this warp's own stage: x goes back in place
+    const double* Ab = Ainv + (int64_t)bat * abstride;
+    const int64_t o0 = ((int64_t)bat * pb + lo) * ldp + lo;
     const int c = lane & 15;
-    if (j0 + c >= m) return;
-    float* o = Spart + (int64_t)bat * bstride + (int64_t)z * m * m + j0 + c;
-#pragma unroll 4
+    const int64_t j = j0 + c;
+    double a[16];   // all loads of A_I^{-1} in flight before the first store
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      const int64_t i = row0 + 2 * k + (lane >> 4);
+      a[k] = i < m && j <= i ? Ab[i * m + j] : 0.0;
+    }
+#pragma unroll
     for (int k = 0; k < 16; ++k) {
       const int r = 2 * k + (lane >> 4);
       const int64_t i = row0 + r;
-      if (i < m) o[i * m] = stage[r * 17 + c];
+      if (i < m && j <= i) {
+        const float x = (float)(a[k] - (double)stage[r * 17 + c]);
+        stage[r * 17 + c] = x;
+        put(o0 + i * ldp + j, x);
+      }
+    }
+    __syncwarp();
+    const int64_t i = row0 + lane;
+#pragma unroll 4
+    for (int cc = 0; cc < 16; ++cc) {
+      const int64_t jj = j0 + cc;
+      if (i < m && jj < i) put(o0 + jj * ldp + i, stage[lane * 17 + cc]);
     }
   }
 };
-
-// H[I, I] of matrix sel[z] = A_I^{-1} - P (P = sum of the split-K partials,
-// lower triangle mirrored, so the block is exactly symmetric).
-__global__ void k_b_sym(const int* sel, const float* Spart, int64_t sbstride, int splits, int64_t m, const double* Ainv,
-                        int64_t abstride, int64_t lo, int64_t pb, int64_t ldp, float* Hf, __nv_bfloat16* s0,
-                        __nv_bfloat16* s1, __nv_bfloat16* s2) {
-  const int64_t b = pick(sel, blockIdx.z), i = blockIdx.y, j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= m) return;
-  const int64_t hi_ = i > j ? i : j, lo_ = i > j ? j : i;
-  const float* S = Spart + b * sbstride;
-  float a = 0.f;
-  for (int z = 0; z < splits; ++z) a += S[(int64_t)z * m * m + hi_ * m + lo_];
-  const float x = (float)(Ainv[b * abstride + i * m + j] - (double)a);
-  const int64_t o = (b * pb + lo + i) * ldp + lo + j;
-  Hf[o] = x;
-  __nv_bfloat16 t0, t1, t2;
-  split3(x, t0, t1, t2);
-  s0[o] = t0;
-  s1[o] = t1;
-  if (s2) s2[o] = t2;
-}
 
 // BF16x3 stop test of matrix bat: per unit and epilogue warp, the sum of
 // (delta_ij - acc)^2 over the tile's entries inside the matrix.
@@ -364,7 +376,7 @@ int count_pairs(int na, int nb, int qlo, int qhi) {
 
 struct DevGroup::Impl {
   int64_t pb = 0, ldp = 0, mmax = 0;
-  int K = 0, n = 0, bn = 64, splits = 1;
+  int K = 0, n = 0, bn = 64;
   std::vector<int64_t> lo, hi, m;
   int64_t rows_w = 0, ainv_total = 0, nparts_c = 0, nparts_r = 0;
   std::vector<int64_t> woff, aoff;
@@ -380,7 +392,6 @@ struct DevGroup::Impl {
   float* Hf = nullptr;
   __nv_bfloat16* Hs[3] = {};
   std::vector<__nv_bfloat16*> Ws[3];
-  float* Spart = nullptr;
   __nv_bfloat16* Ao[OZ_SA] = {};
   __nv_bfloat16* Xo[OZ_SX] = {};
   __nv_bfloat16* Qo[NS_S] = {};
@@ -471,10 +482,6 @@ ibmi_status DevGroup::create(int64_t pb, int K, int64_t h, int n) {
     g.ainv_total += g.m[k] * g.m[k];
     if (g.m[k] >= pb) return IBMI_ERR_INVALID_ARG;
   }
-  // a4 split-K factor as in the single-matrix path, for one matrix's lower tiles
-  const int64_t tm = (g.mmax + 127) / 128, tiles2 = tm * (tm + 1) / 2;
-  const int kt = (int)((pb + tc::BK - 1) / tc::BK);
-  g.splits = (int)std::max<int64_t>(1, std::min<int64_t>(std::max<int64_t>(1, 152 / tiles2), kt / 4 > 0 ? kt / 4 : 1));
   g.nparts_c = pb * nblk((pb + 3) / 4);   // k_b_combine: one partial per CTA of four-column threads
   g.nparts_r = ((pb + 127) / 128) * ((pb + kBN - 1) / kBN) * 4;
   const int64_t nparts = std::max(g.nparts_c, g.nparts_r);
@@ -522,7 +529,6 @@ ibmi_status DevGroup::create(int64_t pb, int K, int64_t h, int n) {
     for (int s = 0; s < 3; ++s) add(2 * per * pl);
     for (int s = 0; s < 3; ++s)
       for (int k = 0; k < K; ++k) add(2 * per * g.m[k] * g.ldp);
-    add(sizeof(float) * per * g.splits * g.mmax * g.mmax);
     for (int s = 0; s < OZ_SA + OZ_SX + NS_S + 2; ++s) add(2 * per * pl);
     for (int s = 0; s < kWDigitsA; ++s) add(2 * per * g.rows_w * g.ldp);
     add(sizeof(int) * (size_t)(OZ_QMAX + 1) * per * pl);
@@ -551,7 +557,6 @@ ibmi_status DevGroup::create(int64_t pb, int K, int64_t h, int n) {
   for (int s = 0; s < 3; ++s) g.Hs[s] = a.take<__nv_bfloat16>(nn * pl);
   for (int s = 0; s < 3; ++s)
     for (int k = 0; k < K; ++k) g.Ws[s].push_back(a.take<__nv_bfloat16>(nn * g.m[k] * g.ldp));
-  g.Spart = a.take<float>(nn * g.splits * g.mmax * g.mmax);
   for (int s = 0; s < OZ_SA; ++s) g.Ao[s] = a.take<__nv_bfloat16>(nn * pl);
   for (int s = 0; s < OZ_SX; ++s) g.Xo[s] = a.take<__nv_bfloat16>(nn * pl);
   for (int s = 0; s < NS_S; ++s) g.Qo[s] = a.take<__nv_bfloat16>(nn * pl);
@@ -859,31 +864,27 @@ ibmi_status DevGroup::run(const BatchMat* mats, int nrun, const ibmi_batch_opts&
           if (S == 2) IBMI_CUDA_TRY((tc::launch<2, kBN>(maps, t, nr.count(), (int)((m + 127) / 128), epi, st)));
           else IBMI_CUDA_TRY((tc::launch<3, kBN>(maps, t, nr.count(), (int)((m + 127) / 128), epi, st)));
         }
-        {  // a4: P = X W^T (lower tiles, split K) and H[I, I] = A_I^{-1} - P
-          const int nk = kr.count();
-          const int splits = std::max(1, std::min(g.splits, nk / 2));
+        {  // a4: P = X W^T (lower tiles; one K split, so that a matrix's sums do not
+           // depend on its group: the group's matrices fill the GPU) and
+           // H[I, I] = A_I^{-1} - P in the epilogue
           tc::Maps maps;
           for (int s = 0; s < S; ++s) {
             maps.a[s] = g.mapH[s];
             maps.b[s] = g.mapW[s][k];
           }
           const int ntn = (int)((m + kBN - 1) / kBN);
-          tc::Tiles t{m, lo, 0, ntn, ntn, kr.r0_end, kr.r1_begin, kr.r1_end, splits, g.err};
+          tc::Tiles t{m, lo, 0, ntn, ntn, kr.r0_end, kr.r1_begin, kr.r1_end, 1, g.err};
           t.lower = 1;
           t.nb = nl;
           t.bsel = dl;
-          EpiBPartial epi;
-          epi.Spart = g.Spart; epi.m = m; epi.bstride = (int64_t)g.splits * g.mmax * g.mmax;
+          EpiBSymFinish epi;
+          epi.Ainv = g.F.pool + g.aoff[k]; epi.abstride = g.ainv_total; epi.m = m; epi.lo = lo; epi.pb = pb;
+          epi.ldp = ldp; epi.Hf = g.Hf; epi.s0 = g.Hs[0]; epi.s1 = g.Hs[1]; epi.s2 = S == 3 ? g.Hs[2] : nullptr;
           ProfScope ps(IBMI_K_SWEEP_S, st,
                        (S == 2 ? 3.0 : 6.0) * 2.0 * nl * nn * (double)(ntn * (ntn + 1) / 2) * kBN * kBN,
                        2.0 * nl * m * m * nn);
           if (S == 2) IBMI_CUDA_TRY((tc::launch<2, kBN>(maps, t, ntn, (int)((m + 127) / 128), epi, st)));
           else IBMI_CUDA_TRY((tc::launch<3, kBN>(maps, t, ntn, (int)((m + 127) / 128), epi, st)));
-          note_launch();
-          k_b_sym<<<dim3(nblk(m), (unsigned)m, (unsigned)nl), 256, 0, st>>>(
-              dl, g.Spart, (int64_t)g.splits * g.mmax * g.mmax, splits, m, g.F.pool + g.aoff[k], g.ainv_total, lo, pb,
-              ldp, g.Hf, g.Hs[0], g.Hs[1], S == 3 ? g.Hs[2] : nullptr);
-          IBMI_CUDA_TRY(cudaGetLastError());
         }
       }
     }
