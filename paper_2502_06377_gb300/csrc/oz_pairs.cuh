@@ -13,6 +13,7 @@
 #pragma once
 #include <algorithm>
 
+#include "oz_tiles.h"
 #include "tc_gemm.cuh"
 
 namespace ibmi {
@@ -56,17 +57,9 @@ struct OzPairArgs {
   const int2* mkr;
 };
 
-// Tiles of row mt of a lower launch: those whose first column is at most the
-// row tile's last row.
-inline __host__ __device__ int oz_lower_row_tiles(int mt, int grid_n, int bn) {
-  const int n = ((mt + 1) * BM + bn - 1) / bn;
-  return n < grid_n ? n : grid_n;
-}
-inline int oz_lower_tiles(int grid_m, int grid_n, int bn) {
-  int n = 0;
-  for (int mt = 0; mt < grid_m; ++mt) n += oz_lower_row_tiles(mt, grid_n, bn);
-  return n;
-}
+static_assert(OZT_BM == BM, "lower-tile enumeration and the kernels' row tile");
+using ibmi::oz_lower_row_tiles;
+using ibmi::oz_lower_tiles;
 
 // Output tile (mt, ntl) of tile index tl of a problem.
 template <int BN>
@@ -76,12 +69,7 @@ __device__ __forceinline__ void oz_tile(const OzPairArgs& g, int tl, int& mt, in
     ntl = tl - mt * g.grid_n;
     return;
   }
-  mt = 0;
-  for (int n = oz_lower_row_tiles(0, g.grid_n, BN); tl >= n; n = oz_lower_row_tiles(mt, g.grid_n, BN)) {
-    tl -= n;
-    ++mt;
-  }
-  ntl = tl;
+  oz_lower_tile(tl, g.grid_n, BN, mt, ntl);
 }
 
 // Splits the pair list (in group order) into segments: a pair's product,
