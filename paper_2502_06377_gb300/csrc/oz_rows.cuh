@@ -20,6 +20,72 @@ struct SlicePtrs {
   __nv_bfloat16* s[OZ_S];
 };
 
+// The nslices digits of column c of a row whose maximum is below 2^e (zero
+// outside [c0, c0 + ncols)): F = rint(x 2^{55-e}) and Flo = the remainder
+// carried 14 bits further, from the bit pattern of x with integer operations
+// only (no FP64 ALU), cut as described above; with `sq_on`, (x 2^-e)^2 is
+// added to sq.
+__device__ __forceinline__ void oz_elem_digits(const double* row, int64_t c, int64_t c0, int64_t ncols, int e,
+                                               bool nonfinite, int nslices, bool sq_on, int (&d)[OZ_S], float& sq) {
+  long long F = 0, Flo = 0;
+  if (c >= c0 && c < c0 + ncols) {
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(row[c - c0]);
+    const int ex = (int)((bits >> 52) & 0x7ff);
+    const bool neg = (bits >> 63) != 0;
+    if (ex != 0 && !nonfinite) {   // zeros and subnormals are far below 2^(e-69)
+      const unsigned long long m = (bits & 0xfffffffffffffull) | 0x10000000000000ull;   // 53-bit significand
+      const int sh = ex - 1075 + 55 - e;   // x 2^{55-e} = m 2^sh, sh <= 2 because |x| < 2^e
+      if (sq_on) {   // |x| 2^-e ~ (m >> 29) 2^(ex - 1046 - e), 24 bits
+        const float xs = ldexpf((float)(m >> 29), ex - 1046 - e);
+        sq += xs * xs;
+      }
+      long long qq = 0, lo14 = 0;
+      if (sh >= 0) {
+        qq = (long long)(m << sh);
+      } else if (sh > -68) {
+        const int rs = -sh;
+        if (rs >= 54) {   // |x 2^{55-e}| < 1/2: remainder only
+          lo14 = (long long)(m >> (rs - 14));
+        } else {
+          const unsigned long long q = m >> rs;
+          const unsigned long long rem = m - (q << rs);   // 0 <= rem < 2^rs
+          const unsigned long long half = 1ull << (rs - 1);
+          const bool up = rem >= half;                      // round half away from zero
+          qq = (long long)q + (up ? 1 : 0);
+          if (rs > 14)
+            lo14 = up ? -(long long)(((half << 1) - rem) >> (rs - 14)) : (long long)(rem >> (rs - 14));
+          else
+            lo14 = up ? -(long long)(((half << 1) - rem) << (14 - rs)) : (long long)(rem << (14 - rs));
+        }
+      }
+      F = neg ? -qq : qq;
+      Flo = neg ? -lo14 : lo14;
+    }
+  }
+#pragma unroll
+  for (int s = 0; s < 7; ++s) {
+    const int sh = 49 - 7 * s;
+    const long long dd = (F + (1ll << (sh - 1))) >> sh;
+    F -= dd * (1ll << sh);
+    d[s] = (int)dd;
+  }
+  if (nslices > 7) {
+    long long G = F * 16384 + Flo;   // F = F_7 in [-64, 64)
+#pragma unroll
+    for (int s = 7; s < OZ_S; ++s) {
+      const int sh = 14 - 7 * (s - 7);
+      long long dd;
+      if (s == OZ_S - 1 || sh == 0) {
+        dd = G;
+      } else {
+        dd = (G + (1ll << (sh - 1))) >> sh;
+        G -= dd * (1ll << sh);
+      }
+      d[s] = (int)dd;
+    }
+  }
+}
+
 // rowsq (optional): sum over the row of (x 2^-e)^2 in float, so that the
 // row's squared norm is rowsq 2^(2e) (integer and float operations only).
 // Called by all threads of a CTA for one row: `row` (ncols values, placed at
@@ -48,68 +114,17 @@ __device__ __forceinline__ void oz_slice_row(const double* row, int64_t i, int64
     else frexp(ozr_bits_to_double(red[0]), &e);   // subnormal maximum
   }
   if (threadIdx.x == 0) expo[i] = nonfinite ? OZ_NONFINITE_EXP : e;
-  // F = rint(x 2^{55-e}) and Flo = the remainder carried 14 bits further,
-  // from the bit pattern of x with integer operations only (no FP64 ALU).
+  // Two adjacent columns per thread (ldp is even), stored as BF16 pairs.
   float sq = 0.f;
-  for (int64_t c = threadIdx.x; c < ldp; c += blockDim.x) {
-    long long F = 0, Flo = 0;
-    if (c >= c0 && c < c0 + ncols) {
-      const unsigned long long bits = (unsigned long long)__double_as_longlong(row[c - c0]);
-      const int ex = (int)((bits >> 52) & 0x7ff);
-      const bool neg = (bits >> 63) != 0;
-      if (ex != 0 && !nonfinite) {   // zeros and subnormals are far below 2^(e-69)
-        const unsigned long long m = (bits & 0xfffffffffffffull) | 0x10000000000000ull;   // 53-bit significand
-        const int sh = ex - 1075 + 55 - e;   // x 2^{55-e} = m 2^sh, sh <= 2 because |x| < 2^e
-        if (rowsq) {   // |x| 2^-e ~ (m >> 29) 2^(ex - 1046 - e), 24 bits
-          const float xs = ldexpf((float)(m >> 29), ex - 1046 - e);
-          sq += xs * xs;
-        }
-        long long qq = 0, lo14 = 0;
-        if (sh >= 0) {
-          qq = (long long)(m << sh);
-        } else if (sh > -68) {
-          const int rs = -sh;
-          if (rs >= 54) {   // |x 2^{55-e}| < 1/2: remainder only
-            lo14 = (long long)(m >> (rs - 14));
-          } else {
-            const unsigned long long q = m >> rs;
-            const unsigned long long rem = m - (q << rs);   // 0 <= rem < 2^rs
-            const unsigned long long half = 1ull << (rs - 1);
-            const bool up = rem >= half;                      // round half away from zero
-            qq = (long long)q + (up ? 1 : 0);
-            if (rs > 14)
-              lo14 = up ? -(long long)(((half << 1) - rem) >> (rs - 14)) : (long long)(rem >> (rs - 14));
-            else
-              lo14 = up ? -(long long)(((half << 1) - rem) << (14 - rs)) : (long long)(rem << (14 - rs));
-          }
-        }
-        F = neg ? -qq : qq;
-        Flo = neg ? -lo14 : lo14;
-      }
-    }
+  for (int64_t c = 2 * (int64_t)threadIdx.x; c < ldp; c += 2 * (int64_t)blockDim.x) {
+    int d0[OZ_S], d1[OZ_S];
+    oz_elem_digits(row, c, c0, ncols, e, nonfinite, nslices, rowsq != nullptr, d0, sq);
+    oz_elem_digits(row, c + 1, c0, ncols, e, nonfinite, nslices, rowsq != nullptr, d1, sq);
 #pragma unroll
-    for (int s = 0; s < 7; ++s) {
+    for (int s = 0; s < OZ_S; ++s) {
       if (s >= nslices) break;
-      const int sh = 49 - 7 * s;
-      const long long d = (F + (1ll << (sh - 1))) >> sh;
-      F -= d * (1ll << sh);
-      out.s[s][i * ldp + c] = __int2bfloat16_rn((int)d);
-    }
-    if (nslices > 7) {
-      long long G = F * 16384 + Flo;   // F = F_7 in [-64, 64)
-#pragma unroll
-      for (int s = 7; s < OZ_S; ++s) {
-        if (s >= nslices) break;
-        const int sh = 14 - 7 * (s - 7);
-        long long d;
-        if (s == OZ_S - 1 || sh == 0) {
-          d = G;
-        } else {
-          d = (G + (1ll << (sh - 1))) >> sh;
-          G -= d * (1ll << sh);
-        }
-        out.s[s][i * ldp + c] = __int2bfloat16_rn((int)d);
-      }
+      *reinterpret_cast<__nv_bfloat162*>(out.s[s] + i * ldp + c) =
+          __halves2bfloat162(__int2bfloat16_rn(d0[s]), __int2bfloat16_rn(d1[s]));
     }
   }
   if (rowsq) {   // the same for every thread of the block
